@@ -1,0 +1,370 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks one part of the oracle against something other than the oracle itself:
+a dense LU solve, an exact discrete closed form, the continuous cable solution, a
+conservation law, an independent ODE integrator, a literature value, or a hand-written
+recurrence on a one-compartment model.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+from inputs import Model, make_config, small_tree_model, uniform_cable_model
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _single_cv(length=20.0, radius=5.0, cm=1.0, g_pas=1e-4, e_pas=-65.0, hh=False, n_syn=0):
+    m = Model(cv_offset=[0, 1], parent=[-1], length_um=[length], radius_um=[radius], cm=[cm], Ra=[100.0],
+              branch_of_cv=[0], detector_cv=[0])
+    if hh:
+        m.hh_cv, m.gnabar, m.gkbar, m.gl = np.array([0]), np.array([0.12]), np.array([0.036]), np.array([3e-4])
+    else:
+        m.pas_cv, m.g_pas, m.e_pas = np.array([0]), np.array([g_pas]), np.array([e_pas])
+    if n_syn:
+        m.syn_cv, m.syn_tau, m.syn_e = np.zeros(n_syn, np.int64), np.full(n_syn, 2.0), np.zeros(n_syn)
+    m.__post_init__()
+    return m
+
+
+# ---------------------------------------------------------------- P1: Hines solve vs dense LU
+def _random_tree_system(rng, n):
+    parent = np.array([-1] + [int(rng.integers(0, i)) for i in range(1, n)], np.int32)
+    sigma = rng.uniform(0.01, 5.0, n)
+    sigma[0] = 0.0
+    cdt = rng.uniform(1e-3, 2.0, n)
+    d = cdt.copy()
+    a = np.zeros(n)
+    for i in range(1, n):
+        d[i] += sigma[i]
+        d[parent[i]] += sigma[i]
+        a[i] = -sigma[i]
+    A = np.diag(d)
+    for i in range(1, n):
+        A[i, parent[i]] = A[parent[i], i] = a[i]
+    return parent, d, a, A
+
+
+def test_p1_hines_solve_matches_dense_lu(oracle_lib):
+    rng = np.random.default_rng(1)
+    worst = 0.0
+    for _ in range(1000):
+        n = int(rng.integers(1, 65))
+        parent, d, a, A = _random_tree_system(rng, n)
+        assert np.allclose(A, A.T)
+        np.linalg.cholesky(A)                 # symmetric positive definite
+        b = rng.normal(size=n) * 10
+        x = oracle_lib.hines_solve(parent, d, a, b)
+        xr = np.linalg.solve(A, b)
+        worst = max(worst, np.max(np.abs(x - xr)) / np.max(np.abs(xr)))
+    assert worst <= 1e-12, worst
+
+
+def test_p1_hines_solve_on_model_tree(oracle_lib):
+    # trees produced by the workload generator (branch-by-branch numbering)
+    m = small_tree_model(3, n_cells=1, n_branches=12, cv_range=(1, 9))
+    n = m.n_cv
+    rng = np.random.default_rng(5)
+    _, cap, sig = oracle_lib.cv_geometry(m)
+    d = cap / 0.025
+    a = np.zeros(n)
+    for i in range(1, n):
+        d[i] += sig[i]
+        d[m.parent[i]] += sig[i]
+        a[i] = -sig[i]
+    A = np.diag(d)
+    for i in range(1, n):
+        A[i, m.parent[i]] = A[m.parent[i], i] = a[i]
+    b = rng.normal(size=n)
+    x = oracle_lib.hines_solve(m.parent, d, a, b)
+    assert np.max(np.abs(x - np.linalg.solve(A, b))) <= 1e-12 * np.max(np.abs(x))
+
+
+# ---------------------------------------------------------------- P2: passive sealed cable
+def _cable_run(oracle_lib, N, L=1000.0, r=1.0, I0=0.1, t_end=500.0, dt=0.025):
+    m = uniform_cable_model(N, L, r)
+    m.stim_cv, m.stim_t_on, m.stim_dur, m.stim_amp = np.array([0]), np.array([0.0]), np.array([1e9]), np.array([I0])
+    m.__post_init__()
+    sim = oracle_lib.OracleSim(m, dt, 400)
+    sim.run(t_end)
+    return m, sim.voltage()
+
+
+def _discrete_cosh(N, L, r, I0, cm=1.0, Ra=100.0, g=1e-4):
+    """Exact fixed point of the discrete sealed cable: u_k = A cosh((N - 1/2 - k) theta)."""
+    h = L / N
+    area = 2 * math.pi * r * h
+    G = g * area * 1e-2
+    sigma = 100.0 * math.pi * r * r / (Ra * h)
+    theta = math.acosh(1.0 + G / (2.0 * sigma))
+    k = np.arange(N)
+    prof = np.cosh((N - 0.5 - k) * theta)
+    A = I0 / (sigma * (prof[0] - prof[1]) + G * prof[0]) if N > 1 else I0 / (G * prof[0])
+    return A * prof
+
+
+def test_p2_cable_steady_state_discrete_closed_form(oracle_lib):
+    for N in (1, 2, 7, 50, 200):
+        m, V = _cable_run(oracle_lib, N)
+        u = V - (-65.0)
+        ref = _discrete_cosh(N, 1000.0, 1.0, 0.1)
+        assert np.max(np.abs(u - ref)) <= 1e-10 * np.max(np.abs(ref)), (N, np.max(np.abs(u - ref)))
+
+
+def test_p2_cable_converges_second_order_to_continuous(oracle_lib):
+    L, r, I0, Ra, g = 1000.0, 1.0, 0.1, 100.0, 1e-4
+    # lambda = sqrt(d Rm / (4 Ra)) in cm; r_a = Ra / (pi r^2) in Ohm/cm
+    r_cm = r * 1e-4
+    lam = math.sqrt(2 * r_cm * (1.0 / g) / (4 * Ra))
+    ra = Ra / (math.pi * r_cm ** 2)
+    L_cm = L * 1e-4
+
+    def v_exact(x_um):  # mV, I0 in nA
+        x = x_um * 1e-4
+        return (I0 * 1e-9) * ra * lam * np.cosh((L_cm - x) / lam) / math.sinh(L_cm / lam) * 1e3
+
+    errs = []
+    for N in (10, 20, 40, 80):
+        u = _discrete_cosh(N, L, r, I0)          # equals the oracle's fixed point (previous test)
+        x = (np.arange(N) + 0.5) * (L / N)
+        errs.append(np.max(np.abs(u - v_exact(x))) / np.max(np.abs(v_exact(x))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(abs(o - 2.0) < 0.1 for o in orders), (errs, orders)
+    # and the oracle itself lands on the same profile at N = 40
+    m, V = _cable_run(oracle_lib, 40)
+    x = (np.arange(40) + 0.5) * 25.0
+    assert np.max(np.abs((V + 65.0) - v_exact(x))) / np.max(v_exact(x)) < 2 * errs[2]
+
+
+# ---------------------------------------------------------------- P3: charge conservation
+def test_p3_charge_conservation_passive_tree(oracle_lib):
+    rng = np.random.default_rng(11)
+    for seed in range(20):
+        m = small_tree_model(seed, n_cells=3, n_branches=6, cv_range=(1, 7), passive_only=True)
+        nst = 3
+        m.stim_cv = rng.integers(0, m.n_cv, nst)
+        m.stim_t_on, m.stim_dur, m.stim_amp = np.zeros(nst), np.full(nst, 1e9), rng.uniform(-1, 1, nst)
+        m.__post_init__()
+        area, cap, _ = oracle_lib.cv_geometry(m)
+        dt = 0.025
+        sim = oracle_lib.OracleSim(m, dt, 10)
+        st = sim.get_state()
+        st["V"] = rng.uniform(-80, -40, m.n_cv)
+        sim.set_state(st)
+        for _ in range(3):
+            V0 = sim.voltage()
+            sim.run_steps(1)
+            V1 = sim.voltage()
+            G = m.g_pas * area[m.pas_cv] * 1e-2
+            I = np.zeros(m.n_cv)
+            np.add.at(I, m.pas_cv, G * (V0[m.pas_cv] - m.e_pas))
+            np.add.at(I, m.stim_cv, -m.stim_amp)
+            for c in range(m.n_cells):
+                s = slice(m.cv_offset[c], m.cv_offset[c + 1])
+                lhs = np.sum(cap[s] * (V1[s] - V0[s]) / dt)
+                rhs = -np.sum(I[s])
+                scale = np.sum(np.abs(cap[s] * V0[s] / dt)) + np.sum(np.abs(I[s]))
+                assert abs(lhs - rhs) <= 1e-12 * scale, (seed, c, lhs, rhs)
+
+
+# ---------------------------------------------------------------- P4: explicit membrane current
+def test_p4_single_passive_cv_forward_euler(oracle_lib):
+    for g, cm in ((1e-4, 1.0), (5e-3, 0.8), (0.02, 1.0)):
+        m = _single_cv(g_pas=g, cm=cm, e_pas=-70.0)
+        dt = 0.025
+        sim = oracle_lib.OracleSim(m, dt, 100)
+        st = sim.get_state()
+        st["V"] = np.array([-20.0])
+        sim.set_state(st)
+        tr = sim.set_probes([0], 400)
+        sim.run_steps(400)
+        q = 1.0 - dt * (g / cm) * 1e3
+        k = np.arange(1, 401)
+        ref = -70.0 + q ** k * (-20.0 + 70.0)
+        assert np.max(np.abs(tr[:, 0] - ref) / np.abs(ref)) <= 1e-13
+
+
+# ---------------------------------------------------------------- P5: exact gate update (cnexp)
+def test_p5_gates_at_clamped_voltage_match_ode(oracle_lib):
+    # a huge capacitance clamps V; the gates must follow dx/dt = alpha - (alpha+beta) x exactly
+    for v in (-80.0, -65.0, -40.0, -10.0, 20.0):
+        m = _single_cv(cm=1e18, hh=True)
+        sim = oracle_lib.OracleSim(m, 0.025, 100)
+        st = sim.get_state()
+        st["V"] = np.array([v])
+        st["m"], st["h"], st["n"] = np.array([0.3]), np.array([0.2]), np.array([0.9])
+        sim.set_state(st)
+        sim.run_steps(200)
+        st1 = sim.get_state()
+        r = oracle_lib.hh_rates(v)
+        for key, (ia, ib), x0 in (("m", (0, 1), 0.3), ("h", (2, 3), 0.2), ("n", (4, 5), 0.9)):
+            al, be = r[ia], r[ib]
+            sol = solve_ivp(lambda t, x: al - (al + be) * x, (0, 5.0), [x0], method="DOP853", rtol=1e-13, atol=1e-15)
+            assert abs(st1[key][0] - sol.y[0, -1]) <= 1e-11, (v, key, st1[key][0], sol.y[0, -1])
+
+
+def test_hh_rest_gate_values_match_literature(oracle_lib):
+    g = json.load(open(os.path.join(HERE, "golden", "hh_rest_gates.json")))
+    r = oracle_lib.hh_rates(g["v_mV"])
+    assert abs(r[0] / (r[0] + r[1]) - g["m_inf"]) < g["abs_tol"]
+    assert abs(r[2] / (r[2] + r[3]) - g["h_inf"]) < g["abs_tol"]
+    assert abs(r[4] / (r[4] + r[5]) - g["n_inf"]) < g["abs_tol"]
+
+
+def test_exprelr_limits(oracle_lib):
+    assert oracle_lib.exprelr(0.0) == 1.0
+    for x in (1e-12, -1e-9, 1e-4, 0.3, -2.0, 5.0):
+        series = 1 - x / 2 + x * x / 12 - x ** 4 / 720
+        exact = x / math.expm1(x)
+        assert abs(oracle_lib.exprelr(x) - exact) <= 1e-15 * abs(exact)
+        if abs(x) < 1e-3:
+            assert abs(oracle_lib.exprelr(x) - series) <= 1e-14
+
+
+# ---------------------------------------------------------------- P6: HH splitting vs ODE
+def _hh_ode_spikes(J, t_end, thr=-10.0):
+    def ex(x):
+        return 1.0 if x == 0 else x / math.expm1(x)
+
+    def rhs(t, y):
+        V, m, h, n = y
+        am, bm = ex(-(V + 40) / 10), 4 * math.exp(-(V + 65) / 18)
+        ah, bh = 0.07 * math.exp(-(V + 65) / 20), 1 / (1 + math.exp(-(V + 35) / 10))
+        an, bn = 0.1 * ex(-(V + 55) / 10), 0.125 * math.exp(-(V + 65) / 80)
+        Iion = 120 * m ** 3 * h * (V - 50) + 36 * n ** 4 * (V + 77) + 0.3 * (V + 54.3)   # mS/cm^2 * mV
+        return [(J - Iion) / 1.0, am - (am + bm) * m, ah - (ah + bh) * h, an - (an + bn) * n]
+
+    def ev(t, y):
+        return y[0] - thr
+    ev.direction = 1
+    V0 = -65.0
+    am, bm = ex(-(V0 + 40) / 10), 4 * math.exp(-(V0 + 65) / 18)
+    ah, bh = 0.07 * math.exp(-(V0 + 65) / 20), 1 / (1 + math.exp(-(V0 + 35) / 10))
+    an, bn = 0.1 * ex(-(V0 + 55) / 10), 0.125 * math.exp(-(V0 + 65) / 80)
+    y0 = [V0, am / (am + bm), ah / (ah + bh), an / (an + bn)]
+    sol = solve_ivp(rhs, (0, t_end), y0, method="Radau", rtol=1e-10, atol=1e-12, events=ev)
+    return sol.t_events[0]
+
+
+def _oracle_hh_spikes(oracle_lib, J, t_end, dt):
+    m = _single_cv(hh=True)
+    area = 2 * math.pi * 5.0 * 20.0
+    m.stim_cv, m.stim_t_on, m.stim_dur = np.array([0]), np.array([0.0]), np.array([1e9])
+    m.stim_amp = np.array([J * area * 1e-5])       # uA/cm^2 -> nA
+    m.__post_init__()
+    sim = oracle_lib.OracleSim(m, dt, 1000)
+    sim.run(t_end)
+    return sim.spikes()[1]
+
+
+@pytest.mark.slow
+def test_p6_hh_spike_counts_match_ode_outside_onset_band(oracle_lib):
+    t_end = 100.0
+    for J in (0.0, 2.0, 4.0, 12.0, 16.0, 20.0):
+        ref = _hh_ode_spikes(J, t_end)
+        got = _oracle_hh_spikes(oracle_lib, J, t_end, 0.025)
+        near_end = any(t_end - t < 2.0 for t in list(ref) + list(got))
+        assert len(got) == len(ref) or (near_end and abs(len(got) - len(ref)) == 1), (J, len(got), len(ref))
+    # rest potential: with no input the cell stays near -65 mV and never fires
+    assert len(_oracle_hh_spikes(oracle_lib, 0.0, 50.0, 0.025)) == 0
+
+
+@pytest.mark.slow
+def test_p6_hh_spike_times_converge_first_order(oracle_lib):
+    J, t_end = 15.0, 40.0
+    ref = _hh_ode_spikes(J, t_end)[:3]
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        got = _oracle_hh_spikes(oracle_lib, J, t_end, dt)[:3]
+        assert len(got) == 3
+        errs.append(np.max(np.abs(got - ref)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(0.7 < o < 1.3 for o in orders), (errs, orders)
+    assert errs[-1] < 0.05
+
+
+# ---------------------------------------------------------------- P7: event path
+def test_p7_single_synapse_event_recurrence(oracle_lib):
+    m = _single_cv(g_pas=1e-4, e_pas=-65.0, n_syn=1)
+    area = 2 * math.pi * 5.0 * 20.0
+    C = 1.0 * area * 1e-5
+    G = 1e-4 * area * 1e-2
+    dt, w, te = 0.025, 0.004, 1.2345
+    sim = oracle_lib.OracleSim(m, dt, 40)
+    sim.enqueue([0], [te], [w])
+    tr = sim.set_probes([0], 400)
+    sim.run_steps(400)
+    s = math.ceil(te / dt)
+    V, g = -65.0, 0.0
+    ref = []
+    dec = math.exp(-dt / 2.0)
+    for k in range(400):
+        if k == s:
+            g += w
+        I = G * (V + 65.0) + g * (V - 0.0)
+        V = V - dt / C * I
+        g *= dec
+        ref.append(V)
+    ref = np.array(ref)
+    assert np.max(np.abs(tr[:, 0] - ref)) <= 1e-13 * np.max(np.abs(ref))
+    assert tr[s - 1, 0] == -65.0 and tr[s, 0] > -65.0        # applied at the start of step ceil(te/dt)
+
+
+# ---------------------------------------------------------------- P8: spike interpolation
+def test_p8_threshold_crossing_time_on_linear_ramp(oracle_lib):
+    m = _single_cv(g_pas=0.0)
+    area = 2 * math.pi * 5.0 * 20.0
+    C = area * 1e-5
+    I = 0.3
+    m.stim_cv, m.stim_t_on, m.stim_dur, m.stim_amp = np.array([0]), np.array([0.0]), np.array([1e9]), np.array([I])
+    m.__post_init__()
+    sim = oracle_lib.OracleSim(m, 0.025, 100)
+    sim.run(10.0)
+    gid, t = sim.spikes()
+    t_exact = (-10.0 + 65.0) * C / I
+    assert len(t) == 1 and abs(t[0] - t_exact) <= 1e-12, (t, t_exact)
+
+
+# ---------------------------------------------------------------- P10: epochs, threads, determinism
+def _ring_run(oracle_lib, epoch, threads):
+    m, spec = make_config(1, n_cells=24, t_end=60.0, variant="ring_active")
+    sim = oracle_lib.OracleSim(m, spec.dt, epoch, threads, record_delivered=True)
+    sim.run_steps(spec.n_steps)
+    return sim
+
+
+def test_p10_epoch_length_and_threads_do_not_change_results(oracle_lib):
+    a = _ring_run(oracle_lib, 200, 1)
+    b = _ring_run(oracle_lib, 100, 4)
+    c = _ring_run(oracle_lib, 37, 8)
+    va = a.voltage()
+    assert np.array_equal(va, b.voltage()) and np.array_equal(va, c.voltage())
+    ga, ta = a.spikes()
+    assert len(ta) > 12                      # activity travels around the ring
+    for o in (b, c):
+        g, t = o.spikes()
+        assert np.array_equal(ga, g) and np.array_equal(ta, t)
+    d = a.delivered()
+    assert np.all(d["src"] >= 0) and len(d["t"]) > 0
+    # events are applied at the start of step ceil(t_e/dt) ...
+    assert np.array_equal(d["step"], np.ceil(d["t"] / 0.025).astype(np.int64))
+    # ... which is never inside the epoch (200 steps) in which the spike was produced
+    spike_step = np.floor((d["t"] - 5.0) / 0.025).astype(np.int64)
+    assert np.all(d["step"] >= (spike_step // 200 + 1) * 200)
+
+
+def test_ring_default_stimulus_propagates(oracle_lib):
+    # 0.2 nA for 1 ms into the small HH soma CV of cell 0 is suprathreshold; the wave then
+    # moves one cell per synaptic delay (5 ms) plus the postsynaptic latency (< 1 ms)
+    m, spec = make_config(1, n_cells=8, t_end=20.0)
+    sim = oracle_lib.OracleSim(m, spec.dt, spec.epoch_steps)
+    sim.run_steps(spec.n_steps)
+    gid, t = sim.spikes()
+    assert list(gid) == list(range(len(gid))) and len(gid) >= 3
+    assert 0.0 < t[0] < 2.0
+    hops = np.diff(t)
+    assert np.all(hops > 5.0) and np.all(hops < 6.0)
