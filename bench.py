@@ -1,0 +1,337 @@
+"""Benchmark: compartment-steps per second of the batched cable-equation stepper on one B300.
+
+A "step" of this benchmark is one epoch: the full hot path (event delivery, mechanism
+currents, implicit-Euler assembly, Hines solve, state update, threshold detection for every
+time step of the epoch, then the spike exchange) over all cells of the workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ring|batched|mixed|small]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0). With torchrun and N > 1 every rank runs its own replica of
+the workload (cells are independent within an epoch; no collective is needed on one GPU's
+data) and value = total compartment-steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+WORKLOADS = {
+    # name: (config index, precision)
+    "small": (0, "fp64"),
+    "ring": (1, "fp64"),
+    "batched": (2, "fp64"),
+    "mixed": (3, "mixed"),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def algorithmic_bytes_per_cv_step(model, precision):
+    """Streaming bytes one CV-step must move if nothing stayed on chip: V read+write (16),
+    capacitance/dt (8), axial conductance to the parent (8), parent index (4); passive G (8) per
+    passive CV; HH gates m,h,n read+write and three conductances (72 FP64, 36 FP32-mechanism)
+    per HH CV; per synapse g read+write and its CV index (20 FP64, 12 FP32)."""
+    n_cv = model.n_cv
+    hh = np.asarray(model.hh_cv).size
+    pas = np.asarray(model.pas_cv).size
+    syn = model.n_syn
+    mixed = precision == "mixed"
+    total = 36.0 * n_cv + 8.0 * pas + (36.0 if mixed else 72.0) * hh + (12.0 if mixed else 20.0) * syn
+    return total / n_cv
+
+
+class ClockSampler:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, model, spec, precision, workload_name):
+    """The oracle (FP64 CPU) as it stands, timed on the host cores; each step is one epoch of
+    the workload over a bounded sample of its cells."""
+    import oracle
+    from inputs.sample import cell_sample
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    sub, sspec, ncells = cell_sample(model, spec, args.ref_cells)
+    E = spec.epoch_steps
+    sim = oracle.OracleSim(sub, spec.dt, E, nthreads=0)
+    sim.enqueue(sspec.ev_syn, sspec.ev_t, sspec.ev_w)
+    for _ in range(args.warmup):
+        sim.run_steps(E)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.run_steps(E)
+    el = time.perf_counter() - t0
+    units = sub.n_cv * E * args.steps
+    value = units / el
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "compartment-steps/sec", "value": value, "unit": "CV-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name, "cells": model.n_cells, "cvs": model.n_cv, "epoch_steps": E,
+                   "dt_ms": spec.dt, "sampled_cells": ncells},
+        "cpu_baseline": {"value": value, "unit": "CV-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d of %d cells, %d epochs of %d steps" % (ncells, model.n_cells, args.steps, E)},
+        "e2e": {"value": value, "unit": "CV-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(model, spec, budget_s):
+    """Oracle on all host cores over a bounded sample: whole epochs of all cells until about
+    budget_s seconds have passed (at least one epoch)."""
+    import oracle
+    from inputs.sample import cell_sample
+    oracle.build()
+    sub, sspec, ncells = cell_sample(model, spec, 0)
+    E = spec.epoch_steps
+    sim = oracle.OracleSim(sub, spec.dt, E, nthreads=0)
+    sim.enqueue(sspec.ev_syn, sspec.ev_t, sspec.ev_w)
+    t0 = time.perf_counter()
+    ep = 0
+    while True:
+        sim.run_steps(E)
+        ep += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": sub.n_cv * E * ep / el, "unit": "CV-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d of %d cells, first %d epochs (%d steps), %.1f s" % (ncells, model.n_cells, ep, ep * E, el)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ring", choices=sorted(WORKLOADS))
+    ap.add_argument("--cells-per-pack", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-cells", type=int, default=0, help="reference arm: cells sampled (0 = all)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 0 and args.steps >= 1
+
+    from inputs import make_config
+    cfg, precision = WORKLOADS[args.workload]
+    E_ms = None
+    model, spec = make_config(cfg, t_end=None)
+    E = spec.epoch_steps
+    # the run must cover warm-up + timed epochs: extend external inputs if needed
+    need_t = (args.warmup + args.steps) * E * spec.dt
+    if need_t > spec.t_end + 1e-9:
+        model, spec = make_config(cfg, t_end=need_t)
+    workload_name = "%s: %s, %d cells, %d CVs, dt %.3f ms, epoch %d steps" % (
+        args.workload, spec.name, model.n_cells, model.n_cv, spec.dt, E)
+
+    if args.impl == "reference":
+        run_reference(args, model, spec, precision, workload_name)
+        return
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1901_07454_b300 as arb
+
+    sim = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision,
+                         cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
+    sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
+    info = sim.plan_info()
+    stream = torch.cuda.current_stream()
+    k = 0
+    for _ in range(args.warmup):
+        k += E
+        sim.advance(k * spec.dt)
+    # L2 flush buffer (larger than the 126 MB L2), written between timed steps
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms = []
+    launches = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev0[i].record(stream)
+        k += E
+        sim.advance(k * spec.dt)
+        ev1[i].record(stream)
+        ms, nl = sim.last_timing()
+        kern_ms.append(ms)
+        launches += nl
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    units = model.n_cv * E * args.steps * world
+    value = units / (tot_ms * 1e-3)
+    nspk = sim.num_spikes()
+
+    # roofline of the dominant kernel (the epoch kernel): algorithmic bytes per launch over
+    # its mean launch time (CUDA events around it on the library's stream)
+    bpc = algorithmic_bytes_per_cv_step(model, precision)
+    kern_mean_ms = sum(kern_ms) / len(kern_ms)
+    achieved = bpc * model.n_cv * E / (kern_mean_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API with host buffers: create + upload from host arrays,
+    # per step advance one epoch and read all voltages and spikes back to the host
+    e2e = None
+    if rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision,
+                              cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
+        h2d = model_bytes(model)
+        kk = 0
+        ev_per_epoch = 0
+        for i in range(args.steps):
+            lo, hi = kk * spec.dt, (kk + E) * spec.dt
+            sel = (spec.ev_t >= lo) & (spec.ev_t < hi) if i > 0 else (spec.ev_t < hi)
+            sim2.enqueue(spec.ev_syn[sel], spec.ev_t[sel], spec.ev_w[sel])
+            ev_per_epoch += int(sel.sum())
+            kk += E
+            sim2.advance(kk * spec.dt)
+            v = sim2.voltage()
+            g, ts = sim2.spikes()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": model.n_cv * E * args.steps / el, "unit": "CV-steps/s",
+               "h2d_bytes_per_step": int(h2d / args.steps + 28 * ev_per_epoch / args.steps + 8),
+               "d2h_bytes_per_step": int(8 * model.n_cv + 12 * nspk / max(1, args.steps) + 8),
+               "includes": "handle creation and model upload from host arrays, per step: events from host, "
+                           "advance one epoch, all voltages and spikes to host"}
+        del sim2
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(model, spec, args.cpu_budget)
+        line = {
+            "metric": "compartment-steps/sec", "value": value, "unit": "CV-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "f64 solve / f32 mechanisms", "data": "synthetic",
+            "config": {"workload": workload_name, "cells": model.n_cells, "cvs": model.n_cv, "epoch_steps": E,
+                       "dt_ms": spec.dt, "step": "one epoch (%d time steps) of all cells incl. spike exchange" % E,
+                       "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],
+                       "lane_efficiency": round(info["lane_efficiency"], 4), "smem_packs": info["smem_packs"],
+                       "spikes": nspk, "wall_s": wall, "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "arb_epoch_kernel", "kernel_ms_mean": kern_mean_ms,
+                         "algorithmic_bytes_per_cv_step": bpc},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def model_bytes(m):
+    tot = 0
+    for name in ("cv_offset", "parent", "length_um", "radius_um", "cm", "Ra", "hh_cv", "gnabar", "gkbar", "gl",
+                 "pas_cv", "g_pas", "e_pas", "syn_cv", "syn_tau", "syn_e", "stim_cv", "stim_t_on", "stim_dur",
+                 "stim_amp", "detector_cv", "conn_src", "conn_dst_syn", "conn_delay", "conn_weight"):
+        tot += np.asarray(getattr(m, name)).nbytes
+    return tot
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * arb.h -- C ABI of the B300 batched cable-equation stepper.
+ *
+ * The library advances a batch of multicompartment neurons with the method of
+ * arXiv 1901.07454 (Arbor), Sec. "Model": finite-volume cable equation per cell,
+ * membrane currents at V(t), one implicit-Euler voltage step solved on each cell's
+ * tree-shaped (Hines) matrix, then channel/synapse state updates with the new voltage,
+ * threshold spike detection, and spike exchange once per minimum-delay epoch
+ * (Sec. "Implementation", "Simulation workflow"). Every stage of a time step runs in the
+ * library's own sm_103a CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Units: mV, ms, um, uF/cm^2, Ohm*cm, S/cm^2 (channel densities), uS (synaptic
+ *    weights), nA (injected current, positive = depolarising).
+ *  - Every call returns an arb_status; nothing throws across the ABI. arb_last_error()
+ *    gives a message for the last failing call on a handle.
+ *  - Host input arrays belong to the caller and are copied before the call returns.
+ *  - The library allocates no device memory itself: the caller provides one device
+ *    workspace (see arb_workspace_bytes / arb_bind_workspace) and any output buffers.
+ *  - Calls on one handle are not thread-safe. All device work of a handle is issued on
+ *    the stream given in arb_params.stream (0 = legacy default stream).
+ */
+#ifndef ARB_B300_H
+#define ARB_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct arb_sim arb_sim;
+
+typedef enum {
+    ARB_OK = 0,
+    ARB_E_ARG = -1,        /* invalid argument or model (message says which) */
+    ARB_E_CUDA = -2,       /* a CUDA runtime call failed */
+    ARB_E_OVERFLOW = -3,   /* an event, spike or bucket capacity was exceeded */
+    ARB_E_NONFINITE = -4,  /* a voltage became NaN or infinite */
+    ARB_E_STATE = -5,      /* call not valid in the handle's current state */
+    ARB_E_NOMEM = -6       /* host allocation failed, or the workspace is too small */
+} arb_status;
+
+enum { ARB_FP64 = 0, ARB_MIXED = 1 };
+
+/* Run settings. Fill with arb_default_params, then override. */
+typedef struct {
+    double dt;                   /* time step, ms (> 0) */
+    int32_t epoch_steps;         /* steps per epoch; 0 = floor(min delay / dt), 400 without connections */
+    int32_t precision;           /* ARB_FP64, or ARB_MIXED: mechanism states and currents in FP32,
+                                    matrix solve and voltages in FP64 */
+    int32_t cells_per_pack;      /* packing override: 0 = chosen by the library's cost model,
+                                    32 = one cell per lane, 1..31 = cells sharing one warp */
+    int32_t smem_budget;         /* bytes of shared memory per warp for state tiles; 0 = default */
+    int64_t event_capacity;      /* pending network events held on the device at once */
+    int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
+    int64_t spike_capacity;      /* spikes recorded over the whole run */
+    int64_t bucket_capacity;     /* events delivered within one epoch */
+    void* stream;                /* cudaStream_t */
+} arb_params;
+
+/* Model: host arrays, copied at arb_create. CV indices are global (cell offset + local index). */
+typedef struct {
+    int32_t n_cells;
+    const int64_t* cv_offset;    /* [n_cells+1] CVs of cell c are cv_offset[c] .. cv_offset[c+1]-1 */
+    const int32_t* parent;       /* [n_cv] cell-local parent, -1 for the first CV of a cell only,
+                                    otherwise 0 <= parent[i] < local index of i */
+    const double* length_um;     /* [n_cv] cylinder length of each CV (> 0) */
+    const double* radius_um;     /* [n_cv] cylinder radius (> 0) */
+    const double* cm;            /* [n_cv] specific capacitance, uF/cm^2 (> 0) */
+    const double* Ra;            /* [n_cv] axial resistivity, Ohm*cm (> 0) */
+    /* Hodgkin-Huxley Na/K/leak (E_Na 50, E_K -77, E_L -54.3 mV), at most one per CV */
+    int64_t n_hh;
+    const int64_t* hh_cv;
+    const double* gnabar;
+    const double* gkbar;
+    const double* gl;
+    /* passive leak */
+    int64_t n_pas;
+    const int64_t* pas_cv;
+    const double* g_pas;
+    const double* e_pas;
+    /* exponential synapses: dg/dt = -g/tau, I = g (V - e), an event adds its weight to g */
+    int64_t n_syn;
+    const int64_t* syn_cv;
+    const double* syn_tau;
+    const double* syn_e;
+    /* current clamps: amp nA while t_on <= t_k < t_on + dur */
+    int64_t n_stim;
+    const int64_t* stim_cv;
+    const double* stim_t_on;
+    const double* stim_dur;
+    const double* stim_amp;
+    /* one threshold detector per cell */
+    const int64_t* detector_cv;  /* [n_cells] a CV of that cell */
+    double threshold;            /* mV, upward crossing */
+    /* connections: a spike of cell conn_src[i] at t adds conn_weight[i] to synapse
+       conn_dst_syn[i] at t + conn_delay[i]; every delay must be >= epoch_steps*dt */
+    int64_t n_conn;
+    const int32_t* conn_src;
+    const int64_t* conn_dst_syn;
+    const double* conn_delay;
+    const double* conn_weight;
+} arb_model;
+
+/* Sets dt = 0.025, precision FP64, automatic epoch and packing, and capacities sized
+ * for typical runs. Never fails for a non-NULL argument. */
+arb_status arb_default_params(arb_params* p);
+
+/* Validates the model and prepares everything on the host (per-CV geometry; the constant
+ * implicit-Euler matrix of Sec. "Model" and its Hines factorisation, since with a fixed dt and
+ * all membrane current on the right-hand side only the right-hand side changes per step;
+ * the packing of cells into warps and the solve schedule). Makes no CUDA call.
+ * On success *out owns a handle that must be released with arb_destroy. */
+arb_status arb_create(const arb_model* model, const arb_params* params, arb_sim** out);
+
+/* Releases the handle. Does not free the caller's workspace. NULL is ignored. */
+void arb_destroy(arb_sim* sim);
+
+/* Device bytes the handle needs (256-byte aligned start). */
+arb_status arb_workspace_bytes(const arb_sim* sim, int64_t* bytes);
+
+/* Binds a caller-owned device buffer of at least arb_workspace_bytes bytes, uploads the
+ * model and sets the initial state (V = -65 mV, gates at steady state, synapses closed,
+ * t = 0). The buffer must stay valid until arb_destroy. May be called once per handle. */
+arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes);
+
+/* Queues external events (host arrays of length n): at time t[i] the weight w[i] (uS) is
+ * added to synapse syn[i]. Applied at the start of step ceil(t/dt) (the paper shortens the
+ * step to land on event times; this library keeps dt fixed). Times must not lie before the
+ * current time. Events may be enqueued in any order and across several calls, but all
+ * calls for a time window must come before arb_advance passes it. */
+arb_status arb_enqueue_events(arb_sim* sim, int64_t n, const int64_t* syn, const double* t,
+                              const double* w);
+
+/* Advances to step round(t_end/dt) in epochs of epoch_steps steps (the last one may be
+ * shorter), exchanging spikes between epochs. Returns ARB_E_OVERFLOW / ARB_E_NONFINITE
+ * when a device-side check failed during the call (state is then unspecified). */
+arb_status arb_advance(arb_sim* sim, double t_end);
+
+/* Current simulation time (steps * dt) and step count. */
+arb_status arb_time(const arb_sim* sim, double* t, int64_t* steps);
+
+/* Copies the voltage of all n_cv CVs, in the model's CV order, to out (a host pointer if
+ * on_device == 0, else a device pointer). n_cv must equal the model's CV count. */
+arb_status arb_read_voltage(arb_sim* sim, double* out, int64_t n_cv, int32_t on_device);
+
+/* Number of spikes recorded so far. */
+arb_status arb_num_spikes(arb_sim* sim, int64_t* n);
+
+/* Copies up to cap recorded spikes (host arrays), sorted by (time, gid); *n_out = count. */
+arb_status arb_read_spikes(arb_sim* sim, int32_t* gid, double* t, int64_t cap, int64_t* n_out);
+
+/* Records V(t_{k+1}) at n CVs after every step k, starting with the next step, into the
+ * device array trace[max_steps][n] (row r = the r-th step after this call). Steps beyond
+ * max_steps are not recorded. n = 0 switches probes off. cv: host array. */
+arb_status arb_set_probes(arb_sim* sim, int64_t n, const int64_t* cv, double* dev_trace,
+                          int64_t max_steps);
+
+/* Full dynamic state, host arrays in model order: V [n_cv], HH gates m, h, n [n_hh],
+ * synapse conductances g [n_syn]. Pending events are not part of it. */
+arb_status arb_get_state(arb_sim* sim, double* V, double* m, double* h, double* n, double* g);
+arb_status arb_set_state(arb_sim* sim, const double* V, const double* m, const double* h,
+                         const double* n, const double* g);
+
+/* Packing summary: number of packs (warp programs), solve rows, lanes, and the fraction of
+ * lane-rows that carry a CV. Valid after arb_create. */
+arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_rows,
+                         int64_t* smem_packs, double* lane_efficiency, int32_t* epoch_steps);
+
+/* Device time of the epoch kernel summed over the last arb_advance call, in ms, and the
+ * number of kernel launches it issued. Requires arb_params timing (always on). */
+arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t* launches);
+
+const char* arb_last_error(const arb_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,12 @@
+"""B300-native batched cable-equation stepper (the hot path of arXiv 1901.07454's method).
+
+The CUDA library libarb_b300.so (sm_103a) does all the work; this package is its binding.
+Importing it fails when the library has not been built: there is no CPU fallback.
+"""
+from . import _lib
+from ._lib import ArbError, load, EXPORTED
+from .sim import Plan, Simulation, default_params
+
+load()
+
+__all__ = ["ArbError", "Plan", "Simulation", "default_params", "load", "EXPORTED"]

@@ -1,0 +1,169 @@
+// Internal types shared by the host runtime (arb_runtime.cu) and the kernels (arb_kernels.cu).
+#pragma once
+#include <cstdint>
+
+namespace arbk {
+
+constexpr int kWarp = 32;
+
+// Reversal potentials of the Hodgkin-Huxley channels (mV).
+constexpr double kENa = 50.0;
+constexpr double kEK = -77.0;
+constexpr double kEL = -54.3;
+
+// One pack = the program of one warp: a group of cells whose CVs are laid out in
+// "rows" of 32 lanes. Entry (row j, lane l) of pack p lives at global index
+// (row0 + j) * 32 + l of every per-entry array; its state slot inside the pack's tile
+// is j * 32 + l.
+struct PackDesc {
+    int32_t row0;        // first solve row (global)
+    int32_t nrow;        // solve rows J
+    int32_t round_rows;  // rows per synchronisation round; 0 = lanes are independent
+    int32_t smem;        // 1: S and V tiles staged in shared memory, 0: tiles in global memory
+    int64_t sg_off;      // offset (in doubles) of this pack's S scratch in global memory (smem == 0)
+    int32_t syn_row0, nsyn_row;
+    int32_t hh_row0, nhh_row;
+    int32_t st_row0, nst_row;
+    int32_t ncell;       // detectors: lane d < ncell owns detector d
+    int32_t pr0, npr;    // probes of this pack: entries [pr0, pr0 + npr) of the probe arrays
+};
+
+// Event delivered inside one epoch, bucketed per owner lane and sorted by
+// (step_rel, js, t, src, idx).
+struct EvRec {
+    double t;
+    double w;
+    int32_t step_rel;   // step index relative to the epoch start
+    int32_t js;         // synapse row of the owner lane (relative to the pack's syn_row0)
+    int32_t src;        // source gid, -1 external
+    int32_t idx;        // connection index or external enqueue index
+};
+
+// Event waiting on the device for a later epoch.
+struct PendEv {
+    double t;
+    double w;
+    int64_t step;       // absolute step at whose start it is applied
+    int32_t syn;        // global synapse index
+    int32_t src;
+    int32_t idx;
+    int32_t pad;
+};
+
+// Device control block: values that change from epoch to epoch live here, so one
+// captured CUDA graph serves every epoch.
+struct Ctl {
+    int64_t k0, k1, k_end;     // current epoch [k0, k1); run target k_end
+    int64_t ext_lo, ext_hi;    // external events of this epoch in the sorted external array
+    int64_t n_ext;             // external events resident
+    int64_t n_spikes;          // spikes recorded so far
+    int64_t spk_lo;            // first spike of this epoch
+    int64_t probe_k0;          // step at which probe row 0 is taken
+    int64_t probe_max;         // probe rows available
+    int32_t pool_n[2];         // pending network events in pool 0 / 1
+    int32_t parity;            // pool holding the events not yet delivered
+    int32_t n_due;             // events delivered in this epoch
+    int32_t pack_next;         // work counter of the persistent epoch kernel
+    int32_t status;            // ARBK_* flags
+    int32_t pad[2];
+};
+
+enum : int32_t {
+    kStSpikeOverflow = 1,
+    kStPoolOverflow = 2,
+    kStBucketOverflow = 4,
+    kStNonFinite = 8,
+    kStLateEvent = 16,
+};
+
+// Everything the device kernels read; pointers into the caller's workspace.
+template <class MT>
+struct DevModel {
+    const PackDesc* packs;
+    int32_t n_packs;
+    int32_t n_owner;          // n_packs * 32
+    // solve entries (total_rows * 32)
+    const double* ca;         // alpha' = (c/dt - G_lin) / d'
+    const double* cb;         // beta'  = (G_lin E_lin) / d'
+    const double* ck;         // a' : contribution of the entry to its parent, scaled by the parent's 1/d'
+    const double* ce;         // e  : a / d' (back substitution)
+    const int32_t* pslot;     // -1 parent is the next row of this lane, -2 none, >= 0 parent's tile slot
+    double* V;                // voltages, tile layout
+    double* Sg;               // S scratch for packs whose tiles live in global memory
+    // synapses (syn_rows * 32)
+    const int32_t* syn_slot;  // tile slot of the synapse's CV, -1 padding
+    MT* syn_g;
+    const double* syn_e;
+    const double* syn_decay;  // exp(-dt/tau)
+    const double* syn_sc;     // 1/d' of the CV
+    // Hodgkin-Huxley (hh_rows * 32)
+    const int32_t* hh_slot;
+    const double* hh_sc;
+    const double* hh_gna;     // uS
+    const double* hh_gk;      // uS
+    MT* hh_m;
+    MT* hh_h;
+    MT* hh_n;
+    // current clamps (st_rows * 32)
+    const int32_t* st_slot;
+    const double* st_sc;
+    const double* st_on;
+    const double* st_off;
+    const double* st_amp;
+    // detectors (n_owner)
+    const int32_t* det_slot;
+    const int32_t* det_gid;
+    // probes, grouped by pack: tile slot of the CV and trace column
+    const int32_t* probe_slot;
+    const int32_t* probe_col;
+    int64_t n_probe;
+    double* trace;
+    // events
+    const int32_t* ev_off;    // [n_owner + 1]
+    const EvRec* ev;
+    // spikes
+    int32_t* spk_gid;
+    double* spk_t;
+    int64_t spike_cap;
+    Ctl* ctl;
+    double dt;
+    double threshold;
+};
+
+// Arguments of the event-delivery kernels.
+struct EvArgs {
+    Ctl* ctl;
+    PendEv* pool[2];
+    int64_t pool_cap;
+    const int64_t* ext_step;
+    const double* ext_t;
+    const double* ext_w;
+    const int32_t* ext_syn;
+    const int32_t* ext_idx;
+    const int32_t* syn_owner;
+    const int32_t* syn_js;
+    int32_t* counts;
+    int32_t* off;
+    EvRec* rec;
+    int64_t bucket_cap;
+    int32_t n_owner;
+    int32_t epoch_steps;
+};
+
+// Arguments of the spike-exchange kernel.
+struct SpkArgs {
+    Ctl* ctl;
+    const int32_t* spk_gid;
+    const double* spk_t;
+    int64_t spike_cap;
+    const int64_t* out_ptr;
+    const int32_t* out_syn;
+    const int32_t* out_idx;
+    const double* out_delay;
+    const double* out_w;
+    PendEv* pool[2];
+    int64_t pool_cap;
+    double dt;
+};
+
+}  // namespace arbk

@@ -1,0 +1,1442 @@
+// Host runtime and C ABI of the batched cable-equation stepper (declarations in include/arb.h).
+//
+// arb_create does all preparation on the host (no CUDA call):
+//   1. per-CV geometry of the finite-volume discretisation (Sec. "Model", Eq. discrete-v);
+//   2. the implicit-Euler matrix of Sec. "Model" and its Hines factorisation, once: with fixed
+//      dt and all membrane current on the right-hand side it never changes;
+//   3. the packing of cells into warp programs ("packs") and the solve schedule of each pack.
+// arb_bind_workspace uploads it into the caller's device buffer; arb_advance replays one
+// captured CUDA graph per epoch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "../../include/arb.h"
+#include "arb_internal.h"
+
+namespace arbk {
+template <class MT>
+cudaError_t launch_epoch(const DevModel<MT>& d, int grid, int warps_per_cta, int tile_doubles, cudaStream_t s);
+template <class MT>
+cudaError_t epoch_occupancy(int warps_per_cta, int tile_doubles, int* blocks_per_sm);
+cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
+cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s);
+template <class T>
+cudaError_t launch_gather(double* out, const T* src, const int64_t* idx, int64_t n, cudaStream_t s);
+template <class T>
+cudaError_t launch_scatter(T* dst, const double* src, const int64_t* idx, int64_t n, cudaStream_t s);
+
+}  // namespace arbk
+
+using namespace arbk;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kGraphRing = 4;
+
+struct ExtEvent {
+    int64_t step;
+    double t;
+    double w;
+    int32_t syn;
+    int32_t idx;
+};
+
+struct Plan {
+    std::vector<PackDesc> packs;
+    int64_t total_rows = 0;
+    std::vector<double> ca, cb, ck, ce;     // total_rows*32
+    std::vector<int32_t> pslot;
+    std::vector<double> V0;                 // initial voltage per tile entry
+    std::vector<int64_t> cv_tile;           // model CV -> global tile index
+    std::vector<int32_t> cv_pack;           // model CV -> pack
+    // synapses
+    int64_t syn_rows = 0;
+    std::vector<int32_t> syn_slot;
+    std::vector<double> syn_e, syn_decay, syn_sc;
+    std::vector<int64_t> syn_entry;         // model synapse -> entry
+    std::vector<int32_t> syn_owner, syn_js;
+    // HH
+    int64_t hh_rows = 0;
+    std::vector<int32_t> hh_slot;
+    std::vector<double> hh_sc, hh_gna, hh_gk;
+    std::vector<int64_t> hh_entry;
+    // clamps
+    int64_t st_rows = 0;
+    std::vector<int32_t> st_slot;
+    std::vector<double> st_sc, st_on, st_off, st_amp;
+    // detectors
+    std::vector<int32_t> det_slot, det_gid;
+    int64_t sg_total = 0;                   // doubles of global S scratch
+    int64_t smem_packs = 0;
+    double lane_eff = 0.0;
+    int tile_doubles = 0;                   // per-warp shared tile (doubles), 0 = none
+    int cells_per_pack = 0;
+};
+
+struct Region {
+    size_t off = 0, bytes = 0;
+};
+
+}  // namespace
+
+struct arb_sim {
+    // ---- settings and model copy
+    arb_params prm{};
+    int32_t n_cells = 0;
+    int64_t n_cv = 0;
+    std::vector<int64_t> cv_offset;
+    std::vector<int32_t> parent;
+    std::vector<double> length, radius, cm, Ra;
+    std::vector<int64_t> hh_cv, pas_cv, syn_cv, st_cv, det_cv;
+    std::vector<double> gnabar, gkbar, gl, g_pas, e_pas, syn_tau, syn_e, st_on, st_dur, st_amp;
+    double threshold = -10.0;
+    std::vector<int32_t> conn_src;
+    std::vector<int64_t> conn_dst;
+    std::vector<double> conn_delay, conn_w;
+    int32_t epoch_steps = 0;
+    bool mixed = false;
+    std::vector<int64_t> syn_cell;
+    // ---- prepared data
+    Plan plan;
+    std::vector<double> init_m, init_h, init_n;   // HH initial gates, model order
+    // connections grouped by source
+    std::vector<int64_t> out_ptr;
+    std::vector<int32_t> out_syn, out_idx;
+    std::vector<double> out_delay, out_w;
+    // ---- device
+    bool bound = false;
+    char* ws = nullptr;
+    int64_t ws_bytes = 0;
+    std::vector<std::pair<std::string, Region>> regions;
+    int n_sm = 148;
+    int warps_per_cta = 2;
+    int grid = 148;
+    cudaStream_t s = nullptr;       // library stream (graphs are captured here)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[kGraphRing] = {};
+    cudaEvent_t t0[kGraphRing] = {}, t1[kGraphRing] = {};
+    bool pending_time[kGraphRing] = {};
+    DevModel<double> dm64{};
+    DevModel<float> dm32{};
+    EvArgs ev_args{};
+    SpkArgs spk_args{};
+    Ctl* ctl = nullptr;
+    // host mirrors
+    int64_t k = 0;
+    std::vector<ExtEvent> ext;          // external events not yet known to be consumed
+    bool ext_dirty = false;
+    int64_t ext_counter = 0;
+    int64_t n_probe = 0;
+    double* trace = nullptr;
+    std::vector<int32_t> probe_slot, probe_col;
+    double last_epoch_ms = 0.0;
+    int64_t last_launches = 0;
+    int64_t graph_replays = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+arb_status fail(arb_sim* s, arb_status st, const std::string& msg) {
+    if (s) s->err = msg;
+    return st;
+}
+
+#define CU(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e__ = (call);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            return fail(sim, ARB_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Steady state of the Hodgkin-Huxley gates at voltage v (classic rates, 1/ms).
+void hh_steady(double v, double& m, double& h, double& n) {
+    auto exr = [](double x) { return x == 0.0 ? 1.0 : x / std::expm1(x); };
+    const double am = exr(-(v + 40.0) * 0.1), bm = 4.0 * std::exp(-(v + 65.0) / 18.0);
+    const double ah = 0.07 * std::exp(-(v + 65.0) * 0.05), bh = 1.0 / (1.0 + std::exp(-(v + 35.0) * 0.1));
+    const double an = 0.1 * exr(-(v + 55.0) * 0.1), bn = 0.125 * std::exp(-(v + 65.0) * 0.0125);
+    m = am / (am + bm);
+    h = ah / (ah + bh);
+    n = an / (an + bn);
+}
+
+// ---------------------------------------------------------------------------------------
+// Solve schedule of one pack.
+//
+// A cell's CVs are renumbered depth first (each child subtree contiguous, the larger subtree
+// first), so a CV's parent is the CV just before it except at branch points. The forward
+// sweep visits children before parents; a "row" holds one CV per lane.
+
+struct CellOrder {
+    std::vector<int32_t> dfs;      // dfs position -> local CV
+    std::vector<int32_t> pos;      // local CV -> dfs position
+    std::vector<int32_t> dpar;     // dfs position -> dfs position of the parent (-1 root)
+};
+
+CellOrder dfs_order(const int32_t* par, int32_t n) {
+    CellOrder o;
+    std::vector<int32_t> nch(n, 0), first(n + 1, 0), kids(n > 0 ? n - 1 : 0), size(n, 1);
+    for (int32_t i = 1; i < n; ++i) nch[par[i]]++;
+    for (int32_t i = 0; i < n; ++i) first[i + 1] = first[i] + nch[i];
+    std::vector<int32_t> fill(first.begin(), first.end() - 1);
+    for (int32_t i = 1; i < n; ++i) kids[fill[par[i]]++] = i;
+    for (int32_t i = n - 1; i >= 1; --i) size[par[i]] += size[i];
+    for (int32_t i = 0; i < n; ++i)
+        std::stable_sort(kids.begin() + first[i], kids.begin() + first[i + 1],
+                         [&](int32_t a, int32_t b) { return size[a] > size[b]; });
+    o.dfs.reserve(n);
+    std::vector<int32_t> stack;
+    if (n > 0) stack.push_back(0);
+    while (!stack.empty()) {
+        const int32_t v = stack.back();
+        stack.pop_back();
+        o.dfs.push_back(v);
+        for (int32_t q = first[v + 1] - 1; q >= first[v]; --q) stack.push_back(kids[q]);
+    }
+    o.pos.assign(n, 0);
+    for (int32_t q = 0; q < n; ++q) o.pos[o.dfs[q]] = q;
+    o.dpar.assign(n, -1);
+    for (int32_t q = 1; q < n; ++q) o.dpar[q] = o.pos[par[o.dfs[q]]];
+    return o;
+}
+
+// rows[j][l] = global model CV at (row j, lane l), or -1.
+struct PackRows {
+    std::vector<std::array<int64_t, 32>> rows;
+    int round_rows = 0;
+};
+
+// One cell per lane: lane l walks its cell from the last DFS position to the root.
+PackRows schedule_affinity(const std::vector<int32_t>& cells, const std::vector<CellOrder>& ord,
+                           const std::vector<int64_t>& cv_offset) {
+    PackRows pr;
+    int32_t J = 0;
+    for (int32_t c : cells) J = std::max<int32_t>(J, (int32_t)ord[c].dfs.size());
+    std::array<int64_t, 32> empty;
+    empty.fill(-1);
+    pr.rows.assign(J, empty);
+    for (size_t l = 0; l < cells.size(); ++l) {
+        const int32_t c = cells[l];
+        const int32_t n = (int32_t)ord[c].dfs.size();
+        for (int32_t j = 0; j < n; ++j) pr.rows[j][l] = cv_offset[c] + ord[c].dfs[n - 1 - j];
+    }
+    pr.round_rows = 0;
+    return pr;
+}
+
+// Several cells share the 32 lanes. Unbranched runs of CVs ("chains") are list-scheduled,
+// deepest first, in rounds of R rows separated by a warp barrier. A chain whose parent runs
+// on another lane hands its contribution over through shared memory, so the parent must
+// start in a later round; at most one lane writes a given parent per round, which keeps the
+// accumulation order fixed. A lane that completes the last child of a chain may continue
+// straight into that chain (the contribution then stays in a register).
+PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<CellOrder>& ord,
+                         const std::vector<int64_t>& cv_offset, int R) {
+    struct Chain {
+        int64_t base;        // global CV offset of the cell
+        const CellOrder* o;
+        int32_t head, tail;  // dfs positions, head < tail
+        int32_t parent;      // chain index of the parent chain, -1 root
+        int32_t pending;     // children not finished
+        int64_t prio;
+        int32_t finish_round;
+    };
+    std::vector<Chain> ch;
+    for (int32_t c : cells) {
+        const CellOrder& o = ord[c];
+        const int32_t n = (int32_t)o.dfs.size();
+        std::vector<int32_t> nch(n, 0);
+        for (int32_t q = 1; q < n; ++q) nch[o.dpar[q]]++;
+        std::vector<int32_t> chain_of(n, -1);
+        for (int32_t q = 0; q < n; ++q) {
+            const bool starts = (q == 0) || nch[o.dpar[q]] != 1;
+            if (starts) {
+                Chain x;
+                x.base = cv_offset[c];
+                x.o = &o;
+                x.head = q;
+                x.tail = q;
+                x.parent = (q == 0) ? -1 : chain_of[o.dpar[q]];
+                x.pending = 0;
+                x.prio = 0;
+                x.finish_round = -1;
+                ch.push_back(x);
+            } else {
+                ch.back().tail = q;   // single child directly follows its parent in DFS order
+            }
+            chain_of[q] = (int32_t)ch.size() - 1;
+        }
+    }
+    const int32_t nchain = (int32_t)ch.size();
+    for (int32_t i = 0; i < nchain; ++i)
+        if (ch[i].parent >= 0) ch[ch[i].parent].pending++;
+    // priority: CVs on the path to the root, own chain included (parents precede children)
+    for (int32_t i = 0; i < nchain; ++i) {
+        const int64_t len = ch[i].tail - ch[i].head + 1;
+        ch[i].prio = len + (ch[i].parent >= 0 ? ch[ch[i].parent].prio : 0);
+    }
+    auto cmp = [&](int32_t a, int32_t b) {
+        if (ch[a].prio != ch[b].prio) return ch[a].prio < ch[b].prio;
+        return a > b;
+    };
+    std::priority_queue<int32_t, std::vector<int32_t>, decltype(cmp)> ready(cmp);
+    for (int32_t i = 0; i < nchain; ++i)
+        if (ch[i].pending == 0) ready.push(i);
+
+    PackRows pr;
+    pr.round_rows = R;
+    std::array<int64_t, 32> empty;
+    empty.fill(-1);
+    std::array<int32_t, 32> cur, pos;
+    cur.fill(-1);
+    pos.fill(0);
+    int32_t done = 0;
+    int32_t round = 0;
+    while (done < nchain) {
+        const size_t r0 = pr.rows.size();
+        for (int rr = 0; rr < R; ++rr) pr.rows.push_back(empty);
+        std::vector<int32_t> newly;
+        std::vector<int32_t> written;   // parent chains that received a remote contribution this round
+        int32_t progressed = 0;
+        for (int l = 0; l < 32; ++l) {
+            for (int rr = 0; rr < R; ++rr) {
+                if (cur[l] < 0) {
+                    if (ready.empty()) break;
+                    cur[l] = ready.top();
+                    ready.pop();
+                    pos[l] = 0;
+                }
+                Chain& x = ch[cur[l]];
+                const int32_t len = x.tail - x.head + 1;
+                const bool head_row = pos[l] == len - 1;
+                bool cont = false;
+                if (head_row && x.parent >= 0) {
+                    Chain& P = ch[x.parent];
+                    // continuation: this is the last child and every sibling ended in an earlier round
+                    if (P.pending == 1) {
+                        cont = true;
+                    } else if (std::find(written.begin(), written.end(), x.parent) != written.end()) {
+                        break;   // a sibling already writes this parent in this round: wait
+                    }
+                }
+                pr.rows[r0 + rr][l] = x.base + x.o->dfs[x.tail - pos[l]];
+                ++progressed;
+                pos[l]++;
+                if (pos[l] == len) {
+                    x.finish_round = round;
+                    ++done;
+                    const int32_t pidx = x.parent;
+                    cur[l] = -1;
+                    if (pidx >= 0) {
+                        ch[pidx].pending--;
+                        if (cont) {
+                            cur[l] = pidx;
+                            pos[l] = 0;
+                        } else {
+                            written.push_back(pidx);
+                            if (ch[pidx].pending == 0) newly.push_back(pidx);
+                        }
+                    }
+                }
+            }
+        }
+        for (int32_t i : newly) ready.push(i);
+        ++round;
+        if (progressed == 0 && done < nchain) {
+            // cannot happen: some chain is always ready or running
+            break;
+        }
+    }
+    // trim trailing empty rows
+    while (!pr.rows.empty()) {
+        bool any = false;
+        for (int l = 0; l < 32; ++l) any |= pr.rows.back()[l] >= 0;
+        if (any) break;
+        pr.rows.pop_back();
+    }
+    return pr;
+}
+
+// Cost of a packing in rows per SM: packs share the SMs, rows of one pack are sequential.
+double packing_cost(const std::vector<int64_t>& pack_rows, int n_sm) {
+    int64_t sum = 0, mx = 0;
+    for (int64_t j : pack_rows) { sum += j; mx = std::max(mx, j); }
+    std::vector<int64_t> sorted = pack_rows;
+    std::sort(sorted.begin(), sorted.end(), std::greater<int64_t>());
+    std::priority_queue<int64_t, std::vector<int64_t>, std::greater<int64_t>> bins;
+    for (int i = 0; i < n_sm; ++i) bins.push(0);
+    for (int64_t j : sorted) {
+        int64_t b = bins.top();
+        bins.pop();
+        bins.push(b + j);
+    }
+    int64_t ms = 0;
+    while (!bins.empty()) { ms = std::max(ms, bins.top()); bins.pop(); }
+    return (double)std::max(ms, mx);
+}
+
+}  // namespace
+
+static void layout_regions(arb_sim* sim) {
+    const Plan& pl = sim->plan;
+    const arb_params& p = sim->prm;
+    const int64_t ne = pl.total_rows * kWarp;
+    const int64_t npk = (int64_t)pl.packs.size();
+    const int64_t nowner = npk * kWarp;
+    const bool mx = sim->mixed;
+    const size_t mt = mx ? sizeof(float) : sizeof(double);
+    const int64_t nsyn = (int64_t)sim->syn_cv.size(), nhh = (int64_t)sim->hh_cv.size();
+    const int64_t scratch = std::max<int64_t>({sim->n_cv, 3 * nhh, nsyn, 1});
+    std::vector<std::pair<std::string, size_t>> want = {
+        {"ctl", sizeof(Ctl)},
+        {"packs", sizeof(PackDesc) * std::max<int64_t>(npk, 1)},
+        {"ca", 8 * ne}, {"cb", 8 * ne}, {"ck", 8 * ne}, {"ce", 8 * ne}, {"pslot", 4 * ne},
+        {"V", 8 * ne}, {"Sg", 8 * std::max<int64_t>(pl.sg_total, 1)},
+        {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
+        {"syn_e", 8 * pl.syn_rows * kWarp}, {"syn_decay", 8 * pl.syn_rows * kWarp}, {"syn_sc", 8 * pl.syn_rows * kWarp},
+        {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
+        {"hh_gk", 8 * pl.hh_rows * kWarp}, {"hh_m", mt * pl.hh_rows * kWarp}, {"hh_h", mt * pl.hh_rows * kWarp},
+        {"hh_n", mt * pl.hh_rows * kWarp},
+        {"st_slot", 4 * pl.st_rows * kWarp}, {"st_sc", 8 * pl.st_rows * kWarp}, {"st_on", 8 * pl.st_rows * kWarp},
+        {"st_off", 8 * pl.st_rows * kWarp}, {"st_amp", 8 * pl.st_rows * kWarp},
+        {"det_slot", 4 * nowner}, {"det_gid", 4 * nowner},
+        {"probe_slot", 4 * std::max<int64_t>(sim->n_cv, 1)}, {"probe_col", 4 * std::max<int64_t>(sim->n_cv, 1)},
+        {"ev_off", 4 * (nowner + 1)}, {"counts", 4 * std::max<int64_t>(nowner, 1)},
+        {"ev", sizeof(EvRec) * p.bucket_capacity},
+        {"pool0", sizeof(PendEv) * p.event_capacity}, {"pool1", sizeof(PendEv) * p.event_capacity},
+        {"ext_step", 8 * p.ext_event_capacity}, {"ext_t", 8 * p.ext_event_capacity}, {"ext_w", 8 * p.ext_event_capacity},
+        {"ext_syn", 4 * p.ext_event_capacity}, {"ext_idx", 4 * p.ext_event_capacity},
+        {"syn_owner", 4 * std::max<int64_t>(nsyn, 1)}, {"syn_js", 4 * std::max<int64_t>(nsyn, 1)},
+        {"out_ptr", 8 * (sim->n_cells + 1)}, {"out_syn", 4 * std::max<size_t>(sim->out_syn.size(), 1)},
+        {"out_idx", 4 * std::max<size_t>(sim->out_syn.size(), 1)}, {"out_delay", 8 * std::max<size_t>(sim->out_syn.size(), 1)},
+        {"out_w", 8 * std::max<size_t>(sim->out_syn.size(), 1)},
+        {"spk_gid", 4 * p.spike_capacity}, {"spk_t", 8 * p.spike_capacity},
+        {"cv_tile", 8 * std::max<int64_t>(sim->n_cv, 1)}, {"hh_entry", 8 * std::max<int64_t>(nhh, 1)},
+        {"syn_entry", 8 * std::max<int64_t>(nsyn, 1)}, {"scratch", 8 * scratch},
+    };
+    sim->regions.clear();
+    size_t off = 0;
+    for (auto& w : want) {
+        off = (off + 255) & ~(size_t)255;
+        Region r;
+        r.off = off;
+        r.bytes = w.second;
+        sim->regions.push_back({w.first, r});
+        off += w.second;
+    }
+    sim->ws_bytes = (int64_t)((off + 255) & ~(size_t)255);
+}
+
+static char* region(arb_sim* sim, const char* name) {
+    for (auto& r : sim->regions)
+        if (r.first == name) return sim->ws + r.second.off;
+    return nullptr;
+}
+
+template <class T>
+static arb_status up(arb_sim* sim, const char* name, const std::vector<T>& v) {
+    if (v.empty()) return ARB_OK;
+    char* dst = region(sim, name);
+    if (!dst) return fail(sim, ARB_E_STATE, std::string("internal: no region ") + name);
+    CU(cudaMemcpyAsync(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, sim->s));
+    return ARB_OK;
+}
+
+template <class MT>
+static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
+    const Plan& pl = sim->plan;
+    d.packs = (const PackDesc*)region(sim, "packs");
+    d.n_packs = (int32_t)pl.packs.size();
+    d.n_owner = d.n_packs * kWarp;
+    d.ca = (const double*)region(sim, "ca");
+    d.cb = (const double*)region(sim, "cb");
+    d.ck = (const double*)region(sim, "ck");
+    d.ce = (const double*)region(sim, "ce");
+    d.pslot = (const int32_t*)region(sim, "pslot");
+    d.V = (double*)region(sim, "V");
+    d.Sg = (double*)region(sim, "Sg");
+    d.syn_slot = (const int32_t*)region(sim, "syn_slot");
+    d.syn_g = (MT*)region(sim, "syn_g");
+    d.syn_e = (const double*)region(sim, "syn_e");
+    d.syn_decay = (const double*)region(sim, "syn_decay");
+    d.syn_sc = (const double*)region(sim, "syn_sc");
+    d.hh_slot = (const int32_t*)region(sim, "hh_slot");
+    d.hh_sc = (const double*)region(sim, "hh_sc");
+    d.hh_gna = (const double*)region(sim, "hh_gna");
+    d.hh_gk = (const double*)region(sim, "hh_gk");
+    d.hh_m = (MT*)region(sim, "hh_m");
+    d.hh_h = (MT*)region(sim, "hh_h");
+    d.hh_n = (MT*)region(sim, "hh_n");
+    d.st_slot = (const int32_t*)region(sim, "st_slot");
+    d.st_sc = (const double*)region(sim, "st_sc");
+    d.st_on = (const double*)region(sim, "st_on");
+    d.st_off = (const double*)region(sim, "st_off");
+    d.st_amp = (const double*)region(sim, "st_amp");
+    d.det_slot = (const int32_t*)region(sim, "det_slot");
+    d.det_gid = (const int32_t*)region(sim, "det_gid");
+    d.probe_slot = (const int32_t*)region(sim, "probe_slot");
+    d.probe_col = (const int32_t*)region(sim, "probe_col");
+    d.n_probe = sim->n_probe;
+    d.trace = sim->trace;
+    d.ev_off = (const int32_t*)region(sim, "ev_off");
+    d.ev = (const EvRec*)region(sim, "ev");
+    d.spk_gid = (int32_t*)region(sim, "spk_gid");
+    d.spk_t = (double*)region(sim, "spk_t");
+    d.spike_cap = sim->prm.spike_capacity;
+    d.ctl = (Ctl*)region(sim, "ctl");
+    d.dt = sim->prm.dt;
+    d.threshold = sim->threshold;
+}
+
+// ===========================================================================================
+// C ABI
+
+extern "C" {
+
+arb_status arb_default_params(arb_params* p) {
+    if (!p) return ARB_E_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->dt = 0.025;
+    p->epoch_steps = 0;
+    p->precision = ARB_FP64;
+    p->cells_per_pack = 0;
+    p->smem_budget = 0;
+    p->event_capacity = 1 << 22;
+    p->ext_event_capacity = 1 << 20;
+    p->spike_capacity = 1 << 22;
+    p->bucket_capacity = 1 << 21;
+    p->stream = nullptr;
+    return ARB_OK;
+}
+
+const char* arb_last_error(const arb_sim* sim) { return sim ? sim->err.c_str() : g_create_error.c_str(); }
+
+arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
+    if (!out) return ARB_E_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!m || !pp) { g_create_error = "model or params is NULL"; return ARB_E_ARG; }
+    arb_sim* sim = new (std::nothrow) arb_sim();
+    if (!sim) return ARB_E_NOMEM;
+    auto bad = [&](const std::string& msg) {
+        g_create_error = msg;   // readable with arb_last_error(NULL)
+        delete sim;
+        return ARB_E_ARG;
+    };
+    sim->prm = *pp;
+    const arb_params& p = sim->prm;
+    if (!finite_pos(p.dt)) return bad("dt must be finite and > 0");
+    if (p.precision != ARB_FP64 && p.precision != ARB_MIXED) return bad("precision must be ARB_FP64 or ARB_MIXED");
+    if (p.event_capacity < 1 || p.ext_event_capacity < 1 || p.spike_capacity < 1 || p.bucket_capacity < 1)
+        return bad("capacities must be >= 1");
+    if (p.event_capacity > INT32_MAX || p.bucket_capacity > INT32_MAX) return bad("event and bucket capacities must be < 2^31");
+    if (p.cells_per_pack < 0 || p.cells_per_pack > 32) return bad("cells_per_pack must be 0..32");
+    sim->mixed = p.precision == ARB_MIXED;
+    if (m->n_cells < 0) return bad("n_cells < 0");
+    const int32_t nc = m->n_cells;
+    sim->n_cells = nc;
+    if (nc > 0 && !m->cv_offset) return bad("cv_offset is NULL");
+    sim->cv_offset.assign(nc + 1, 0);
+    if (nc > 0) std::copy(m->cv_offset, m->cv_offset + nc + 1, sim->cv_offset.begin());
+    if (sim->cv_offset[0] != 0) return bad("cv_offset[0] must be 0");
+    for (int32_t c = 0; c < nc; ++c)
+        if (sim->cv_offset[c + 1] <= sim->cv_offset[c]) return bad("every cell needs at least one CV (cv_offset must increase)");
+    const int64_t ncv = sim->cv_offset[nc];
+    sim->n_cv = ncv;
+    if (ncv > (int64_t)INT32_MAX / 2) return bad("too many CVs");
+    if (ncv > 0 && (!m->parent || !m->length_um || !m->radius_um || !m->cm || !m->Ra)) return bad("morphology array is NULL");
+    sim->parent.assign(m->parent, m->parent + ncv);
+    sim->length.assign(m->length_um, m->length_um + ncv);
+    sim->radius.assign(m->radius_um, m->radius_um + ncv);
+    sim->cm.assign(m->cm, m->cm + ncv);
+    sim->Ra.assign(m->Ra, m->Ra + ncv);
+    for (int32_t c = 0; c < nc; ++c) {
+        const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
+        if (sim->parent[off] != -1) return bad("cell " + std::to_string(c) + ": first CV must have parent -1");
+        for (int64_t i = 1; i < n; ++i) {
+            const int32_t pi = sim->parent[off + i];
+            if (pi < 0 || pi >= i) return bad("cell " + std::to_string(c) + ": parent of local CV " + std::to_string(i) + " must be in [0, i)");
+        }
+    }
+    for (int64_t i = 0; i < ncv; ++i)
+        if (!finite_pos(sim->length[i]) || !finite_pos(sim->radius[i]) || !finite_pos(sim->cm[i]) || !finite_pos(sim->Ra[i]))
+            return bad("CV " + std::to_string(i) + ": length, radius, cm and Ra must be finite and > 0");
+    auto copy_idx = [&](int64_t n, const int64_t* src, std::vector<int64_t>& dst, const char* what) -> bool {
+        if (n < 0 || (n > 0 && !src)) return false;
+        dst.assign(src, src + n);
+        for (int64_t i = 0; i < n; ++i)
+            if (dst[i] < 0 || dst[i] >= ncv) { sim->err = std::string(what) + " CV index out of range"; return false; }
+        return true;
+    };
+    auto copy_d = [&](int64_t n, const double* src, std::vector<double>& dst) -> bool {
+        if (n > 0 && !src) return false;
+        dst.assign(src, src + n);
+        for (double x : dst) if (!std::isfinite(x)) return false;
+        return true;
+    };
+    if (!copy_idx(m->n_hh, m->hh_cv, sim->hh_cv, "hh") || !copy_d(m->n_hh, m->gnabar, sim->gnabar) ||
+        !copy_d(m->n_hh, m->gkbar, sim->gkbar) || !copy_d(m->n_hh, m->gl, sim->gl))
+        return bad(sim->err.empty() ? "bad Hodgkin-Huxley arrays" : sim->err);
+    if (!copy_idx(m->n_pas, m->pas_cv, sim->pas_cv, "pas") || !copy_d(m->n_pas, m->g_pas, sim->g_pas) ||
+        !copy_d(m->n_pas, m->e_pas, sim->e_pas))
+        return bad(sim->err.empty() ? "bad passive arrays" : sim->err);
+    if (!copy_idx(m->n_syn, m->syn_cv, sim->syn_cv, "syn") || !copy_d(m->n_syn, m->syn_tau, sim->syn_tau) ||
+        !copy_d(m->n_syn, m->syn_e, sim->syn_e))
+        return bad(sim->err.empty() ? "bad synapse arrays" : sim->err);
+    for (double tau : sim->syn_tau) if (!(tau > 0)) return bad("synapse tau must be > 0");
+    if (m->n_syn > INT32_MAX / 2) return bad("too many synapses");
+    if (!copy_idx(m->n_stim, m->stim_cv, sim->st_cv, "stim") || !copy_d(m->n_stim, m->stim_t_on, sim->st_on) ||
+        !copy_d(m->n_stim, m->stim_dur, sim->st_dur) || !copy_d(m->n_stim, m->stim_amp, sim->st_amp))
+        return bad(sim->err.empty() ? "bad clamp arrays" : sim->err);
+    if (nc > 0 && !m->detector_cv) return bad("detector_cv is NULL");
+    sim->det_cv.assign(m->detector_cv, m->detector_cv + nc);
+    for (int32_t c = 0; c < nc; ++c)
+        if (sim->det_cv[c] < sim->cv_offset[c] || sim->det_cv[c] >= sim->cv_offset[c + 1])
+            return bad("detector of cell " + std::to_string(c) + " is not one of its CVs");
+    if (!std::isfinite(m->threshold)) return bad("threshold must be finite");
+    sim->threshold = m->threshold;
+    {   // at most one HH per CV
+        std::vector<char> seen(ncv, 0);
+        for (int64_t cv : sim->hh_cv) {
+            if (seen[cv]) return bad("more than one Hodgkin-Huxley instance on CV " + std::to_string(cv));
+            seen[cv] = 1;
+        }
+    }
+    const int64_t ncon = m->n_conn;
+    if (ncon < 0 || (ncon > 0 && (!m->conn_src || !m->conn_dst_syn || !m->conn_delay || !m->conn_weight)))
+        return bad("bad connection arrays");
+    if (ncon > INT32_MAX) return bad("too many connections");
+    sim->conn_src.assign(m->conn_src, m->conn_src + ncon);
+    sim->conn_dst.assign(m->conn_dst_syn, m->conn_dst_syn + ncon);
+    sim->conn_delay.assign(m->conn_delay, m->conn_delay + ncon);
+    sim->conn_w.assign(m->conn_weight, m->conn_weight + ncon);
+    double dmin = INFINITY;
+    for (int64_t i = 0; i < ncon; ++i) {
+        if (sim->conn_src[i] < 0 || sim->conn_src[i] >= nc) return bad("connection source gid out of range");
+        if (sim->conn_dst[i] < 0 || sim->conn_dst[i] >= m->n_syn) return bad("connection target synapse out of range");
+        if (!finite_pos(sim->conn_delay[i])) return bad("connection delays must be finite and > 0");
+        if (!std::isfinite(sim->conn_w[i])) return bad("connection weights must be finite");
+        dmin = std::min(dmin, sim->conn_delay[i]);
+    }
+    // epoch: no longer than the minimum delay (Sec. "Model": a positive minimum delay lets
+    // cells advance independently over that interval)
+    if (p.epoch_steps > 0) {
+        sim->epoch_steps = p.epoch_steps;
+    } else if (ncon > 0) {
+        const double e = std::floor(dmin / p.dt * (1.0 + 1e-12));
+        sim->epoch_steps = (int32_t)std::max(1.0, std::min(e, 100000.0));
+    } else {
+        sim->epoch_steps = 400;
+    }
+    if (ncon > 0 && dmin < sim->epoch_steps * p.dt * (1.0 - 1e-12))
+        return bad("epoch of " + std::to_string(sim->epoch_steps) + " steps is longer than the minimum delay");
+
+    // ------------------------------------------------------------------ discretisation
+    std::vector<double> area(ncv), cap(ncv), sigma(ncv, 0.0), Glin(ncv, 0.0), GElin(ncv, 0.0);
+    for (int32_t c = 0; c < nc; ++c) {
+        const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t g = off + i;
+            const double h = sim->length[g], r = sim->radius[g];
+            area[g] = 2.0 * kPi * r * h;                  // um^2
+            cap[g] = sim->cm[g] * area[g] * 1e-5;         // nF
+            if (i > 0) {
+                const int64_t pg = off + sim->parent[g];
+                // half-cylinder resistances in series, MOhm
+                const double half_i = sim->Ra[g] * h / (200.0 * kPi * r * r);
+                const double half_p = sim->Ra[pg] * sim->length[pg] / (200.0 * kPi * sim->radius[pg] * sim->radius[pg]);
+                sigma[g] = 1.0 / (half_i + half_p);       // uS
+            }
+        }
+    }
+    for (size_t i = 0; i < sim->pas_cv.size(); ++i) {
+        const int64_t cv = sim->pas_cv[i];
+        const double G = sim->g_pas[i] * area[cv] * 1e-2;  // S/cm^2 * um^2 -> uS
+        Glin[cv] += G;
+        GElin[cv] += G * sim->e_pas[i];
+    }
+    std::vector<double> hh_gna(sim->hh_cv.size()), hh_gk(sim->hh_cv.size());
+    for (size_t i = 0; i < sim->hh_cv.size(); ++i) {
+        const int64_t cv = sim->hh_cv[i];
+        const double G = sim->gl[i] * area[cv] * 1e-2;
+        Glin[cv] += G;
+        GElin[cv] += G * kEL;
+        hh_gna[i] = sim->gnabar[i] * area[cv] * 1e-2;
+        hh_gk[i] = sim->gkbar[i] * area[cv] * 1e-2;
+    }
+
+    // ------------------------------------------------------------------ factorisation
+    std::vector<CellOrder> ord(nc);
+    std::vector<double> invd(ncv), ck(ncv, 0.0), ce(ncv, 0.0), ca(ncv), cb(ncv);
+    {
+        std::vector<double> dd;
+        for (int32_t c = 0; c < nc; ++c) {
+            const int64_t off = sim->cv_offset[c];
+            const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
+            ord[c] = dfs_order(sim->parent.data() + off, n);
+            const CellOrder& o = ord[c];
+            dd.assign(n, 0.0);
+            for (int32_t q = 0; q < n; ++q) dd[q] = cap[off + o.dfs[q]] / p.dt;
+            for (int32_t q = 1; q < n; ++q) {
+                const double sg = sigma[off + o.dfs[q]];
+                dd[q] += sg;
+                dd[o.dpar[q]] += sg;
+            }
+            // eliminate children into parents, leaves first (dfs positions descending)
+            for (int32_t q = n - 1; q >= 1; --q) {
+                const double a = -sigma[off + o.dfs[q]];
+                dd[o.dpar[q]] -= (a / dd[q]) * a;
+            }
+            for (int32_t q = 0; q < n; ++q) {
+                const int64_t g = off + o.dfs[q];
+                invd[g] = 1.0 / dd[q];
+            }
+            for (int32_t q = 0; q < n; ++q) {
+                const int64_t g = off + o.dfs[q];
+                ca[g] = (cap[g] / p.dt - Glin[g]) * invd[g];
+                cb[g] = GElin[g] * invd[g];
+                if (q > 0) {
+                    const double a = -sigma[g];
+                    ck[g] = a * invd[off + o.dfs[o.dpar[q]]];
+                    ce[g] = a * invd[g];
+                }
+            }
+        }
+    }
+
+    // ------------------------------------------------------------------ packing
+    int n_sm = 148;
+    const int64_t budget = p.smem_budget > 0 ? p.smem_budget : 112 * 1024;
+    Plan& pl = sim->plan;
+    pl.tile_doubles = (int)(budget / 8);
+    std::vector<int32_t> by_size(nc);
+    std::iota(by_size.begin(), by_size.end(), 0);
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t b) {
+        return sim->cv_offset[a + 1] - sim->cv_offset[a] > sim->cv_offset[b + 1] - sim->cv_offset[b];
+    });
+    const int R = 4;
+    auto build = [&](int kpp, std::vector<PackRows>& rows, std::vector<std::vector<int32_t>>& groups) {
+        rows.clear();
+        groups.clear();
+        for (int32_t i = 0; i < nc; i += kpp) {
+            std::vector<int32_t> g(by_size.begin() + i, by_size.begin() + std::min<int32_t>(nc, i + kpp));
+            rows.push_back(kpp == 32 ? schedule_affinity(g, ord, sim->cv_offset)
+                                     : schedule_shared(g, ord, sim->cv_offset, R));
+            groups.push_back(std::move(g));
+        }
+    };
+    std::vector<PackRows> rows;
+    std::vector<std::vector<int32_t>> groups;
+    int kpp = p.cells_per_pack;
+    if (kpp == 0) {
+        if (nc >= 32 * 2 * n_sm) {
+            kpp = 32;
+        } else {
+            double best = INFINITY;
+            for (int cand : {32, 16, 12, 8, 6, 4, 3, 2, 1}) {
+                std::vector<PackRows> r;
+                std::vector<std::vector<int32_t>> g;
+                build(cand, r, g);
+                std::vector<int64_t> jr;
+                for (auto& x : r) jr.push_back((int64_t)x.rows.size());
+                const double cost = packing_cost(jr, n_sm);
+                if (cost < best * 0.97) { best = cost; kpp = cand; rows = std::move(r); groups = std::move(g); }
+            }
+        }
+    }
+    if (rows.empty() && nc > 0) build(kpp, rows, groups);
+    pl.cells_per_pack = kpp;
+    const int32_t npk = (int32_t)rows.size();
+    // order packs by decreasing length: the persistent kernel takes them in this order
+    std::vector<int32_t> porder(npk);
+    std::iota(porder.begin(), porder.end(), 0);
+    std::stable_sort(porder.begin(), porder.end(), [&](int32_t a, int32_t b) { return rows[a].rows.size() > rows[b].rows.size(); });
+
+    pl.packs.resize(npk);
+    pl.cv_tile.assign(ncv, -1);
+    pl.cv_pack.assign(ncv, -1);
+    int64_t row0 = 0, cvs_placed = 0;
+    for (int32_t pi = 0; pi < npk; ++pi) {
+        PackDesc& pd = pl.packs[pi];
+        const PackRows& pr = rows[porder[pi]];
+        pd.row0 = (int32_t)row0;
+        pd.nrow = (int32_t)pr.rows.size();
+        pd.round_rows = pr.round_rows;
+        const int64_t tile = (int64_t)pd.nrow * kWarp * 2;
+        pd.smem = (tile <= pl.tile_doubles) ? 1 : 0;
+        if (pd.smem) pl.smem_packs++;
+        pd.sg_off = pd.smem ? 0 : pl.sg_total;
+        if (!pd.smem) pl.sg_total += (int64_t)pd.nrow * kWarp;
+        for (int32_t j = 0; j < pd.nrow; ++j)
+            for (int l = 0; l < kWarp; ++l) {
+                const int64_t cv = pr.rows[j][l];
+                if (cv >= 0) {
+                    pl.cv_tile[cv] = (row0 + j) * kWarp + l;
+                    pl.cv_pack[cv] = pi;
+                    ++cvs_placed;
+                }
+            }
+        row0 += pd.nrow;
+    }
+    pl.total_rows = row0;
+    if (cvs_placed != ncv) return bad("internal error: packing lost CVs");
+    pl.lane_eff = pl.total_rows > 0 ? (double)ncv / (double)(pl.total_rows * kWarp) : 1.0;
+    const int64_t ne = pl.total_rows * kWarp;
+    if (ne > INT32_MAX) return bad("model too large for one handle");
+    pl.ca.assign(ne, 0.0);
+    pl.cb.assign(ne, 0.0);
+    pl.ck.assign(ne, 0.0);
+    pl.ce.assign(ne, 0.0);
+    pl.pslot.assign(ne, -2);
+    pl.V0.assign(ne, 0.0);
+    std::vector<int64_t> tile_cv(ne, -1);
+    for (int64_t cv = 0; cv < ncv; ++cv) tile_cv[pl.cv_tile[cv]] = cv;
+    for (int32_t c = 0; c < nc; ++c) {
+        const int64_t off = sim->cv_offset[c];
+        const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t g = off + i;
+            const int64_t t = pl.cv_tile[g];
+            pl.ca[t] = ca[g];
+            pl.cb[t] = cb[g];
+            pl.ck[t] = ck[g];
+            pl.ce[t] = ce[g];
+            pl.V0[t] = -65.0;
+            if (i == 0) {
+                pl.pslot[t] = -2;
+            } else {
+                const int64_t tp = pl.cv_tile[off + sim->parent[g]];
+                const int32_t pk = pl.cv_pack[g];
+                const int64_t base = (int64_t)pl.packs[pk].row0 * kWarp;
+                pl.pslot[t] = (tp == t + kWarp) ? -1 : (int32_t)(tp - base);
+            }
+        }
+    }
+
+    // ------------------------------------------------------------------ mechanisms per pack
+    // Mechanism entries may sit on any lane: the loops touch S only through tile slots.
+    // Synapses (and clamps) on one CV stay on one lane so that no two lanes update the same
+    // slot within a loop.
+    const int32_t nsyn = (int32_t)sim->syn_cv.size();
+    std::vector<std::vector<int32_t>> pk_syn(npk), pk_hh(npk), pk_st(npk);
+    for (int32_t i = 0; i < nsyn; ++i) pk_syn[pl.cv_pack[sim->syn_cv[i]]].push_back(i);
+    for (size_t i = 0; i < sim->hh_cv.size(); ++i) pk_hh[pl.cv_pack[sim->hh_cv[i]]].push_back((int32_t)i);
+    for (size_t i = 0; i < sim->st_cv.size(); ++i) pk_st[pl.cv_pack[sim->st_cv[i]]].push_back((int32_t)i);
+    // lane assignment of grouped items: groups by CV, largest first, onto the least loaded lane
+    auto assign_grouped = [&](const std::vector<int32_t>& items, const std::vector<int64_t>& item_cv,
+                              std::array<std::vector<int32_t>, 32>& lanes) {
+        std::vector<std::pair<int64_t, std::vector<int32_t>>> grp;
+        {
+            std::vector<int32_t> it = items;
+            std::stable_sort(it.begin(), it.end(), [&](int32_t a, int32_t b) { return item_cv[a] < item_cv[b]; });
+            for (size_t i = 0; i < it.size(); ++i) {
+                if (i == 0 || item_cv[it[i]] != item_cv[it[i - 1]]) grp.push_back({item_cv[it[i]], {}});
+                grp.back().second.push_back(it[i]);
+            }
+        }
+        std::stable_sort(grp.begin(), grp.end(), [](const auto& a, const auto& b) { return a.second.size() > b.second.size(); });
+        std::array<int64_t, 32> load{};
+        for (auto& g : grp) {
+            int best = 0;
+            for (int l = 1; l < 32; ++l) if (load[l] < load[best]) best = l;
+            for (int32_t x : g.second) lanes[best].push_back(x);
+            load[best] += (int64_t)g.second.size();
+        }
+    };
+    pl.syn_entry.assign(nsyn, -1);
+    pl.syn_owner.assign(nsyn, 0);
+    pl.syn_js.assign(nsyn, 0);
+    pl.hh_entry.assign(sim->hh_cv.size(), -1);
+    std::vector<int64_t> syn_cv_tmp(sim->syn_cv), st_cv_tmp(sim->st_cv);
+    int64_t syn_rows = 0, hh_rows = 0, st_rows = 0;
+    std::vector<std::array<std::vector<int32_t>, 32>> syn_lanes(npk), st_lanes(npk);
+    for (int32_t pi = 0; pi < npk; ++pi) {
+        assign_grouped(pk_syn[pi], syn_cv_tmp, syn_lanes[pi]);
+        assign_grouped(pk_st[pi], st_cv_tmp, st_lanes[pi]);
+        size_t ms = 0, mt = 0;
+        for (int l = 0; l < 32; ++l) { ms = std::max(ms, syn_lanes[pi][l].size()); mt = std::max(mt, st_lanes[pi][l].size()); }
+        PackDesc& pd = pl.packs[pi];
+        pd.syn_row0 = (int32_t)syn_rows;
+        pd.nsyn_row = (int32_t)ms;
+        syn_rows += (int64_t)ms;
+        pd.hh_row0 = (int32_t)hh_rows;
+        pd.nhh_row = (int32_t)((pk_hh[pi].size() + 31) / 32);
+        hh_rows += pd.nhh_row;
+        pd.st_row0 = (int32_t)st_rows;
+        pd.nst_row = (int32_t)mt;
+        st_rows += (int64_t)mt;
+        pd.ncell = 0;
+        pd.pr0 = 0;
+        pd.npr = 0;
+    }
+    pl.syn_rows = syn_rows;
+    pl.hh_rows = hh_rows;
+    pl.st_rows = st_rows;
+    pl.syn_slot.assign(syn_rows * kWarp, -1);
+    pl.syn_e.assign(syn_rows * kWarp, 0.0);
+    pl.syn_decay.assign(syn_rows * kWarp, 0.0);
+    pl.syn_sc.assign(syn_rows * kWarp, 0.0);
+    pl.hh_slot.assign(hh_rows * kWarp, -1);
+    pl.hh_sc.assign(hh_rows * kWarp, 0.0);
+    pl.hh_gna.assign(hh_rows * kWarp, 0.0);
+    pl.hh_gk.assign(hh_rows * kWarp, 0.0);
+    pl.st_slot.assign(st_rows * kWarp, -1);
+    pl.st_sc.assign(st_rows * kWarp, 0.0);
+    pl.st_on.assign(st_rows * kWarp, 0.0);
+    pl.st_off.assign(st_rows * kWarp, 0.0);
+    pl.st_amp.assign(st_rows * kWarp, 0.0);
+    pl.det_slot.assign((size_t)npk * kWarp, -1);
+    pl.det_gid.assign((size_t)npk * kWarp, -1);
+    for (int32_t pi = 0; pi < npk; ++pi) {
+        PackDesc& pd = pl.packs[pi];
+        const int64_t base = (int64_t)pd.row0 * kWarp;
+        for (int l = 0; l < 32; ++l) {
+            const auto& v = syn_lanes[pi][l];
+            for (size_t r = 0; r < v.size(); ++r) {
+                const int32_t i = v[r];
+                const int64_t q = ((int64_t)pd.syn_row0 + (int64_t)r) * kWarp + l;
+                const int64_t cv = sim->syn_cv[i];
+                pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+                pl.syn_e[q] = sim->syn_e[i];
+                pl.syn_decay[q] = std::exp(-p.dt / sim->syn_tau[i]);
+                pl.syn_sc[q] = invd[cv];
+                pl.syn_entry[i] = q;
+                pl.syn_owner[i] = pi * kWarp + l;
+                pl.syn_js[i] = (int32_t)r;
+            }
+            const auto& w = st_lanes[pi][l];
+            for (size_t r = 0; r < w.size(); ++r) {
+                const int32_t i = w[r];
+                const int64_t q = ((int64_t)pd.st_row0 + (int64_t)r) * kWarp + l;
+                const int64_t cv = sim->st_cv[i];
+                pl.st_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+                pl.st_sc[q] = invd[cv];
+                pl.st_on[q] = sim->st_on[i];
+                pl.st_off[q] = sim->st_on[i] + sim->st_dur[i];
+                pl.st_amp[q] = sim->st_amp[i];
+            }
+        }
+        for (size_t r = 0; r < pk_hh[pi].size(); ++r) {
+            const int32_t i = pk_hh[pi][r];
+            const int64_t q = ((int64_t)pd.hh_row0 + (int64_t)(r / 32)) * kWarp + (int64_t)(r % 32);
+            const int64_t cv = sim->hh_cv[i];
+            pl.hh_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+            pl.hh_sc[q] = invd[cv];
+            pl.hh_gna[q] = hh_gna[i];
+            pl.hh_gk[q] = hh_gk[i];
+            pl.hh_entry[i] = q;
+        }
+        const std::vector<int32_t>& g = groups[porder[pi]];
+        pd.ncell = (int32_t)g.size();
+        for (size_t d = 0; d < g.size(); ++d) {
+            pl.det_slot[(size_t)pi * kWarp + d] = (int32_t)(pl.cv_tile[sim->det_cv[g[d]]] - base);
+            pl.det_gid[(size_t)pi * kWarp + d] = g[d];
+        }
+    }
+    // initial gates
+    {
+        double mi, hi, ni;
+        hh_steady(-65.0, mi, hi, ni);
+        sim->init_m.assign(sim->hh_cv.size(), mi);
+        sim->init_h.assign(sim->hh_cv.size(), hi);
+        sim->init_n.assign(sim->hh_cv.size(), ni);
+    }
+    // connections grouped by source, ascending connection index
+    sim->out_ptr.assign(nc + 1, 0);
+    for (int64_t i = 0; i < ncon; ++i) sim->out_ptr[sim->conn_src[i] + 1]++;
+    for (int32_t c = 0; c < nc; ++c) sim->out_ptr[c + 1] += sim->out_ptr[c];
+    sim->out_syn.resize(ncon);
+    sim->out_idx.resize(ncon);
+    sim->out_delay.resize(ncon);
+    sim->out_w.resize(ncon);
+    {
+        std::vector<int64_t> fill(sim->out_ptr.begin(), sim->out_ptr.end() - 1);
+        for (int64_t i = 0; i < ncon; ++i) {
+            const int64_t q = fill[sim->conn_src[i]]++;
+            sim->out_syn[q] = (int32_t)sim->conn_dst[i];
+            sim->out_idx[q] = (int32_t)i;
+            sim->out_delay[q] = sim->conn_delay[i];
+            sim->out_w[q] = sim->conn_w[i];
+        }
+    }
+    *out = sim;
+    return ARB_OK;
+}
+
+void arb_destroy(arb_sim* sim) {
+    if (!sim) return;
+    if (sim->bound) {
+        for (int g = 0; g < kGraphRing; ++g) {
+            if (sim->graph[g]) cudaGraphExecDestroy(sim->graph[g]);
+            if (sim->t0[g]) cudaEventDestroy(sim->t0[g]);
+            if (sim->t1[g]) cudaEventDestroy(sim->t1[g]);
+        }
+        if (sim->ev_in) cudaEventDestroy(sim->ev_in);
+        if (sim->ev_out) cudaEventDestroy(sim->ev_out);
+        if (sim->s) {
+            cudaStreamSynchronize(sim->s);
+            cudaStreamDestroy(sim->s);
+        }
+    }
+    delete sim;
+}
+
+
+
+arb_status arb_workspace_bytes(const arb_sim* csim, int64_t* bytes) {
+    arb_sim* sim = const_cast<arb_sim*>(csim);
+    if (!sim || !bytes) return ARB_E_ARG;
+    layout_regions(sim);
+    *bytes = sim->ws_bytes;
+    return ARB_OK;
+}
+
+arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_rows, int64_t* smem_packs,
+                         double* lane_efficiency, int32_t* epoch_steps) {
+    if (!sim) return ARB_E_ARG;
+    if (n_packs) *n_packs = (int64_t)sim->plan.packs.size();
+    if (total_rows) *total_rows = sim->plan.total_rows;
+    if (smem_packs) *smem_packs = sim->plan.smem_packs;
+    if (lane_efficiency) *lane_efficiency = sim->plan.lane_eff;
+    if (epoch_steps) *epoch_steps = sim->epoch_steps;
+    return ARB_OK;
+}
+
+
+
+static arb_status upload_mech_state(arb_sim* sim, const std::vector<double>& m, const std::vector<double>& h,
+                                    const std::vector<double>& n, const std::vector<double>& g);
+
+static arb_status capture_graphs(arb_sim* sim) {
+    for (int gi = 0; gi < kGraphRing; ++gi) {
+        if (sim->graph[gi]) { cudaGraphExecDestroy(sim->graph[gi]); sim->graph[gi] = nullptr; }
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(sim->s, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = launch_events_pre(sim->ev_args, sim->n_sm, sim->s);
+        cudaError_t e2 = cudaEventRecord(sim->t0[gi], sim->s);
+        cudaError_t e3 = sim->mixed ? launch_epoch<float>(sim->dm32, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
+                                    : launch_epoch<double>(sim->dm64, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
+        cudaError_t e4 = cudaEventRecord(sim->t1[gi], sim->s);
+        cudaError_t e5 = launch_events_post(sim->spk_args, sim->n_sm, sim->s);
+        cudaError_t e6 = cudaStreamEndCapture(sim->s, &g);
+        for (cudaError_t e : {e1, e2, e3, e4, e5, e6})
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return fail(sim, ARB_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            }
+        cudaError_t ei = cudaGraphInstantiate(&sim->graph[gi], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+    return ARB_OK;
+}
+
+arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
+    if (!sim) return ARB_E_ARG;
+    if (sim->bound) return fail(sim, ARB_E_STATE, "workspace already bound");
+    layout_regions(sim);
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 255) != 0) return fail(sim, ARB_E_ARG, "workspace must be a 256-byte aligned device pointer");
+    if (bytes < sim->ws_bytes) return fail(sim, ARB_E_NOMEM, "workspace too small: need " + std::to_string(sim->ws_bytes) + " bytes");
+    cudaPointerAttributes pa;
+    CU(cudaPointerGetAttributes(&pa, dev_ptr));
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return fail(sim, ARB_E_ARG, "workspace is not device memory");
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sim->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    sim->ws = (char*)dev_ptr;
+    CU(cudaStreamCreateWithFlags(&sim->s, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&sim->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&sim->ev_out, cudaEventDisableTiming));
+    for (int g = 0; g < kGraphRing; ++g) {
+        CU(cudaEventCreate(&sim->t0[g]));
+        CU(cudaEventCreate(&sim->t1[g]));
+    }
+    cudaStream_t us = (cudaStream_t)sim->prm.stream;
+    CU(cudaEventRecord(sim->ev_in, us));
+    CU(cudaStreamWaitEvent(sim->s, sim->ev_in, 0));
+    const Plan& pl = sim->plan;
+    arb_status st;
+#define UP(name, vec) if ((st = up(sim, name, vec)) != ARB_OK) return st
+    UP("packs", pl.packs);
+    UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot);
+    UP("V", pl.V0);
+    UP("syn_slot", pl.syn_slot); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
+    UP("hh_slot", pl.hh_slot); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
+    UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
+    UP("det_slot", pl.det_slot); UP("det_gid", pl.det_gid);
+    UP("syn_owner", pl.syn_owner); UP("syn_js", pl.syn_js);
+    UP("out_ptr", sim->out_ptr); UP("out_syn", sim->out_syn); UP("out_idx", sim->out_idx);
+    UP("out_delay", sim->out_delay); UP("out_w", sim->out_w);
+    UP("cv_tile", pl.cv_tile); UP("hh_entry", pl.hh_entry); UP("syn_entry", pl.syn_entry);
+#undef UP
+    {   // zero the mechanism state arrays (padding entries), then set the initial state
+        const size_t mt = sim->mixed ? 4 : 8;
+        CU(cudaMemsetAsync(region(sim, "syn_g"), 0, mt * pl.syn_rows * kWarp, sim->s));
+        CU(cudaMemsetAsync(region(sim, "hh_m"), 0, mt * pl.hh_rows * kWarp, sim->s));
+        CU(cudaMemsetAsync(region(sim, "hh_h"), 0, mt * pl.hh_rows * kWarp, sim->s));
+        CU(cudaMemsetAsync(region(sim, "hh_n"), 0, mt * pl.hh_rows * kWarp, sim->s));
+    }
+    Ctl c0;
+    std::memset(&c0, 0, sizeof(c0));
+    CU(cudaMemcpyAsync(region(sim, "ctl"), &c0, sizeof(Ctl), cudaMemcpyHostToDevice, sim->s));
+    fill_devmodel(sim, sim->dm64);
+    fill_devmodel(sim, sim->dm32);
+    sim->bound = true;
+    st = upload_mech_state(sim, sim->init_m, sim->init_h, sim->init_n, std::vector<double>(sim->syn_cv.size(), 0.0));
+    if (st != ARB_OK) return st;
+    EvArgs& a = sim->ev_args;
+    a.ctl = (Ctl*)region(sim, "ctl");
+    a.pool[0] = (PendEv*)region(sim, "pool0");
+    a.pool[1] = (PendEv*)region(sim, "pool1");
+    a.pool_cap = sim->prm.event_capacity;
+    a.ext_step = (const int64_t*)region(sim, "ext_step");
+    a.ext_t = (const double*)region(sim, "ext_t");
+    a.ext_w = (const double*)region(sim, "ext_w");
+    a.ext_syn = (const int32_t*)region(sim, "ext_syn");
+    a.ext_idx = (const int32_t*)region(sim, "ext_idx");
+    a.syn_owner = (const int32_t*)region(sim, "syn_owner");
+    a.syn_js = (const int32_t*)region(sim, "syn_js");
+    a.counts = (int32_t*)region(sim, "counts");
+    a.off = (int32_t*)region(sim, "ev_off");
+    a.rec = (EvRec*)region(sim, "ev");
+    a.bucket_cap = sim->prm.bucket_capacity;
+    a.n_owner = (int32_t)(pl.packs.size() * kWarp);
+    a.epoch_steps = sim->epoch_steps;
+    SpkArgs& b = sim->spk_args;
+    b.ctl = a.ctl;
+    b.spk_gid = (const int32_t*)region(sim, "spk_gid");
+    b.spk_t = (const double*)region(sim, "spk_t");
+    b.spike_cap = sim->prm.spike_capacity;
+    b.out_ptr = (const int64_t*)region(sim, "out_ptr");
+    b.out_syn = (const int32_t*)region(sim, "out_syn");
+    b.out_idx = (const int32_t*)region(sim, "out_idx");
+    b.out_delay = (const double*)region(sim, "out_delay");
+    b.out_w = (const double*)region(sim, "out_w");
+    b.pool[0] = a.pool[0];
+    b.pool[1] = a.pool[1];
+    b.pool_cap = sim->prm.event_capacity;
+    b.dt = sim->prm.dt;
+    // launch shape of the persistent epoch kernel
+    const bool any_smem = pl.smem_packs > 0;
+    sim->warps_per_cta = any_smem ? (int)std::max<int64_t>(1, (int64_t)(227 * 1024 / 8) / std::max(1, pl.tile_doubles)) : 4;
+    sim->warps_per_cta = std::min(sim->warps_per_cta, 8);
+    if (!any_smem) sim->plan.tile_doubles = 0;
+    int bps = 0;
+    cudaError_t eo = sim->mixed ? epoch_occupancy<float>(sim->warps_per_cta, sim->plan.tile_doubles, &bps)
+                                : epoch_occupancy<double>(sim->warps_per_cta, sim->plan.tile_doubles, &bps);
+    if (eo != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("epoch kernel occupancy: ") + cudaGetErrorString(eo));
+    if (bps < 1) return fail(sim, ARB_E_CUDA, "epoch kernel does not fit on an SM");
+    sim->grid = sim->n_sm * bps;
+    st = capture_graphs(sim);
+    if (st != ARB_OK) return st;
+    CU(cudaStreamSynchronize(sim->s));
+    return ARB_OK;
+}
+
+arb_status arb_enqueue_events(arb_sim* sim, int64_t n, const int64_t* syn, const double* t, const double* w) {
+    if (!sim) return ARB_E_ARG;
+    if (n < 0 || (n > 0 && (!syn || !t || !w))) return fail(sim, ARB_E_ARG, "bad event arrays");
+    const int64_t nsyn = (int64_t)sim->syn_cv.size();
+    for (int64_t i = 0; i < n; ++i) {
+        if (syn[i] < 0 || syn[i] >= nsyn) return fail(sim, ARB_E_ARG, "event synapse index out of range");
+        if (!std::isfinite(t[i]) || !std::isfinite(w[i])) return fail(sim, ARB_E_ARG, "event time and weight must be finite");
+        const int64_t step = (int64_t)std::ceil(t[i] / sim->prm.dt);
+        if (step < sim->k) return fail(sim, ARB_E_ARG, "event time lies before the current time");
+    }
+    if (sim->ext_counter + n > INT32_MAX) return fail(sim, ARB_E_OVERFLOW, "too many external events over the run");
+    for (int64_t i = 0; i < n; ++i) {
+        ExtEvent e;
+        e.t = t[i];
+        e.w = w[i];
+        e.syn = (int32_t)syn[i];
+        e.idx = (int32_t)(sim->ext_counter++);
+        e.step = (int64_t)std::ceil(t[i] / sim->prm.dt);
+        sim->ext.push_back(e);
+    }
+    if (n > 0) sim->ext_dirty = true;
+    return ARB_OK;
+}
+
+static arb_status sync_in(arb_sim* sim) {
+    CU(cudaEventRecord(sim->ev_in, (cudaStream_t)sim->prm.stream));
+    CU(cudaStreamWaitEvent(sim->s, sim->ev_in, 0));
+    return ARB_OK;
+}
+static arb_status sync_out(arb_sim* sim) {
+    CU(cudaEventRecord(sim->ev_out, sim->s));
+    CU(cudaStreamWaitEvent((cudaStream_t)sim->prm.stream, sim->ev_out, 0));
+    return ARB_OK;
+}
+
+arb_status arb_advance(arb_sim* sim, double t_end) {
+    if (!sim) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    if (!std::isfinite(t_end)) return fail(sim, ARB_E_ARG, "t_end must be finite");
+    const int64_t k_end = (int64_t)std::llround(t_end / sim->prm.dt);
+    sim->last_epoch_ms = 0.0;
+    sim->last_launches = 0;
+    if (k_end <= sim->k) return ARB_OK;
+    arb_status st = sync_in(sim);
+    if (st != ARB_OK) return st;
+    Ctl* dctl = (Ctl*)region(sim, "ctl");
+    if (sim->ext_dirty) {
+        // keep only events not yet delivered, sorted by (step, enqueue order)
+        std::vector<ExtEvent> keep;
+        keep.reserve(sim->ext.size());
+        for (const auto& e : sim->ext) if (e.step >= sim->k) keep.push_back(e);
+        std::stable_sort(keep.begin(), keep.end(), [](const ExtEvent& a, const ExtEvent& b) {
+            return a.step != b.step ? a.step < b.step : a.idx < b.idx;
+        });
+        sim->ext.swap(keep);
+        const int64_t n = (int64_t)sim->ext.size();
+        if (n > sim->prm.ext_event_capacity)
+            return fail(sim, ARB_E_OVERFLOW, "more pending external events than ext_event_capacity");
+        std::vector<int64_t> step(n);
+        std::vector<double> tt(n), ww(n);
+        std::vector<int32_t> sy(n), ix(n);
+        for (int64_t i = 0; i < n; ++i) {
+            step[i] = sim->ext[i].step; tt[i] = sim->ext[i].t; ww[i] = sim->ext[i].w;
+            sy[i] = sim->ext[i].syn; ix[i] = sim->ext[i].idx;
+        }
+        if ((st = up(sim, "ext_step", step)) != ARB_OK) return st;
+        if ((st = up(sim, "ext_t", tt)) != ARB_OK) return st;
+        if ((st = up(sim, "ext_w", ww)) != ARB_OK) return st;
+        if ((st = up(sim, "ext_syn", sy)) != ARB_OK) return st;
+        if ((st = up(sim, "ext_idx", ix)) != ARB_OK) return st;
+        static thread_local int64_t zero_and_n[2];
+        zero_and_n[0] = 0;
+        zero_and_n[1] = n;
+        CU(cudaMemcpyAsync(&dctl->ext_lo, &zero_and_n[0], sizeof(int64_t), cudaMemcpyHostToDevice, sim->s));
+        CU(cudaMemcpyAsync(&dctl->n_ext, &zero_and_n[1], sizeof(int64_t), cudaMemcpyHostToDevice, sim->s));
+        CU(cudaStreamSynchronize(sim->s));   // host vectors above go out of scope
+        sim->ext_dirty = false;
+    }
+    static thread_local int64_t kend_host;
+    kend_host = k_end;
+    CU(cudaMemcpyAsync(&dctl->k_end, &kend_host, sizeof(int64_t), cudaMemcpyHostToDevice, sim->s));
+    const int64_t E = sim->epoch_steps;
+    const int64_t pieces = (k_end - sim->k + E - 1) / E;
+    for (int g = 0; g < kGraphRing; ++g) sim->pending_time[g] = false;
+    double ms_sum = 0.0;
+    for (int64_t i = 0; i < pieces; ++i) {
+        const int g = (int)(sim->graph_replays % kGraphRing);
+        if (sim->pending_time[g]) {
+            CU(cudaEventSynchronize(sim->t1[g]));
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, sim->t0[g], sim->t1[g]));
+            ms_sum += ms;
+            sim->pending_time[g] = false;
+        }
+        CU(cudaGraphLaunch(sim->graph[g], sim->s));
+        sim->pending_time[g] = true;
+        sim->graph_replays++;
+    }
+    Ctl hc;
+    CU(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sim->s));
+    CU(cudaStreamSynchronize(sim->s));
+    for (int g = 0; g < kGraphRing; ++g)
+        if (sim->pending_time[g]) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, sim->t0[g], sim->t1[g]));
+            ms_sum += ms;
+            sim->pending_time[g] = false;
+        }
+    sim->last_epoch_ms = ms_sum;
+    sim->last_launches = pieces * 8;
+    sim->k = k_end;
+    if ((st = sync_out(sim)) != ARB_OK) return st;
+    if (hc.k0 != k_end) return fail(sim, ARB_E_STATE, "internal: device step count disagrees with the host");
+    if (hc.status & (kStSpikeOverflow | kStPoolOverflow | kStBucketOverflow)) {
+        std::string what;
+        if (hc.status & kStSpikeOverflow) what += " spike_capacity";
+        if (hc.status & kStPoolOverflow) what += " event_capacity";
+        if (hc.status & kStBucketOverflow) what += " bucket_capacity";
+        return fail(sim, ARB_E_OVERFLOW, "capacity exceeded:" + what);
+    }
+    if (hc.status & kStNonFinite) return fail(sim, ARB_E_NONFINITE, "a voltage became NaN or infinite");
+    if (hc.status & kStLateEvent) return fail(sim, ARB_E_STATE, "internal: an event arrived after its step");
+    return ARB_OK;
+}
+
+arb_status arb_time(const arb_sim* sim, double* t, int64_t* steps) {
+    if (!sim) return ARB_E_ARG;
+    if (t) *t = (double)sim->k * sim->prm.dt;
+    if (steps) *steps = sim->k;
+    return ARB_OK;
+}
+
+arb_status arb_read_voltage(arb_sim* sim, double* out, int64_t n_cv, int32_t on_device) {
+    if (!sim || !out) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    if (n_cv != sim->n_cv) return fail(sim, ARB_E_ARG, "n_cv does not match the model");
+    arb_status st = sync_in(sim);
+    if (st != ARB_OK) return st;
+    double* dst = on_device ? out : (double*)region(sim, "scratch");
+    CU(launch_gather<double>(dst, (const double*)region(sim, "V"), (const int64_t*)region(sim, "cv_tile"), n_cv, sim->s));
+    if (!on_device) {
+        CU(cudaMemcpyAsync(out, dst, sizeof(double) * n_cv, cudaMemcpyDeviceToHost, sim->s));
+        CU(cudaStreamSynchronize(sim->s));
+    }
+    return sync_out(sim);
+}
+
+arb_status arb_num_spikes(arb_sim* sim, int64_t* n) {
+    if (!sim || !n) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    int64_t v = 0;
+    CU(cudaMemcpyAsync(&v, &((Ctl*)region(sim, "ctl"))->n_spikes, sizeof(int64_t), cudaMemcpyDeviceToHost, sim->s));
+    CU(cudaStreamSynchronize(sim->s));
+    *n = std::min(v, sim->prm.spike_capacity);
+    return ARB_OK;
+}
+
+arb_status arb_read_spikes(arb_sim* sim, int32_t* gid, double* t, int64_t cap, int64_t* n_out) {
+    if (!sim || !n_out || cap < 0 || (cap > 0 && (!gid || !t))) return ARB_E_ARG;
+    int64_t n = 0;
+    arb_status st = arb_num_spikes(sim, &n);
+    if (st != ARB_OK) return st;
+    std::vector<int32_t> g(n);
+    std::vector<double> tt(n);
+    if (n > 0) {
+        CU(cudaMemcpyAsync(g.data(), region(sim, "spk_gid"), 4 * n, cudaMemcpyDeviceToHost, sim->s));
+        CU(cudaMemcpyAsync(tt.data(), region(sim, "spk_t"), 8 * n, cudaMemcpyDeviceToHost, sim->s));
+        CU(cudaStreamSynchronize(sim->s));
+    }
+    std::vector<int64_t> o(n);
+    std::iota(o.begin(), o.end(), 0);
+    std::sort(o.begin(), o.end(), [&](int64_t a, int64_t b) { return tt[a] != tt[b] ? tt[a] < tt[b] : g[a] < g[b]; });
+    const int64_t m = std::min(n, cap);
+    for (int64_t i = 0; i < m; ++i) { gid[i] = g[o[i]]; t[i] = tt[o[i]]; }
+    *n_out = m;
+    return ARB_OK;
+}
+
+arb_status arb_set_probes(arb_sim* sim, int64_t n, const int64_t* cv, double* dev_trace, int64_t max_steps) {
+    if (!sim) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    if (n < 0 || n > sim->n_cv || (n > 0 && (!cv || !dev_trace || max_steps < 0)))
+        return fail(sim, ARB_E_ARG, "bad probe arguments (at most n_cv probes)");
+    Plan& pl = sim->plan;
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> per(pl.packs.size());
+    for (int64_t i = 0; i < n; ++i) {
+        if (cv[i] < 0 || cv[i] >= sim->n_cv) return fail(sim, ARB_E_ARG, "probe CV out of range");
+        const int32_t pk = pl.cv_pack[cv[i]];
+        per[pk].push_back({(int32_t)(pl.cv_tile[cv[i]] - (int64_t)pl.packs[pk].row0 * kWarp), (int32_t)i});
+    }
+    sim->probe_slot.clear();
+    sim->probe_col.clear();
+    for (size_t pk = 0; pk < per.size(); ++pk) {
+        pl.packs[pk].pr0 = (int32_t)sim->probe_slot.size();
+        pl.packs[pk].npr = (int32_t)per[pk].size();
+        for (auto& x : per[pk]) { sim->probe_slot.push_back(x.first); sim->probe_col.push_back(x.second); }
+    }
+    arb_status st = sync_in(sim);
+    if (st != ARB_OK) return st;
+    if ((st = up(sim, "packs", pl.packs)) != ARB_OK) return st;
+    if ((st = up(sim, "probe_slot", sim->probe_slot)) != ARB_OK) return st;
+    if ((st = up(sim, "probe_col", sim->probe_col)) != ARB_OK) return st;
+    sim->n_probe = n;
+    sim->trace = n > 0 ? dev_trace : nullptr;
+    Ctl* dctl = (Ctl*)region(sim, "ctl");
+    static thread_local int64_t pk0[2];
+    pk0[0] = sim->k;
+    pk0[1] = n > 0 ? max_steps : 0;
+    CU(cudaMemcpyAsync(&dctl->probe_k0, &pk0[0], sizeof(int64_t), cudaMemcpyHostToDevice, sim->s));
+    CU(cudaMemcpyAsync(&dctl->probe_max, &pk0[1], sizeof(int64_t), cudaMemcpyHostToDevice, sim->s));
+    CU(cudaStreamSynchronize(sim->s));
+    // kernel arguments changed: capture again
+    fill_devmodel(sim, sim->dm64);
+    fill_devmodel(sim, sim->dm32);
+    if ((st = capture_graphs(sim)) != ARB_OK) return st;
+    return sync_out(sim);
+}
+
+static arb_status upload_mech_state(arb_sim* sim, const std::vector<double>& m, const std::vector<double>& h,
+                                    const std::vector<double>& n, const std::vector<double>& g) {
+    double* scr = (double*)region(sim, "scratch");
+    const int64_t nhh = (int64_t)sim->hh_cv.size(), nsyn = (int64_t)sim->syn_cv.size();
+    const int64_t* hidx = (const int64_t*)region(sim, "hh_entry");
+    const int64_t* sidx = (const int64_t*)region(sim, "syn_entry");
+    auto put = [&](const std::vector<double>& v, const char* name, const int64_t* idx, int64_t cnt) -> arb_status {
+        if (cnt == 0) return ARB_OK;
+        CU(cudaMemcpyAsync(scr, v.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, sim->s));
+        if (sim->mixed) CU(launch_scatter<float>((float*)region(sim, name), scr, idx, cnt, sim->s));
+        else CU(launch_scatter<double>((double*)region(sim, name), scr, idx, cnt, sim->s));
+        CU(cudaStreamSynchronize(sim->s));
+        return ARB_OK;
+    };
+    arb_status st;
+    if ((st = put(m, "hh_m", hidx, nhh)) != ARB_OK) return st;
+    if ((st = put(h, "hh_h", hidx, nhh)) != ARB_OK) return st;
+    if ((st = put(n, "hh_n", hidx, nhh)) != ARB_OK) return st;
+    if ((st = put(g, "syn_g", sidx, nsyn)) != ARB_OK) return st;
+    return ARB_OK;
+}
+
+arb_status arb_get_state(arb_sim* sim, double* V, double* m, double* h, double* n, double* g) {
+    if (!sim) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    arb_status st = sync_in(sim);
+    if (st != ARB_OK) return st;
+    double* scr = (double*)region(sim, "scratch");
+    const int64_t nhh = (int64_t)sim->hh_cv.size(), nsyn = (int64_t)sim->syn_cv.size();
+    auto get = [&](double* out, const char* name, const char* idxname, int64_t cnt, bool is_mech) -> arb_status {
+        if (!out || cnt == 0) return ARB_OK;
+        const int64_t* idx = (const int64_t*)region(sim, idxname);
+        if (is_mech && sim->mixed) CU(launch_gather<float>(scr, (const float*)region(sim, name), idx, cnt, sim->s));
+        else CU(launch_gather<double>(scr, (const double*)region(sim, name), idx, cnt, sim->s));
+        CU(cudaMemcpyAsync(out, scr, sizeof(double) * cnt, cudaMemcpyDeviceToHost, sim->s));
+        CU(cudaStreamSynchronize(sim->s));
+        return ARB_OK;
+    };
+    if ((st = get(V, "V", "cv_tile", sim->n_cv, false)) != ARB_OK) return st;
+    if ((st = get(m, "hh_m", "hh_entry", nhh, true)) != ARB_OK) return st;
+    if ((st = get(h, "hh_h", "hh_entry", nhh, true)) != ARB_OK) return st;
+    if ((st = get(n, "hh_n", "hh_entry", nhh, true)) != ARB_OK) return st;
+    if ((st = get(g, "syn_g", "syn_entry", nsyn, true)) != ARB_OK) return st;
+    return sync_out(sim);
+}
+
+arb_status arb_set_state(arb_sim* sim, const double* V, const double* m, const double* h, const double* n, const double* g) {
+    if (!sim) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    const int64_t nhh = (int64_t)sim->hh_cv.size(), nsyn = (int64_t)sim->syn_cv.size();
+    if ((sim->n_cv > 0 && !V) || (nhh > 0 && (!m || !h || !n)) || (nsyn > 0 && !g)) return fail(sim, ARB_E_ARG, "state array is NULL");
+    for (int64_t i = 0; i < sim->n_cv; ++i) if (!std::isfinite(V[i])) return fail(sim, ARB_E_ARG, "voltages must be finite");
+    arb_status st = sync_in(sim);
+    if (st != ARB_OK) return st;
+    double* scr = (double*)region(sim, "scratch");
+    if (sim->n_cv > 0) {
+        CU(cudaMemcpyAsync(scr, V, sizeof(double) * sim->n_cv, cudaMemcpyHostToDevice, sim->s));
+        CU(launch_scatter<double>((double*)region(sim, "V"), scr, (const int64_t*)region(sim, "cv_tile"), sim->n_cv, sim->s));
+        CU(cudaStreamSynchronize(sim->s));
+    }
+    st = upload_mech_state(sim, std::vector<double>(m, m + nhh), std::vector<double>(h, h + nhh),
+                           std::vector<double>(n, n + nhh), std::vector<double>(g, g + nsyn));
+    if (st != ARB_OK) return st;
+    return sync_out(sim);
+}
+
+arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t* launches) {
+    if (!sim) return ARB_E_ARG;
+    if (epoch_kernel_ms) *epoch_kernel_ms = sim->last_epoch_ms;
+    if (launches) *launches = sim->last_launches;
+    return ARB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+"""Python front end of the C ABI: torch provides the device workspace and the stream.
+
+Every step of the simulation runs in the library's CUDA kernels; this module only marshals
+arrays and owns the torch buffers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+def _model_struct(m):
+    """Builds an arb_model from an inputs.Model (or any object with the same array fields)."""
+    keep = {}
+
+    def arr(name, dtype):
+        a = np.ascontiguousarray(getattr(m, name), dtype=dtype)
+        keep[name] = a
+        return _p(a)
+
+    s = L.arb_model()
+    s.n_cells = int(np.asarray(m.cv_offset).size - 1)
+    s.cv_offset = arr("cv_offset", np.int64)
+    s.parent = arr("parent", np.int32)
+    s.length_um, s.radius_um = arr("length_um", np.float64), arr("radius_um", np.float64)
+    s.cm, s.Ra = arr("cm", np.float64), arr("Ra", np.float64)
+    s.n_hh = int(np.asarray(m.hh_cv).size)
+    s.hh_cv = arr("hh_cv", np.int64)
+    s.gnabar, s.gkbar, s.gl = arr("gnabar", np.float64), arr("gkbar", np.float64), arr("gl", np.float64)
+    s.n_pas = int(np.asarray(m.pas_cv).size)
+    s.pas_cv, s.g_pas, s.e_pas = arr("pas_cv", np.int64), arr("g_pas", np.float64), arr("e_pas", np.float64)
+    s.n_syn = int(np.asarray(m.syn_cv).size)
+    s.syn_cv, s.syn_tau, s.syn_e = arr("syn_cv", np.int64), arr("syn_tau", np.float64), arr("syn_e", np.float64)
+    s.n_stim = int(np.asarray(m.stim_cv).size)
+    s.stim_cv = arr("stim_cv", np.int64)
+    s.stim_t_on, s.stim_dur, s.stim_amp = arr("stim_t_on", np.float64), arr("stim_dur", np.float64), arr("stim_amp", np.float64)
+    s.detector_cv = arr("detector_cv", np.int64)
+    s.threshold = float(m.threshold)
+    s.n_conn = int(np.asarray(m.conn_src).size)
+    s.conn_src, s.conn_dst_syn = arr("conn_src", np.int32), arr("conn_dst_syn", np.int64)
+    s.conn_delay, s.conn_weight = arr("conn_delay", np.float64), arr("conn_weight", np.float64)
+    return s, keep
+
+
+def default_params():
+    p = L.arb_params()
+    L.check(L.load().arb_default_params(C.byref(p)))
+    return p
+
+
+class Plan:
+    """Host-side preparation only (arb_create): usable without a GPU."""
+
+    def __init__(self, model, dt=0.025, epoch_steps=0, precision="fp64", cells_per_pack=0, smem_budget=0,
+                 event_capacity=None, ext_event_capacity=None, spike_capacity=None, bucket_capacity=None,
+                 stream=None):
+        lib = L.load()
+        self.model = model
+        p = default_params()
+        p.dt = float(dt)
+        p.epoch_steps = int(epoch_steps)
+        p.precision = L.ARB_MIXED if precision == "mixed" else L.ARB_FP64
+        p.cells_per_pack = int(cells_per_pack)
+        p.smem_budget = int(smem_budget)
+        if event_capacity is not None:
+            p.event_capacity = int(event_capacity)
+        if ext_event_capacity is not None:
+            p.ext_event_capacity = int(ext_event_capacity)
+        if spike_capacity is not None:
+            p.spike_capacity = int(spike_capacity)
+        if bucket_capacity is not None:
+            p.bucket_capacity = int(bucket_capacity)
+        p.stream = stream
+        self.params = p
+        self._ms, self._keep = _model_struct(model)
+        h = C.c_void_p()
+        st = lib.arb_create(C.byref(self._ms), C.byref(p), C.byref(h))
+        L.check(st, None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.load().arb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        n = C.c_int64()
+        L.check(L.load().arb_workspace_bytes(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def plan_info(self):
+        npk, rows, smem = C.c_int64(), C.c_int64(), C.c_int64()
+        eff, ep = C.c_double(), C.c_int32()
+        L.check(L.load().arb_plan_info(self.h, C.byref(npk), C.byref(rows), C.byref(smem), C.byref(eff), C.byref(ep)), self.h)
+        return dict(n_packs=npk.value, total_rows=rows.value, smem_packs=smem.value, lane_efficiency=eff.value,
+                    epoch_steps=ep.value)
+
+
+class Simulation(Plan):
+    """A bound handle: device workspace from torch, all stepping in the CUDA library."""
+
+    def __init__(self, model, dt=0.025, device="cuda", stream=None, **kw):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise RuntimeError("Simulation needs a CUDA device; there is no CPU fallback")
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        super().__init__(model, dt=dt, stream=C.c_void_p(self.stream.cuda_stream), **kw)
+        nbytes = self.workspace_bytes()
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) & ~255
+        L.check(L.load().arb_bind_workspace(self.h, C.c_void_p(aligned), nbytes), self.h)
+        self.dt = float(dt)
+        self._trace = None
+
+    # --- events and time
+    def enqueue(self, syn, t, w):
+        syn = np.ascontiguousarray(syn, np.int64)
+        t = np.ascontiguousarray(t, np.float64)
+        w = np.ascontiguousarray(w, np.float64)
+        if syn.size:
+            L.check(L.load().arb_enqueue_events(self.h, syn.size, _p(syn), _p(t), _p(w)), self.h)
+
+    def advance(self, t_end: float):
+        L.check(L.load().arb_advance(self.h, float(t_end)), self.h)
+
+    def time(self):
+        t, k = C.c_double(), C.c_int64()
+        L.check(L.load().arb_time(self.h, C.byref(t), C.byref(k)), self.h)
+        return t.value, k.value
+
+    # --- outputs
+    def voltage(self, out=None):
+        """Voltages in model CV order: a numpy array, or into a given CUDA float64 tensor."""
+        n = int(self.model.n_cv)
+        if out is not None:
+            assert out.is_cuda and out.dtype == self.torch.float64 and out.numel() == n
+            L.check(L.load().arb_read_voltage(self.h, C.c_void_p(out.data_ptr()), n, 1), self.h)
+            return out
+        v = np.zeros(n)
+        L.check(L.load().arb_read_voltage(self.h, _p(v), n, 0), self.h)
+        return v
+
+    def num_spikes(self) -> int:
+        n = C.c_int64()
+        L.check(L.load().arb_num_spikes(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def spikes(self):
+        n = self.num_spikes()
+        gid = np.zeros(max(n, 1), np.int32)
+        t = np.zeros(max(n, 1))
+        got = C.c_int64()
+        L.check(L.load().arb_read_spikes(self.h, _p(gid), _p(t), n, C.byref(got)), self.h)
+        return gid[:got.value], t[:got.value]
+
+    def set_probes(self, cvs, max_steps):
+        cvs = np.ascontiguousarray(cvs, np.int64)
+        self._trace = self.torch.full((int(max_steps), cvs.size), float("nan"), dtype=self.torch.float64, device=self.device)
+        L.check(L.load().arb_set_probes(self.h, cvs.size, _p(cvs), C.c_void_p(self._trace.data_ptr()), int(max_steps)), self.h)
+        return self._trace
+
+    def get_state(self):
+        m = self.model
+        nh = np.asarray(m.hh_cv).size
+        V, mm, hh, nn, g = np.zeros(m.n_cv), np.zeros(nh), np.zeros(nh), np.zeros(nh), np.zeros(m.n_syn)
+        L.check(L.load().arb_get_state(self.h, _p(V), _p(mm), _p(hh), _p(nn), _p(g)), self.h)
+        return dict(V=V, m=mm, h=hh, n=nn, g=g)
+
+    def set_state(self, st):
+        arrs = [np.ascontiguousarray(st[k], np.float64) for k in ("V", "m", "h", "n", "g")]
+        L.check(L.load().arb_set_state(self.h, *[_p(a) for a in arrs]), self.h)
+
+    def last_timing(self):
+        ms, n = C.c_double(), C.c_int64()
+        L.check(L.load().arb_last_timing(self.h, C.byref(ms), C.byref(n)), self.h)
+        return ms.value, n.value

@@ -1,0 +1,92 @@
+"""C-ABI library: load, exported symbols, host-side validation and planning (no GPU)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from inputs import make_config, small_tree_model
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def arb():
+    from paper_1901_07454_b300 import _build
+    _build.build()
+    import paper_1901_07454_b300 as m
+    return m
+
+
+def _header_symbols():
+    txt = open(os.path.join(ROOT, "include", "arb.h")).read()
+    return sorted(set(re.findall(r"\b(arb_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(arb):
+    declared = _header_symbols()
+    assert len(declared) >= 15
+    lib = arb.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(arb.EXPORTED) == declared
+
+
+def test_default_params(arb):
+    p = arb.default_params()
+    assert p.dt == 0.025 and p.precision == 0 and p.epoch_steps == 0
+
+
+def _expect_error(arb, model, match, **kw):
+    with pytest.raises(arb.ArbError) as ei:
+        arb.Plan(model, **kw)
+    assert "ARB_E_ARG" in str(ei.value)
+    assert re.search(match, str(ei.value)), str(ei.value)
+
+
+def test_validation_errors(arb):
+    m = small_tree_model(1, n_cells=2, n_branches=4, cv_range=(2, 4))
+    bad = small_tree_model(1, n_cells=2, n_branches=4, cv_range=(2, 4))
+    bad.parent[3] = 5
+    _expect_error(arb, bad, "parent")
+    bad = small_tree_model(1, n_cells=2, n_branches=4, cv_range=(2, 4))
+    bad.length_um[0] = -1.0
+    _expect_error(arb, bad, "length")
+    bad = small_tree_model(1, n_cells=2, n_branches=4, cv_range=(2, 4))
+    bad.detector_cv = np.array([bad.cv_offset[1], 0])
+    _expect_error(arb, bad, "detector")
+    _expect_error(arb, m, "dt", dt=0.0)
+    # delays shorter than the requested epoch
+    r, spec = make_config(1, n_cells=4, t_end=10.0)
+    _expect_error(arb, r, "epoch", dt=0.025, epoch_steps=400)
+    # two HH instances on one CV
+    bad = small_tree_model(2, n_cells=1, n_branches=2, cv_range=(2, 3))
+    bad.hh_cv = np.array([0, 0])
+    bad.gnabar = bad.gkbar = bad.gl = np.array([0.1, 0.1])
+    _expect_error(arb, bad, "Hodgkin")
+
+
+def test_planning_covers_every_cv(arb):
+    for kpp in (32, 8, 3, 1):
+        m = small_tree_model(5, n_cells=40, n_branches=9, cv_range=(1, 12), n_syn=3)
+        p = arb.Plan(m, cells_per_pack=kpp)
+        info = p.plan_info()
+        assert info["total_rows"] * 32 >= m.n_cv
+        assert 0 < info["lane_efficiency"] <= 1.0
+        assert p.workspace_bytes() > 0
+
+
+def test_epoch_is_derived_from_min_delay(arb):
+    m, spec = make_config(1, n_cells=8, t_end=10.0)
+    assert arb.Plan(m, dt=0.025).plan_info()["epoch_steps"] == 200
+    m, spec = make_config(2, n_cells=64, t_end=10.0)
+    assert arb.Plan(m, dt=0.025).plan_info()["epoch_steps"] == 40
+
+
+def test_bind_requires_device_pointer(arb):
+    m = small_tree_model(1, n_cells=1)
+    p = arb.Plan(m)
+    buf = (C.c_char * 1024)()
+    st = arb.load().arb_bind_workspace(p.h, C.cast(buf, C.c_void_p), 1024)
+    assert st != 0
