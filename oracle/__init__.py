@@ -73,6 +73,7 @@ def lib():
         L.orc_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
         L.orc_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
         L.orc_record_delivered.argtypes = [vp, i32]
+        L.orc_set_explicit.argtypes = [vp, i32]
         L.orc_num_delivered.restype = i64
         L.orc_num_delivered.argtypes = [vp]
         L.orc_get_delivered.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -146,7 +147,10 @@ def exprelr(x):
 class OracleSim:
     """FP64 CPU simulation of a Model; mirrors the library's create/enqueue/advance/read cycle."""
 
-    def __init__(self, model, dt: float, epoch_steps: int, nthreads: int = 0, record_delivered=False):
+    def __init__(self, model, dt: float, epoch_steps: int, nthreads: int = 0, record_delivered=False,
+                 explicit=False):
+        """explicit=False: fully implicit voltage step (membrane conductance on the diagonal);
+        explicit=True: the printed linear system with the membrane current at V(t)."""
         self.model = model
         self.dt = float(dt)
         self.epoch_steps = int(epoch_steps)
@@ -154,6 +158,8 @@ class OracleSim:
         self.h = lib().orc_create(C.byref(self._b.s), self.dt, self.epoch_steps, int(nthreads))
         if record_delivered:
             lib().orc_record_delivered(self.h, 1)
+        if explicit:
+            lib().orc_set_explicit(self.h, 1)
         self._probe_buf = None
 
     def __del__(self):
@@ -225,10 +231,10 @@ class OracleSim:
         return dict(syn=syn, t=t, w=w, step=step, src=src, idx=idx)
 
 
-def simulate(model, spec, nthreads: int = 0, probes=None, record_delivered=False, n_steps=None):
+def simulate(model, spec, nthreads: int = 0, probes=None, record_delivered=False, n_steps=None, explicit=False):
     """Run a whole SimSpec (or its first n_steps); returns (sim, probe trace or None)."""
     steps = spec.n_steps if n_steps is None else int(n_steps)
-    sim = OracleSim(model, spec.dt, spec.epoch_steps or 400, nthreads, record_delivered)
+    sim = OracleSim(model, spec.dt, spec.epoch_steps or 400, nthreads, record_delivered, explicit)
     sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
     trace = sim.set_probes(probes, steps) if probes is not None else None
     sim.run_steps(steps)

@@ -8,12 +8,18 @@
  *  - the vertex-centred finite-volume semi-discretisation of the cable equation, Eq.
  *    (discrete-v): c_i dV_i/dt = sum_j sigma_ij (V_j - V_i) - I_inj - I_syn - sum S_i g_k (V_i - e_k);
  *    here one control volume (CV) per compartment, node at the compartment centre;
- *  - the operator splitting of Sec. "Model": membrane currents at V(t), then one implicit
- *    Euler step of the voltage, then the channel and synapse states with the new voltage;
- *  - the implicit Euler linear system of Sec. "Model":
- *        (c_i/dt) V'_i + sum_j sigma_ij V'_i - sum_j sigma_ij V'_j = -I_i^memb + (c_i/dt) V_i,
- *    solved every step by Gaussian elimination in Hines order (parent index < child index),
- *    i.e. the Thomas algorithm extended to trees (Sec. "Model", Hines 1984);
+ *  - the operator splitting of Sec. "Model": channel, synapse and injection currents are
+ *    evaluated with the states at t, V(t+dt) is computed from Eq. (discrete-v) by the implicit
+ *    Euler method, then the channel and synapse states are advanced with the new voltage;
+ *  - two readings of the implicit Euler step (both kept, selected per simulation):
+ *    IMPLICIT (default): with the states frozen at t every membrane current is g_k (V - E_k),
+ *      linear in V, and the step of Eq. (discrete-v) is fully implicit:
+ *        (c_i/dt + g_i) V'_i + sum_j sigma_ij (V'_i - V'_j) = (c_i/dt) V_i + sum_k g_k E_k + I_inj;
+ *    EXPLICIT: the linear system printed in Sec. "Model", membrane current taken at V(t):
+ *        (c_i/dt) V'_i + sum_j sigma_ij V'_i - sum_j sigma_ij V'_j = -I_i^memb + (c_i/dt) V_i;
+ *      it diverges on the ring and batched workloads (tiny compartments, dt*g/c > 2);
+ *    either system is solved every step by Gaussian elimination in Hines order (parent index <
+ *    child index), i.e. the Thomas algorithm extended to trees (Sec. "Model", Hines 1984);
  *  - spike events change the synapse state at the start of a step (Sec. "Model");
  *  - a spike is emitted when the detector voltage crosses a fixed threshold (Sec. "Model");
  *  - cells advance independently within an epoch no longer than the minimum delay; spikes
@@ -181,6 +187,7 @@ typedef struct {
 typedef struct {
     orc_model m;
     double dt;
+    int explicit_current;    /* 1: membrane current at V(t) on the right-hand side */
     int64_t epoch_steps;
     int nthreads;
     int64_t k;               /* steps taken */
@@ -360,6 +367,7 @@ void orc_destroy(orc_sim* s) {
 }
 
 void orc_record_delivered(orc_sim* s, int on) { s->record_delivered = on; }
+void orc_set_explicit(orc_sim* s, int on) { s->explicit_current = on; }
 
 /* External events: applied at the start of step ceil(t/dt). Returns -1 if one lies in the past. */
 int orc_enqueue(orc_sim* s, int64_t n, const int64_t* syn, const double* t, const double* w) {
@@ -411,37 +419,54 @@ static void step_cell(orc_sim* s, int32_t c, int64_t k, double* I, double* d, do
         }
     }
 
-    /* 2. membrane currents (outward, nA) at V(t_k) */
-    for (int64_t i = 0; i < n; ++i) I[i] = 0.0;
+    /* 2. membrane terms with the states at t_k: conductance g_i (uS) and g_i*E (nA) per CV for
+     *    the implicit step, or the outward current I_i (nA) at V(t_k) for the explicit one;
+     *    injected current Iinj (nA, depolarising) active at t_k */
+    double* G = d;        /* reuse: conductance sums */
+    double* GE = a;       /* reuse: sum g*E */
+    double* Iinj = Vn;    /* reuse: injected current */
+    for (int64_t i = 0; i < n; ++i) { I[i] = 0.0; G[i] = 0.0; GE[i] = 0.0; Iinj[i] = 0.0; }
     for (int64_t j = s->hh_ptr[c]; j < s->hh_ptr[c + 1]; ++j) {
         int64_t h = s->hh_list[j];
         int64_t i = m->hh_cv[h] - off;
         double v = V[i], mm = s->hh_m[h], hh = s->hh_h[h], nn = s->hh_n[h];
-        I[i] += s->hh_gna[h] * mm * mm * mm * hh * (v - ORC_ENA)
-              + s->hh_gk[h] * nn * nn * nn * nn * (v - ORC_EK)
-              + s->hh_gl[h] * (v - ORC_EL);
+        double gna = s->hh_gna[h] * mm * mm * mm * hh;
+        double gk = s->hh_gk[h] * nn * nn * nn * nn;
+        double gl = s->hh_gl[h];
+        I[i] += gna * (v - ORC_ENA) + gk * (v - ORC_EK) + gl * (v - ORC_EL);
+        G[i] += gna + gk + gl;
+        GE[i] += gna * ORC_ENA + gk * ORC_EK + gl * ORC_EL;
     }
     for (int64_t j = s->pas_ptr[c]; j < s->pas_ptr[c + 1]; ++j) {
         int64_t p = s->pas_list[j];
         int64_t i = m->pas_cv[p] - off;
         I[i] += s->pas_g[p] * (V[i] - m->e_pas[p]);
+        G[i] += s->pas_g[p];
+        GE[i] += s->pas_g[p] * m->e_pas[p];
     }
     for (int64_t j = s->syn_ptr[c]; j < s->syn_ptr[c + 1]; ++j) {
         int64_t y = s->syn_list[j];
         int64_t i = m->syn_cv[y] - off;
         I[i] += s->syn_g[y] * (V[i] - m->syn_e[y]);
+        G[i] += s->syn_g[y];
+        GE[i] += s->syn_g[y] * m->syn_e[y];
     }
     for (int64_t j = s->st_ptr[c]; j < s->st_ptr[c + 1]; ++j) {
         int64_t y = s->st_list[j];
         int64_t i = m->stim_cv[y] - off;
-        if (m->stim_t_on[y] <= t && t < m->stim_t_on[y] + m->stim_dur[y]) I[i] -= m->stim_amp[y];
+        if (m->stim_t_on[y] <= t && t < m->stim_t_on[y] + m->stim_dur[y]) Iinj[i] += m->stim_amp[y];
     }
 
     /* 3. assemble the implicit Euler system */
     for (int64_t i = 0; i < n; ++i) {
         double cdt = s->cap[off + i] / dt;
-        d[i] = cdt;
-        b[i] = cdt * V[i] - I[i];
+        if (s->explicit_current) {
+            b[i] = cdt * V[i] - I[i] + Iinj[i];
+            d[i] = cdt;
+        } else {
+            b[i] = cdt * V[i] + GE[i] + Iinj[i];
+            d[i] = cdt + G[i];
+        }
         a[i] = 0.0;
     }
     for (int64_t i = 1; i < n; ++i) {
