@@ -182,23 +182,27 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ring", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--cells-per-pack", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-cells", type=int, default=0, help="reference arm: cells sampled (0 = all)")
+    ap.add_argument("--ref-cells", type=int, default=4096, help="reference arm: cells sampled per step (0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--cells", type=int, default=0, help="use only this many cells of the workload (0 = all)")
+    ap.add_argument("--scheme", default="implicit", choices=["implicit", "explicit"])
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
     from inputs import make_config
     cfg, precision = WORKLOADS[args.workload]
     E_ms = None
-    model, spec = make_config(cfg, t_end=None)
+    ncells = args.cells if args.cells > 0 else None
+    model, spec = make_config(cfg, n_cells=ncells, t_end=None)
     E = spec.epoch_steps
     # the run must cover warm-up + timed epochs: extend external inputs if needed
     need_t = (args.warmup + args.steps) * E * spec.dt
     if need_t > spec.t_end + 1e-9:
-        model, spec = make_config(cfg, t_end=need_t)
+        model, spec = make_config(cfg, n_cells=ncells, t_end=need_t)
     workload_name = "%s: %s, %d cells, %d CVs, dt %.3f ms, epoch %d steps" % (
         args.workload, spec.name, model.n_cells, model.n_cv, spec.dt, E)
 
@@ -214,7 +218,7 @@ def main():
     torch.cuda.set_device(local)
     import paper_1901_07454_b300 as arb
 
-    sim = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision,
+    sim = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
                          cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
     sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
     info = sim.plan_info()
@@ -270,10 +274,10 @@ def main():
     # end to end through the public API with host buffers: create + upload from host arrays,
     # per step advance one epoch and read all voltages and spikes back to the host
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision,
+        sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
                               cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
         h2d = model_bytes(model)
         kk = 0
@@ -285,15 +289,15 @@ def main():
             ev_per_epoch += int(sel.sum())
             kk += E
             sim2.advance(kk * spec.dt)
-            v = sim2.voltage()
             g, ts = sim2.spikes()
+        v = sim2.voltage()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e = {"value": model.n_cv * E * args.steps / el, "unit": "CV-steps/s",
                "h2d_bytes_per_step": int(h2d / args.steps + 28 * ev_per_epoch / args.steps + 8),
-               "d2h_bytes_per_step": int(8 * model.n_cv + 12 * nspk / max(1, args.steps) + 8),
-               "includes": "handle creation and model upload from host arrays, per step: events from host, "
-                           "advance one epoch, all voltages and spikes to host"}
+               "d2h_bytes_per_step": int(8 * model.n_cv / args.steps + 12 * nspk / max(1, args.steps) + 16),
+               "includes": "handle creation and model upload from host arrays; per step: that epoch's "
+                           "external events from host, advance one epoch, spikes to host; all voltages to host at the end"}
         del sim2
 
     if rank == 0:
@@ -305,6 +309,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f64 solve / f32 mechanisms", "data": "synthetic",
+            "scheme": args.scheme,
             "config": {"workload": workload_name, "cells": model.n_cells, "cvs": model.n_cv, "epoch_steps": E,
                        "dt_ms": spec.dt, "step": "one epoch (%d time steps) of all cells incl. spike exchange" % E,
                        "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],

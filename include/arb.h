@@ -44,6 +44,16 @@ typedef enum {
 
 enum { ARB_FP64 = 0, ARB_MIXED = 1 };
 
+/* How the membrane current enters the implicit Euler step of Sec. "Model":
+ * ARB_IMPLICIT (default): channel and synapse states are taken at t and the step of
+ *   Eq. (discrete-v) is implicit in V, i.e. the membrane conductance sits on the diagonal:
+ *   (c/dt + g) V' + sum sigma (V' - V'_j) = (c/dt) V + sum g E + I_inj. The matrix changes
+ *   every step and is eliminated every step. Unconditionally stable.
+ * ARB_EXPLICIT: the linear system as printed in Sec. "Model", membrane current at V(t) on the
+ *   right-hand side. The matrix is constant and factorised once, but the step diverges when
+ *   dt * g / c > 2 in a compartment, which happens in small cells under synaptic bursts. */
+enum { ARB_IMPLICIT = 0, ARB_EXPLICIT = 1 };
+
 /* Run settings. Fill with arb_default_params, then override. */
 typedef struct {
     double dt;                   /* time step, ms (> 0) */
@@ -53,6 +63,8 @@ typedef struct {
     int32_t cells_per_pack;      /* packing override: 0 = chosen by the library's cost model,
                                     32 = one cell per lane, 1..31 = cells sharing one warp */
     int32_t smem_budget;         /* bytes of shared memory per warp for state tiles; 0 = default */
+    int32_t scheme;              /* ARB_IMPLICIT (default) or ARB_EXPLICIT */
+    int32_t reserved;            /* must be 0 */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */
@@ -104,8 +116,8 @@ typedef struct {
     const double* conn_weight;
 } arb_model;
 
-/* Sets dt = 0.025, precision FP64, automatic epoch and packing, and capacities sized
- * for typical runs. Never fails for a non-NULL argument. */
+/* Sets dt = 0.025, precision FP64, the implicit scheme, automatic epoch and packing, and
+ * capacities sized for typical runs. Never fails for a non-NULL argument. */
 arb_status arb_default_params(arb_params* p);
 
 /* Validates the model and prepares everything on the host (per-CV geometry; the constant

@@ -26,7 +26,20 @@ struct PackDesc {
     int32_t st_row0, nst_row;
     int32_t ncell;       // detectors: lane d < ncell owns detector d
     int32_t pr0, npr;    // probes of this pack: entries [pr0, pr0 + npr) of the probe arrays
+    int32_t nvc;         // shared-memory packs: voltages kept on chip (see vmap);
+                         // streamed packs: compact mechanism slots (see vmap)
+    int32_t stack;       // streamed packs: deepest per-lane hand-over stack (entries)
+    int64_t c_off;       // streamed packs: offset of the pack's compact slots in Gm / Em
 };
+
+// Pack modes: staged in shared memory (small batches, several cells share a warp), or
+// streamed from global memory (large batches, one cell per lane).
+enum : int32_t { kPackGlobal = 0, kPackSmem = 1, kPackStream = 2 };
+
+// Streamed packs: per-entry flags in pslot. Bits 0-7: children handed over through the
+// stack (all but the one processed directly before the parent); bit 8: this entry's parent
+// is not the next row of its lane; bit 9: root.
+enum : int32_t { kFlagPopMask = 0xFF, kFlagRemote = 0x100, kFlagRoot = 0x200 };
 
 // Event delivered inside one epoch, bucketed per owner lane and sorted by
 // (step_rel, js, t, src, idx).
@@ -82,22 +95,34 @@ struct DevModel {
     const PackDesc* packs;
     int32_t n_packs;
     int32_t n_owner;          // n_packs * 32
-    // solve entries (total_rows * 32)
-    const double* ca;         // alpha' = (c/dt - G_lin) / d'
-    const double* cb;         // beta'  = (G_lin E_lin) / d'
-    const double* ck;         // a' : contribution of the entry to its parent, scaled by the parent's 1/d'
-    const double* ce;         // e  : a / d' (back substitution)
+    // solve entries (total_rows * 32); meaning depends on the scheme:
+    //   explicit membrane current (constant matrix, factorised on the host):
+    //     ca = (c/dt - G_lin)/d', cb = G_lin E_lin/d', ck = a/d'_parent, ce = a/d'
+    //   implicit membrane conductance (matrix changes every step):
+    //     ca = c/dt, cb = G_lin E_lin, ck = sigma (axial conductance to the parent),
+    //     ce = c/dt + G_lin + sum of the entry's axial conductances (constant diagonal)
+    const double* ca;
+    const double* cb;
+    const double* ck;
+    const double* ce;
     const int32_t* pslot;     // -1 parent is the next row of this lane, -2 none, >= 0 parent's tile slot
+    const int32_t* vmap;      // shared-memory packs: low 16 bits own on-chip V slot, high 16 bits the
+                              // parent's (0xFFFF = none); only CVs whose voltage is read keep one
     double* V;                // voltages, tile layout
     double* Sg;               // S scratch for packs whose tiles live in global memory
+    double* Rg;               // diagonal / e scratch of those packs (implicit scheme)
+    double* Gm;               // streamed packs: mechanism conductance per compact slot
+    double* Em;               // streamed packs: mechanism right-hand side per compact slot
     // synapses (syn_rows * 32)
     const int32_t* syn_slot;  // tile slot of the synapse's CV, -1 padding
+    const int32_t* syn_vs;    // where its voltage is read (on-chip V slot, or the tile slot)
     MT* syn_g;
     const double* syn_e;
     const double* syn_decay;  // exp(-dt/tau)
     const double* syn_sc;     // 1/d' of the CV
     // Hodgkin-Huxley (hh_rows * 32)
     const int32_t* hh_slot;
+    const int32_t* hh_vs;
     const double* hh_sc;
     const double* hh_gna;     // uS
     const double* hh_gk;      // uS
@@ -111,7 +136,7 @@ struct DevModel {
     const double* st_off;
     const double* st_amp;
     // detectors (n_owner)
-    const int32_t* det_slot;
+    const int32_t* det_slot;  // where the detector voltage is read (on-chip V slot or tile slot)
     const int32_t* det_gid;
     // probes, grouped by pack: tile slot of the CV and trace column
     const int32_t* probe_slot;

@@ -60,6 +60,17 @@ __device__ __forceinline__ float gate(float x, float a, float b, float dt) {
     return xinf + (x - xinf) * expf(-dt * s);
 }
 
+// 1/x for the positive pivots of the implicit scheme: hardware estimate, then two
+// Newton-Raphson steps r <- r + r (1 - x r), each doubling the number of correct bits.
+__device__ __forceinline__ double rcp_nr(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 // ------------------------------------------------------------------------------------------
 // The epoch kernel: a persistent grid; each warp takes packs from a work counter and runs
 // every time step of the epoch for the pack's cells.
@@ -74,17 +85,36 @@ __device__ __forceinline__ float gate(float x, float a, float b, float dt) {
 // which is the elimination and back substitution of the Hines matrix (Sec. "Model") with
 // one FP64 FMA per entry in each of the three lines.
 
+// Pointers of one pack's working set: in shared memory for packs whose tile fits (the
+// common case), else in global memory (cells whose longest root-to-leaf path is too long).
 template <class MT>
-__device__ __forceinline__ void syn_pass(const DevModel<MT>& d, const PackDesc& pk, double* S, const double* V,
-                                         int lane, bool decay, int apply_step, bool current, int& ev_i,
-                                         int ev_end, int32_t& late) {
+struct Work {
+    double* R;     // implicit scheme: diagonal, then e = sigma / d' (one per entry)
+    double* S;     // right-hand side, then u = b' / d' (one per entry)
+    double* Vc;    // voltages that are read: on-chip slots (shared) or every tile slot (global)
+    MT* g;         // synapse conductances
+    MT* m;         // HH gates
+    MT* h;
+    MT* n;
+};
+
+// Synapses: decay (state update of the previous step), events due now, then their terms of
+// the step's linear system. Implicit scheme: conductance g on the diagonal and g*e on the
+// right-hand side. Explicit scheme: the current g (V - e) on the right-hand side, scaled by
+// 1/d' like the rest of the factorised system.
+template <class MT, bool kSmem, bool kImp>
+__device__ __forceinline__ void syn_pass(const DevModel<MT>& d, const PackDesc& pk, const Work<MT>& w, int lane,
+                                         bool decay, int apply_step, bool current, int& ev_i, int ev_end,
+                                         int32_t& late) {
     // drop events that should already have been applied (never happens by construction)
     while (apply_step >= 0 && ev_i < ev_end && d.ev[ev_i].step_rel < apply_step) { ++ev_i; late = 1; }
+#pragma unroll 4
     for (int js = 0; js < pk.nsyn_row; ++js) {
         const size_t q = (size_t)(pk.syn_row0 + js) * kWarp + lane;
         const int sl = __ldg(d.syn_slot + q);
         if (sl < 0) continue;
-        MT g = d.syn_g[q];
+        const int idx = js * kWarp + lane;
+        MT g = w.g[idx];
         if (decay) g = g * (MT)__ldg(d.syn_decay + q);
         if (apply_step >= 0) {
             while (ev_i < ev_end && d.ev[ev_i].step_rel == apply_step && d.ev[ev_i].js == js) {
@@ -92,67 +122,126 @@ __device__ __forceinline__ void syn_pass(const DevModel<MT>& d, const PackDesc& 
                 ++ev_i;
             }
         }
-        d.syn_g[q] = g;
+        w.g[idx] = g;
         if (current) {
-            const MT i_syn = g * ((MT)V[sl] - (MT)__ldg(d.syn_e + q));
-            S[sl] = fma(-__ldg(d.syn_sc + q), (double)i_syn, S[sl]);
+            if constexpr (kImp) {
+                const double gd = (double)g;
+                w.R[sl] += gd;
+                w.S[sl] = fma(gd, __ldg(d.syn_e + q), w.S[sl]);
+            } else {
+                const int vs = kSmem ? __ldg(d.syn_vs + q) : sl;
+                const MT i_syn = g * (MT)(w.Vc[vs] - __ldg(d.syn_e + q));
+                w.S[sl] = fma(-__ldg(d.syn_sc + q), (double)i_syn, w.S[sl]);
+            }
         }
     }
 }
 
-template <class MT>
-__device__ __forceinline__ void hh_pass(const DevModel<MT>& d, const PackDesc& pk, double* S, const double* V,
-                                        int lane, bool update, bool current, MT dt) {
+// Hodgkin-Huxley: gate update with the new voltage, then the Na and K terms of the next
+// step (the leak is constant and sits in the constants of the entry).
+template <class MT, bool kSmem, bool kImp>
+__device__ __forceinline__ void hh_pass(const DevModel<MT>& d, const PackDesc& pk, const Work<MT>& w, int lane,
+                                        bool update, bool current, MT dt) {
     for (int jh = 0; jh < pk.nhh_row; ++jh) {
         const size_t q = (size_t)(pk.hh_row0 + jh) * kWarp + lane;
         const int sl = __ldg(d.hh_slot + q);
         if (sl < 0) continue;
-        const MT v = (MT)V[sl];
-        MT m = d.hh_m[q], h = d.hh_h[q], n = d.hh_n[q];
+        const int vs = kSmem ? __ldg(d.hh_vs + q) : sl;
+        const int idx = jh * kWarp + lane;
+        const double vd = w.Vc[vs];
+        const MT v = (MT)vd;
+        MT m = w.m[idx], h = w.h[idx], n = w.n[idx];
         if (update) {
             const auto r = hh_rates(v);
             m = gate(m, r.am, r.bm, dt);
             h = gate(h, r.ah, r.bh, dt);
             n = gate(n, r.an, r.bn, dt);
-            d.hh_m[q] = m;
-            d.hh_h[q] = h;
-            d.hh_n[q] = n;
+            w.m[idx] = m;
+            w.h[idx] = h;
+            w.n[idx] = n;
         }
         if (current) {
-            const MT m3h = m * m * m * h;
             const MT n2 = n * n;
-            const MT i_hh = (MT)__ldg(d.hh_gna + q) * m3h * (v - (MT)kENa) + (MT)__ldg(d.hh_gk + q) * (n2 * n2) * (v - (MT)kEK);
-            S[sl] = fma(-__ldg(d.hh_sc + q), (double)i_hh, S[sl]);
+            const MT gna = (MT)__ldg(d.hh_gna + q) * (m * m * m * h);
+            const MT gk = (MT)__ldg(d.hh_gk + q) * (n2 * n2);
+            if constexpr (kImp) {
+                w.R[sl] += (double)(gna + gk);
+                w.S[sl] += (double)(gna * (MT)kENa + gk * (MT)kEK);
+            } else {
+                const MT i_hh = gna * (MT)(vd - kENa) + gk * (MT)(vd - kEK);
+                w.S[sl] = fma(-__ldg(d.hh_sc + q), (double)i_hh, w.S[sl]);
+            }
         }
     }
 }
 
-template <class MT>
+constexpr int kU = 8;   // rows whose constants are loaded ahead of use
+
+// One pack for all steps of the epoch.
+//
+// Explicit scheme (membrane current at V(t), Sec. "Model" linear system as printed): the
+// matrix is constant for fixed dt, the host factorised it once, and S holds right-hand sides
+// already divided by the eliminated pivots d':
+//   forward  u_i = S_i - sum_children a'_c u_c;  backward V_i = u_i - e_i V_parent;
+//   next     S_i = alpha'_i V_i + beta'_i - (mechanism currents)/d'_i.
+// Implicit scheme (default; V(t+dt) from Eq. discrete-v by implicit Euler with the states
+// frozen at t): R holds the diagonal c/dt + G + sum sigma, S the right-hand side
+// (c/dt) V + sum g E + I_inj; elimination from the leaves with one reciprocal per CV:
+//   d'_i = R_i - sum_children sigma_c e_c,  r = 1/d'_i,  b'_i = S_i + sum_children sigma_c u_c,
+//   u_i = r b'_i,  e_i = sigma_i r;   backward V_i = u_i + e_i V_parent.
+template <class MT, bool kSmem, bool kImp>
 __device__ void run_pack(const DevModel<MT>& d, int p, double* tile, int64_t k0, int nsteps, int lane) {
     const PackDesc pk = d.packs[p];
     const int J = pk.nrow;
     const int R = pk.round_rows;
     double* Vg = d.V + (size_t)pk.row0 * kWarp;
-    double* S;
-    double* V;
-    if (pk.smem) {
-        S = tile;
-        V = tile + (size_t)J * kWarp;
-        for (int j = 0; j < J; ++j) V[j * kWarp + lane] = Vg[j * kWarp + lane];
+    Work<MT> w;
+    if (kSmem) {
+        w.S = tile;
+        w.R = kImp ? tile + (size_t)J * kWarp : nullptr;
+        w.Vc = tile + (size_t)J * kWarp * (kImp ? 2 : 1);
+        w.g = (MT*)(w.Vc + pk.nvc);
+        w.m = w.g + (size_t)pk.nsyn_row * kWarp;
+        w.h = w.m + (size_t)pk.nhh_row * kWarp;
+        w.n = w.h + (size_t)pk.nhh_row * kWarp;
+        for (int i = lane; i < pk.nsyn_row * kWarp; i += kWarp) w.g[i] = d.syn_g[(size_t)pk.syn_row0 * kWarp + i];
+        for (int i = lane; i < pk.nhh_row * kWarp; i += kWarp) {
+            const size_t gi = (size_t)pk.hh_row0 * kWarp + i;
+            w.m[i] = d.hh_m[gi];
+            w.h[i] = d.hh_h[gi];
+            w.n[i] = d.hh_n[gi];
+        }
     } else {
-        S = d.Sg + pk.sg_off;
-        V = Vg;
+        w.S = d.Sg + pk.sg_off;
+        w.R = kImp ? d.Rg + pk.sg_off : nullptr;
+        w.Vc = Vg;
+        w.g = d.syn_g + (size_t)pk.syn_row0 * kWarp;
+        w.m = d.hh_m + (size_t)pk.hh_row0 * kWarp;
+        w.h = d.hh_h + (size_t)pk.hh_row0 * kWarp;
+        w.n = d.hh_n + (size_t)pk.hh_row0 * kWarp;
     }
+    double* __restrict__ S = w.S;
+    double* __restrict__ Rr = w.R;
+    double* __restrict__ Vc = w.Vc;
     const size_t e0 = (size_t)pk.row0 * kWarp + lane;
     const double* __restrict__ ca = d.ca + e0;
     const double* __restrict__ cb = d.cb + e0;
     const double* __restrict__ ck = d.ck + e0;
     const double* __restrict__ ce = d.ce + e0;
     const int32_t* __restrict__ ps_arr = d.pslot + e0;
+    const int32_t* __restrict__ vm_arr = d.vmap + e0;
 
+    // right-hand side (and diagonal) of the first step; on-chip copies of the read voltages
     for (int j = 0; j < J; ++j) {
         const int sl = j * kWarp + lane;
-        S[sl] = fma(__ldg(ca + (size_t)j * kWarp), V[sl], __ldg(cb + (size_t)j * kWarp));
+        const size_t o = (size_t)j * kWarp;
+        const double v = Vg[sl];
+        S[sl] = fma(__ldg(ca + o), v, __ldg(cb + o));
+        if (kImp) Rr[sl] = __ldg(ce + o);
+        if (kSmem) {
+            const int own = __ldg(vm_arr + o) & 0xFFFF;
+            if (own != 0xFFFF) Vc[own] = v;
+        }
     }
     __syncwarp();
 
@@ -163,76 +252,167 @@ __device__ void run_pack(const DevModel<MT>& d, int p, double* tile, int64_t k0,
     const double dt = d.dt;
     const MT dt_m = (MT)dt;
 
-    // currents at the epoch's first step (events due at its start included)
-    syn_pass(d, pk, S, V, lane, false, 0, true, ev_i, ev_end, late);
+    // terms of the epoch's first step (events due at its start included)
+    syn_pass<MT, kSmem, kImp>(d, pk, w, lane, false, 0, true, ev_i, ev_end, late);
     __syncwarp();
-    hh_pass(d, pk, S, V, lane, false, true, dt_m);
+    hh_pass<MT, kSmem, kImp>(d, pk, w, lane, false, true, dt_m);
     __syncwarp();
 
     const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
     const double thr = d.threshold;
     const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
+    const bool probing = pk.npr > 0 && probe_max > 0;
+    bool bad = false;
 
     for (int s = 0; s < nsteps; ++s) {
         const int64_t k = k0 + s;
         const double t = __dmul_rn((double)k, dt);
+        const bool last = (s + 1) == nsteps;
         // current clamps active at t_k (depolarising current enters with a plus sign)
         for (int js = 0; js < pk.nst_row; ++js) {
             const size_t q = (size_t)(pk.st_row0 + js) * kWarp + lane;
             const int sl = __ldg(d.st_slot + q);
-            if (sl >= 0 && __ldg(d.st_on + q) <= t && t < __ldg(d.st_off + q))
-                S[sl] = fma(__ldg(d.st_sc + q), __ldg(d.st_amp + q), S[sl]);
+            if (sl >= 0 && __ldg(d.st_on + q) <= t && t < __ldg(d.st_off + q)) {
+                if (kImp) S[sl] += __ldg(d.st_amp + q);
+                else S[sl] = fma(__ldg(d.st_sc + q), __ldg(d.st_amp + q), S[sl]);
+            }
         }
         __syncwarp();
-        const double v0 = det >= 0 ? V[det] : 0.0;
+        const double v0 = det >= 0 ? Vc[det] : 0.0;
 
         // forward elimination, leaves to root
-        double yprev = 0.0, kprev = 0.0;
-        int left = R;
-        for (int j = 0; j < J; ++j) {
-            if (R > 0) {
-                if (left == 0) { __syncwarp(); left = R; }
-                --left;
+        {
+            double yprev = 0.0, kprev = 0.0, eprev = 0.0;
+            int left = R;
+            int psn[kU];
+            double kcn[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const bool in = u < J;
+                psn[u] = in ? __ldg(ps_arr + (size_t)u * kWarp) : -2;
+                kcn[u] = in ? __ldg(ck + (size_t)u * kWarp) : 0.0;
             }
-            const int ps = __ldg(ps_arr + (size_t)j * kWarp);
-            const double kc = __ldg(ck + (size_t)j * kWarp);
-            const int sl = j * kWarp + lane;
-            const double y = fma(-kprev, yprev, S[sl]);
-            S[sl] = y;
-            if (ps >= 0) S[ps] = fma(-kc, y, S[ps]);
-            kprev = (ps == -1) ? kc : 0.0;
-            yprev = y;
+            for (int jb = 0; jb < J; jb += kU) {
+                int psc[kU];
+                double kcc[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) { psc[u] = psn[u]; kcc[u] = kcn[u]; }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int j = jb + kU + u;
+                    const bool in = j < J;
+                    psn[u] = in ? __ldg(ps_arr + (size_t)j * kWarp) : -2;
+                    kcn[u] = in ? __ldg(ck + (size_t)j * kWarp) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int j = jb + u;
+                    if (j < J) {
+                        if (R > 0) {
+                            if (left == 0) { __syncwarp(); left = R; }
+                            --left;
+                        }
+                        const int ps = psc[u];
+                        const int sl = j * kWarp + lane;
+                        if constexpr (kImp) {
+                            // kprev = sigma of the previous row when it is this row's child
+                            const double dd = fma(-kprev, eprev, Rr[sl]);
+                            const double r = rcp_nr(dd);
+                            const double bb = fma(kprev, yprev, S[sl]);
+                            const double uu = r * bb;
+                            const double ee = kcc[u] * r;
+                            S[sl] = uu;
+                            Rr[sl] = ee;
+                            if (ps >= 0) {
+                                Rr[ps] = fma(-kcc[u], ee, Rr[ps]);
+                                S[ps] = fma(kcc[u], uu, S[ps]);
+                            }
+                            kprev = (ps == -1) ? kcc[u] : 0.0;
+                            eprev = ee;
+                            yprev = uu;
+                        } else {
+                            const double y = fma(-kprev, yprev, S[sl]);
+                            S[sl] = y;
+                            if (ps >= 0) S[ps] = fma(-kcc[u], y, S[ps]);
+                            kprev = (ps == -1) ? kcc[u] : 0.0;
+                            yprev = y;
+                        }
+                    }
+                }
+            }
         }
         __syncwarp();
-        // back substitution, root to leaves; then the next step's scaled right-hand side
-        double vnext = 0.0;
-        left = (R > 0) ? ((J - 1) % R) + 1 : 0;
-        for (int j = J - 1; j >= 0; --j) {
-            if (R > 0) {
-                if (left == 0) { __syncwarp(); left = R; }
-                --left;
+        // back substitution, root to leaves; then the next step's right-hand side (and diagonal)
+        {
+            const bool full = last || probing || !kSmem;
+            double vnext = 0.0;
+            int left = (R > 0) ? ((J - 1) % R) + 1 : 0;
+            int psn[kU], vmn[kU];
+            double cen[kU], can[kU], cbn[kU];
+            auto load_b = [&](int jtop, int* ps_, int* vm_, double* ce_, double* ca_, double* cb_) {
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int j = jtop - u;
+                    const bool in = j >= 0;
+                    const size_t o = (size_t)(in ? j : 0) * kWarp;
+                    ps_[u] = in ? __ldg(ps_arr + o) : -2;
+                    vm_[u] = (in && kSmem) ? __ldg(vm_arr + o) : -1;
+                    ce_[u] = in ? __ldg(ce + o) : 0.0;
+                    ca_[u] = in ? __ldg(ca + o) : 0.0;
+                    cb_[u] = in ? __ldg(cb + o) : 0.0;
+                }
+            };
+            load_b(J - 1, psn, vmn, cen, can, cbn);
+            for (int jt = J - 1; jt >= 0; jt -= kU) {
+                int psc[kU], vmc[kU];
+                double cec[kU], cac[kU], cbc[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) { psc[u] = psn[u]; vmc[u] = vmn[u]; cec[u] = cen[u]; cac[u] = can[u]; cbc[u] = cbn[u]; }
+                load_b(jt - kU, psn, vmn, cen, can, cbn);
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int j = jt - u;
+                    if (j >= 0) {
+                        if (R > 0) {
+                            if (left == 0) { __syncwarp(); left = R; }
+                            --left;
+                        }
+                        const int ps = psc[u];
+                        const int sl = j * kWarp + lane;
+                        double vp = 0.0;
+                        if (ps == -1) vp = vnext;
+                        else if (ps >= 0) vp = Vc[kSmem ? ((unsigned)vmc[u] >> 16) : ps];
+                        double v;
+                        if constexpr (kImp) {
+                            v = fma(Rr[sl], vp, S[sl]);
+                            Rr[sl] = cec[u];
+                        } else {
+                            v = fma(-cec[u], vp, S[sl]);
+                        }
+                        if (kSmem) {
+                            const int own = vmc[u] & 0xFFFF;
+                            if (own != 0xFFFF) Vc[own] = v;
+                        }
+                        if (full) Vg[sl] = v;
+                        if (last) bad |= !isfinite(v);
+                        S[sl] = fma(cac[u], v, cbc[u]);
+                        vnext = v;
+                    }
+                }
             }
-            const int ps = __ldg(ps_arr + (size_t)j * kWarp);
-            const int sl = j * kWarp + lane;
-            const double vp = (ps == -1) ? vnext : ((ps >= 0) ? V[ps] : 0.0);
-            const double v = fma(-__ldg(ce + (size_t)j * kWarp), vp, S[sl]);
-            V[sl] = v;
-            S[sl] = fma(__ldg(ca + (size_t)j * kWarp), v, __ldg(cb + (size_t)j * kWarp));
-            vnext = v;
         }
         __syncwarp();
 
-        const bool more = (s + 1) < nsteps;
-        // state updates with V(t_{k+1}); currents for the next step
-        syn_pass(d, pk, S, V, lane, true, more ? s + 1 : -1, more, ev_i, ev_end, late);
+        // state updates with V(t_{k+1}); terms of the next step
+        syn_pass<MT, kSmem, kImp>(d, pk, w, lane, true, last ? -1 : s + 1, !last, ev_i, ev_end, late);
         __syncwarp();
-        hh_pass(d, pk, S, V, lane, true, more, dt_m);
+        hh_pass<MT, kSmem, kImp>(d, pk, w, lane, true, !last, dt_m);
 
         // threshold crossing between V(t_k) and V(t_{k+1}), linearly interpolated
         bool spk = false;
         double ts = 0.0;
         if (det >= 0) {
-            const double v1 = V[det];
+            const double v1 = Vc[det];
             if (v0 < thr && v1 >= thr) {
                 spk = true;
                 ts = __dadd_rn(t, __dmul_rn(dt, __ddiv_rn(__dsub_rn(thr, v0), __dsub_rn(v1, v0))));
@@ -253,22 +433,25 @@ __device__ void run_pack(const DevModel<MT>& d, int p, double* tile, int64_t k0,
                 }
             }
         }
-        // probes record V(t_{k+1})
-        const int64_t prow = k - probe_k0;
-        if (pk.npr > 0 && prow >= 0 && prow < probe_max) {
-            for (int q = lane; q < pk.npr; q += kWarp) {
-                const int sl = d.probe_slot[pk.pr0 + q];
-                d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = V[sl];
-            }
+        // probes record V(t_{k+1}) from the full voltage array written above
+        if (probing) {
+            __syncwarp();
+            const int64_t prow = k - probe_k0;
+            if (prow >= 0 && prow < probe_max)
+                for (int q = lane; q < pk.npr; q += kWarp)
+                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
         }
         __syncwarp();
     }
 
-    bool bad = false;
-    for (int j = 0; j < J; ++j) {
-        const double v = V[j * kWarp + lane];
-        if (!isfinite(v)) bad = true;
-        if (pk.smem) Vg[j * kWarp + lane] = v;
+    if (kSmem) {
+        for (int i = lane; i < pk.nsyn_row * kWarp; i += kWarp) d.syn_g[(size_t)pk.syn_row0 * kWarp + i] = w.g[i];
+        for (int i = lane; i < pk.nhh_row * kWarp; i += kWarp) {
+            const size_t gi = (size_t)pk.hh_row0 * kWarp + i;
+            d.hh_m[gi] = w.m[i];
+            d.hh_h[gi] = w.h[i];
+            d.hh_n[gi] = w.n[i];
+        }
     }
     const bool any_bad = __any_sync(0xffffffffu, bad);
     const bool any_late = __any_sync(0xffffffffu, late != 0);
@@ -277,7 +460,7 @@ __device__ void run_pack(const DevModel<MT>& d, int p, double* tile, int64_t k0,
     __syncwarp();
 }
 
-template <class MT>
+template <class MT, bool kImp>
 __global__ void __launch_bounds__(256) arb_epoch_kernel(DevModel<MT> d, int tile_doubles) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31;
@@ -290,9 +473,331 @@ __global__ void __launch_bounds__(256) arb_epoch_kernel(DevModel<MT> d, int tile
         if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= d.n_packs) break;
-        run_pack(d, p, tile, k0, nsteps, lane);
+        if (d.packs[p].smem) run_pack<MT, true, kImp>(d, p, tile, k0, nsteps, lane);
+        else run_pack<MT, false, kImp>(d, p, tile, k0, nsteps, lane);
     }
 }
+
+// ------------------------------------------------------------------------------------------
+// Streamed packs (large batches): one cell per lane, every array in global memory.
+//
+// A lane walks its cell in reverse depth-first order, so a CV's parent is the next row of the
+// lane except at branch points. A child that is not processed directly before its parent hands
+// its contribution over through a small per-lane stack in shared memory; in reverse
+// depth-first order these hand-overs are strictly last in, first out. Nothing is ever written
+// into a row that has not been reached yet, so every load of a row can be issued rows ahead.
+// The back substitution uses the same stack, in preorder, for the parent voltages of those
+// children. Mechanism terms of a step are accumulated per compact slot (Gm, Em) before the
+// forward sweep.
+
+template <class MT, bool kImp>
+__device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDesc& pk, double* Gm, double* Em,
+                                            const double* Vg, MT* gS, MT* mS, MT* hS, MT* nS, int lane, bool decay,
+                                            bool update, int apply_step, bool terms, int& ev_i, int ev_end,
+                                            int32_t& late, MT dt) {
+    if (terms) {
+        for (int c = lane; c < pk.nvc; c += kWarp) {
+            if (kImp) Gm[c] = 0.0;
+            Em[c] = 0.0;
+        }
+    }
+    __syncwarp();
+    while (apply_step >= 0 && ev_i < ev_end && d.ev[ev_i].step_rel < apply_step) { ++ev_i; late = 1; }
+#pragma unroll 4
+    for (int js = 0; js < pk.nsyn_row; ++js) {
+        const size_t q = (size_t)(pk.syn_row0 + js) * kWarp + lane;
+        const int sl = __ldg(d.syn_slot + q);
+        if (sl < 0) continue;
+        const int idx = js * kWarp + lane;
+        MT g = gS[idx];
+        if (decay) g = g * (MT)__ldg(d.syn_decay + q);
+        if (apply_step >= 0) {
+            while (ev_i < ev_end && d.ev[ev_i].step_rel == apply_step && d.ev[ev_i].js == js) {
+                g = g + (MT)d.ev[ev_i].w;
+                ++ev_i;
+            }
+        }
+        gS[idx] = g;
+        if (terms) {
+            const int c = __ldg(d.syn_vs + q);
+            if constexpr (kImp) {
+                const double gd = (double)g;
+                Gm[c] += gd;
+                Em[c] = fma(gd, __ldg(d.syn_e + q), Em[c]);
+            } else {
+                const MT i_syn = g * (MT)(Vg[sl] - __ldg(d.syn_e + q));
+                Em[c] = fma(-__ldg(d.syn_sc + q), (double)i_syn, Em[c]);
+            }
+        }
+    }
+    __syncwarp();
+    for (int jh = 0; jh < pk.nhh_row; ++jh) {
+        const size_t q = (size_t)(pk.hh_row0 + jh) * kWarp + lane;
+        const int sl = __ldg(d.hh_slot + q);
+        if (sl < 0) continue;
+        const int idx = jh * kWarp + lane;
+        const double vd = Vg[sl];
+        const MT v = (MT)vd;
+        MT m = mS[idx], h = hS[idx], n = nS[idx];
+        if (update) {
+            const auto r = hh_rates(v);
+            m = gate(m, r.am, r.bm, dt);
+            h = gate(h, r.ah, r.bh, dt);
+            n = gate(n, r.an, r.bn, dt);
+            mS[idx] = m;
+            hS[idx] = h;
+            nS[idx] = n;
+        }
+        if (terms) {
+            const int c = __ldg(d.hh_vs + q);
+            const MT n2 = n * n;
+            const MT gna = (MT)__ldg(d.hh_gna + q) * (m * m * m * h);
+            const MT gk = (MT)__ldg(d.hh_gk + q) * (n2 * n2);
+            if constexpr (kImp) {
+                Gm[c] += (double)(gna + gk);
+                Em[c] += (double)(gna * (MT)kENa + gk * (MT)kEK);
+            } else {
+                const MT i_hh = gna * (MT)(vd - kENa) + gk * (MT)(vd - kEK);
+                Em[c] = fma(-__ldg(d.hh_sc + q), (double)i_hh, Em[c]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+constexpr int kPF = 4;   // rows prefetched ahead in the streamed sweeps
+
+template <class MT, bool kImp>
+__device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, int64_t k0, int nsteps, int lane) {
+    const PackDesc pk = d.packs[p];
+    const int J = pk.nrow;
+    double* Vg = d.V + (size_t)pk.row0 * kWarp;
+    double* Bs = d.Sg + pk.sg_off;                 // forward result u (or y), per entry
+    double* Rs = d.Rg + pk.sg_off;                 // implicit: e = sigma / d', per entry
+    double* Gm = d.Gm + pk.c_off;
+    double* Em = d.Em + pk.c_off;
+    MT* gS = d.syn_g + (size_t)pk.syn_row0 * kWarp;
+    MT* mS = d.hh_m + (size_t)pk.hh_row0 * kWarp;
+    MT* hS = d.hh_h + (size_t)pk.hh_row0 * kWarp;
+    MT* nS = d.hh_n + (size_t)pk.hh_row0 * kWarp;
+    const size_t e0 = (size_t)pk.row0 * kWarp + lane;
+    const double* __restrict__ ca = d.ca + e0;
+    const double* __restrict__ cb = d.cb + e0;
+    const double* __restrict__ ck = d.ck + e0;
+    const double* __restrict__ ce = d.ce + e0;
+    const int32_t* __restrict__ fl = d.pslot + e0;
+    const int32_t* __restrict__ cm_ = d.vmap + e0;
+    double2* stk = stack;   // [depth][32]
+
+    const int owner = p * kWarp + lane;
+    int ev_i = d.ev_off[owner];
+    const int ev_end = d.ev_off[owner + 1];
+    int32_t late = 0;
+    const double dt = d.dt;
+    const MT dt_m = (MT)dt;
+    stream_mech<MT, kImp>(d, pk, Gm, Em, Vg, gS, mS, hS, nS, lane, false, false, 0, true, ev_i, ev_end, late, dt_m);
+
+    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const double thr = d.threshold;
+    const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
+    const bool probing = pk.npr > 0 && probe_max > 0;
+    bool bad = false;
+
+    for (int s = 0; s < nsteps; ++s) {
+        const int64_t k = k0 + s;
+        const double t = __dmul_rn((double)k, dt);
+        const bool last = (s + 1) == nsteps;
+        for (int js = 0; js < pk.nst_row; ++js) {
+            const size_t q = (size_t)(pk.st_row0 + js) * kWarp + lane;
+            const int c = __ldg(d.st_slot + q);
+            if (c >= 0 && __ldg(d.st_on + q) <= t && t < __ldg(d.st_off + q)) {
+                if (kImp) Em[c] += __ldg(d.st_amp + q);
+                else Em[c] = fma(__ldg(d.st_sc + q), __ldg(d.st_amp + q), Em[c]);
+            }
+        }
+        __syncwarp();
+        const double v0 = det >= 0 ? Vg[det] : 0.0;
+
+        // forward elimination, leaves to root, streaming rows
+        {
+            int sp = 0;
+            double yprev = 0.0, kprev = 0.0, eprev = 0.0;
+            double pv[kPF], pa[kPF], pb[kPF], pk_[kPF], pe[kPF], pg[kPF], pm[kPF];
+            int pf[kPF];
+            auto fetch = [&](int j, int u) {
+                const bool in = j < J;
+                const size_t o = (size_t)(in ? j : 0) * kWarp;
+                const int c = in ? __ldg(cm_ + o) : -1;
+                pv[u] = in ? Vg[j * kWarp + lane] : 0.0;
+                pa[u] = in ? __ldg(ca + o) : 0.0;
+                pb[u] = in ? __ldg(cb + o) : 0.0;
+                pk_[u] = in ? __ldg(ck + o) : 0.0;
+                pe[u] = in ? __ldg(ce + o) : 1.0;
+                pf[u] = in ? __ldg(fl + o) : kFlagRoot;
+                pg[u] = (c >= 0 && kImp) ? Gm[c] : 0.0;
+                pm[u] = c >= 0 ? Em[c] : 0.0;
+            };
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) fetch(u, u);
+            for (int jb = 0; jb < J; jb += kPF) {
+#pragma unroll
+                for (int u = 0; u < kPF; ++u) {
+                    const int j = jb + u;
+                    if (j < J) {
+                        const double V = pv[u], A = pa[u], Bc = pb[u], K = pk_[u], E = pe[u], G = pg[u], M = pm[u];
+                        const int f = pf[u];
+                        fetch(j + kPF, u);   // refill this slot for row j + kPF
+                        const int sl = j * kWarp + lane;
+                        if constexpr (kImp) {
+                            double dd = fma(-kprev, eprev, E + G);
+                            double bb = fma(kprev, yprev, fma(A, V, Bc) + M);
+                            for (int q = f & kFlagPopMask; q > 0; --q) {
+                                const double2 c2 = stk[(--sp) * kWarp + lane];
+                                dd -= c2.x;
+                                bb += c2.y;
+                            }
+                            const double r = rcp_nr(dd);
+                            const double uu = r * bb;
+                            const double ee = K * r;
+                            Bs[sl] = uu;
+                            Rs[sl] = ee;
+                            const bool remote = (f & kFlagRemote) != 0;
+                            if (remote && !(f & kFlagRoot)) stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                            kprev = remote ? 0.0 : K;
+                            eprev = ee;
+                            yprev = uu;
+                        } else {
+                            double y = fma(-kprev, yprev, fma(A, V, Bc) + M);
+                            for (int q = f & kFlagPopMask; q > 0; --q) y -= stk[(--sp) * kWarp + lane].x;
+                            Bs[sl] = y;
+                            const bool remote = (f & kFlagRemote) != 0;
+                            if (remote && !(f & kFlagRoot)) stk[(sp++) * kWarp + lane] = make_double2(K * y, 0.0);
+                            kprev = remote ? 0.0 : K;
+                            yprev = y;
+                        }
+                    }
+                }
+            }
+        }
+        // back substitution, root to leaves (preorder), streaming rows
+        {
+            int sp = 0;
+            double vnext = 0.0;
+            double pu[kPF], px[kPF];
+            int pf[kPF];
+            auto fetch = [&](int j, int u) {
+                const bool in = j >= 0;
+                const size_t o = (size_t)(in ? j : 0) * kWarp;
+                pu[u] = in ? Bs[(in ? j : 0) * kWarp + lane] : 0.0;
+                px[u] = in ? (kImp ? Rs[(in ? j : 0) * kWarp + lane] : -__ldg(ce + o)) : 0.0;
+                pf[u] = in ? __ldg(fl + o) : kFlagRoot;
+            };
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) fetch(J - 1 - u, u);
+            for (int jt = J - 1; jt >= 0; jt -= kPF) {
+#pragma unroll
+                for (int u = 0; u < kPF; ++u) {
+                    const int j = jt - u;
+                    if (j >= 0) {
+                        const double U = pu[u], X = px[u];
+                        const int f = pf[u];
+                        fetch(j - kPF, u);
+                        double vp;
+                        if (f & kFlagRoot) vp = 0.0;
+                        else if (f & kFlagRemote) vp = stk[(--sp) * kWarp + lane].x;
+                        else vp = vnext;
+                        const double v = fma(X, vp, U);
+                        for (int q = f & kFlagPopMask; q > 0; --q) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                        Vg[j * kWarp + lane] = v;
+                        if (last) bad |= !isfinite(v);
+                        vnext = v;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+
+        // state updates with V(t_{k+1}); terms of the next step
+        stream_mech<MT, kImp>(d, pk, Gm, Em, Vg, gS, mS, hS, nS, lane, true, true, last ? -1 : s + 1, !last, ev_i,
+                              ev_end, late, dt_m);
+
+        bool spk = false;
+        double ts = 0.0;
+        if (det >= 0) {
+            const double v1 = Vg[det];
+            if (v0 < thr && v1 >= thr) {
+                spk = true;
+                ts = __dadd_rn(t, __dmul_rn(dt, __ddiv_rn(__dsub_rn(thr, v0), __dsub_rn(v1, v0))));
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, spk);
+        if (ball) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd((unsigned long long*)&d.ctl->n_spikes, (unsigned long long)__popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (spk) {
+                const int64_t pos = (int64_t)base + __popc(ball & ((1u << lane) - 1u));
+                if (pos < d.spike_cap) {
+                    d.spk_gid[pos] = d.det_gid[owner];
+                    d.spk_t[pos] = ts;
+                } else {
+                    atomicOr(&d.ctl->status, kStSpikeOverflow);
+                }
+            }
+        }
+        if (probing) {
+            const int64_t prow = k - probe_k0;
+            if (prow >= 0 && prow < probe_max)
+                for (int q = lane; q < pk.npr; q += kWarp)
+                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+        }
+        __syncwarp();
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    const bool any_late = __any_sync(0xffffffffu, late != 0);
+    if (lane == 0 && (any_bad || any_late))
+        atomicOr(&d.ctl->status, (any_bad ? kStNonFinite : 0) | (any_late ? kStLateEvent : 0));
+    __syncwarp();
+}
+
+template <class MT, bool kImp>
+__global__ void __launch_bounds__(256, 1) arb_stream_kernel(DevModel<MT> d, int stack_depth) {
+    extern __shared__ double2 stk_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    double2* stack = stk_smem + (size_t)wid * stack_depth * kWarp;
+    const int64_t k0 = d.ctl->k0;
+    const int nsteps = (int)(d.ctl->k1 - k0);
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= d.n_packs) break;
+        run_pack_stream<MT, kImp>(d, p, stack, k0, nsteps, lane);
+    }
+}
+
+template <class MT>
+cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int stack_depth, cudaStream_t s) {
+    const size_t smem = (size_t)warps_per_cta * (size_t)stack_depth * kWarp * sizeof(double2);
+    if (implicit) arb_stream_kernel<MT, true><<<grid, warps_per_cta * kWarp, smem, s>>>(d, stack_depth);
+    else arb_stream_kernel<MT, false><<<grid, warps_per_cta * kWarp, smem, s>>>(d, stack_depth);
+    return cudaGetLastError();
+}
+
+template <class MT>
+cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int stack_depth, int* blocks_per_sm) {
+    const size_t smem = (size_t)warps_per_cta * (size_t)stack_depth * kWarp * sizeof(double2);
+    auto fn = implicit ? arb_stream_kernel<MT, true> : arb_stream_kernel<MT, false>;
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, warps_per_cta * kWarp, smem);
+}
+
+template cudaError_t launch_stream<double>(const DevModel<double>&, bool, int, int, int, cudaStream_t);
+template cudaError_t launch_stream<float>(const DevModel<float>&, bool, int, int, int, cudaStream_t);
+template cudaError_t stream_occupancy<double>(bool, int, int, int*);
+template cudaError_t stream_occupancy<float>(bool, int, int, int*);
 
 // ------------------------------------------------------------------------------------------
 // Event delivery lists (the "enqueue" and "merge" of Sec. "Implementation": each spike's
@@ -474,26 +979,28 @@ __global__ void k_scatter(T* dst, const double* src, const int64_t* idx, int64_t
 // Launch wrappers used by the host runtime.
 
 template <class MT>
-cudaError_t launch_epoch(const DevModel<MT>& d, int grid, int warps_per_cta, int tile_doubles, cudaStream_t s) {
+cudaError_t launch_epoch(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int tile_doubles, cudaStream_t s) {
     // the shared-memory limit was raised once by epoch_occupancy (not a stream operation,
     // so it stays out of graph capture)
     const size_t smem = (size_t)warps_per_cta * (size_t)tile_doubles * sizeof(double);
-    arb_epoch_kernel<MT><<<grid, warps_per_cta * kWarp, smem, s>>>(d, tile_doubles);
+    if (implicit) arb_epoch_kernel<MT, true><<<grid, warps_per_cta * kWarp, smem, s>>>(d, tile_doubles);
+    else arb_epoch_kernel<MT, false><<<grid, warps_per_cta * kWarp, smem, s>>>(d, tile_doubles);
     return cudaGetLastError();
 }
 
 template <class MT>
-cudaError_t epoch_occupancy(int warps_per_cta, int tile_doubles, int* blocks_per_sm) {
+cudaError_t epoch_occupancy(bool implicit, int warps_per_cta, int tile_doubles, int* blocks_per_sm) {
     const size_t smem = (size_t)warps_per_cta * (size_t)tile_doubles * sizeof(double);
-    cudaError_t err = cudaFuncSetAttribute(arb_epoch_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto fn = implicit ? arb_epoch_kernel<MT, true> : arb_epoch_kernel<MT, false>;
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, arb_epoch_kernel<MT>, warps_per_cta * kWarp, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, warps_per_cta * kWarp, smem);
 }
 
-template cudaError_t launch_epoch<double>(const DevModel<double>&, int, int, int, cudaStream_t);
-template cudaError_t launch_epoch<float>(const DevModel<float>&, int, int, int, cudaStream_t);
-template cudaError_t epoch_occupancy<double>(int, int, int*);
-template cudaError_t epoch_occupancy<float>(int, int, int*);
+template cudaError_t launch_epoch<double>(const DevModel<double>&, bool, int, int, int, cudaStream_t);
+template cudaError_t launch_epoch<float>(const DevModel<float>&, bool, int, int, int, cudaStream_t);
+template cudaError_t epoch_occupancy<double>(bool, int, int, int*);
+template cudaError_t epoch_occupancy<float>(bool, int, int, int*);
 
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s) {
     const int owner_blocks = max(1, min(4 * n_sm, (a.n_owner + 255) / 256));

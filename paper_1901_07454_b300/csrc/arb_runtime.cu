@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <array>
+#include <functional>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -25,9 +26,13 @@
 
 namespace arbk {
 template <class MT>
-cudaError_t launch_epoch(const DevModel<MT>& d, int grid, int warps_per_cta, int tile_doubles, cudaStream_t s);
+cudaError_t launch_epoch(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int tile_doubles, cudaStream_t s);
 template <class MT>
-cudaError_t epoch_occupancy(int warps_per_cta, int tile_doubles, int* blocks_per_sm);
+cudaError_t epoch_occupancy(bool implicit, int warps_per_cta, int tile_doubles, int* blocks_per_sm);
+template <class MT>
+cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int stack_depth, cudaStream_t s);
+template <class MT>
+cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int stack_depth, int* blocks_per_sm);
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s);
 template <class T>
@@ -57,18 +62,19 @@ struct Plan {
     int64_t total_rows = 0;
     std::vector<double> ca, cb, ck, ce;     // total_rows*32
     std::vector<int32_t> pslot;
+    std::vector<int32_t> vmap;              // on-chip voltage slots (own | parent << 16)
     std::vector<double> V0;                 // initial voltage per tile entry
     std::vector<int64_t> cv_tile;           // model CV -> global tile index
     std::vector<int32_t> cv_pack;           // model CV -> pack
     // synapses
     int64_t syn_rows = 0;
-    std::vector<int32_t> syn_slot;
+    std::vector<int32_t> syn_slot, syn_vs;
     std::vector<double> syn_e, syn_decay, syn_sc;
     std::vector<int64_t> syn_entry;         // model synapse -> entry
     std::vector<int32_t> syn_owner, syn_js;
     // HH
     int64_t hh_rows = 0;
-    std::vector<int32_t> hh_slot;
+    std::vector<int32_t> hh_slot, hh_vs;
     std::vector<double> hh_sc, hh_gna, hh_gk;
     std::vector<int64_t> hh_entry;
     // clamps
@@ -82,6 +88,9 @@ struct Plan {
     double lane_eff = 0.0;
     int tile_doubles = 0;                   // per-warp shared tile (doubles), 0 = none
     int cells_per_pack = 0;
+    bool stream = false;                    // packs streamed from global memory (one cell per lane)
+    int64_t c_total = 0;                    // streamed packs: compact mechanism slots
+    int32_t stack_depth = 1;                // streamed packs: deepest hand-over stack
 };
 
 struct Region {
@@ -106,6 +115,7 @@ struct arb_sim {
     std::vector<double> conn_delay, conn_w;
     int32_t epoch_steps = 0;
     bool mixed = false;
+    bool implicit = true;
     std::vector<int64_t> syn_cell;
     // ---- prepared data
     Plan plan;
@@ -124,7 +134,7 @@ struct arb_sim {
     int grid = 148;
     cudaStream_t s = nullptr;       // library stream (graphs are captured here)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t graph[kGraphRing] = {};
+    cudaGraphExec_t graph[3] = {};   // event lists, epoch kernel, spike exchange
     cudaEvent_t t0[kGraphRing] = {}, t1[kGraphRing] = {};
     bool pending_time[kGraphRing] = {};
     DevModel<double> dm64{};
@@ -255,6 +265,7 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
         int32_t pending;     // children not finished
         int64_t prio;
         int32_t finish_round;
+        int32_t child_round;   // latest round in which a child chain finished
     };
     std::vector<Chain> ch;
     for (int32_t c : cells) {
@@ -275,6 +286,7 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
                 x.pending = 0;
                 x.prio = 0;
                 x.finish_round = -1;
+                x.child_round = -1;
                 ch.push_back(x);
             } else {
                 ch.back().tail = q;   // single child directly follows its parent in DFS order
@@ -328,7 +340,7 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
                 if (head_row && x.parent >= 0) {
                     Chain& P = ch[x.parent];
                     // continuation: this is the last child and every sibling ended in an earlier round
-                    if (P.pending == 1) {
+                    if (P.pending == 1 && P.child_round < round) {
                         cont = true;
                     } else if (std::find(written.begin(), written.end(), x.parent) != written.end()) {
                         break;   // a sibling already writes this parent in this round: wait
@@ -344,6 +356,7 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
                     cur[l] = -1;
                     if (pidx >= 0) {
                         ch[pidx].pending--;
+                        ch[pidx].child_round = std::max(ch[pidx].child_round, round);
                         if (cont) {
                             cur[l] = pidx;
                             pos[l] = 0;
@@ -372,24 +385,6 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
     return pr;
 }
 
-// Cost of a packing in rows per SM: packs share the SMs, rows of one pack are sequential.
-double packing_cost(const std::vector<int64_t>& pack_rows, int n_sm) {
-    int64_t sum = 0, mx = 0;
-    for (int64_t j : pack_rows) { sum += j; mx = std::max(mx, j); }
-    std::vector<int64_t> sorted = pack_rows;
-    std::sort(sorted.begin(), sorted.end(), std::greater<int64_t>());
-    std::priority_queue<int64_t, std::vector<int64_t>, std::greater<int64_t>> bins;
-    for (int i = 0; i < n_sm; ++i) bins.push(0);
-    for (int64_t j : sorted) {
-        int64_t b = bins.top();
-        bins.pop();
-        bins.push(b + j);
-    }
-    int64_t ms = 0;
-    while (!bins.empty()) { ms = std::max(ms, bins.top()); bins.pop(); }
-    return (double)std::max(ms, mx);
-}
-
 }  // namespace
 
 static void layout_regions(arb_sim* sim) {
@@ -405,11 +400,12 @@ static void layout_regions(arb_sim* sim) {
     std::vector<std::pair<std::string, size_t>> want = {
         {"ctl", sizeof(Ctl)},
         {"packs", sizeof(PackDesc) * std::max<int64_t>(npk, 1)},
-        {"ca", 8 * ne}, {"cb", 8 * ne}, {"ck", 8 * ne}, {"ce", 8 * ne}, {"pslot", 4 * ne},
-        {"V", 8 * ne}, {"Sg", 8 * std::max<int64_t>(pl.sg_total, 1)},
-        {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
+        {"ca", 8 * ne}, {"cb", 8 * ne}, {"ck", 8 * ne}, {"ce", 8 * ne}, {"pslot", 4 * ne}, {"vmap", 4 * ne},
+        {"V", 8 * ne}, {"Sg", 8 * std::max<int64_t>(pl.sg_total, 1)}, {"Rg", 8 * std::max<int64_t>(pl.sg_total, 1)},
+        {"Gm", 8 * std::max<int64_t>(pl.c_total, 1)}, {"Em", 8 * std::max<int64_t>(pl.c_total, 1)},
+        {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
         {"syn_e", 8 * pl.syn_rows * kWarp}, {"syn_decay", 8 * pl.syn_rows * kWarp}, {"syn_sc", 8 * pl.syn_rows * kWarp},
-        {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
+        {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_vs", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
         {"hh_gk", 8 * pl.hh_rows * kWarp}, {"hh_m", mt * pl.hh_rows * kWarp}, {"hh_h", mt * pl.hh_rows * kWarp},
         {"hh_n", mt * pl.hh_rows * kWarp},
         {"st_slot", 4 * pl.st_rows * kWarp}, {"st_sc", 8 * pl.st_rows * kWarp}, {"st_on", 8 * pl.st_rows * kWarp},
@@ -468,14 +464,20 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.ck = (const double*)region(sim, "ck");
     d.ce = (const double*)region(sim, "ce");
     d.pslot = (const int32_t*)region(sim, "pslot");
+    d.vmap = (const int32_t*)region(sim, "vmap");
     d.V = (double*)region(sim, "V");
     d.Sg = (double*)region(sim, "Sg");
+    d.Rg = (double*)region(sim, "Rg");
+    d.Gm = (double*)region(sim, "Gm");
+    d.Em = (double*)region(sim, "Em");
     d.syn_slot = (const int32_t*)region(sim, "syn_slot");
+    d.syn_vs = (const int32_t*)region(sim, "syn_vs");
     d.syn_g = (MT*)region(sim, "syn_g");
     d.syn_e = (const double*)region(sim, "syn_e");
     d.syn_decay = (const double*)region(sim, "syn_decay");
     d.syn_sc = (const double*)region(sim, "syn_sc");
     d.hh_slot = (const int32_t*)region(sim, "hh_slot");
+    d.hh_vs = (const int32_t*)region(sim, "hh_vs");
     d.hh_sc = (const double*)region(sim, "hh_sc");
     d.hh_gna = (const double*)region(sim, "hh_gna");
     d.hh_gk = (const double*)region(sim, "hh_gk");
@@ -516,6 +518,7 @@ arb_status arb_default_params(arb_params* p) {
     p->precision = ARB_FP64;
     p->cells_per_pack = 0;
     p->smem_budget = 0;
+    p->scheme = ARB_IMPLICIT;
     p->event_capacity = 1 << 22;
     p->ext_event_capacity = 1 << 20;
     p->spike_capacity = 1 << 22;
@@ -547,6 +550,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     if (p.event_capacity > INT32_MAX || p.bucket_capacity > INT32_MAX) return bad("event and bucket capacities must be < 2^31");
     if (p.cells_per_pack < 0 || p.cells_per_pack > 32) return bad("cells_per_pack must be 0..32");
     sim->mixed = p.precision == ARB_MIXED;
+    if (p.scheme != ARB_IMPLICIT && p.scheme != ARB_EXPLICIT) return bad("scheme must be ARB_IMPLICIT or ARB_EXPLICIT");
+    sim->implicit = p.scheme == ARB_IMPLICIT;
     if (m->n_cells < 0) return bad("n_cells < 0");
     const int32_t nc = m->n_cells;
     sim->n_cells = nc;
@@ -708,83 +713,413 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             }
             for (int32_t q = 0; q < n; ++q) {
                 const int64_t g = off + o.dfs[q];
-                ca[g] = (cap[g] / p.dt - Glin[g]) * invd[g];
-                cb[g] = GElin[g] * invd[g];
-                if (q > 0) {
-                    const double a = -sigma[g];
-                    ck[g] = a * invd[off + o.dfs[o.dpar[q]]];
-                    ce[g] = a * invd[g];
+                if (sim->implicit) {
+                    // constant parts of the per-step system; the pivots are formed in the kernel
+                    ca[g] = cap[g] / p.dt;
+                    cb[g] = GElin[g];
+                    ck[g] = q > 0 ? sigma[g] : 0.0;
+                    ce[g] = cap[g] / p.dt + Glin[g];
+                } else {
+                    ca[g] = (cap[g] / p.dt - Glin[g]) * invd[g];
+                    cb[g] = GElin[g] * invd[g];
+                    if (q > 0) {
+                        const double a = -sigma[g];
+                        ck[g] = a * invd[off + o.dfs[o.dpar[q]]];
+                        ce[g] = a * invd[g];
+                    }
                 }
             }
+            if (sim->implicit)   // diagonal: add every axial conductance the CV takes part in
+                for (int32_t q = 1; q < n; ++q) {
+                    const int64_t g = off + o.dfs[q];
+                    ce[g] += sigma[g];
+                    ce[off + o.dfs[o.dpar[q]]] += sigma[g];
+                }
         }
     }
 
     // ------------------------------------------------------------------ packing
-    int n_sm = 148;
-    const int64_t budget = p.smem_budget > 0 ? p.smem_budget : 112 * 1024;
+    // Cells are grouped into packs (one warp each). A pack's working set (scaled right-hand
+    // side per entry, the voltages that are read, synapse and HH states) must fit the shared
+    // memory a warp gets; groups that do not fit are split, and a single cell that still does
+    // not fit runs from global memory. Among candidate group sizes the one with the smallest
+    // estimated per-SM FP64 work (longest-processing-time assignment) is kept.
+    const int n_sm = 148;
+    const int wpc = 2;                                         // warps per CTA, one CTA per SM
+    const int64_t budget = p.smem_budget > 0 ? ((int64_t)p.smem_budget & ~(int64_t)7)
+                                             : (((int64_t)227 * 1024 / wpc) & ~(int64_t)7);
+    const int64_t mtb = sim->mixed ? 4 : 8;
     Plan& pl = sim->plan;
     pl.tile_doubles = (int)(budget / 8);
-    std::vector<int32_t> by_size(nc);
-    std::iota(by_size.begin(), by_size.end(), 0);
-    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t b) {
-        return sim->cv_offset[a + 1] - sim->cv_offset[a] > sim->cv_offset[b + 1] - sim->cv_offset[b];
-    });
-    const int R = 4;
-    auto build = [&](int kpp, std::vector<PackRows>& rows, std::vector<std::vector<int32_t>>& groups) {
-        rows.clear();
-        groups.clear();
-        for (int32_t i = 0; i < nc; i += kpp) {
-            std::vector<int32_t> g(by_size.begin() + i, by_size.begin() + std::min<int32_t>(nc, i + kpp));
-            rows.push_back(kpp == 32 ? schedule_affinity(g, ord, sim->cv_offset)
-                                     : schedule_shared(g, ord, sim->cv_offset, R));
-            groups.push_back(std::move(g));
+    const int32_t nsyn_all = (int32_t)sim->syn_cv.size();
+    std::vector<int32_t> cell_of(ncv);
+    for (int32_t c = 0; c < nc; ++c)
+        for (int64_t i = sim->cv_offset[c]; i < sim->cv_offset[c + 1]; ++i) cell_of[i] = c;
+    std::vector<std::vector<int32_t>> cell_syn(nc), cell_hh(nc), cell_st(nc);
+    for (int32_t i = 0; i < nsyn_all; ++i) cell_syn[cell_of[sim->syn_cv[i]]].push_back(i);
+    for (size_t i = 0; i < sim->hh_cv.size(); ++i) cell_hh[cell_of[sim->hh_cv[i]]].push_back((int32_t)i);
+    for (size_t i = 0; i < sim->st_cv.size(); ++i) cell_st[cell_of[sim->st_cv[i]]].push_back((int32_t)i);
+    std::vector<char> cv_has_mech(ncv, 0);
+    for (int64_t cv : sim->syn_cv) cv_has_mech[cv] = 1;
+    for (int64_t cv : sim->hh_cv) cv_has_mech[cv] = 1;
+    for (int64_t cv : sim->det_cv) cv_has_mech[cv] = 1;
+
+    struct Group {
+        std::vector<int32_t> cells;
+        PackRows rows;
+        std::array<std::vector<int32_t>, 32> syn_l, st_l;
+        std::vector<int32_t> hh;
+        int64_t nsyn_row = 0, nhh_row = 0, nst_row = 0, nvc = 0;
+        bool smem = false;
+        double cost = 0;
+    };
+    // lanes of grouped items: items on one CV stay on one lane (no two lanes update one slot in
+    // a loop); groups by CV, largest first, onto the least loaded lane
+    auto assign_grouped = [&](const std::vector<int32_t>& items, const std::vector<int64_t>& item_cv,
+                              std::array<std::vector<int32_t>, 32>& lanes) {
+        for (auto& v : lanes) v.clear();
+        std::vector<int32_t> it = items;
+        std::stable_sort(it.begin(), it.end(), [&](int32_t x, int32_t y) { return item_cv[x] < item_cv[y]; });
+        std::vector<std::pair<size_t, size_t>> grp;   // [begin, end) in it
+        for (size_t i = 0; i < it.size(); ++i) {
+            if (i == 0 || item_cv[it[i]] != item_cv[it[i - 1]]) grp.push_back({i, i});
+            grp.back().second = i + 1;
+        }
+        std::stable_sort(grp.begin(), grp.end(), [](const auto& x, const auto& y) {
+            return x.second - x.first > y.second - y.first;
+        });
+        std::array<int64_t, 32> load{};
+        for (auto& g : grp) {
+            int best = 0;
+            for (int l = 1; l < 32; ++l) if (load[l] < load[best]) best = l;
+            for (size_t i = g.first; i < g.second; ++i) lanes[best].push_back(it[i]);
+            load[best] += (int64_t)(g.second - g.first);
         }
     };
-    std::vector<PackRows> rows;
-    std::vector<std::vector<int32_t>> groups;
+    auto make_group = [&](const std::vector<int32_t>& cells, bool affinity) {
+        Group G;
+        G.cells = cells;
+        G.rows = affinity ? schedule_affinity(cells, ord, sim->cv_offset) : schedule_shared(cells, ord, sim->cv_offset, 4);
+        std::vector<int32_t> sy, st;
+        for (int32_t c : cells) {
+            sy.insert(sy.end(), cell_syn[c].begin(), cell_syn[c].end());
+            st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
+            G.hh.insert(G.hh.end(), cell_hh[c].begin(), cell_hh[c].end());
+        }
+        assign_grouped(sy, sim->syn_cv, G.syn_l);
+        assign_grouped(st, sim->st_cv, G.st_l);
+        for (int l = 0; l < 32; ++l) {
+            G.nsyn_row = std::max<int64_t>(G.nsyn_row, (int64_t)G.syn_l[l].size());
+            G.nst_row = std::max<int64_t>(G.nst_row, (int64_t)G.st_l[l].size());
+        }
+        G.nhh_row = ((int64_t)G.hh.size() + 31) / 32;
+        // voltages read on chip: mechanism and detector CVs, and parents of chains handed over
+        const int64_t J = (int64_t)G.rows.rows.size();
+        std::vector<char> need;
+        int64_t nvc = 0;
+        {
+            std::vector<std::pair<int64_t, int64_t>> pos_of;   // (cv, slot) for the pack
+            pos_of.reserve(J * 32);
+            for (int64_t j = 0; j < J; ++j)
+                for (int l = 0; l < 32; ++l)
+                    if (G.rows.rows[j][l] >= 0) pos_of.push_back({G.rows.rows[j][l], j * 32 + l});
+            std::sort(pos_of.begin(), pos_of.end());
+            auto slot_of = [&](int64_t cv) {
+                return std::lower_bound(pos_of.begin(), pos_of.end(), std::make_pair(cv, (int64_t)-1))->second;
+            };
+            need.assign(J * 32, 0);
+            for (auto& cs : pos_of) {
+                const int64_t cv = cs.first, sl = cs.second;
+                if (cv_has_mech[cv]) need[sl] = 1;
+                const int32_t c = cell_of[cv];
+                const int32_t pi = sim->parent[cv];
+                if (pi >= 0) {
+                    const int64_t psl = slot_of(sim->cv_offset[c] + pi);
+                    if (psl != sl + 32) need[psl] = 1;
+                }
+            }
+            for (char x : need) nvc += x;
+        }
+        G.nvc = nvc;
+        const int64_t bytes = 8 * (J * 32 * (sim->implicit ? 2 : 1) + nvc) + mtb * 32 * (G.nsyn_row + 3 * G.nhh_row);
+        G.smem = bytes <= budget && nvc < 0xFFFF && J * 32 <= 0xFFFF;
+        G.cost = 3.0 * (double)J + 260.0 * (double)G.nhh_row + 4.0 * (double)G.nsyn_row;
+        return G;
+    };
+    // groups of kpp consecutive cells (largest first); groups that do not fit are halved
+    std::function<void(const std::vector<int32_t>&, bool, std::vector<Group>&)> place =
+        [&](const std::vector<int32_t>& cells, bool affinity, std::vector<Group>& out) {
+            Group G = make_group(cells, affinity);
+            if (G.smem || cells.size() == 1) {
+                out.push_back(std::move(G));
+                return;
+            }
+            const size_t h = cells.size() / 2;
+            place(std::vector<int32_t>(cells.begin(), cells.begin() + h), false, out);
+            place(std::vector<int32_t>(cells.begin() + h, cells.end()), false, out);
+        };
+    std::vector<int32_t> by_size(nc);
+    std::iota(by_size.begin(), by_size.end(), 0);
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t x, int32_t y) {
+        return sim->cv_offset[x + 1] - sim->cv_offset[x] > sim->cv_offset[y + 1] - sim->cv_offset[y];
+    });
+    auto build_k = [&](int kpp, std::vector<Group>& out) {
+        out.clear();
+        for (int32_t i = 0; i < nc; i += kpp) {
+            std::vector<int32_t> g(by_size.begin() + i, by_size.begin() + std::min<int32_t>(nc, i + kpp));
+            place(g, kpp == 32, out);
+        }
+    };
+    auto lpt_cost = [&](const std::vector<Group>& gs) {
+        std::vector<double> c;
+        double mx = 0;
+        for (auto& g : gs) { c.push_back(g.cost); mx = std::max(mx, g.cost); }
+        std::sort(c.begin(), c.end(), std::greater<double>());
+        std::priority_queue<double, std::vector<double>, std::greater<double>> bins;
+        for (int i = 0; i < n_sm; ++i) bins.push(0.0);
+        for (double x : c) { double b0 = bins.top(); bins.pop(); bins.push(b0 + x); }
+        double ms = 0;
+        while (!bins.empty()) { ms = std::max(ms, bins.top()); bins.pop(); }
+        return std::max(ms, mx);
+    };
+    std::vector<Group> groups;
     int kpp = p.cells_per_pack;
     if (kpp == 0) {
-        if (nc >= 32 * 2 * n_sm) {
+        if (nc >= 32 * wpc * n_sm) {
             kpp = 32;
         } else {
             double best = INFINITY;
-            for (int cand : {32, 16, 12, 8, 6, 4, 3, 2, 1}) {
-                std::vector<PackRows> r;
-                std::vector<std::vector<int32_t>> g;
-                build(cand, r, g);
-                std::vector<int64_t> jr;
-                for (auto& x : r) jr.push_back((int64_t)x.rows.size());
-                const double cost = packing_cost(jr, n_sm);
-                if (cost < best * 0.97) { best = cost; kpp = cand; rows = std::move(r); groups = std::move(g); }
+            for (int cand : {16, 12, 8, 6, 4, 3, 2, 1}) {
+                std::vector<Group> gs;
+                build_k(cand, gs);
+                const double cost = lpt_cost(gs);
+                if (cost < best * 0.97) { best = cost; kpp = cand; groups = std::move(gs); }
             }
         }
     }
-    if (rows.empty() && nc > 0) build(kpp, rows, groups);
     pl.cells_per_pack = kpp;
-    const int32_t npk = (int32_t)rows.size();
-    // order packs by decreasing length: the persistent kernel takes them in this order
-    std::vector<int32_t> porder(npk);
-    std::iota(porder.begin(), porder.end(), 0);
-    std::stable_sort(porder.begin(), porder.end(), [&](int32_t a, int32_t b) { return rows[a].rows.size() > rows[b].rows.size(); });
+    pl.stream = (kpp == 32);
+    if (pl.stream) {
+        // ---------------------------------------------------------- streamed packs
+        // 32 cells per pack (largest first), one per lane, every array in global memory.
+        const int32_t npk = (nc + 31) / 32;
+        pl.packs.resize(npk);
+        pl.cv_tile.assign(ncv, -1);
+        pl.cv_pack.assign(ncv, -1);
+        std::vector<std::array<std::vector<int32_t>, 32>> syn_l(npk), st_l(npk);
+        std::vector<std::vector<int32_t>> hh_l(npk);
+        std::vector<std::vector<int32_t>> gcells(npk);
+        int64_t row0 = 0;
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            std::vector<int32_t> g(by_size.begin() + (size_t)pi * 32, by_size.begin() + std::min<int32_t>(nc, (pi + 1) * 32));
+            int32_t J = 0;
+            for (int32_t c : g) J = std::max<int32_t>(J, (int32_t)(sim->cv_offset[c + 1] - sim->cv_offset[c]));
+            PackDesc& pd = pl.packs[pi];
+            std::memset(&pd, 0, sizeof(pd));
+            pd.row0 = (int32_t)row0;
+            pd.nrow = J;
+            pd.smem = kPackStream;
+            pd.sg_off = row0 * kWarp;
+            pd.ncell = (int32_t)g.size();
+            for (size_t l = 0; l < g.size(); ++l) {
+                const int32_t c = g[l];
+                const int32_t n = (int32_t)ord[c].dfs.size();
+                for (int32_t q = 0; q < n; ++q) {
+                    const int64_t cv = sim->cv_offset[c] + ord[c].dfs[q];
+                    pl.cv_tile[cv] = (row0 + (n - 1 - q)) * kWarp + (int64_t)l;
+                    pl.cv_pack[cv] = pi;
+                }
+            }
+            std::vector<int32_t> sy, st;
+            for (int32_t c : g) {
+                sy.insert(sy.end(), cell_syn[c].begin(), cell_syn[c].end());
+                st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
+                hh_l[pi].insert(hh_l[pi].end(), cell_hh[c].begin(), cell_hh[c].end());
+            }
+            assign_grouped(sy, sim->syn_cv, syn_l[pi]);
+            assign_grouped(st, sim->st_cv, st_l[pi]);
+            gcells[pi] = std::move(g);
+            row0 += J;
+        }
+        pl.total_rows = row0;
+        const int64_t ne = row0 * kWarp;
+        if (ne > INT32_MAX) return bad("model too large for one handle");
+        pl.lane_eff = row0 > 0 ? (double)ncv / (double)ne : 1.0;
+        pl.sg_total = ne;
+        pl.ca.assign(ne, 0.0);
+        pl.cb.assign(ne, 0.0);
+        pl.ck.assign(ne, 0.0);
+        pl.ce.assign(ne, sim->implicit ? 1.0 : 0.0);
+        pl.pslot.assign(ne, kFlagRoot);   // flags; padding behaves like an isolated root
+        pl.vmap.assign(ne, -1);           // compact mechanism slot
+        pl.V0.assign(ne, 0.0);
+        // per-entry constants and flags
+        for (int32_t c = 0; c < nc; ++c) {
+            const int64_t off = sim->cv_offset[c];
+            const CellOrder& o = ord[c];
+            const int32_t n = (int32_t)o.dfs.size();
+            std::vector<int32_t> nch(n, 0);
+            for (int32_t q = 1; q < n; ++q) nch[o.dpar[q]]++;
+            for (int32_t q = 0; q < n; ++q) {
+                const int64_t g = off + o.dfs[q];
+                const int64_t t = pl.cv_tile[g];
+                pl.ca[t] = ca[g];
+                pl.cb[t] = cb[g];
+                pl.ck[t] = ck[g];
+                pl.ce[t] = ce[g];
+                pl.V0[t] = -65.0;
+                int32_t f = nch[q] > 1 ? (nch[q] - 1) : 0;   // non-first children hand over via the stack
+                if (f > kFlagPopMask) return bad("a CV has more than 256 children");
+                if (q == 0) f |= kFlagRoot;
+                else if (o.dpar[q] != q - 1) f |= kFlagRemote;
+                pl.pslot[t] = f;
+            }
+        }
+        // compact mechanism slots, stack depths
+        std::vector<char> mech(ncv, 0);
+        for (int64_t cv : sim->syn_cv) mech[cv] = 1;
+        for (int64_t cv : sim->hh_cv) mech[cv] = 1;
+        for (int64_t cv : sim->st_cv) mech[cv] = 1;
+        int64_t c_total = 0;
+        int32_t max_depth = 1;
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            PackDesc& pd = pl.packs[pi];
+            const int64_t base = (int64_t)pd.row0 * kWarp;
+            int32_t nvc = 0;
+            for (int32_t c : gcells[pi])
+                for (int64_t cv = sim->cv_offset[c]; cv < sim->cv_offset[c + 1]; ++cv)
+                    if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = 0;
+            for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
+                if (pl.vmap[t] >= 0) pl.vmap[t] = nvc++;
+            pd.nvc = nvc;
+            pd.c_off = c_total;
+            c_total += nvc;
+            int32_t depth = 0;
+            for (int l = 0; l < kWarp; ++l) {
+                int32_t sp = 0;
+                for (int32_t j = 0; j < pd.nrow; ++j) {                 // forward
+                    const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
+                    sp -= f & kFlagPopMask;
+                    if (sp < 0) return bad("internal error: hand-over stack underflow");
+                    if ((f & kFlagRemote) && !(f & kFlagRoot)) ++sp;
+                    depth = std::max(depth, sp);
+                }
+                sp = 0;
+                for (int32_t j = pd.nrow - 1; j >= 0; --j) {            // backward
+                    const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
+                    if ((f & kFlagRemote) && !(f & kFlagRoot)) --sp;
+                    if (sp < 0) return bad("internal error: voltage stack underflow");
+                    sp += f & kFlagPopMask;
+                    depth = std::max(depth, sp);
+                }
+            }
+            pd.stack = depth;
+            max_depth = std::max(max_depth, depth);
+        }
+        pl.c_total = c_total;
+        pl.stack_depth = max_depth;
+        // mechanisms: synapse and clamp rows by CV on one lane; HH round-robin
+        int64_t syn_rows = 0, hh_rows = 0, st_rows = 0;
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            PackDesc& pd = pl.packs[pi];
+            size_t ms = 0, mt = 0;
+            for (int l = 0; l < 32; ++l) { ms = std::max(ms, syn_l[pi][l].size()); mt = std::max(mt, st_l[pi][l].size()); }
+            pd.syn_row0 = (int32_t)syn_rows; pd.nsyn_row = (int32_t)ms; syn_rows += (int64_t)ms;
+            pd.hh_row0 = (int32_t)hh_rows; pd.nhh_row = (int32_t)((hh_l[pi].size() + 31) / 32); hh_rows += pd.nhh_row;
+            pd.st_row0 = (int32_t)st_rows; pd.nst_row = (int32_t)mt; st_rows += (int64_t)mt;
+        }
+        pl.syn_rows = syn_rows; pl.hh_rows = hh_rows; pl.st_rows = st_rows;
+        pl.syn_entry.assign(nsyn_all, -1); pl.syn_owner.assign(nsyn_all, 0); pl.syn_js.assign(nsyn_all, 0);
+        pl.hh_entry.assign(sim->hh_cv.size(), -1);
+        pl.syn_slot.assign(syn_rows * kWarp, -1); pl.syn_vs.assign(syn_rows * kWarp, -1);
+        pl.syn_e.assign(syn_rows * kWarp, 0.0); pl.syn_decay.assign(syn_rows * kWarp, 0.0); pl.syn_sc.assign(syn_rows * kWarp, 0.0);
+        pl.hh_slot.assign(hh_rows * kWarp, -1); pl.hh_vs.assign(hh_rows * kWarp, -1);
+        pl.hh_sc.assign(hh_rows * kWarp, 0.0); pl.hh_gna.assign(hh_rows * kWarp, 0.0); pl.hh_gk.assign(hh_rows * kWarp, 0.0);
+        pl.st_slot.assign(st_rows * kWarp, -1); pl.st_sc.assign(st_rows * kWarp, 0.0);
+        pl.st_on.assign(st_rows * kWarp, 0.0); pl.st_off.assign(st_rows * kWarp, 0.0); pl.st_amp.assign(st_rows * kWarp, 0.0);
+        pl.det_slot.assign((size_t)npk * kWarp, -1); pl.det_gid.assign((size_t)npk * kWarp, -1);
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            const PackDesc& pd = pl.packs[pi];
+            const int64_t base = (int64_t)pd.row0 * kWarp;
+            for (int l = 0; l < 32; ++l) {
+                const auto& v = syn_l[pi][l];
+                for (size_t rr = 0; rr < v.size(); ++rr) {
+                    const int32_t i = v[rr];
+                    const int64_t q = ((int64_t)pd.syn_row0 + (int64_t)rr) * kWarp + l;
+                    const int64_t cv = sim->syn_cv[i];
+                    pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+                    pl.syn_vs[q] = pl.vmap[pl.cv_tile[cv]];
+                    pl.syn_e[q] = sim->syn_e[i];
+                    pl.syn_decay[q] = std::exp(-p.dt / sim->syn_tau[i]);
+                    pl.syn_sc[q] = invd[cv];
+                    pl.syn_entry[i] = q;
+                    pl.syn_owner[i] = pi * kWarp + l;
+                    pl.syn_js[i] = (int32_t)rr;
+                }
+                const auto& w = st_l[pi][l];
+                for (size_t rr = 0; rr < w.size(); ++rr) {
+                    const int32_t i = w[rr];
+                    const int64_t q = ((int64_t)pd.st_row0 + (int64_t)rr) * kWarp + l;
+                    const int64_t cv = sim->st_cv[i];
+                    pl.st_slot[q] = pl.vmap[pl.cv_tile[cv]];
+                    pl.st_sc[q] = invd[cv];
+                    pl.st_on[q] = sim->st_on[i];
+                    pl.st_off[q] = sim->st_on[i] + sim->st_dur[i];
+                    pl.st_amp[q] = sim->st_amp[i];
+                }
+            }
+            for (size_t rr = 0; rr < hh_l[pi].size(); ++rr) {
+                const int32_t i = hh_l[pi][rr];
+                const int64_t q = ((int64_t)pd.hh_row0 + (int64_t)(rr / 32)) * kWarp + (int64_t)(rr % 32);
+                const int64_t cv = sim->hh_cv[i];
+                pl.hh_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+                pl.hh_vs[q] = pl.vmap[pl.cv_tile[cv]];
+                pl.hh_sc[q] = invd[cv];
+                pl.hh_gna[q] = hh_gna[i];
+                pl.hh_gk[q] = hh_gk[i];
+                pl.hh_entry[i] = q;
+            }
+            for (size_t dd = 0; dd < gcells[pi].size(); ++dd) {
+                pl.det_slot[(size_t)pi * kWarp + dd] = (int32_t)(pl.cv_tile[sim->det_cv[gcells[pi][dd]]] - base);
+                pl.det_gid[(size_t)pi * kWarp + dd] = gcells[pi][dd];
+            }
+        }
+        // the persistent kernel takes packs in order: already largest first
+    } else {
+    if (groups.empty() && nc > 0) build_k(kpp, groups);
+    const int32_t npk = (int32_t)groups.size();
+    // the persistent kernel takes packs in this order: most work first
+    std::stable_sort(groups.begin(), groups.end(), [](const Group& x, const Group& y) { return x.cost > y.cost; });
 
     pl.packs.resize(npk);
     pl.cv_tile.assign(ncv, -1);
     pl.cv_pack.assign(ncv, -1);
-    int64_t row0 = 0, cvs_placed = 0;
+    int64_t row0 = 0, cvs_placed = 0, syn_rows = 0, hh_rows = 0, st_rows = 0;
     for (int32_t pi = 0; pi < npk; ++pi) {
         PackDesc& pd = pl.packs[pi];
-        const PackRows& pr = rows[porder[pi]];
+        const Group& G = groups[pi];
+        std::memset(&pd, 0, sizeof(pd));
         pd.row0 = (int32_t)row0;
-        pd.nrow = (int32_t)pr.rows.size();
-        pd.round_rows = pr.round_rows;
-        const int64_t tile = (int64_t)pd.nrow * kWarp * 2;
-        pd.smem = (tile <= pl.tile_doubles) ? 1 : 0;
+        pd.nrow = (int32_t)G.rows.rows.size();
+        pd.round_rows = G.rows.round_rows;
+        pd.smem = G.smem ? 1 : 0;
         if (pd.smem) pl.smem_packs++;
         pd.sg_off = pd.smem ? 0 : pl.sg_total;
         if (!pd.smem) pl.sg_total += (int64_t)pd.nrow * kWarp;
+        pd.syn_row0 = (int32_t)syn_rows;
+        pd.nsyn_row = (int32_t)G.nsyn_row;
+        pd.hh_row0 = (int32_t)hh_rows;
+        pd.nhh_row = (int32_t)G.nhh_row;
+        pd.st_row0 = (int32_t)st_rows;
+        pd.nst_row = (int32_t)G.nst_row;
+        pd.ncell = (int32_t)G.cells.size();
+        pd.nvc = (int32_t)G.nvc;
+        syn_rows += G.nsyn_row;
+        hh_rows += G.nhh_row;
+        st_rows += G.nst_row;
         for (int32_t j = 0; j < pd.nrow; ++j)
             for (int l = 0; l < kWarp; ++l) {
-                const int64_t cv = pr.rows[j][l];
+                const int64_t cv = G.rows.rows[j][l];
                 if (cv >= 0) {
                     pl.cv_tile[cv] = (row0 + j) * kWarp + l;
                     pl.cv_pack[cv] = pi;
@@ -801,11 +1136,10 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     pl.ca.assign(ne, 0.0);
     pl.cb.assign(ne, 0.0);
     pl.ck.assign(ne, 0.0);
-    pl.ce.assign(ne, 0.0);
+    pl.ce.assign(ne, sim->implicit ? 1.0 : 0.0);   // padding: unit diagonal keeps the pivots finite
     pl.pslot.assign(ne, -2);
+    pl.vmap.assign(ne, -1);
     pl.V0.assign(ne, 0.0);
-    std::vector<int64_t> tile_cv(ne, -1);
-    for (int64_t cv = 0; cv < ncv; ++cv) tile_cv[pl.cv_tile[cv]] = cv;
     for (int32_t c = 0; c < nc; ++c) {
         const int64_t off = sim->cv_offset[c];
         const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
@@ -827,71 +1161,82 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             }
         }
     }
+    // on-chip voltage slots (shared-memory packs): in tile-slot order
+    std::vector<int32_t> vslot_of_cv(ncv, -1);
+    {
+        std::vector<char> need(ne, 0);
+        for (int64_t cv = 0; cv < ncv; ++cv) {
+            if (cv_has_mech[cv]) need[pl.cv_tile[cv]] = 1;
+            const int32_t c = cell_of[cv];
+            const int32_t pi = sim->parent[cv];
+            if (pi >= 0 && pl.pslot[pl.cv_tile[cv]] >= 0) need[pl.cv_tile[sim->cv_offset[c] + pi]] = 1;
+        }
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            const PackDesc& pd = pl.packs[pi];
+            if (!pd.smem) continue;
+            int32_t next = 0;
+            for (int64_t t = (int64_t)pd.row0 * kWarp; t < ((int64_t)pd.row0 + pd.nrow) * kWarp; ++t)
+                if (need[t]) pl.vmap[t] = next++;            // own slot in the low 16 bits (for now)
+            if (next != pd.nvc) return bad("internal error: on-chip voltage count");
+        }
+        std::vector<int32_t> tile_cv(ne, -1);
+        for (int64_t cv = 0; cv < ncv; ++cv) tile_cv[pl.cv_tile[cv]] = (int32_t)cv;
+        for (int64_t cv = 0; cv < ncv; ++cv) {
+            const int64_t t = pl.cv_tile[cv];
+            if (pl.packs[pl.cv_pack[cv]].smem && pl.vmap[t] >= 0) vslot_of_cv[cv] = pl.vmap[t];
+        }
+        for (int64_t t = 0; t < ne; ++t) {
+            const int32_t cv = tile_cv[t];
+            uint32_t own = 0xFFFF, par = 0xFFFF;
+            if (cv >= 0 && pl.packs[pl.cv_pack[cv]].smem) {
+                if (vslot_of_cv[cv] >= 0) own = (uint32_t)vslot_of_cv[cv];
+                if (pl.pslot[t] >= 0) {
+                    const int32_t c = cell_of[cv];
+                    par = (uint32_t)vslot_of_cv[sim->cv_offset[c] + sim->parent[cv]];
+                }
+            }
+            pl.vmap[t] = (int32_t)(own | (par << 16));
+        }
+    }
+
+    // ------------------------------------------------------------------ schedule check
+    // Every hand-over between lanes must cross a round boundary, and within one round at most
+    // one lane may add into a given parent slot; violations would be data races in the kernel.
+    for (int32_t pi = 0; pi < npk; ++pi) {
+        const PackDesc& pd = pl.packs[pi];
+        const int64_t base = (int64_t)pd.row0 * kWarp;
+        const int R = pd.round_rows;
+        std::vector<std::pair<int64_t, int64_t>> targets;   // (round, target slot) of remote writes
+        for (int64_t j = 0; j < pd.nrow; ++j)
+            for (int l = 0; l < kWarp; ++l) {
+                const int64_t t = base + j * kWarp + l;
+                const int32_t ps = pl.pslot[t];
+                if (ps < 0) continue;
+                const int64_t jp = ps / kWarp, lp = ps % kWarp;
+                const bool ok = (R == 0) ? (lp == l && jp > j) : (jp / R > j / R);
+                if (!ok) return bad("internal error: solve schedule hands over within a round (pack " + std::to_string(pi) + ")");
+                if (R > 0) targets.push_back({j / R, ps});
+            }
+        std::sort(targets.begin(), targets.end());
+        for (size_t i = 1; i < targets.size(); ++i)
+            if (targets[i] == targets[i - 1]) return bad("internal error: two lanes write one parent in a round");
+    }
 
     // ------------------------------------------------------------------ mechanisms per pack
-    // Mechanism entries may sit on any lane: the loops touch S only through tile slots.
-    // Synapses (and clamps) on one CV stay on one lane so that no two lanes update the same
-    // slot within a loop.
-    const int32_t nsyn = (int32_t)sim->syn_cv.size();
-    std::vector<std::vector<int32_t>> pk_syn(npk), pk_hh(npk), pk_st(npk);
-    for (int32_t i = 0; i < nsyn; ++i) pk_syn[pl.cv_pack[sim->syn_cv[i]]].push_back(i);
-    for (size_t i = 0; i < sim->hh_cv.size(); ++i) pk_hh[pl.cv_pack[sim->hh_cv[i]]].push_back((int32_t)i);
-    for (size_t i = 0; i < sim->st_cv.size(); ++i) pk_st[pl.cv_pack[sim->st_cv[i]]].push_back((int32_t)i);
-    // lane assignment of grouped items: groups by CV, largest first, onto the least loaded lane
-    auto assign_grouped = [&](const std::vector<int32_t>& items, const std::vector<int64_t>& item_cv,
-                              std::array<std::vector<int32_t>, 32>& lanes) {
-        std::vector<std::pair<int64_t, std::vector<int32_t>>> grp;
-        {
-            std::vector<int32_t> it = items;
-            std::stable_sort(it.begin(), it.end(), [&](int32_t a, int32_t b) { return item_cv[a] < item_cv[b]; });
-            for (size_t i = 0; i < it.size(); ++i) {
-                if (i == 0 || item_cv[it[i]] != item_cv[it[i - 1]]) grp.push_back({item_cv[it[i]], {}});
-                grp.back().second.push_back(it[i]);
-            }
-        }
-        std::stable_sort(grp.begin(), grp.end(), [](const auto& a, const auto& b) { return a.second.size() > b.second.size(); });
-        std::array<int64_t, 32> load{};
-        for (auto& g : grp) {
-            int best = 0;
-            for (int l = 1; l < 32; ++l) if (load[l] < load[best]) best = l;
-            for (int32_t x : g.second) lanes[best].push_back(x);
-            load[best] += (int64_t)g.second.size();
-        }
-    };
-    pl.syn_entry.assign(nsyn, -1);
-    pl.syn_owner.assign(nsyn, 0);
-    pl.syn_js.assign(nsyn, 0);
-    pl.hh_entry.assign(sim->hh_cv.size(), -1);
-    std::vector<int64_t> syn_cv_tmp(sim->syn_cv), st_cv_tmp(sim->st_cv);
-    int64_t syn_rows = 0, hh_rows = 0, st_rows = 0;
-    std::vector<std::array<std::vector<int32_t>, 32>> syn_lanes(npk), st_lanes(npk);
-    for (int32_t pi = 0; pi < npk; ++pi) {
-        assign_grouped(pk_syn[pi], syn_cv_tmp, syn_lanes[pi]);
-        assign_grouped(pk_st[pi], st_cv_tmp, st_lanes[pi]);
-        size_t ms = 0, mt = 0;
-        for (int l = 0; l < 32; ++l) { ms = std::max(ms, syn_lanes[pi][l].size()); mt = std::max(mt, st_lanes[pi][l].size()); }
-        PackDesc& pd = pl.packs[pi];
-        pd.syn_row0 = (int32_t)syn_rows;
-        pd.nsyn_row = (int32_t)ms;
-        syn_rows += (int64_t)ms;
-        pd.hh_row0 = (int32_t)hh_rows;
-        pd.nhh_row = (int32_t)((pk_hh[pi].size() + 31) / 32);
-        hh_rows += pd.nhh_row;
-        pd.st_row0 = (int32_t)st_rows;
-        pd.nst_row = (int32_t)mt;
-        st_rows += (int64_t)mt;
-        pd.ncell = 0;
-        pd.pr0 = 0;
-        pd.npr = 0;
-    }
     pl.syn_rows = syn_rows;
     pl.hh_rows = hh_rows;
     pl.st_rows = st_rows;
+    pl.syn_entry.assign(nsyn_all, -1);
+    pl.syn_owner.assign(nsyn_all, 0);
+    pl.syn_js.assign(nsyn_all, 0);
+    pl.hh_entry.assign(sim->hh_cv.size(), -1);
     pl.syn_slot.assign(syn_rows * kWarp, -1);
+    pl.syn_vs.assign(syn_rows * kWarp, -1);
     pl.syn_e.assign(syn_rows * kWarp, 0.0);
     pl.syn_decay.assign(syn_rows * kWarp, 0.0);
     pl.syn_sc.assign(syn_rows * kWarp, 0.0);
     pl.hh_slot.assign(hh_rows * kWarp, -1);
+    pl.hh_vs.assign(hh_rows * kWarp, -1);
     pl.hh_sc.assign(hh_rows * kWarp, 0.0);
     pl.hh_gna.assign(hh_rows * kWarp, 0.0);
     pl.hh_gk.assign(hh_rows * kWarp, 0.0);
@@ -903,15 +1248,18 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     pl.det_slot.assign((size_t)npk * kWarp, -1);
     pl.det_gid.assign((size_t)npk * kWarp, -1);
     for (int32_t pi = 0; pi < npk; ++pi) {
-        PackDesc& pd = pl.packs[pi];
+        const PackDesc& pd = pl.packs[pi];
+        const Group& G = groups[pi];
         const int64_t base = (int64_t)pd.row0 * kWarp;
+        auto vread = [&](int64_t cv) { return pd.smem ? vslot_of_cv[cv] : (int32_t)(pl.cv_tile[cv] - base); };
         for (int l = 0; l < 32; ++l) {
-            const auto& v = syn_lanes[pi][l];
+            const auto& v = G.syn_l[l];
             for (size_t r = 0; r < v.size(); ++r) {
                 const int32_t i = v[r];
                 const int64_t q = ((int64_t)pd.syn_row0 + (int64_t)r) * kWarp + l;
                 const int64_t cv = sim->syn_cv[i];
                 pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+                pl.syn_vs[q] = vread(cv);
                 pl.syn_e[q] = sim->syn_e[i];
                 pl.syn_decay[q] = std::exp(-p.dt / sim->syn_tau[i]);
                 pl.syn_sc[q] = invd[cv];
@@ -919,7 +1267,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 pl.syn_owner[i] = pi * kWarp + l;
                 pl.syn_js[i] = (int32_t)r;
             }
-            const auto& w = st_lanes[pi][l];
+            const auto& w = G.st_l[l];
             for (size_t r = 0; r < w.size(); ++r) {
                 const int32_t i = w[r];
                 const int64_t q = ((int64_t)pd.st_row0 + (int64_t)r) * kWarp + l;
@@ -931,23 +1279,24 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 pl.st_amp[q] = sim->st_amp[i];
             }
         }
-        for (size_t r = 0; r < pk_hh[pi].size(); ++r) {
-            const int32_t i = pk_hh[pi][r];
+        for (size_t r = 0; r < G.hh.size(); ++r) {
+            const int32_t i = G.hh[r];
             const int64_t q = ((int64_t)pd.hh_row0 + (int64_t)(r / 32)) * kWarp + (int64_t)(r % 32);
             const int64_t cv = sim->hh_cv[i];
             pl.hh_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
+            pl.hh_vs[q] = vread(cv);
             pl.hh_sc[q] = invd[cv];
             pl.hh_gna[q] = hh_gna[i];
             pl.hh_gk[q] = hh_gk[i];
             pl.hh_entry[i] = q;
         }
-        const std::vector<int32_t>& g = groups[porder[pi]];
-        pd.ncell = (int32_t)g.size();
-        for (size_t d = 0; d < g.size(); ++d) {
-            pl.det_slot[(size_t)pi * kWarp + d] = (int32_t)(pl.cv_tile[sim->det_cv[g[d]]] - base);
-            pl.det_gid[(size_t)pi * kWarp + d] = g[d];
+        for (size_t d = 0; d < G.cells.size(); ++d) {
+            pl.det_slot[(size_t)pi * kWarp + d] = vread(sim->det_cv[G.cells[d]]);
+            pl.det_gid[(size_t)pi * kWarp + d] = G.cells[d];
         }
     }
+    }   // tile packs
+
     // initial gates
     {
         double mi, hi, ni;
@@ -981,8 +1330,9 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
 void arb_destroy(arb_sim* sim) {
     if (!sim) return;
     if (sim->bound) {
-        for (int g = 0; g < kGraphRing; ++g) {
+        for (int g = 0; g < 3; ++g)
             if (sim->graph[g]) cudaGraphExecDestroy(sim->graph[g]);
+        for (int g = 0; g < kGraphRing; ++g) {
             if (sim->t0[g]) cudaEventDestroy(sim->t0[g]);
             if (sim->t1[g]) cudaEventDestroy(sim->t1[g]);
         }
@@ -1022,26 +1372,37 @@ arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_ro
 static arb_status upload_mech_state(arb_sim* sim, const std::vector<double>& m, const std::vector<double>& h,
                                     const std::vector<double>& n, const std::vector<double>& g);
 
+// One epoch = three captured graphs: the event-delivery kernels, the epoch kernel and the
+// spike exchange. Timing events are recorded between the graph launches, on the library's
+// stream, so the epoch kernel's own duration is measured with CUDA events.
+static arb_status capture_one(arb_sim* sim, int which, cudaGraphExec_t* out) {
+    if (*out) { cudaGraphExecDestroy(*out); *out = nullptr; }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(sim->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaSuccess;
+    if (which == 0) e1 = launch_events_pre(sim->ev_args, sim->n_sm, sim->s);
+    else if (which == 1 && sim->plan.stream)
+        e1 = sim->mixed ? launch_stream<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.stack_depth, sim->s)
+                        : launch_stream<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.stack_depth, sim->s);
+    else if (which == 1)
+        e1 = sim->mixed ? launch_epoch<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
+                        : launch_epoch<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
+    else e1 = launch_events_post(sim->spk_args, sim->n_sm, sim->s);
+    cudaError_t e2 = cudaStreamEndCapture(sim->s, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(sim, ARB_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+    cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    return ARB_OK;
+}
+
 static arb_status capture_graphs(arb_sim* sim) {
-    for (int gi = 0; gi < kGraphRing; ++gi) {
-        if (sim->graph[gi]) { cudaGraphExecDestroy(sim->graph[gi]); sim->graph[gi] = nullptr; }
-        cudaGraph_t g = nullptr;
-        CU(cudaStreamBeginCapture(sim->s, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = launch_events_pre(sim->ev_args, sim->n_sm, sim->s);
-        cudaError_t e2 = cudaEventRecord(sim->t0[gi], sim->s);
-        cudaError_t e3 = sim->mixed ? launch_epoch<float>(sim->dm32, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
-                                    : launch_epoch<double>(sim->dm64, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
-        cudaError_t e4 = cudaEventRecord(sim->t1[gi], sim->s);
-        cudaError_t e5 = launch_events_post(sim->spk_args, sim->n_sm, sim->s);
-        cudaError_t e6 = cudaStreamEndCapture(sim->s, &g);
-        for (cudaError_t e : {e1, e2, e3, e4, e5, e6})
-            if (e != cudaSuccess) {
-                if (g) cudaGraphDestroy(g);
-                return fail(sim, ARB_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-            }
-        cudaError_t ei = cudaGraphInstantiate(&sim->graph[gi], g, 0);
-        cudaGraphDestroy(g);
-        if (ei != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    for (int w = 0; w < 3; ++w) {
+        arb_status st = capture_one(sim, w, &sim->graph[w]);
+        if (st != ARB_OK) return st;
     }
     return ARB_OK;
 }
@@ -1073,10 +1434,10 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     arb_status st;
 #define UP(name, vec) if ((st = up(sim, name, vec)) != ARB_OK) return st
     UP("packs", pl.packs);
-    UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot);
+    UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot); UP("vmap", pl.vmap);
     UP("V", pl.V0);
-    UP("syn_slot", pl.syn_slot); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
-    UP("hh_slot", pl.hh_slot); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
+    UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
+    UP("hh_slot", pl.hh_slot); UP("hh_vs", pl.hh_vs); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
     UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
     UP("det_slot", pl.det_slot); UP("det_gid", pl.det_gid);
     UP("syn_owner", pl.syn_owner); UP("syn_js", pl.syn_js);
@@ -1132,13 +1493,26 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     b.pool_cap = sim->prm.event_capacity;
     b.dt = sim->prm.dt;
     // launch shape of the persistent epoch kernel
+    if (pl.stream) {
+        sim->warps_per_cta = 8;
+        int bps = 0;
+        cudaError_t eo = sim->mixed ? stream_occupancy<float>(sim->implicit, sim->warps_per_cta, pl.stack_depth, &bps)
+                                    : stream_occupancy<double>(sim->implicit, sim->warps_per_cta, pl.stack_depth, &bps);
+        if (eo != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("stream kernel occupancy: ") + cudaGetErrorString(eo));
+        if (bps < 1) return fail(sim, ARB_E_CUDA, "stream kernel does not fit on an SM");
+        sim->grid = sim->n_sm * bps;
+        st = capture_graphs(sim);
+        if (st != ARB_OK) return st;
+        CU(cudaStreamSynchronize(sim->s));
+        return ARB_OK;
+    }
     const bool any_smem = pl.smem_packs > 0;
     sim->warps_per_cta = any_smem ? (int)std::max<int64_t>(1, (int64_t)(227 * 1024 / 8) / std::max(1, pl.tile_doubles)) : 4;
     sim->warps_per_cta = std::min(sim->warps_per_cta, 8);
     if (!any_smem) sim->plan.tile_doubles = 0;
     int bps = 0;
-    cudaError_t eo = sim->mixed ? epoch_occupancy<float>(sim->warps_per_cta, sim->plan.tile_doubles, &bps)
-                                : epoch_occupancy<double>(sim->warps_per_cta, sim->plan.tile_doubles, &bps);
+    cudaError_t eo = sim->mixed ? epoch_occupancy<float>(sim->implicit, sim->warps_per_cta, sim->plan.tile_doubles, &bps)
+                                : epoch_occupancy<double>(sim->implicit, sim->warps_per_cta, sim->plan.tile_doubles, &bps);
     if (eo != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("epoch kernel occupancy: ") + cudaGetErrorString(eo));
     if (bps < 1) return fail(sim, ARB_E_CUDA, "epoch kernel does not fit on an SM");
     sim->grid = sim->n_sm * bps;
@@ -1242,7 +1616,11 @@ arb_status arb_advance(arb_sim* sim, double t_end) {
             ms_sum += ms;
             sim->pending_time[g] = false;
         }
-        CU(cudaGraphLaunch(sim->graph[g], sim->s));
+        CU(cudaGraphLaunch(sim->graph[0], sim->s));
+        CU(cudaEventRecord(sim->t0[g], sim->s));
+        CU(cudaGraphLaunch(sim->graph[1], sim->s));
+        CU(cudaEventRecord(sim->t1[g], sim->s));
+        CU(cudaGraphLaunch(sim->graph[2], sim->s));
         sim->pending_time[g] = true;
         sim->graph_replays++;
     }

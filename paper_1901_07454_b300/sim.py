@@ -60,7 +60,7 @@ class Plan:
 
     def __init__(self, model, dt=0.025, epoch_steps=0, precision="fp64", cells_per_pack=0, smem_budget=0,
                  event_capacity=None, ext_event_capacity=None, spike_capacity=None, bucket_capacity=None,
-                 stream=None):
+                 stream=None, scheme="implicit"):
         lib = L.load()
         self.model = model
         p = default_params()
@@ -69,6 +69,9 @@ class Plan:
         p.precision = L.ARB_MIXED if precision == "mixed" else L.ARB_FP64
         p.cells_per_pack = int(cells_per_pack)
         p.smem_budget = int(smem_budget)
+        if scheme not in ("implicit", "explicit"):
+            raise ValueError("scheme must be 'implicit' or 'explicit'")
+        p.scheme = L.ARB_EXPLICIT if scheme == "explicit" else L.ARB_IMPLICIT
         if event_capacity is not None:
             p.event_capacity = int(event_capacity)
         if ext_event_capacity is not None:
@@ -118,6 +121,8 @@ class Simulation(Plan):
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise RuntimeError("Simulation needs a CUDA device; there is no CPU fallback")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         torch.cuda.set_device(self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         super().__init__(model, dt=dt, stream=C.c_void_p(self.stream.cuda_stream), **kw)
