@@ -185,7 +185,34 @@ arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_ro
  * number of kernel launches it issued. Requires arb_params timing (always on). */
 arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t* launches);
 
+/* Message of the last failing call on this handle; with NULL, of the last failing call on
+ * this thread that has no handle (arb_create, arb_solve_trees_noalloc). */
 const char* arb_last_error(const arb_sim* sim);
+
+/* Tree solve that allocates no memory. The paper has no counterpart to this entry point; it
+ * serves callers that cannot call cudaMalloc where they need a solve: code that runs while a
+ * stream is being captured into a CUDA graph, host callbacks, or runtimes whose device memory
+ * pool is fixed up front.
+ *
+ * For each of n_cells cells it solves the symmetric tree system of the implicit Euler step
+ * (Sec. "Model"): diagonal d[i], off-diagonal a[i] at (i, parent(i)) and (parent(i), i),
+ * right-hand side b[i], solution x[i], by elimination from the leaves and back substitution
+ * (Hines' extension of the Thomas algorithm). All arrays are caller-owned DEVICE memory, in the
+ * layout of arb_model: cv_offset [n_cells+1] (cv_offset[0] = 0, n_cv = cv_offset[n_cells]),
+ * parent [n_cv] cell-local with parent of a cell's first CV = -1 and 0 <= parent[i] < i
+ * otherwise (a cell that breaks this gets NaN in x), d, a, b, x [n_cv] (a of a first CV unused).
+ * The launch goes on `stream` (cudaStream_t, 0 = legacy default) and is asynchronous.
+ *
+ * Scratch: a fixed array of 262,144 CVs x 16 bytes (4 MiB) in the library's device memory,
+ * which every GPU that loads the library holds until the process exits. Larger n_cv returns
+ * ARB_E_ARG (message via arb_last_error(NULL)). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) for that device; make that first call before
+ * any stream capture. Every call reuses the same array: calls whose kernels overlap on the GPU
+ * (different streams, or several devices sharing a context) race and must be serialised by
+ * the caller. Nothing from an earlier call is read; nothing needs clearing. */
+arb_status arb_solve_trees_noalloc(int32_t n_cells, int64_t n_cv, const int64_t* cv_offset,
+                                   const int32_t* parent, const double* d, const double* a,
+                                   const double* b, double* x, void* stream);
 
 #ifdef __cplusplus
 }

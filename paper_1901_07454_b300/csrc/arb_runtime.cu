@@ -158,7 +158,7 @@ struct arb_sim {
 
 namespace {
 
-thread_local std::string g_create_error;
+thread_local std::string g_create_error;   // errors of calls without a handle
 
 arb_status fail(arb_sim* s, arb_status st, const std::string& msg) {
     if (s) s->err = msg;
@@ -386,6 +386,10 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
 }
 
 }  // namespace
+
+namespace arbk {
+void set_handle_free_error(const std::string& msg) { g_create_error = msg; }
+}
 
 static void layout_regions(arb_sim* sim) {
     const Plan& pl = sim->plan;
