@@ -60,15 +60,14 @@ __device__ __forceinline__ float gate(float x, float a, float b, float dt) {
     return xinf + (x - xinf) * expf(-dt * s);
 }
 
-// 1/x for the positive pivots of the implicit scheme: hardware estimate, then two
-// Newton-Raphson steps r <- r + r (1 - x r), each doubling the number of correct bits.
+// 1/x for the positive pivots of the implicit scheme: the hardware estimate (about 20 correct
+// bits) refined by one third-order step, r <- r + r (e + e^2) with e = 1 - x r, which triples
+// the number of correct bits (error e^3).
 __device__ __forceinline__ double rcp_nr(double x) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -502,33 +501,85 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         }
     }
     __syncwarp();
+    // the lane's next event, kept in registers
     while (apply_step >= 0 && ev_i < ev_end && d.ev[ev_i].step_rel < apply_step) { ++ev_i; late = 1; }
-#pragma unroll 4
-    for (int js = 0; js < pk.nsyn_row; ++js) {
-        const size_t q = (size_t)(pk.syn_row0 + js) * kWarp + lane;
-        const int sl = __ldg(d.syn_slot + q);
-        if (sl < 0) continue;
-        const int idx = js * kWarp + lane;
-        MT g = gS[idx];
-        if (decay) g = g * (MT)__ldg(d.syn_decay + q);
-        if (apply_step >= 0) {
-            while (ev_i < ev_end && d.ev[ev_i].step_rel == apply_step && d.ev[ev_i].js == js) {
-                g = g + (MT)d.ev[ev_i].w;
+    int n_step = 0x7fffffff, n_js = -1;
+    double n_w = 0.0;
+    if (apply_step >= 0 && ev_i < ev_end) {
+        const EvRec r = d.ev[ev_i];
+        n_step = r.step_rel;
+        n_js = r.js;
+        n_w = r.w;
+    }
+    // synapses of one CV are consecutive on one lane: their terms are summed in registers and
+    // stored once per CV. Rows are fetched kSP ahead so that no load is waited for in the row
+    // that issued it.
+    constexpr int kSP = 4;
+    int cur = -1;
+    double gsum = 0.0, esum = 0.0;
+    int s_sl[kSP], s_c[kSP];
+    double s_dec[kSP], s_e[kSP], s_sc[kSP];
+    MT s_g[kSP];
+    auto sfetch = [&](int js, int u) {
+        const bool in = js < pk.nsyn_row;
+        const size_t q = (size_t)(pk.syn_row0 + (in ? js : 0)) * kWarp + lane;
+        s_sl[u] = in ? __ldg(d.syn_slot + q) : -1;
+        s_c[u] = in ? __ldg(d.syn_vs + q) : -1;
+        s_dec[u] = in ? __ldg(d.syn_decay + q) : 1.0;
+        s_e[u] = in ? __ldg(d.syn_e + q) : 0.0;
+        s_sc[u] = (in && !kImp) ? __ldg(d.syn_sc + q) : 0.0;
+        s_g[u] = in ? gS[(in ? js : 0) * kWarp + lane] : (MT)0;
+    };
+#pragma unroll
+    for (int u = 0; u < kSP; ++u) sfetch(u, u);
+    for (int jb = 0; jb < pk.nsyn_row; jb += kSP) {
+#pragma unroll
+        for (int u = 0; u < kSP; ++u) {
+            const int js = jb + u;
+            if (js >= pk.nsyn_row) break;
+            const int sl = s_sl[u], c = s_c[u];
+            const double dec = s_dec[u], esyn = s_e[u], sc = s_sc[u];
+            MT g = s_g[u];
+            sfetch(js + kSP, u);
+            if (sl < 0) continue;
+            if (decay) g = g * (MT)dec;
+            while (n_step == apply_step && n_js == js) {
+                g = g + (MT)n_w;
                 ++ev_i;
+                if (ev_i < ev_end) {
+                    const EvRec r = d.ev[ev_i];
+                    n_step = r.step_rel;
+                    n_js = r.js;
+                    n_w = r.w;
+                } else {
+                    n_step = 0x7fffffff;
+                }
+            }
+            gS[js * kWarp + lane] = g;
+            if (terms) {
+                if (c != cur) {
+                    if (cur >= 0) {
+                        if (kImp) Gm[cur] = gsum;
+                        Em[cur] = esum;
+                    }
+                    cur = c;
+                    gsum = 0.0;
+                    esum = 0.0;
+                }
+                if constexpr (kImp) {
+                    const double gd = (double)g;
+                    gsum += gd;
+                    esum = fma(gd, esyn, esum);
+                } else {
+                    const MT i_syn = g * (MT)(Vg[sl] - esyn);
+                    esum = fma(-sc, (double)i_syn, esum);
+                }
             }
         }
-        gS[idx] = g;
-        if (terms) {
-            const int c = __ldg(d.syn_vs + q);
-            if constexpr (kImp) {
-                const double gd = (double)g;
-                Gm[c] += gd;
-                Em[c] = fma(gd, __ldg(d.syn_e + q), Em[c]);
-            } else {
-                const MT i_syn = g * (MT)(Vg[sl] - __ldg(d.syn_e + q));
-                Em[c] = fma(-__ldg(d.syn_sc + q), (double)i_syn, Em[c]);
-            }
-        }
+    }
+    if (terms && cur >= 0) {
+        if (kImp) Gm[cur] = gsum;
+        Em[cur] = esum;
     }
     __syncwarp();
     for (int jh = 0; jh < pk.nhh_row; ++jh) {
@@ -565,7 +616,8 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     __syncwarp();
 }
 
-constexpr int kPF = 4;   // rows prefetched ahead in the streamed sweeps
+constexpr int kPF = 4;    // rows prefetched ahead in the streamed forward sweep
+constexpr int kPB = 16;   // rows prefetched ahead in the streamed back substitution (light rows)
 
 template <class MT, bool kImp>
 __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, int64_t k0, int nsteps, int lane) {
@@ -622,13 +674,15 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
         {
             int sp = 0;
             double yprev = 0.0, kprev = 0.0, eprev = 0.0;
+            // rows are fetched kPF ahead; the compact mechanism slot of a row is fetched 2*kPF
+            // ahead so that the load of its terms never waits on the index load
             double pv[kPF], pa[kPF], pb[kPF], pk_[kPF], pe[kPF], pg[kPF], pm[kPF];
-            int pf[kPF];
-            auto fetch = [&](int j, int u) {
+            int pf[kPF], pc[kPF];
+            auto fetch_c = [&](int j) { return j < J ? __ldg(cm_ + (size_t)j * kWarp) : -1; };
+            auto fetch = [&](int j, int u, int c) {
                 const bool in = j < J;
                 const size_t o = (size_t)(in ? j : 0) * kWarp;
-                const int c = in ? __ldg(cm_ + o) : -1;
-                pv[u] = in ? Vg[j * kWarp + lane] : 0.0;
+                pv[u] = in ? Vg[(in ? j : 0) * kWarp + lane] : 0.0;
                 pa[u] = in ? __ldg(ca + o) : 0.0;
                 pb[u] = in ? __ldg(cb + o) : 0.0;
                 pk_[u] = in ? __ldg(ck + o) : 0.0;
@@ -637,8 +691,15 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                 pg[u] = (c >= 0 && kImp) ? Gm[c] : 0.0;
                 pm[u] = c >= 0 ? Em[c] : 0.0;
             };
+            {
+                int c0[kPF];
 #pragma unroll
-            for (int u = 0; u < kPF; ++u) fetch(u, u);
+                for (int u = 0; u < kPF; ++u) c0[u] = fetch_c(u);
+#pragma unroll
+                for (int u = 0; u < kPF; ++u) pc[u] = fetch_c(kPF + u);
+#pragma unroll
+                for (int u = 0; u < kPF; ++u) fetch(u, u, c0[u]);
+            }
             for (int jb = 0; jb < J; jb += kPF) {
 #pragma unroll
                 for (int u = 0; u < kPF; ++u) {
@@ -646,7 +707,8 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                     if (j < J) {
                         const double V = pv[u], A = pa[u], Bc = pb[u], K = pk_[u], E = pe[u], G = pg[u], M = pm[u];
                         const int f = pf[u];
-                        fetch(j + kPF, u);   // refill this slot for row j + kPF
+                        fetch(j + kPF, u, pc[u]);        // row j + kPF, its slot index is ready
+                        pc[u] = fetch_c(j + 2 * kPF);    // slot index of row j + 2 kPF
                         const int sl = j * kWarp + lane;
                         if constexpr (kImp) {
                             double dd = fma(-kprev, eprev, E + G);
@@ -683,8 +745,8 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
         {
             int sp = 0;
             double vnext = 0.0;
-            double pu[kPF], px[kPF];
-            int pf[kPF];
+            double pu[kPB], px[kPB];
+            int pf[kPB];
             auto fetch = [&](int j, int u) {
                 const bool in = j >= 0;
                 const size_t o = (size_t)(in ? j : 0) * kWarp;
@@ -693,15 +755,15 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                 pf[u] = in ? __ldg(fl + o) : kFlagRoot;
             };
 #pragma unroll
-            for (int u = 0; u < kPF; ++u) fetch(J - 1 - u, u);
-            for (int jt = J - 1; jt >= 0; jt -= kPF) {
+            for (int u = 0; u < kPB; ++u) fetch(J - 1 - u, u);
+            for (int jt = J - 1; jt >= 0; jt -= kPB) {
 #pragma unroll
-                for (int u = 0; u < kPF; ++u) {
+                for (int u = 0; u < kPB; ++u) {
                     const int j = jt - u;
                     if (j >= 0) {
                         const double U = pu[u], X = px[u];
                         const int f = pf[u];
-                        fetch(j - kPF, u);
+                        fetch(j - kPB, u);
                         double vp;
                         if (f & kFlagRoot) vp = 0.0;
                         else if (f & kFlagRemote) vp = stk[(--sp) * kWarp + lane].x;
