@@ -64,7 +64,10 @@ typedef struct {
                                     32 = one cell per lane, 1..31 = cells sharing one warp */
     int32_t smem_budget;         /* bytes of shared memory per warp for state tiles; 0 = default */
     int32_t scheme;              /* ARB_IMPLICIT (default) or ARB_EXPLICIT */
-    int32_t reserved;            /* must be 0 */
+    int32_t split_cvs;           /* cells_per_pack 32 only: a cell with more CVs than this is spread
+                                    over several lanes (chains scheduled in rounds, hand-overs
+                                    through shared memory); 0 = threshold chosen by the library
+                                    from the load of a warp slot, -1 = never spread */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */
@@ -176,10 +179,14 @@ arb_status arb_get_state(arb_sim* sim, double* V, double* m, double* h, double* 
 arb_status arb_set_state(arb_sim* sim, const double* V, const double* m, const double* h,
                          const double* n, const double* g);
 
-/* Packing summary: number of packs (warp programs), solve rows, lanes, and the fraction of
- * lane-rows that carry a CV. Valid after arb_create. */
+/* Packing summary, valid after arb_create (any pointer may be NULL): number of packs (warp
+ * programs); solve rows over all packs and in the longest pack; packs that use shared memory
+ * (state tiles, or in streamed plans the mailbox of cells spread over lanes); the fraction of
+ * lane-rows that carry a CV; steps per epoch; cells per pack (32 = streamed plan); and the
+ * CV count above which a cell is spread over several lanes (-1 = none). */
 arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_rows,
-                         int64_t* smem_packs, double* lane_efficiency, int32_t* epoch_steps);
+                         int64_t* smem_packs, double* lane_efficiency, int32_t* epoch_steps,
+                         int64_t* max_pack_rows, int32_t* cells_per_pack, int64_t* split_cvs);
 
 /* Device time of the epoch kernel summed over the last arb_advance call, in ms, and the
  * number of kernel launches it issued. Requires arb_params timing (always on). */

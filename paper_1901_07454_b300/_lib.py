@@ -26,7 +26,7 @@ EXPORTED = ["arb_default_params", "arb_create", "arb_destroy", "arb_workspace_by
 class arb_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("epoch_steps", C.c_int32), ("precision", C.c_int32),
                 ("cells_per_pack", C.c_int32), ("smem_budget", C.c_int32),
-                ("scheme", C.c_int32), ("reserved", C.c_int32),
+                ("scheme", C.c_int32), ("split_cvs", C.c_int32),
                 ("event_capacity", C.c_int64), ("ext_event_capacity", C.c_int64),
                 ("spike_capacity", C.c_int64), ("bucket_capacity", C.c_int64), ("stream", C.c_void_p)]
 
@@ -75,7 +75,8 @@ def load():
         "arb_set_probes": (i32, [vp, i64, vp, vp, i64]),
         "arb_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
         "arb_set_state": (i32, [vp, vp, vp, vp, vp, vp]),
-        "arb_plan_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i32)]),
+        "arb_plan_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i32),
+                               C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]),
         "arb_last_timing": (i32, [vp, C.POINTER(dbl), C.POINTER(i64)]),
         "arb_last_error": (C.c_char_p, [vp]),
         "arb_solve_trees_noalloc": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, vp]),

@@ -30,6 +30,8 @@ struct PackDesc {
                          // streamed packs: compact mechanism slots (see vmap)
     int32_t stack;       // streamed packs: deepest per-lane hand-over stack (entries)
     int64_t c_off;       // streamed packs: offset of the pack's compact slots in Gm / Em
+    int32_t nmb;         // streamed shared packs: mailbox slots (cross-lane hand-overs)
+    int32_t pad2;
 };
 
 // Pack modes: staged in shared memory (small batches, several cells share a warp), or
@@ -40,6 +42,17 @@ enum : int32_t { kPackGlobal = 0, kPackSmem = 1, kPackStream = 2 };
 // stack (all but the one processed directly before the parent); bit 8: this entry's parent
 // is not the next row of its lane; bit 9: root.
 enum : int32_t { kFlagPopMask = 0xFF, kFlagRemote = 0x100, kFlagRoot = 0x200 };
+// Streamed shared packs (cells spread over several lanes, rounds of round_rows rows separated
+// by __syncwarp): no stack; hand-overs go through a per-warp mailbox in shared memory, and
+// the flags word also holds two 11-bit mailbox slots. out (bits 10..20): the slot this entry
+// adds its contribution to and reads its parent's voltage from; in (bits 21..31): the slot
+// that holds the contributions of this entry's handed-over children and where its voltage is
+// published for them. kMbNone = no slot.
+constexpr int32_t kMbNone = 0x7FF;
+constexpr int kMbOutShift = 10;
+constexpr int kMbInShift = 21;
+constexpr int kStreamWarps = 8;        // warps per CTA of the streamed kernel (one CTA per SM)
+constexpr int kStreamRound = 8;        // rows per round in streamed shared packs
 
 // Event delivered inside one epoch, bucketed per owner lane and sorted by
 // (step_rel, js, t, src, idx).

@@ -619,7 +619,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
 constexpr int kPF = 4;    // rows prefetched ahead in the streamed forward sweep
 constexpr int kPB = 16;   // rows prefetched ahead in the streamed back substitution (light rows)
 
-template <class MT, bool kImp>
+template <class MT, bool kImp, bool kShared>
 __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, int64_t k0, int nsteps, int lane) {
     const PackDesc pk = d.packs[p];
     const int J = pk.nrow;
@@ -639,7 +639,11 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
     const double* __restrict__ ce = d.ce + e0;
     const int32_t* __restrict__ fl = d.pslot + e0;
     const int32_t* __restrict__ cm_ = d.vmap + e0;
-    double2* stk = stack;   // [depth][32]
+    double2* stk = stack;   // [depth][32] (one cell per lane)
+    double* mbd = (double*)stack;           // mailbox (cells spread over lanes): [nmb] x (d, b, v)
+    double* mbb = mbd + pk.nmb;
+    double* mbv = mbb + pk.nmb;
+    const int R = kShared ? pk.round_rows : 0;
 
     const int owner = p * kWarp + lane;
     int ev_i = d.ev_off[owner];
@@ -672,7 +676,11 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
 
         // forward elimination, leaves to root, streaming rows
         {
-            int sp = 0;
+            if (kShared) {
+                for (int i = lane; i < pk.nmb; i += kWarp) { mbd[i] = 0.0; mbb[i] = 0.0; }
+                __syncwarp();
+            }
+            int sp = 0, left = R;
             double yprev = 0.0, kprev = 0.0, eprev = 0.0;
             // rows are fetched kPF ahead; the compact mechanism slot of a row is fetched 2*kPF
             // ahead so that the load of its terms never waits on the index load
@@ -705,18 +713,28 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                 for (int u = 0; u < kPF; ++u) {
                     const int j = jb + u;
                     if (j < J) {
+                        if (kShared && R > 0) {
+                            if (left == 0) { __syncwarp(); left = R; }
+                            --left;
+                        }
                         const double V = pv[u], A = pa[u], Bc = pb[u], K = pk_[u], E = pe[u], G = pg[u], M = pm[u];
                         const int f = pf[u];
                         fetch(j + kPF, u, pc[u]);        // row j + kPF, its slot index is ready
                         pc[u] = fetch_c(j + 2 * kPF);    // slot index of row j + 2 kPF
                         const int sl = j * kWarp + lane;
+                        const int mb_in = kShared ? (int)((unsigned)f >> kMbInShift) : kMbNone;
+                        const int mb_out = kShared ? ((f >> kMbOutShift) & kMbNone) : kMbNone;
                         if constexpr (kImp) {
                             double dd = fma(-kprev, eprev, E + G);
                             double bb = fma(kprev, yprev, fma(A, V, Bc) + M);
-                            for (int q = f & kFlagPopMask; q > 0; --q) {
-                                const double2 c2 = stk[(--sp) * kWarp + lane];
-                                dd -= c2.x;
-                                bb += c2.y;
+                            if (kShared) {
+                                if (mb_in != kMbNone) { dd -= mbd[mb_in]; bb += mbb[mb_in]; }
+                            } else {
+                                for (int q = f & kFlagPopMask; q > 0; --q) {
+                                    const double2 c2 = stk[(--sp) * kWarp + lane];
+                                    dd -= c2.x;
+                                    bb += c2.y;
+                                }
                             }
                             const double r = rcp_nr(dd);
                             const double uu = r * bb;
@@ -724,16 +742,26 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                             Bs[sl] = uu;
                             Rs[sl] = ee;
                             const bool remote = (f & kFlagRemote) != 0;
-                            if (remote && !(f & kFlagRoot)) stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                            if (remote && !(f & kFlagRoot)) {
+                                if (kShared) { mbd[mb_out] += K * ee; mbb[mb_out] += K * uu; }
+                                else stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                            }
                             kprev = remote ? 0.0 : K;
                             eprev = ee;
                             yprev = uu;
                         } else {
                             double y = fma(-kprev, yprev, fma(A, V, Bc) + M);
-                            for (int q = f & kFlagPopMask; q > 0; --q) y -= stk[(--sp) * kWarp + lane].x;
+                            if (kShared) {
+                                if (mb_in != kMbNone) y -= mbd[mb_in];
+                            } else {
+                                for (int q = f & kFlagPopMask; q > 0; --q) y -= stk[(--sp) * kWarp + lane].x;
+                            }
                             Bs[sl] = y;
                             const bool remote = (f & kFlagRemote) != 0;
-                            if (remote && !(f & kFlagRoot)) stk[(sp++) * kWarp + lane] = make_double2(K * y, 0.0);
+                            if (remote && !(f & kFlagRoot)) {
+                                if (kShared) mbd[mb_out] += K * y;
+                                else stk[(sp++) * kWarp + lane] = make_double2(K * y, 0.0);
+                            }
                             kprev = remote ? 0.0 : K;
                             yprev = y;
                         }
@@ -741,12 +769,14 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                 }
             }
         }
+        if (kShared) __syncwarp();
         // back substitution, root to leaves (preorder), streaming rows
         {
             int sp = 0;
             double vnext = 0.0;
             double pu[kPB], px[kPB];
             int pf[kPB];
+            int left = kShared ? ((R > 0) ? ((J - 1) % R) + 1 : 0) : 0;
             auto fetch = [&](int j, int u) {
                 const bool in = j >= 0;
                 const size_t o = (size_t)(in ? j : 0) * kWarp;
@@ -761,15 +791,24 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                 for (int u = 0; u < kPB; ++u) {
                     const int j = jt - u;
                     if (j >= 0) {
+                        if (kShared && R > 0) {
+                            if (left == 0) { __syncwarp(); left = R; }
+                            --left;
+                        }
                         const double U = pu[u], X = px[u];
                         const int f = pf[u];
                         fetch(j - kPB, u);
                         double vp;
                         if (f & kFlagRoot) vp = 0.0;
-                        else if (f & kFlagRemote) vp = stk[(--sp) * kWarp + lane].x;
+                        else if (f & kFlagRemote) vp = kShared ? mbv[(f >> kMbOutShift) & kMbNone] : stk[(--sp) * kWarp + lane].x;
                         else vp = vnext;
                         const double v = fma(X, vp, U);
-                        for (int q = f & kFlagPopMask; q > 0; --q) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                        if (kShared) {
+                            const int mb_in = (int)((unsigned)f >> kMbInShift);
+                            if (mb_in != kMbNone) mbv[mb_in] = v;
+                        } else {
+                            for (int q = f & kFlagPopMask; q > 0; --q) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                        }
                         Vg[j * kWarp + lane] = v;
                         if (last) bad |= !isfinite(v);
                         vnext = v;
@@ -823,11 +862,11 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
 }
 
 template <class MT, bool kImp>
-__global__ void __launch_bounds__(256, 1) arb_stream_kernel(DevModel<MT> d, int stack_depth) {
+__global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(DevModel<MT> d, int warp_smem_double2) {
     extern __shared__ double2 stk_smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    double2* stack = stk_smem + (size_t)wid * stack_depth * kWarp;
+    double2* stack = stk_smem + (size_t)wid * warp_smem_double2;
     const int64_t k0 = d.ctl->k0;
     const int nsteps = (int)(d.ctl->k1 - k0);
     for (;;) {
@@ -835,21 +874,22 @@ __global__ void __launch_bounds__(256, 1) arb_stream_kernel(DevModel<MT> d, int 
         if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= d.n_packs) break;
-        run_pack_stream<MT, kImp>(d, p, stack, k0, nsteps, lane);
+        if (d.packs[p].round_rows > 0) run_pack_stream<MT, kImp, true>(d, p, stack, k0, nsteps, lane);
+        else run_pack_stream<MT, kImp, false>(d, p, stack, k0, nsteps, lane);
     }
 }
 
 template <class MT>
-cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int stack_depth, cudaStream_t s) {
-    const size_t smem = (size_t)warps_per_cta * (size_t)stack_depth * kWarp * sizeof(double2);
-    if (implicit) arb_stream_kernel<MT, true><<<grid, warps_per_cta * kWarp, smem, s>>>(d, stack_depth);
-    else arb_stream_kernel<MT, false><<<grid, warps_per_cta * kWarp, smem, s>>>(d, stack_depth);
+cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int warp_smem_double2, cudaStream_t s) {
+    const size_t smem = (size_t)warps_per_cta * (size_t)warp_smem_double2 * sizeof(double2);
+    if (implicit) arb_stream_kernel<MT, true><<<grid, warps_per_cta * kWarp, smem, s>>>(d, warp_smem_double2);
+    else arb_stream_kernel<MT, false><<<grid, warps_per_cta * kWarp, smem, s>>>(d, warp_smem_double2);
     return cudaGetLastError();
 }
 
 template <class MT>
-cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int stack_depth, int* blocks_per_sm) {
-    const size_t smem = (size_t)warps_per_cta * (size_t)stack_depth * kWarp * sizeof(double2);
+cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm) {
+    const size_t smem = (size_t)warps_per_cta * (size_t)warp_smem_double2 * sizeof(double2);
     auto fn = implicit ? arb_stream_kernel<MT, true> : arb_stream_kernel<MT, false>;
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <numeric>
 #include <queue>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -30,9 +31,9 @@ cudaError_t launch_epoch(const DevModel<MT>& d, bool implicit, int grid, int war
 template <class MT>
 cudaError_t epoch_occupancy(bool implicit, int warps_per_cta, int tile_doubles, int* blocks_per_sm);
 template <class MT>
-cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int stack_depth, cudaStream_t s);
+cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int warp_smem_double2, cudaStream_t s);
 template <class MT>
-cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int stack_depth, int* blocks_per_sm);
+cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm);
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s);
 template <class T>
@@ -91,6 +92,8 @@ struct Plan {
     bool stream = false;                    // packs streamed from global memory (one cell per lane)
     int64_t c_total = 0;                    // streamed packs: compact mechanism slots
     int32_t stack_depth = 1;                // streamed packs: deepest hand-over stack
+    int64_t warp_smem = 32;                 // streamed packs: shared memory per warp (double2)
+    int64_t split_cvs = -1;                 // streamed packs: cells above this size are spread
 };
 
 struct Region {
@@ -553,6 +556,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         return bad("capacities must be >= 1");
     if (p.event_capacity > INT32_MAX || p.bucket_capacity > INT32_MAX) return bad("event and bucket capacities must be < 2^31");
     if (p.cells_per_pack < 0 || p.cells_per_pack > 32) return bad("cells_per_pack must be 0..32");
+    if (p.split_cvs < -1) return bad("split_cvs must be >= -1");
     sim->mixed = p.precision == ARB_MIXED;
     if (p.scheme != ARB_IMPLICIT && p.scheme != ARB_EXPLICIT) return bad("scheme must be ARB_IMPLICIT or ARB_EXPLICIT");
     sim->implicit = p.scheme == ARB_IMPLICIT;
@@ -905,49 +909,182 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     pl.stream = (kpp == 32);
     if (pl.stream) {
         // ---------------------------------------------------------- streamed packs
-        // 32 cells per pack (largest first), one per lane, every array in global memory.
-        const int32_t npk = (nc + 31) / 32;
+        // Every array in global memory. Cells up to split_cvs CVs run one per lane, 32 to a pack
+        // (largest first), their branch hand-overs on a per-lane stack. Larger cells are spread
+        // over the lanes of packs of a few cells: their unbranched chains are list-scheduled in
+        // rounds of kStreamRound rows, and hand-overs between chains go through a mailbox in
+        // shared memory. Spreading the largest cells keeps any one pack from running much longer
+        // than the average load of a warp slot.
+        struct SGroup {
+            std::vector<int32_t> cells;
+            PackRows rows;
+            bool shared = false;
+        };
+        const int64_t n_slots = (int64_t)n_sm * kStreamWarps;
+        const int64_t mb_max = std::min<int64_t>(kMbNone - 1, (227 * 1024 / kStreamWarps - 64) / 24);
+        std::vector<int64_t> ncv_of(nc), depth_of(nc);
+        for (int32_t c = 0; c < nc; ++c) {
+            ncv_of[c] = sim->cv_offset[c + 1] - sim->cv_offset[c];
+            const CellOrder& o = ord[c];
+            std::vector<int32_t> dep(o.dfs.size(), 1);
+            int64_t mx = 1;
+            for (size_t q = 1; q < o.dfs.size(); ++q) {
+                dep[q] = dep[o.dpar[q]] + 1;
+                mx = std::max<int64_t>(mx, dep[q]);
+            }
+            depth_of[c] = mx;
+        }
+        // branch points of a set of cells: an upper bound of its mailbox slots
+        auto branch_points = [&](const std::vector<int32_t>& cs) {
+            int64_t nb = 0;
+            for (int32_t c : cs) {
+                std::vector<int32_t> nch(ncv_of[c], 0);
+                for (size_t q = 1; q < ord[c].dfs.size(); ++q) nch[ord[c].dpar[q]]++;
+                for (int32_t x : nch) nb += x > 1;
+            }
+            return nb;
+        };
+        // greedy packs of large cells, about 0.8 x 32 x target CVs each; a pack whose schedule
+        // runs much past the target, or whose mailbox would not fit, is halved
+        std::function<void(const std::vector<int32_t>&, int64_t, std::vector<SGroup>&)> place_shared =
+            [&](const std::vector<int32_t>& cs, int64_t target, std::vector<SGroup>& out) {
+                SGroup G;
+                G.cells = cs;
+                G.shared = true;
+                const bool fits = branch_points(cs) <= mb_max;
+                if (fits) G.rows = schedule_shared(cs, ord, sim->cv_offset, kStreamRound);
+                if (cs.size() > 1 && (!fits || (double)G.rows.rows.size() > 1.25 * (double)target)) {
+                    const size_t h = cs.size() / 2;
+                    place_shared(std::vector<int32_t>(cs.begin(), cs.begin() + h), target, out);
+                    place_shared(std::vector<int32_t>(cs.begin() + h, cs.end()), target, out);
+                    return;
+                }
+                if (!fits) {   // one cell with more branch points than the mailbox holds
+                    G.shared = false;
+                    G.rows = schedule_affinity(cs, ord, sim->cv_offset);
+                }
+                out.push_back(std::move(G));
+            };
+        // rows of a pack of large cells, estimated without scheduling
+        auto est_shared = [&](const std::vector<int32_t>& big, int64_t target, std::vector<double>& cost) {
+            size_t i = 0;
+            while (i < big.size()) {
+                int64_t sum = 0, dep = 0;
+                size_t k = 0;
+                while (i + k < big.size() && k < 32) {
+                    const int64_t n = ncv_of[big[i + k]];
+                    if (k > 0 && (double)(sum + n) > 0.8 * 32.0 * (double)target) break;
+                    sum += n;
+                    dep = std::max(dep, depth_of[big[i + k]]);
+                    ++k;
+                }
+                cost.push_back(std::max((double)sum / (0.8 * 32.0), (double)(dep + kStreamRound)) * 1.1);
+                i += k;
+            }
+        };
+        auto makespan = [&](std::vector<double> c) {
+            std::sort(c.begin(), c.end(), std::greater<double>());
+            std::priority_queue<double, std::vector<double>, std::greater<double>> bins;
+            for (int64_t i = 0; i < n_slots; ++i) bins.push(0.0);
+            double ms = 0;
+            for (double x : c) {
+                const double b0 = bins.top() + x;
+                bins.pop();
+                bins.push(b0);
+                ms = std::max(ms, b0);
+            }
+            return ms;
+        };
+        std::vector<double> ucost;
+        for (int32_t i = 0; i < nc; i += 32) ucost.push_back((double)ncv_of[by_size[i]]);
+        int64_t split = p.split_cvs;
+        if (split == 0) {
+            // choose the threshold with the smallest estimated makespan over the warp slots
+            double sumJ = 0;
+            for (double x : ucost) sumJ += x;
+            const double avg = std::max(1.0, sumJ / (double)n_slots);
+            double best = makespan(ucost);
+            split = -1;
+            for (double f : {2.0, 1.5, 1.25, 1.0, 0.8}) {
+                const int64_t thr = std::max<int64_t>(1, (int64_t)(f * avg));
+                std::vector<int32_t> big, rest;
+                for (int32_t c : by_size) (ncv_of[c] > thr ? big : rest).push_back(c);
+                if (big.empty()) continue;
+                std::vector<double> cost;
+                for (size_t i = 0; i < rest.size(); i += 32) cost.push_back((double)ncv_of[rest[i]]);
+                est_shared(big, thr, cost);
+                const double ms = makespan(cost);
+                if (ms < best * 0.97) { best = ms; split = thr; }
+            }
+        }
+        std::vector<SGroup> sg;
+        {
+            std::vector<int32_t> big, rest;
+            for (int32_t c : by_size) ((split > 0 && ncv_of[c] > split) ? big : rest).push_back(c);
+            size_t i = 0;
+            while (i < big.size()) {
+                std::vector<int32_t> g;
+                int64_t sum = 0;
+                while (i < big.size() && g.size() < 32) {
+                    const int64_t n = ncv_of[big[i]];
+                    if (!g.empty() && (double)(sum + n) > 0.8 * 32.0 * (double)split) break;
+                    g.push_back(big[i]);
+                    sum += n;
+                    ++i;
+                }
+                place_shared(g, split, sg);
+            }
+            for (size_t r = 0; r < rest.size(); r += 32) {
+                SGroup G;
+                G.cells.assign(rest.begin() + r, rest.begin() + std::min(rest.size(), r + 32));
+                G.rows = schedule_affinity(G.cells, ord, sim->cv_offset);
+                sg.push_back(std::move(G));
+            }
+        }
+        // the persistent kernel takes packs in order: longest first
+        std::stable_sort(sg.begin(), sg.end(), [](const SGroup& x, const SGroup& y) {
+            return x.rows.rows.size() > y.rows.rows.size();
+        });
+        const int32_t npk = (int32_t)sg.size();
         pl.packs.resize(npk);
         pl.cv_tile.assign(ncv, -1);
         pl.cv_pack.assign(ncv, -1);
         std::vector<std::array<std::vector<int32_t>, 32>> syn_l(npk), st_l(npk);
         std::vector<std::vector<int32_t>> hh_l(npk);
-        std::vector<std::vector<int32_t>> gcells(npk);
         int64_t row0 = 0;
         for (int32_t pi = 0; pi < npk; ++pi) {
-            std::vector<int32_t> g(by_size.begin() + (size_t)pi * 32, by_size.begin() + std::min<int32_t>(nc, (pi + 1) * 32));
-            int32_t J = 0;
-            for (int32_t c : g) J = std::max<int32_t>(J, (int32_t)(sim->cv_offset[c + 1] - sim->cv_offset[c]));
+            const SGroup& G = sg[pi];
+            const int32_t J = (int32_t)G.rows.rows.size();
             PackDesc& pd = pl.packs[pi];
             std::memset(&pd, 0, sizeof(pd));
             pd.row0 = (int32_t)row0;
             pd.nrow = J;
+            pd.round_rows = G.shared ? kStreamRound : 0;
             pd.smem = kPackStream;
             pd.sg_off = row0 * kWarp;
-            pd.ncell = (int32_t)g.size();
-            for (size_t l = 0; l < g.size(); ++l) {
-                const int32_t c = g[l];
-                const int32_t n = (int32_t)ord[c].dfs.size();
-                for (int32_t q = 0; q < n; ++q) {
-                    const int64_t cv = sim->cv_offset[c] + ord[c].dfs[q];
-                    pl.cv_tile[cv] = (row0 + (n - 1 - q)) * kWarp + (int64_t)l;
+            pd.ncell = (int32_t)G.cells.size();
+            for (int32_t j = 0; j < J; ++j)
+                for (int l = 0; l < kWarp; ++l) {
+                    const int64_t cv = G.rows.rows[j][l];
+                    if (cv < 0) continue;
+                    pl.cv_tile[cv] = (row0 + j) * kWarp + l;
                     pl.cv_pack[cv] = pi;
                 }
-            }
             std::vector<int32_t> sy, st;
-            for (int32_t c : g) {
+            for (int32_t c : G.cells) {
                 sy.insert(sy.end(), cell_syn[c].begin(), cell_syn[c].end());
                 st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
                 hh_l[pi].insert(hh_l[pi].end(), cell_hh[c].begin(), cell_hh[c].end());
             }
             assign_grouped(sy, sim->syn_cv, syn_l[pi]);
             assign_grouped(st, sim->st_cv, st_l[pi]);
-            gcells[pi] = std::move(g);
             row0 += J;
         }
         pl.total_rows = row0;
         const int64_t ne = row0 * kWarp;
         if (ne > INT32_MAX) return bad("model too large for one handle");
+        for (int64_t cv = 0; cv < ncv; ++cv)
+            if (pl.cv_tile[cv] < 0) return bad("internal error: a CV was not placed");
         pl.lane_eff = row0 > 0 ? (double)ncv / (double)ne : 1.0;
         pl.sg_total = ne;
         pl.ca.assign(ne, 0.0);
@@ -957,40 +1094,78 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         pl.pslot.assign(ne, kFlagRoot);   // flags; padding behaves like an isolated root
         pl.vmap.assign(ne, -1);           // compact mechanism slot
         pl.V0.assign(ne, 0.0);
-        // per-entry constants and flags
+        const uint32_t mb_out_mask = (uint32_t)kMbNone << kMbOutShift, mb_in_mask = (uint32_t)kMbNone << kMbInShift;
+        for (int32_t pi = 0; pi < npk; ++pi)
+            if (sg[pi].shared) {
+                const int64_t base = (int64_t)pl.packs[pi].row0 * kWarp;
+                for (int64_t t = base; t < base + (int64_t)pl.packs[pi].nrow * kWarp; ++t)
+                    pl.pslot[t] = (int32_t)((uint32_t)kFlagRoot | mb_out_mask | mb_in_mask);
+            }
+        // per-entry constants; flags from the layout: an entry whose parent is not the next row
+        // of its lane hands over (stack or mailbox)
+        std::vector<int32_t> nmb(npk, 0);
+        std::unordered_map<int64_t, int32_t> mslot;   // parent entry -> mailbox slot (shared packs)
         for (int32_t c = 0; c < nc; ++c) {
             const int64_t off = sim->cv_offset[c];
-            const CellOrder& o = ord[c];
-            const int32_t n = (int32_t)o.dfs.size();
-            std::vector<int32_t> nch(n, 0);
-            for (int32_t q = 1; q < n; ++q) nch[o.dpar[q]]++;
-            for (int32_t q = 0; q < n; ++q) {
-                const int64_t g = off + o.dfs[q];
+            for (int64_t i = 0; i < ncv_of[c]; ++i) {
+                const int64_t g = off + i;
                 const int64_t t = pl.cv_tile[g];
                 pl.ca[t] = ca[g];
                 pl.cb[t] = cb[g];
                 pl.ck[t] = ck[g];
                 pl.ce[t] = ce[g];
                 pl.V0[t] = -65.0;
-                int32_t f = nch[q] > 1 ? (nch[q] - 1) : 0;   // non-first children hand over via the stack
-                if (f > kFlagPopMask) return bad("a CV has more than 256 children");
-                if (q == 0) f |= kFlagRoot;
-                else if (o.dpar[q] != q - 1) f |= kFlagRemote;
-                pl.pslot[t] = f;
             }
         }
-        // compact mechanism slots, stack depths
+        for (int32_t c = 0; c < nc; ++c) {
+            const int64_t off = sim->cv_offset[c];
+            const int32_t pi = pl.cv_pack[off];
+            const bool shared = sg[pi].shared;
+            for (int64_t i = 0; i < ncv_of[c]; ++i) {
+                const int64_t g = off + i;
+                const int64_t t = pl.cv_tile[g];
+                int32_t& f = pl.pslot[t];   // parents come before children: their counts and "in" slots are kept
+                f &= shared ? (int32_t)mb_in_mask : kFlagPopMask;
+                if (shared) f |= (int32_t)mb_out_mask;
+                if (sim->parent[g] < 0) {
+                    f |= kFlagRoot;
+                    continue;
+                }
+                const int64_t tp = pl.cv_tile[off + sim->parent[g]];
+                if (tp == t + kWarp) continue;   // parent is the next row of this lane
+                f |= kFlagRemote;
+                int32_t& fp = pl.pslot[tp];
+                if (!shared) {
+                    if ((fp & kFlagPopMask) == kFlagPopMask) return bad("a CV has more than 255 handed-over children");
+                    fp += 1;
+                } else {
+                    auto it = mslot.find(tp);
+                    uint32_t s;
+                    if (it == mslot.end()) {
+                        s = (uint32_t)nmb[pi]++;
+                        if (s >= (uint32_t)kMbNone) return bad("internal error: mailbox overflow");
+                        mslot.emplace(tp, (int32_t)s);
+                        fp = (int32_t)(((uint32_t)fp & ~mb_in_mask) | (s << kMbInShift));
+                    } else {
+                        s = (uint32_t)it->second;
+                    }
+                    f = (int32_t)(((uint32_t)f & ~mb_out_mask) | (s << kMbOutShift));
+                }
+            }
+        }
+        // compact mechanism slots; stack depths (one cell per lane) and the round rule of the
+        // mailbox (cells over several lanes)
         std::vector<char> mech(ncv, 0);
         for (int64_t cv : sim->syn_cv) mech[cv] = 1;
         for (int64_t cv : sim->hh_cv) mech[cv] = 1;
         for (int64_t cv : sim->st_cv) mech[cv] = 1;
         int64_t c_total = 0;
-        int32_t max_depth = 1;
+        int32_t max_depth = 1, max_mb = 0;
         for (int32_t pi = 0; pi < npk; ++pi) {
             PackDesc& pd = pl.packs[pi];
             const int64_t base = (int64_t)pd.row0 * kWarp;
             int32_t nvc = 0;
-            for (int32_t c : gcells[pi])
+            for (int32_t c : sg[pi].cells)
                 for (int64_t cv = sim->cv_offset[c]; cv < sim->cv_offset[c + 1]; ++cv)
                     if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = 0;
             for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
@@ -998,6 +1173,38 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             pd.nvc = nvc;
             pd.c_off = c_total;
             c_total += nvc;
+            if (sg[pi].shared) {
+                pd.nmb = nmb[pi];
+                max_mb = std::max(max_mb, nmb[pi]);
+                // a hand-over between lanes crosses a round boundary (both sweeps), and within a
+                // round at most one lane adds to a given slot
+                std::unordered_map<int64_t, int> writer;   // round * 2048 + slot -> lane
+                for (int32_t j = 0; j < pd.nrow; ++j)
+                    for (int l = 0; l < kWarp; ++l) {
+                        const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
+                        const int32_t so = (f >> kMbOutShift) & kMbNone, si = (int32_t)((uint32_t)f >> kMbInShift);
+                        if ((so != kMbNone && so >= pd.nmb) || (si != kMbNone && si >= pd.nmb) || (f & kFlagPopMask))
+                            return bad("internal error: mailbox slot out of range");
+                        if (!(f & kFlagRemote) || (f & kFlagRoot)) continue;
+                        if (so == kMbNone) return bad("internal error: hand-over without a mailbox slot");
+                        const int32_t s = so;
+                        const int64_t key = (int64_t)(j / kStreamRound) * 2048 + s;
+                        auto w = writer.find(key);
+                        if (w != writer.end() && w->second != l) return bad("internal error: two lanes add to one mailbox slot in a round");
+                        writer[key] = l;
+                    }
+                for (int32_t c : sg[pi].cells)
+                    for (int64_t cv = sim->cv_offset[c] + 1; cv < sim->cv_offset[c + 1]; ++cv) {
+                        const int64_t t = pl.cv_tile[cv], tp = pl.cv_tile[sim->cv_offset[c] + sim->parent[cv]];
+                        if (t % kWarp == tp % kWarp) {
+                            if (tp <= t) return bad("internal error: parent before child on a lane");
+                        } else if ((t / kWarp - pd.row0) / kStreamRound >= (tp / kWarp - pd.row0) / kStreamRound) {
+                            return bad("internal error: cross-lane hand-over inside one round");
+                        }
+                    }
+                pd.stack = 0;
+                continue;
+            }
             int32_t depth = 0;
             for (int l = 0; l < kWarp; ++l) {
                 int32_t sp = 0;
@@ -1022,6 +1229,10 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         }
         pl.c_total = c_total;
         pl.stack_depth = max_depth;
+        pl.warp_smem = std::max<int64_t>((int64_t)max_depth * kWarp, ((int64_t)3 * max_mb + 1) / 2);
+        pl.split_cvs = split;
+        pl.smem_packs = 0;
+        for (const SGroup& G : sg) pl.smem_packs += G.shared;
         // mechanisms: synapse and clamp rows by CV on one lane; HH round-robin
         int64_t syn_rows = 0, hh_rows = 0, st_rows = 0;
         for (int32_t pi = 0; pi < npk; ++pi) {
@@ -1083,12 +1294,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 pl.hh_gk[q] = hh_gk[i];
                 pl.hh_entry[i] = q;
             }
-            for (size_t dd = 0; dd < gcells[pi].size(); ++dd) {
-                pl.det_slot[(size_t)pi * kWarp + dd] = (int32_t)(pl.cv_tile[sim->det_cv[gcells[pi][dd]]] - base);
-                pl.det_gid[(size_t)pi * kWarp + dd] = gcells[pi][dd];
+            for (size_t dd = 0; dd < sg[pi].cells.size(); ++dd) {
+                pl.det_slot[(size_t)pi * kWarp + dd] = (int32_t)(pl.cv_tile[sim->det_cv[sg[pi].cells[dd]]] - base);
+                pl.det_gid[(size_t)pi * kWarp + dd] = sg[pi].cells[dd];
             }
         }
-        // the persistent kernel takes packs in order: already largest first
     } else {
     if (groups.empty() && nc > 0) build_k(kpp, groups);
     const int32_t npk = (int32_t)groups.size();
@@ -1361,8 +1571,16 @@ arb_status arb_workspace_bytes(const arb_sim* csim, int64_t* bytes) {
 }
 
 arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_rows, int64_t* smem_packs,
-                         double* lane_efficiency, int32_t* epoch_steps) {
+                         double* lane_efficiency, int32_t* epoch_steps, int64_t* max_pack_rows,
+                         int32_t* cells_per_pack, int64_t* split_cvs) {
     if (!sim) return ARB_E_ARG;
+    if (max_pack_rows) {
+        int64_t mx = 0;
+        for (const PackDesc& pd : sim->plan.packs) mx = std::max<int64_t>(mx, pd.nrow);
+        *max_pack_rows = mx;
+    }
+    if (cells_per_pack) *cells_per_pack = sim->plan.cells_per_pack;
+    if (split_cvs) *split_cvs = sim->plan.stream ? sim->plan.split_cvs : -1;
     if (n_packs) *n_packs = (int64_t)sim->plan.packs.size();
     if (total_rows) *total_rows = sim->plan.total_rows;
     if (smem_packs) *smem_packs = sim->plan.smem_packs;
@@ -1386,8 +1604,8 @@ static arb_status capture_one(arb_sim* sim, int which, cudaGraphExec_t* out) {
     cudaError_t e1 = cudaSuccess;
     if (which == 0) e1 = launch_events_pre(sim->ev_args, sim->n_sm, sim->s);
     else if (which == 1 && sim->plan.stream)
-        e1 = sim->mixed ? launch_stream<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.stack_depth, sim->s)
-                        : launch_stream<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.stack_depth, sim->s);
+        e1 = sim->mixed ? launch_stream<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s)
+                        : launch_stream<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s);
     else if (which == 1)
         e1 = sim->mixed ? launch_epoch<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
                         : launch_epoch<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
@@ -1498,10 +1716,13 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     b.dt = sim->prm.dt;
     // launch shape of the persistent epoch kernel
     if (pl.stream) {
-        sim->warps_per_cta = 8;
+        // fewer warps per CTA when one warp's stack or mailbox is large
+        const int64_t per_warp = pl.warp_smem * (int64_t)sizeof(double2);
+        sim->warps_per_cta = (int)std::min<int64_t>(kStreamWarps, (int64_t)(227 * 1024) / std::max<int64_t>(per_warp, 1));
+        if (sim->warps_per_cta < 1) return fail(sim, ARB_E_ARG, "hand-over stack of one warp exceeds shared memory");
         int bps = 0;
-        cudaError_t eo = sim->mixed ? stream_occupancy<float>(sim->implicit, sim->warps_per_cta, pl.stack_depth, &bps)
-                                    : stream_occupancy<double>(sim->implicit, sim->warps_per_cta, pl.stack_depth, &bps);
+        cudaError_t eo = sim->mixed ? stream_occupancy<float>(sim->implicit, sim->warps_per_cta, (int)pl.warp_smem, &bps)
+                                    : stream_occupancy<double>(sim->implicit, sim->warps_per_cta, (int)pl.warp_smem, &bps);
         if (eo != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("stream kernel occupancy: ") + cudaGetErrorString(eo));
         if (bps < 1) return fail(sim, ARB_E_CUDA, "stream kernel does not fit on an SM");
         sim->grid = sim->n_sm * bps;

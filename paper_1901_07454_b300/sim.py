@@ -60,7 +60,7 @@ class Plan:
 
     def __init__(self, model, dt=0.025, epoch_steps=0, precision="fp64", cells_per_pack=0, smem_budget=0,
                  event_capacity=None, ext_event_capacity=None, spike_capacity=None, bucket_capacity=None,
-                 stream=None, scheme="implicit"):
+                 stream=None, scheme="implicit", split_cvs=0):
         lib = L.load()
         self.model = model
         p = default_params()
@@ -69,6 +69,7 @@ class Plan:
         p.precision = L.ARB_MIXED if precision == "mixed" else L.ARB_FP64
         p.cells_per_pack = int(cells_per_pack)
         p.smem_budget = int(smem_budget)
+        p.split_cvs = int(split_cvs)
         if scheme not in ("implicit", "explicit"):
             raise ValueError("scheme must be 'implicit' or 'explicit'")
         p.scheme = L.ARB_EXPLICIT if scheme == "explicit" else L.ARB_IMPLICIT
@@ -105,11 +106,12 @@ class Plan:
         return n.value
 
     def plan_info(self):
-        npk, rows, smem = C.c_int64(), C.c_int64(), C.c_int64()
-        eff, ep = C.c_double(), C.c_int32()
-        L.check(L.load().arb_plan_info(self.h, C.byref(npk), C.byref(rows), C.byref(smem), C.byref(eff), C.byref(ep)), self.h)
+        npk, rows, smem, mxr, split = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        eff, ep, kpp = C.c_double(), C.c_int32(), C.c_int32()
+        L.check(L.load().arb_plan_info(self.h, C.byref(npk), C.byref(rows), C.byref(smem), C.byref(eff), C.byref(ep),
+                                       C.byref(mxr), C.byref(kpp), C.byref(split)), self.h)
         return dict(n_packs=npk.value, total_rows=rows.value, smem_packs=smem.value, lane_efficiency=eff.value,
-                    epoch_steps=ep.value)
+                    epoch_steps=ep.value, max_pack_rows=mxr.value, cells_per_pack=kpp.value, split_cvs=split.value)
 
 
 class Simulation(Plan):

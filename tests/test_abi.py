@@ -77,6 +77,21 @@ def test_planning_covers_every_cv(arb):
         assert p.workspace_bytes() > 0
 
 
+def test_streamed_plan_spreads_large_cells(arb):
+    m = small_tree_model(11, n_cells=37, n_branches=9, cv_range=(1, 12), n_syn=4)
+    one = arb.Plan(m, cells_per_pack=32, split_cvs=-1).plan_info()
+    assert one["split_cvs"] == -1 and one["smem_packs"] == 0
+    assert one["n_packs"] == 2 and one["max_pack_rows"] == int(np.diff(m.cv_offset).max())
+    big = int((np.diff(m.cv_offset) > 40).sum())
+    shared = arb.Plan(m, cells_per_pack=32, split_cvs=40).plan_info()
+    assert shared["split_cvs"] == 40 and shared["smem_packs"] >= 1
+    assert shared["max_pack_rows"] < one["max_pack_rows"]
+    assert 1 <= shared["smem_packs"] <= big
+    auto = arb.Plan(m, cells_per_pack=32).plan_info()      # a small batch: every cell is spread
+    assert auto["split_cvs"] > 0 and auto["max_pack_rows"] <= shared["max_pack_rows"]
+    _expect_error(arb, m, "split_cvs", cells_per_pack=32, split_cvs=-2)
+
+
 def test_epoch_is_derived_from_min_delay(arb):
     m, spec = make_config(1, n_cells=8, t_end=10.0)
     assert arb.Plan(m, dt=0.025).plan_info()["epoch_steps"] == 200

@@ -45,9 +45,13 @@ def test_uniform_cable_every_step(scheme):
     assert rel_err(g["V"], o["V"]) <= TOL
 
 
-@pytest.mark.parametrize("kpp,scheme", [(32, "implicit"), (8, "implicit"), (3, "implicit"), (1, "implicit"),
-                                        (32, "explicit"), (8, "explicit")])
-def test_random_trees_every_cv_every_step(kpp, scheme):
+# cells_per_pack 32 is the streamed plan: split 0 lets the library spread cells over lanes (here
+# every cell, as the batch is far smaller than the GPU), -1 keeps one cell per lane, 40 puts the
+# cells above 40 CVs together into one pack whose lanes they share
+@pytest.mark.parametrize("kpp,scheme,split", [(32, "implicit", 0), (32, "implicit", -1), (32, "implicit", 40),
+                                              (8, "implicit", 0), (3, "implicit", 0), (1, "implicit", 0),
+                                              (32, "explicit", -1), (32, "explicit", 40), (8, "explicit", 0)])
+def test_random_trees_every_cv_every_step(kpp, scheme, split):
     # ragged trees, HH soma, passive dendrites, synapses with events, clamps that make cells fire
     m = small_tree_model(11, n_cells=37, n_branches=9, cv_range=(1, 12), n_syn=4)
     m.stim_cv = m.cv_offset[:-1:3].copy()
@@ -57,7 +61,7 @@ def test_random_trees_every_cv_every_step(kpp, scheme):
     syn, t, w = _with_events(m, 3, 40.0, 30.0)
     spec = SimSpec(dt=0.025, t_end=30.0, epoch_steps=40, ev_syn=syn, ev_t=t, ev_w=w)
     probes = np.arange(m.n_cv)
-    g = run_gpu(m, spec, probes=probes, cells_per_pack=kpp, scheme=scheme)
+    g = run_gpu(m, spec, probes=probes, cells_per_pack=kpp, scheme=scheme, split_cvs=split)
     o = run_oracle(m, spec, probes=probes, scheme=scheme)
     assert rel_err(g["V"], o["V"]) <= TOL
     assert rel_err(g["trace"], o["trace"]) <= trace_bar(TOL, oracle_spread(m, spec, probes, scheme))
@@ -153,16 +157,17 @@ def test_mixed_precision_within_1e3_mV():
     m.__post_init__()
     syn, t, w = _with_events(m, 3, 40.0, 30.0)
     spec = SimSpec(dt=0.025, t_end=30.0, epoch_steps=40, ev_syn=syn, ev_t=t, ev_w=w)
-    g = run_gpu(m, spec, probes=np.arange(m.n_cv), precision="mixed")
     o = run_oracle(m, spec, probes=np.arange(m.n_cv))
-    assert len(g["spikes"][1]) == len(o["spikes"][1])
-    compare_spikes(g["spikes"], o["spikes"], t_tol=1e-3)
-    assert np.max(np.abs(g["V"] - o["V"])) <= 1e-3
     # through spikes, an FP32-sized change (2^-24) of the state moves the FP64 oracle itself by
     # this much: the bar is 1e-3 mV or a small multiple of that, whichever is larger
     sens32 = oracle_sensitivity(m, spec, np.arange(m.n_cv), rel=2.0 ** -24, absolute=True)
-    err = float(np.max(np.abs(g["trace"] - o["trace"])))
-    assert err <= max(1e-3, 20.0 * sens32), (err, sens32)
+    for kw in ({}, {"cells_per_pack": 32, "split_cvs": 40}):
+        g = run_gpu(m, spec, probes=np.arange(m.n_cv), precision="mixed", **kw)
+        assert len(g["spikes"][1]) == len(o["spikes"][1])
+        compare_spikes(g["spikes"], o["spikes"], t_tol=1e-3)
+        assert np.max(np.abs(g["V"] - o["V"])) <= 1e-3
+        err = float(np.max(np.abs(g["trace"] - o["trace"])))
+        assert err <= max(1e-3, 20.0 * sens32), (kw, err, sens32)
 
 
 def test_state_roundtrip_continues_identically():
@@ -205,8 +210,8 @@ def test_edge_cases_single_cv_star_and_long_chain():
               stim_cv=off[:-1], stim_t_on=np.zeros(len(cells)), stim_dur=np.full(len(cells), 5.0),
               stim_amp=np.linspace(0.01, 0.3, len(cells)))
     spec = SimSpec(dt=0.025, t_end=15.0, epoch_steps=64)
-    for kpp in (32, 2):
-        g = run_gpu(m, spec, probes=np.arange(n), cells_per_pack=kpp)
+    for kpp, split in ((32, 0), (32, -1), (2, 0)):
+        g = run_gpu(m, spec, probes=np.arange(n), cells_per_pack=kpp, split_cvs=split)
         o = run_oracle(m, spec, probes=np.arange(n))
         assert rel_err(g["V"], o["V"]) <= TOL
         assert rel_err(g["trace"], o["trace"]) <= trace_bar(TOL, oracle_spread(m, spec, np.arange(n)))
