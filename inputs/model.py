@@ -104,6 +104,39 @@ class Model:
     def cell_sizes(self) -> np.ndarray:
         return np.diff(self.cv_offset)
 
+    # per-branch parameter groups: group = cell * (branches per cell) + branch
+    PARAM_NAMES = ("gnabar", "gkbar", "gl", "cm")
+
+    def param_groups(self):
+        """(group_of_cv int32 [n_cv], n_groups) with one group per (cell, branch)."""
+        nb = int(self.branch_of_cv.max()) + 1 if self.n_cv else 0
+        group = (self.cell_of_cv() * nb + self.branch_of_cv).astype(np.int32)
+        return group, self.n_cells * nb
+
+    def group_params(self):
+        """theta [n_groups, 4] = (gnabar, gkbar, gl, cm), read from the first CV / HH
+        instance of each group (groups are assumed uniform)."""
+        group, ng = self.param_groups()
+        th = np.zeros((ng, 4))
+        th[group[::-1], 3] = self.cm[::-1]
+        hg = group[self.hh_cv]
+        th[hg[::-1], 0] = self.gnabar[::-1]
+        th[hg[::-1], 1] = self.gkbar[::-1]
+        th[hg[::-1], 2] = self.gl[::-1]
+        return th
+
+    def with_group_params(self, theta):
+        """A copy whose per-instance densities and per-CV cm are taken from theta [n_groups, 4]."""
+        import copy
+        theta = np.asarray(theta, np.float64)
+        group, ng = self.param_groups()
+        assert theta.shape == (ng, 4)
+        m = copy.copy(self)
+        hg = group[self.hh_cv]
+        m.gnabar, m.gkbar, m.gl = theta[hg, 0].copy(), theta[hg, 1].copy(), theta[hg, 2].copy()
+        m.cm = theta[group, 3].copy()
+        return m
+
 
 @dataclass
 class SimSpec:

@@ -83,6 +83,11 @@ def lib():
         L.orc_hh_rates.argtypes = [dbl, vp]
         L.orc_exprelr.restype = dbl
         L.orc_exprelr.argtypes = [dbl]
+        L.orc_exprelr_deriv.restype = dbl
+        L.orc_exprelr_deriv.argtypes = [dbl]
+        L.orc_hh_rate_derivs.argtypes = [dbl, vp]
+        L.orc_adjoint.restype = i32
+        L.orc_adjoint.argtypes = [vp, i64, i64, vp, vp, dbl, vp, i32, vp, C.POINTER(dbl)]
         _lib = L
     return _lib
 
@@ -142,6 +147,16 @@ def hh_rates(v):
 
 def exprelr(x):
     return lib().orc_exprelr(float(x))
+
+
+def exprelr_deriv(x):
+    return lib().orc_exprelr_deriv(float(x))
+
+
+def hh_rate_derivs(v):
+    r = np.zeros(6)
+    lib().orc_hh_rate_derivs(float(v), _p(r))
+    return r
 
 
 class OracleSim:
@@ -221,6 +236,20 @@ class OracleSim:
     def set_state(self, st):
         arrs = [np.ascontiguousarray(st[k], np.float64) for k in ("V", "m", "h", "n", "g")]
         lib().orc_set_state(self.h, *[_p(a) for a in arrs])
+
+    def adjoint(self, n_steps, obs_cv, target, loss_scale, group_of_cv, n_groups):
+        """Discrete adjoint over the next n_steps from the current state (which it leaves
+        unchanged): returns (loss, grad [n_groups, 4] = dL/d(gnabar, gkbar, gl, cm))."""
+        obs_cv = np.ascontiguousarray(obs_cv, np.int64)
+        target = np.ascontiguousarray(target, np.float64).reshape(int(n_steps), obs_cv.size)
+        group_of_cv = np.ascontiguousarray(group_of_cv, np.int32)
+        grad = np.zeros((int(n_groups), 4))
+        loss = C.c_double()
+        rc = lib().orc_adjoint(self.h, int(n_steps), obs_cv.size, _p(obs_cv), _p(target), float(loss_scale),
+                               _p(group_of_cv), int(n_groups), _p(grad), C.byref(loss))
+        if rc != 0:
+            raise ValueError("oracle adjoint: models with synapses are not supported")
+        return loss.value, grad
 
     def delivered(self):
         n = lib().orc_num_delivered(self.h)

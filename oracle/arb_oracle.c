@@ -627,3 +627,220 @@ void orc_get_delivered(const orc_sim* s, int64_t* syn, double* t, double* w, int
             syn[o] = e->syn; t[o] = e->t; w[o] = e->w; step[o] = e->step; src[o] = e->src; idx[o] = e->idx;
         }
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Discrete adjoint of the implicit step (gradient of a voltage loss w.r.t. the channel
+ * densities and the membrane capacitance).
+ *
+ * The forward map is the implicit reading of the step above, per cell:
+ *   A(y^k) V^{k+1} = (C/dt) V^k + M(y^k) + Iinj(t_k),
+ *   A(y) = diag(C/dt + G(y)) + axial Laplacian (symmetric),
+ *   y^{k+1} = Phi(y^k, V^{k+1})  (exact gate update at frozen V^{k+1}),
+ * with G = sum of channel conductances and M = sum g*E. The loss is
+ *   L = scale * sum_{k=1..K} sum_obs (V_obs^k - target_obs^k)^2.
+ * Reverse sweep, k = K-1 .. 0, with lam the solve result of step k+1 (zero for k = K-1) and
+ * ybar the adjoint of the gates y^{k+1}:
+ *   Vbar = (C/dt) lam + dL/dV^{k+1} + sum_gates dPhi/dV(y^k, V^{k+1}) ybar
+ *   lam  = A(y^k)^{-1} Vbar                   (the same tree solve: A is symmetric)
+ *   dL/dC_i    += lam_i (V_i^k - V_i^{k+1}) / dt
+ *   dL/dg_chan += lam_i (E_chan - V_i^{k+1}) * (open fraction of the channel at y^k)
+ *   ybar       <- exp(-dt (alpha+beta)(V^{k+1})) ybar + dG/dy^T (-lam V^{k+1}) + dM/dy^T lam
+ * Densities enter as g = gbar * area * 1e-2 and C = cm * area * 1e-5. The initial state is
+ * taken as given (no dependence on the parameters). Models with synapses are not supported.
+ * The reverse sweep needs y^k and V^{k+1}: this reference keeps every state of the run. */
+
+/* d/dx of x/(e^x - 1). For |x| < 0.1 the derivative of its Bernoulli series,
+ * sum_n B_n x^n / n!, up to x^7 (the first omitted term is below 3e-16 there); elsewhere the
+ * closed form (e^x - 1 - x e^x) / (e^x - 1)^2, whose cancellation costs ~eps/|x|. */
+double orc_exprelr_deriv(double x) {
+    if (fabs(x) < 0.1) {
+        double x2 = x * x;
+        return -0.5 + x * (1.0 / 6.0 + x2 * (-1.0 / 180.0 + x2 * (1.0 / 5040.0 - x2 / 151200.0)));
+    }
+    double em = expm1(x);
+    return (em - x * (em + 1.0)) / (em * em);
+}
+
+/* Derivatives of the six rates of orc_hh_rates w.r.t. V (1/(ms mV)). */
+void orc_hh_rate_derivs(double v, double* dr) {
+    double r[6];
+    orc_hh_rates(v, r);
+    dr[0] = -0.1 * orc_exprelr_deriv(-(v + 40.0) / 10.0);
+    dr[1] = -r[1] / 18.0;
+    dr[2] = -r[2] / 20.0;
+    dr[3] = r[3] * (1.0 - r[3]) / 10.0;
+    dr[4] = -0.01 * orc_exprelr_deriv(-(v + 55.0) / 10.0);
+    dr[5] = -r[5] / 80.0;
+}
+
+/* d Phi / dV for one gate: Phi = xinf + (x - xinf) exp(-dt s), s = alpha + beta. */
+static double gate_dv(double x, double al, double be, double dal, double dbe, double dt) {
+    double s = al + be, ds = dal + dbe;
+    double xinf = al / s;
+    double dxinf = (dal * s - al * ds) / (s * s);
+    double e = exp(-dt * s);
+    return dxinf * (1.0 - e) + (x - xinf) * e * (-dt * ds);
+}
+
+/* Runs n_steps from the simulation's current state and time without changing them.
+ * target [n_steps][n_obs]; group_of_cv [n_cv] (-1: no parameter group); grad [n_groups][4]
+ * = dL/d(gnabar, gkbar, gl, cm) summed over the CVs of each group. Returns 0, or -2 for a
+ * model with synapses. */
+int orc_adjoint(orc_sim* s, int64_t n_steps, int64_t n_obs, const int64_t* obs_cv, const double* target,
+                double loss_scale, const int32_t* group_of_cv, int32_t n_groups, double* grad, double* loss) {
+    const orc_model* m = &s->m;
+    if (m->n_syn > 0) return -2;
+    const double dt = s->dt;
+    const int64_t K = n_steps, k0 = s->k, ncv = s->n_cv;
+    int64_t* obs_ptr = NULL;
+    int64_t* obs_list = NULL;
+    build_csr(m->n_cells, n_obs, obs_cv, m->cv_offset, &obs_ptr, &obs_list);
+    /* per-CV and per-instance gradient accumulators */
+    double* g_cm = (double*)xcalloc((size_t)ncv, sizeof(double));
+    double* g_na = (double*)xcalloc((size_t)m->n_hh, sizeof(double));
+    double* g_k = (double*)xcalloc((size_t)m->n_hh, sizeof(double));
+    double* g_l = (double*)xcalloc((size_t)m->n_hh, sizeof(double));
+    double* cell_loss = (double*)xcalloc((size_t)m->n_cells, sizeof(double));
+#ifdef _OPENMP
+    if (s->nthreads > 0) omp_set_num_threads(s->nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t c = 0; c < m->n_cells; ++c) {
+        const int64_t off = m->cv_offset[c], n = m->cv_offset[c + 1] - off;
+        const int32_t* par = m->parent + off;
+        const int64_t h0 = s->hh_ptr[c], nh = s->hh_ptr[c + 1] - h0;
+        double* Vs = (double*)xmalloc(sizeof(double) * (size_t)((K + 1) * n));       /* V^k, k = 0..K */
+        double* Ys = (double*)xmalloc(sizeof(double) * (size_t)((K + 1) * nh * 3));  /* (m,h,n)^k */
+        double* G = (double*)xmalloc(sizeof(double) * (size_t)n);
+        double* GE = (double*)xmalloc(sizeof(double) * (size_t)n);
+        double* d = (double*)xmalloc(sizeof(double) * (size_t)n);
+        double* a = (double*)xmalloc(sizeof(double) * (size_t)n);
+        double* b = (double*)xmalloc(sizeof(double) * (size_t)n);
+        double* lam = (double*)xcalloc((size_t)n, sizeof(double));
+        double* ybar = (double*)xcalloc((size_t)(nh * 3), sizeof(double));
+        for (int64_t i = 0; i < n; ++i) Vs[i] = s->V[off + i];
+        for (int64_t j = 0; j < nh; ++j) {
+            int64_t hh = s->hh_list[h0 + j];
+            Ys[3 * j + 0] = s->hh_m[hh];
+            Ys[3 * j + 1] = s->hh_h[hh];
+            Ys[3 * j + 2] = s->hh_n[hh];
+        }
+        /* assemble A(y^k) into d, a and the membrane terms into G, GE */
+        #define ORC_ASSEMBLE(k_)                                                            \
+            do {                                                                            \
+                const double* Y_ = Ys + (size_t)(k_) * (size_t)nh * 3;                      \
+                for (int64_t i = 0; i < n; ++i) { G[i] = 0.0; GE[i] = 0.0; a[i] = 0.0; }    \
+                for (int64_t j = 0; j < nh; ++j) {                                          \
+                    int64_t hh = s->hh_list[h0 + j];                                        \
+                    int64_t i = m->hh_cv[hh] - off;                                         \
+                    double mm = Y_[3 * j], hv = Y_[3 * j + 1], nv = Y_[3 * j + 2];          \
+                    double gna = s->hh_gna[hh] * mm * mm * mm * hv;                         \
+                    double gk = s->hh_gk[hh] * nv * nv * nv * nv;                           \
+                    G[i] += gna + gk + s->hh_gl[hh];                                        \
+                    GE[i] += gna * ORC_ENA + gk * ORC_EK + s->hh_gl[hh] * ORC_EL;           \
+                }                                                                           \
+                for (int64_t j = s->pas_ptr[c]; j < s->pas_ptr[c + 1]; ++j) {               \
+                    int64_t p = s->pas_list[j];                                             \
+                    int64_t i = m->pas_cv[p] - off;                                         \
+                    G[i] += s->pas_g[p];                                                    \
+                    GE[i] += s->pas_g[p] * m->e_pas[p];                                     \
+                }                                                                           \
+                for (int64_t i = 0; i < n; ++i) d[i] = s->cap[off + i] / dt + G[i];         \
+                for (int64_t i = 1; i < n; ++i) {                                           \
+                    double sg = s->sigma[off + i];                                          \
+                    d[i] += sg;                                                             \
+                    d[par[i]] += sg;                                                        \
+                    a[i] = -sg;                                                             \
+                }                                                                           \
+            } while (0)
+        /* forward, keeping every state */
+        for (int64_t k = 0; k < K; ++k) {
+            const double* V = Vs + (size_t)k * (size_t)n;
+            double* Vn = Vs + (size_t)(k + 1) * (size_t)n;
+            const double t = (double)(k0 + k) * dt;
+            ORC_ASSEMBLE(k);
+            for (int64_t i = 0; i < n; ++i) b[i] = s->cap[off + i] / dt * V[i] + GE[i];
+            for (int64_t j = s->st_ptr[c]; j < s->st_ptr[c + 1]; ++j) {
+                int64_t y = s->st_list[j];
+                if (m->stim_t_on[y] <= t && t < m->stim_t_on[y] + m->stim_dur[y]) b[m->stim_cv[y] - off] += m->stim_amp[y];
+            }
+            orc_hines_solve(n, par, d, a, b, Vn);
+            const double* Y = Ys + (size_t)k * (size_t)nh * 3;
+            double* Yn = Ys + (size_t)(k + 1) * (size_t)nh * 3;
+            for (int64_t j = 0; j < nh; ++j) {
+                double r[6];
+                orc_hh_rates(Vn[m->hh_cv[s->hh_list[h0 + j]] - off], r);
+                Yn[3 * j + 0] = gate_step(Y[3 * j + 0], r[0], r[1], dt);
+                Yn[3 * j + 1] = gate_step(Y[3 * j + 1], r[2], r[3], dt);
+                Yn[3 * j + 2] = gate_step(Y[3 * j + 2], r[4], r[5], dt);
+            }
+            for (int64_t q = obs_ptr[c]; q < obs_ptr[c + 1]; ++q) {
+                int64_t o = obs_list[q];
+                double e = Vn[obs_cv[o] - off] - target[k * n_obs + o];
+                cell_loss[c] += loss_scale * e * e;
+            }
+        }
+        /* reverse sweep */
+        for (int64_t k = K - 1; k >= 0; --k) {
+            const double* V = Vs + (size_t)k * (size_t)n;
+            const double* Vn = Vs + (size_t)(k + 1) * (size_t)n;
+            const double* Y = Ys + (size_t)k * (size_t)nh * 3;
+            /* Vbar: from the next step's right-hand side (C/dt) V^{k+1}, the loss at k+1 and
+             * the gate update y^{k+1} = Phi(y^k, V^{k+1}) */
+            for (int64_t i = 0; i < n; ++i) b[i] = s->cap[off + i] / dt * lam[i];
+            for (int64_t q = obs_ptr[c]; q < obs_ptr[c + 1]; ++q) {
+                int64_t o = obs_list[q];
+                int64_t i = obs_cv[o] - off;
+                b[i] += 2.0 * loss_scale * (Vn[i] - target[k * n_obs + o]);
+            }
+            for (int64_t j = 0; j < nh; ++j) {
+                int64_t i = m->hh_cv[s->hh_list[h0 + j]] - off;
+                double r[6], dr[6];
+                orc_hh_rates(Vn[i], r);
+                orc_hh_rate_derivs(Vn[i], dr);
+                b[i] += gate_dv(Y[3 * j + 0], r[0], r[1], dr[0], dr[1], dt) * ybar[3 * j + 0]
+                      + gate_dv(Y[3 * j + 1], r[2], r[3], dr[2], dr[3], dt) * ybar[3 * j + 1]
+                      + gate_dv(Y[3 * j + 2], r[4], r[5], dr[4], dr[5], dt) * ybar[3 * j + 2];
+            }
+            /* lam = A(y^k)^{-1} Vbar */
+            ORC_ASSEMBLE(k);
+            orc_hines_solve(n, par, d, a, b, lam);
+            /* parameter gradients and the gate adjoint of y^k */
+            for (int64_t i = 0; i < n; ++i)
+                g_cm[off + i] += lam[i] * (V[i] - Vn[i]) / dt * s->area[off + i] * 1e-5;
+            for (int64_t j = 0; j < nh; ++j) {
+                int64_t hh = s->hh_list[h0 + j];
+                int64_t i = m->hh_cv[hh] - off;
+                double mm = Y[3 * j], hv = Y[3 * j + 1], nv = Y[3 * j + 2];
+                double lna = lam[i] * (ORC_ENA - Vn[i]), lk = lam[i] * (ORC_EK - Vn[i]), ll = lam[i] * (ORC_EL - Vn[i]);
+                double sc = s->area[off + i] * 1e-2;
+                g_na[hh] += mm * mm * mm * hv * lna * sc;
+                g_k[hh] += nv * nv * nv * nv * lk * sc;
+                g_l[hh] += ll * sc;
+                double r[6];
+                orc_hh_rates(Vn[i], r);
+                ybar[3 * j + 0] = exp(-dt * (r[0] + r[1])) * ybar[3 * j + 0] + s->hh_gna[hh] * 3.0 * mm * mm * hv * lna;
+                ybar[3 * j + 1] = exp(-dt * (r[2] + r[3])) * ybar[3 * j + 1] + s->hh_gna[hh] * mm * mm * mm * lna;
+                ybar[3 * j + 2] = exp(-dt * (r[4] + r[5])) * ybar[3 * j + 2] + s->hh_gk[hh] * 4.0 * nv * nv * nv * lk;
+            }
+        }
+        #undef ORC_ASSEMBLE
+        free(Vs); free(Ys); free(G); free(GE); free(d); free(a); free(b); free(lam); free(ybar);
+    }
+    /* group sums in ascending CV / instance order */
+    for (int64_t q = 0; q < (int64_t)n_groups * 4; ++q) grad[q] = 0.0;
+    for (int64_t i = 0; i < ncv; ++i)
+        if (group_of_cv[i] >= 0) grad[4 * group_of_cv[i] + 3] += g_cm[i];
+    for (int64_t hh = 0; hh < m->n_hh; ++hh) {
+        int32_t gr = group_of_cv[m->hh_cv[hh]];
+        if (gr < 0) continue;
+        grad[4 * gr + 0] += g_na[hh];
+        grad[4 * gr + 1] += g_k[hh];
+        grad[4 * gr + 2] += g_l[hh];
+    }
+    double L = 0.0;
+    for (int32_t c = 0; c < m->n_cells; ++c) L += cell_loss[c];
+    *loss = L;
+    free(g_cm); free(g_na); free(g_k); free(g_l); free(cell_loss); free(obs_ptr); free(obs_list);
+    return 0;
+}
