@@ -189,8 +189,34 @@ arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_ro
                          int64_t* max_pack_rows, int32_t* cells_per_pack, int64_t* split_cvs);
 
 /* Device time of the epoch kernel summed over the last arb_advance call, in ms, and the
- * number of kernel launches it issued. Requires arb_params timing (always on). */
+ * number of kernel launches it issued; after arb_adjoint, the device time of its forward,
+ * recompute and reverse kernels and their launch count. */
 arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t* launches);
+
+/* Discrete adjoint of the implicit step (the reverse-mode derivative of the time stepper;
+ * the paper has no adjoint, this extends its Sec. "Model" scheme). Starting from the handle's
+ * current state and time t_k, it runs n_steps steps of the implicit step (ARB_IMPLICIT; FP64
+ * whatever the precision setting) and returns
+ *   *loss = loss_scale * sum_{s < n_steps} sum_o (V_{obs_cv[o]}(t_{k+s+1}) - target[s][o])^2
+ * and grad[g][p] = dL/d theta_{g,p} for the per-group densities theta = (gnabar, gkbar, gl
+ * in S/cm^2, cm in uF/cm^2): the derivative w.r.t. a value shared by every CV (and HH
+ * instance) of group g, where group_of_cv[i] in [-1, n_groups) assigns CV i (-1: none). The
+ * initial state is taken as fixed. The handle's state, time and events are not changed.
+ * Gradients go through the conductance terms of the voltage step, the exact gate update
+ * and the capacitance of every CV; models with synapses are refused (ARB_E_ARG).
+ *   obs_cv [n_obs]: host, distinct CVs. target [n_steps][n_obs]: device. group_of_cv [n_cv]: host.
+ *   grad [n_groups][4]: device, written. loss: host, written.
+ *   workspace: caller-owned device memory of arb_adjoint_workspace_bytes bytes, 256-byte
+ *   aligned. It holds one state every checkpoint_every steps and every state of one segment
+ *   of checkpoint_every steps, which the reverse sweep recomputes from its checkpoint.
+ * Work is ordered on the handle's stream after the caller's stream; the call returns after
+ * the loss has been copied back. */
+arb_status arb_adjoint_workspace_bytes(const arb_sim* sim, int64_t n_steps, int32_t checkpoint_every,
+                                       int64_t n_obs, int32_t n_groups, int64_t* bytes);
+arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, int64_t n_obs,
+                       const int64_t* obs_cv, const double* target, double loss_scale,
+                       const int32_t* group_of_cv, int32_t n_groups, void* workspace,
+                       int64_t workspace_bytes, double* grad, double* loss);
 
 /* Message of the last failing call on this handle; with NULL, of the last failing call on
  * this thread that has no handle (arb_create, arb_solve_trees_noalloc). */

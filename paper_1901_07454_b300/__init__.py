@@ -9,4 +9,7 @@ from .sim import Plan, Simulation, default_params
 
 load()
 
-__all__ = ["ArbError", "Plan", "Simulation", "default_params", "load", "EXPORTED"]
+from .adjoint import AdjointLoss, adjoint_loss, spread_params  # noqa: E402  (needs the library)
+
+__all__ = ["ArbError", "Plan", "Simulation", "default_params", "load", "EXPORTED", "AdjointLoss", "adjoint_loss",
+           "spread_params"]

@@ -1,0 +1,90 @@
+// Hodgkin-Huxley rate functions shared by the stepping kernels and the adjoint kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+namespace arbk {
+
+// ------------------------------------------------------------------------------------------
+// Hodgkin-Huxley rates (1/ms) and exact gate update at frozen V, in the precision MT.
+// The model (classic squid axon at 6.3 degC) is the one named by the paper's benchmark
+// (Sec. "Benchmarks", "Models": Hodgkin-Huxley soma, passive dendrites).
+
+__device__ __forceinline__ double exprelr_d(double x) { return x == 0.0 ? 1.0 : x / expm1(x); }
+__device__ __forceinline__ float exprelr_f(float x) { return x == 0.0f ? 1.0f : x / expm1f(x); }
+
+struct Rates { double am, bm, ah, bh, an, bn; };
+struct RatesF { float am, bm, ah, bh, an, bn; };
+
+__device__ __forceinline__ Rates hh_rates(double v) {
+    Rates r;
+    r.am = exprelr_d((v + 40.0) * -0.1);
+    r.bm = 4.0 * exp((v + 65.0) * (-1.0 / 18.0));
+    r.ah = 0.07 * exp((v + 65.0) * -0.05);
+    r.bh = 1.0 / (1.0 + exp((v + 35.0) * -0.1));
+    r.an = 0.1 * exprelr_d((v + 55.0) * -0.1);
+    r.bn = 0.125 * exp((v + 65.0) * -0.0125);
+    return r;
+}
+
+__device__ __forceinline__ RatesF hh_rates(float v) {
+    RatesF r;
+    r.am = exprelr_f((v + 40.0f) * -0.1f);
+    r.bm = 4.0f * expf((v + 65.0f) * (-1.0f / 18.0f));
+    r.ah = 0.07f * expf((v + 65.0f) * -0.05f);
+    r.bh = 1.0f / (1.0f + expf((v + 35.0f) * -0.1f));
+    r.an = 0.1f * exprelr_f((v + 55.0f) * -0.1f);
+    r.bn = 0.125f * expf((v + 65.0f) * -0.0125f);
+    return r;
+}
+
+__device__ __forceinline__ double gate(double x, double a, double b, double dt) {
+    const double s = a + b;
+    const double xinf = a / s;
+    return xinf + (x - xinf) * exp(-dt * s);
+}
+__device__ __forceinline__ float gate(float x, float a, float b, float dt) {
+    const float s = a + b;
+    const float xinf = a / s;
+    return xinf + (x - xinf) * expf(-dt * s);
+}
+
+// ------------------------------------------------------------------------------------------
+// Derivatives for the discrete adjoint (FP64).
+
+// d/dx of x / (e^x - 1): for |x| < 0.1 the derivative of the Bernoulli series
+// sum_n B_n x^n / n! up to x^7 (the first omitted term is below 3e-16 there), elsewhere the
+// closed form (e^x - 1 - x e^x) / (e^x - 1)^2.
+__device__ __forceinline__ double exprelr_deriv_d(double x) {
+    if (fabs(x) < 0.1) {
+        const double x2 = x * x;
+        return -0.5 + x * (1.0 / 6.0 + x2 * (-1.0 / 180.0 + x2 * (1.0 / 5040.0 - x2 * (1.0 / 151200.0))));
+    }
+    const double em = expm1(x);
+    return (em - x * (em + 1.0)) / (em * em);
+}
+
+// dRates/dV (1/(ms mV)) given the rates at v.
+__device__ __forceinline__ Rates hh_rate_derivs(double v, const Rates& r) {
+    Rates d;
+    d.am = -0.1 * exprelr_deriv_d((v + 40.0) * -0.1);
+    d.bm = r.bm * (-1.0 / 18.0);
+    d.ah = r.ah * -0.05;
+    d.bh = r.bh * (1.0 - r.bh) * 0.1;
+    d.an = -0.01 * exprelr_deriv_d((v + 55.0) * -0.1);
+    d.bn = r.bn * -0.0125;
+    return d;
+}
+
+// d/dV of the exact gate update xinf + (x - xinf) exp(-dt s), s = a + b, at frozen V;
+// e = exp(-dt s) is passed in.
+__device__ __forceinline__ double gate_dv(double x, double a, double b, double da, double db, double dt, double e) {
+    const double s = a + b, ds = da + db;
+    const double xinf = a / s;
+    const double dxinf = (da * s - a * ds) / (s * s);
+    return dxinf * (1.0 - e) - (x - xinf) * e * dt * ds;
+}
+
+}  // namespace arbk

@@ -204,4 +204,52 @@ struct SpkArgs {
     double dt;
 };
 
+// Discrete adjoint (model order: CVs of a cell contiguous, parent index below the child's).
+// Per-step state: V [n_cv] and the gates Y [3][n_hh] (m, h, n of HH instance j).
+struct AdjArgs {
+    int32_t n_cells;
+    int64_t n_cv, n_hh;
+    const int64_t* off;        // [n_cells+1]
+    const int32_t* parent;     // [n_cv] cell-local parent, -1 at the root
+    const double* cdt;         // [n_cv] C / dt (nF/ms = uS)
+    const double* sig;         // [n_cv] axial conductance to the parent (uS), 0 at the root
+    const double* dsig;        // [n_cv] sum of the axial conductances of the CV (own + children)
+    const double* glin;        // [n_cv] passive conductance (uS)
+    const double* gelin;       // [n_cv] passive conductance x reversal (nA)
+    const double* area;        // [n_cv] um^2
+    const int32_t* hidx;       // [n_cv] HH instance on the CV, -1 none
+    const double* gna;         // [n_hh] uS
+    const double* gk;
+    const double* gl;
+    const int64_t* st_ptr;     // [n_cells+1] clamps of each cell
+    const int64_t* st_cv;      // global CV
+    const double* st_on;
+    const double* st_dur;
+    const double* st_amp;
+    const int32_t* obs;        // [n_cv] loss column of the CV, -1 none
+    int64_t n_obs;
+    const double* target;      // [n_steps][n_obs]
+    double loss_scale;
+    double dt;
+    int64_t k0;                // step of the handle at the start
+    int64_t n_steps;
+    int32_t ckpt;              // steps between checkpoints
+    double* V;                 // [n_cv] running state (forward pass)
+    double* Y;                 // [3][n_hh]
+    double* ckV;               // [n_ckpt][n_cv]
+    double* ckY;               // [n_ckpt][3][n_hh]
+    double* segV;              // [ckpt+1][n_cv]
+    double* segY;              // [ckpt+1][3][n_hh]
+    double* d;                 // [n_cv] solve scratch
+    double* b;                 // [n_cv]
+    double* lam;               // [n_cv] solve result of the later step
+    double* ybar;              // [3][n_hh]
+    double* gacc;              // [4][n_cv] gradient per CV: gnabar, gkbar, gl, cm
+    double* cell_loss;         // [n_cells]
+    const int64_t* grp_ptr;    // [n_groups+1] CVs of each parameter group, ascending
+    const int64_t* grp_cv;
+    int32_t n_groups;
+    double* grad;              // [n_groups][4] output
+};
+
 }  // namespace arbk

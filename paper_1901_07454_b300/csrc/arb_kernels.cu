@@ -12,53 +12,11 @@
 #include <cmath>
 #include <cstdint>
 
+#include "arb_hh.cuh"
 #include "arb_internal.h"
 
 namespace arbk {
 
-// ------------------------------------------------------------------------------------------
-// Hodgkin-Huxley rates (1/ms) and exact gate update at frozen V, in the precision MT.
-// The model (classic squid axon at 6.3 degC) is the one named by the paper's benchmark
-// (Sec. "Benchmarks", "Models": Hodgkin-Huxley soma, passive dendrites).
-
-__device__ __forceinline__ double exprelr_d(double x) { return x == 0.0 ? 1.0 : x / expm1(x); }
-__device__ __forceinline__ float exprelr_f(float x) { return x == 0.0f ? 1.0f : x / expm1f(x); }
-
-struct Rates { double am, bm, ah, bh, an, bn; };
-struct RatesF { float am, bm, ah, bh, an, bn; };
-
-__device__ __forceinline__ Rates hh_rates(double v) {
-    Rates r;
-    r.am = exprelr_d((v + 40.0) * -0.1);
-    r.bm = 4.0 * exp((v + 65.0) * (-1.0 / 18.0));
-    r.ah = 0.07 * exp((v + 65.0) * -0.05);
-    r.bh = 1.0 / (1.0 + exp((v + 35.0) * -0.1));
-    r.an = 0.1 * exprelr_d((v + 55.0) * -0.1);
-    r.bn = 0.125 * exp((v + 65.0) * -0.0125);
-    return r;
-}
-
-__device__ __forceinline__ RatesF hh_rates(float v) {
-    RatesF r;
-    r.am = exprelr_f((v + 40.0f) * -0.1f);
-    r.bm = 4.0f * expf((v + 65.0f) * (-1.0f / 18.0f));
-    r.ah = 0.07f * expf((v + 65.0f) * -0.05f);
-    r.bh = 1.0f / (1.0f + expf((v + 35.0f) * -0.1f));
-    r.an = 0.1f * exprelr_f((v + 55.0f) * -0.1f);
-    r.bn = 0.125f * expf((v + 65.0f) * -0.0125f);
-    return r;
-}
-
-__device__ __forceinline__ double gate(double x, double a, double b, double dt) {
-    const double s = a + b;
-    const double xinf = a / s;
-    return xinf + (x - xinf) * exp(-dt * s);
-}
-__device__ __forceinline__ float gate(float x, float a, float b, float dt) {
-    const float s = a + b;
-    const float xinf = a / s;
-    return xinf + (x - xinf) * expf(-dt * s);
-}
 
 // 1/x for the positive pivots of the implicit scheme: the hardware estimate (about 20 correct
 // bits) refined by one third-order step, r <- r + r (e + e^2) with e = 1 - x r, which triples

@@ -40,6 +40,9 @@ template <class T>
 cudaError_t launch_gather(double* out, const T* src, const int64_t* idx, int64_t n, cudaStream_t s);
 template <class T>
 cudaError_t launch_scatter(T* dst, const double* src, const int64_t* idx, int64_t n, cudaStream_t s);
+cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, int mode, cudaStream_t s);
+cudaError_t launch_adj_reverse(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s);
+cudaError_t launch_adj_reduce(const AdjArgs& a, cudaStream_t s);
 
 }  // namespace arbk
 
@@ -186,6 +189,32 @@ void hh_steady(double v, double& m, double& h, double& n) {
     m = am / (am + bm);
     h = ah / (ah + bh);
     n = an / (an + bn);
+}
+
+// Per-CV membrane area (um^2), capacitance (nF) and axial conductance to the parent (uS):
+// each CV is a cylinder; the conductance between a CV and its parent is that of the two half
+// cylinders between their centres in series (Sec. "Model", Eq. discrete-v).
+void cv_geometry(const arb_sim* sim, std::vector<double>& area, std::vector<double>& cap, std::vector<double>& sigma) {
+    const int64_t ncv = sim->n_cv;
+    area.assign(ncv, 0.0);
+    cap.assign(ncv, 0.0);
+    sigma.assign(ncv, 0.0);
+    for (int32_t c = 0; c < sim->n_cells; ++c) {
+        const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t g = off + i;
+            const double h = sim->length[g], r = sim->radius[g];
+            area[g] = 2.0 * kPi * r * h;                  // um^2
+            cap[g] = sim->cm[g] * area[g] * 1e-5;         // nF
+            if (i > 0) {
+                const int64_t pg = off + sim->parent[g];
+                // half-cylinder resistances in series, MOhm
+                const double half_i = sim->Ra[g] * h / (200.0 * kPi * r * r);
+                const double half_p = sim->Ra[pg] * sim->length[pg] / (200.0 * kPi * sim->radius[pg] * sim->radius[pg]);
+                sigma[g] = 1.0 / (half_i + half_p);       // uS
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -660,23 +689,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         return bad("epoch of " + std::to_string(sim->epoch_steps) + " steps is longer than the minimum delay");
 
     // ------------------------------------------------------------------ discretisation
-    std::vector<double> area(ncv), cap(ncv), sigma(ncv, 0.0), Glin(ncv, 0.0), GElin(ncv, 0.0);
-    for (int32_t c = 0; c < nc; ++c) {
-        const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t g = off + i;
-            const double h = sim->length[g], r = sim->radius[g];
-            area[g] = 2.0 * kPi * r * h;                  // um^2
-            cap[g] = sim->cm[g] * area[g] * 1e-5;         // nF
-            if (i > 0) {
-                const int64_t pg = off + sim->parent[g];
-                // half-cylinder resistances in series, MOhm
-                const double half_i = sim->Ra[g] * h / (200.0 * kPi * r * r);
-                const double half_p = sim->Ra[pg] * sim->length[pg] / (200.0 * kPi * sim->radius[pg] * sim->radius[pg]);
-                sigma[g] = 1.0 / (half_i + half_p);       // uS
-            }
-        }
-    }
+    std::vector<double> area, cap, sigma, Glin(ncv, 0.0), GElin(ncv, 0.0);
+    cv_geometry(sim, area, cap, sigma);
     for (size_t i = 0; i < sim->pas_cv.size(); ++i) {
         const int64_t cv = sim->pas_cv[i];
         const double G = sim->g_pas[i] * area[cv] * 1e-2;  // S/cm^2 * um^2 -> uS
@@ -2040,6 +2054,255 @@ arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t*
     if (epoch_kernel_ms) *epoch_kernel_ms = sim->last_epoch_ms;
     if (launches) *launches = sim->last_launches;
     return ARB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Discrete adjoint
+
+namespace {
+
+struct AdjLayout {
+    std::vector<std::pair<std::string, Region>> r;
+    size_t total = 0;
+    void add(const char* name, size_t bytes) {
+        Region g;
+        g.off = total;
+        g.bytes = bytes;
+        r.push_back({name, g});
+        total += (bytes + 255) & ~(size_t)255;
+    }
+    char* at(char* base, const char* name) const {
+        for (const auto& x : r) if (x.first == name) return base + x.second.off;
+        return nullptr;
+    }
+};
+
+AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t n_obs, int32_t n_groups) {
+    (void)n_obs;
+    const int64_t nc = sim->n_cells, ncv = sim->n_cv, nhh = (int64_t)sim->hh_cv.size(), nst = (int64_t)sim->st_cv.size();
+    const int64_t nck = (n_steps + ckpt - 1) / ckpt, seg = std::min<int64_t>(ckpt, n_steps);
+    AdjLayout L;
+    L.add("off", 8 * (nc + 1));
+    L.add("parent", 4 * ncv);
+    for (const char* n : {"cdt", "sig", "dsig", "glin", "gelin", "area"}) L.add(n, 8 * ncv);
+    L.add("hidx", 4 * ncv);
+    for (const char* n : {"gna", "gk", "gl"}) L.add(n, 8 * nhh);
+    L.add("st_ptr", 8 * (nc + 1));
+    for (const char* n : {"st_cv", "st_on", "st_dur", "st_amp"}) L.add(n, 8 * nst);
+    L.add("obs", 4 * ncv);
+    L.add("V", 8 * ncv);
+    L.add("Y", 24 * nhh);
+    L.add("ckV", 8 * ncv * nck);
+    L.add("ckY", 24 * nhh * nck);
+    L.add("segV", 8 * ncv * (seg + 1));
+    L.add("segY", 24 * nhh * (seg + 1));
+    for (const char* n : {"d", "b", "lam"}) L.add(n, 8 * ncv);
+    L.add("ybar", 24 * nhh);
+    L.add("gacc", 32 * ncv);
+    L.add("cell_loss", 8 * nc);
+    L.add("grp_ptr", 8 * ((int64_t)n_groups + 1));
+    L.add("grp_cv", 8 * ncv);
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+arb_status arb_adjoint_workspace_bytes(const arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, int64_t n_obs,
+                                       int32_t n_groups, int64_t* bytes) {
+    if (!sim || !bytes) return ARB_E_ARG;
+    if (n_steps < 1 || checkpoint_every < 1 || n_obs < 0 || n_groups < 0) return ARB_E_ARG;
+    *bytes = (int64_t)adj_layout(sim, n_steps, checkpoint_every, n_obs, n_groups).total;
+    return ARB_OK;
+}
+
+arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, int64_t n_obs, const int64_t* obs_cv,
+                       const double* target, double loss_scale, const int32_t* group_of_cv, int32_t n_groups,
+                       void* workspace, int64_t workspace_bytes, double* grad, double* loss) {
+    if (!sim) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "bind a workspace first");
+    if (!sim->implicit) return fail(sim, ARB_E_ARG, "the adjoint is defined for the implicit scheme only");
+    if (!sim->syn_cv.empty()) return fail(sim, ARB_E_ARG, "the adjoint does not support synapses");
+    if (n_steps < 1 || checkpoint_every < 1) return fail(sim, ARB_E_ARG, "n_steps and checkpoint_every must be >= 1");
+    if (n_obs < 0 || n_groups < 0) return fail(sim, ARB_E_ARG, "n_obs and n_groups must be >= 0");
+    if ((n_obs > 0 && (!obs_cv || !target)) || (n_groups > 0 && (!group_of_cv || !grad)) || !loss)
+        return fail(sim, ARB_E_ARG, "NULL array");
+    if (!std::isfinite(loss_scale)) return fail(sim, ARB_E_ARG, "loss_scale must be finite");
+    const int64_t nc = sim->n_cells, ncv = sim->n_cv, nhh = (int64_t)sim->hh_cv.size(), nst = (int64_t)sim->st_cv.size();
+    const AdjLayout L = adj_layout(sim, n_steps, checkpoint_every, n_obs, n_groups);
+    if (!workspace || ((uintptr_t)workspace & 255) != 0) return fail(sim, ARB_E_ARG, "workspace must be 256-byte aligned");
+    if (workspace_bytes < (int64_t)L.total) return fail(sim, ARB_E_ARG, "workspace too small (see arb_adjoint_workspace_bytes)");
+    {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, workspace) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(sim, ARB_E_ARG, "workspace must be device memory");
+        }
+    }
+    // host-side constants, model order
+    std::vector<int32_t> obs(ncv, -1);
+    for (int64_t o = 0; o < n_obs; ++o) {
+        const int64_t cv = obs_cv[o];
+        if (cv < 0 || cv >= ncv) return fail(sim, ARB_E_ARG, "observed CV out of range");
+        if (obs[cv] >= 0) return fail(sim, ARB_E_ARG, "observed CVs must be distinct");
+        obs[cv] = (int32_t)o;
+    }
+    std::vector<int64_t> grp_ptr((size_t)n_groups + 1, 0), grp_cv;
+    if (n_groups > 0) {
+        for (int64_t i = 0; i < ncv; ++i) {
+            const int32_t g = group_of_cv[i];
+            if (g < -1 || g >= n_groups) return fail(sim, ARB_E_ARG, "group_of_cv out of range");
+            if (g >= 0) grp_ptr[g + 1]++;
+        }
+        for (int32_t g = 0; g < n_groups; ++g) grp_ptr[g + 1] += grp_ptr[g];
+        grp_cv.assign(grp_ptr[n_groups], 0);
+        std::vector<int64_t> fill(grp_ptr.begin(), grp_ptr.end() - 1);
+        for (int64_t i = 0; i < ncv; ++i)
+            if (group_of_cv[i] >= 0) grp_cv[fill[group_of_cv[i]]++] = i;
+    }
+    const double dt = sim->prm.dt;
+    std::vector<double> area, cap, sigma;
+    cv_geometry(sim, area, cap, sigma);
+    std::vector<double> cdt(ncv), dsig(sigma), glin(ncv, 0.0), gelin(ncv, 0.0);
+    for (int64_t i = 0; i < ncv; ++i) cdt[i] = cap[i] / dt;
+    for (int32_t c = 0; c < nc; ++c)
+        for (int64_t i = sim->cv_offset[c] + 1; i < sim->cv_offset[c + 1]; ++i) dsig[sim->cv_offset[c] + sim->parent[i]] += sigma[i];
+    for (size_t q = 0; q < sim->pas_cv.size(); ++q) {
+        const int64_t cv = sim->pas_cv[q];
+        const double G = sim->g_pas[q] * area[cv] * 1e-2;
+        glin[cv] += G;
+        gelin[cv] += G * sim->e_pas[q];
+    }
+    std::vector<int32_t> hidx(ncv, -1);
+    std::vector<double> gna(nhh), gk(nhh), gl(nhh);
+    for (int64_t j = 0; j < nhh; ++j) {
+        const int64_t cv = sim->hh_cv[j];
+        hidx[cv] = (int32_t)j;
+        gna[j] = sim->gnabar[j] * area[cv] * 1e-2;
+        gk[j] = sim->gkbar[j] * area[cv] * 1e-2;
+        gl[j] = sim->gl[j] * area[cv] * 1e-2;
+    }
+    // clamps grouped by cell
+    std::vector<int64_t> st_ptr(nc + 1, 0), st_cv(nst);
+    std::vector<double> st_on(nst), st_dur(nst), st_amp(nst);
+    {
+        std::vector<int32_t> cell_of(ncv);
+        for (int32_t c = 0; c < nc; ++c)
+            for (int64_t i = sim->cv_offset[c]; i < sim->cv_offset[c + 1]; ++i) cell_of[i] = c;
+        for (int64_t q = 0; q < nst; ++q) st_ptr[cell_of[sim->st_cv[q]] + 1]++;
+        for (int32_t c = 0; c < nc; ++c) st_ptr[c + 1] += st_ptr[c];
+        std::vector<int64_t> fill(st_ptr.begin(), st_ptr.end() - 1);
+        for (int64_t q = 0; q < nst; ++q) {
+            const int64_t w = fill[cell_of[sim->st_cv[q]]]++;
+            st_cv[w] = sim->st_cv[q];
+            st_on[w] = sim->st_on[q];
+            st_dur[w] = sim->st_dur[q];
+            st_amp[w] = sim->st_amp[q];
+        }
+    }
+    arb_status st = sync_in(sim);
+    if (st != ARB_OK) return st;
+    char* base = (char*)workspace;
+    auto up = [&](const char* name, const void* src, size_t bytes) -> arb_status {
+        if (bytes == 0) return ARB_OK;
+        CU(cudaMemcpyAsync(L.at(base, name), src, bytes, cudaMemcpyHostToDevice, sim->s));
+        return ARB_OK;
+    };
+    if ((st = up("off", sim->cv_offset.data(), 8 * (nc + 1))) != ARB_OK || (st = up("parent", sim->parent.data(), 4 * ncv)) != ARB_OK ||
+        (st = up("cdt", cdt.data(), 8 * ncv)) != ARB_OK || (st = up("sig", sigma.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("dsig", dsig.data(), 8 * ncv)) != ARB_OK || (st = up("glin", glin.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("gelin", gelin.data(), 8 * ncv)) != ARB_OK || (st = up("area", area.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("hidx", hidx.data(), 4 * ncv)) != ARB_OK || (st = up("gna", gna.data(), 8 * nhh)) != ARB_OK ||
+        (st = up("gk", gk.data(), 8 * nhh)) != ARB_OK || (st = up("gl", gl.data(), 8 * nhh)) != ARB_OK ||
+        (st = up("st_ptr", st_ptr.data(), 8 * (nc + 1))) != ARB_OK || (st = up("st_cv", st_cv.data(), 8 * nst)) != ARB_OK ||
+        (st = up("st_on", st_on.data(), 8 * nst)) != ARB_OK || (st = up("st_dur", st_dur.data(), 8 * nst)) != ARB_OK ||
+        (st = up("st_amp", st_amp.data(), 8 * nst)) != ARB_OK || (st = up("obs", obs.data(), 4 * ncv)) != ARB_OK ||
+        (st = up("grp_ptr", grp_ptr.data(), 8 * ((size_t)n_groups + 1))) != ARB_OK ||
+        (st = up("grp_cv", grp_cv.data(), 8 * grp_cv.size())) != ARB_OK)
+        return st;
+    AdjArgs a{};
+    a.n_cells = (int32_t)nc;
+    a.n_cv = ncv;
+    a.n_hh = nhh;
+    a.off = (const int64_t*)L.at(base, "off");
+    a.parent = (const int32_t*)L.at(base, "parent");
+    a.cdt = (const double*)L.at(base, "cdt");
+    a.sig = (const double*)L.at(base, "sig");
+    a.dsig = (const double*)L.at(base, "dsig");
+    a.glin = (const double*)L.at(base, "glin");
+    a.gelin = (const double*)L.at(base, "gelin");
+    a.area = (const double*)L.at(base, "area");
+    a.hidx = (const int32_t*)L.at(base, "hidx");
+    a.gna = (const double*)L.at(base, "gna");
+    a.gk = (const double*)L.at(base, "gk");
+    a.gl = (const double*)L.at(base, "gl");
+    a.st_ptr = (const int64_t*)L.at(base, "st_ptr");
+    a.st_cv = (const int64_t*)L.at(base, "st_cv");
+    a.st_on = (const double*)L.at(base, "st_on");
+    a.st_dur = (const double*)L.at(base, "st_dur");
+    a.st_amp = (const double*)L.at(base, "st_amp");
+    a.obs = (const int32_t*)L.at(base, "obs");
+    a.n_obs = n_obs;
+    a.target = target;
+    a.loss_scale = loss_scale;
+    a.dt = dt;
+    a.k0 = sim->k;
+    a.n_steps = n_steps;
+    a.ckpt = checkpoint_every;
+    a.V = (double*)L.at(base, "V");
+    a.Y = (double*)L.at(base, "Y");
+    a.ckV = (double*)L.at(base, "ckV");
+    a.ckY = (double*)L.at(base, "ckY");
+    a.segV = (double*)L.at(base, "segV");
+    a.segY = (double*)L.at(base, "segY");
+    a.d = (double*)L.at(base, "d");
+    a.b = (double*)L.at(base, "b");
+    a.lam = (double*)L.at(base, "lam");
+    a.ybar = (double*)L.at(base, "ybar");
+    a.gacc = (double*)L.at(base, "gacc");
+    a.cell_loss = (double*)L.at(base, "cell_loss");
+    a.grp_ptr = (const int64_t*)L.at(base, "grp_ptr");
+    a.grp_cv = (const int64_t*)L.at(base, "grp_cv");
+    a.n_groups = n_groups;
+    a.grad = grad;
+    // the handle's current state, in model order
+    CU(launch_gather<double>(a.V, (const double*)region(sim, "V"), (const int64_t*)region(sim, "cv_tile"), ncv, sim->s));
+    const char* gname[3] = {"hh_m", "hh_h", "hh_n"};
+    for (int g = 0; g < 3 && nhh > 0; ++g) {
+        const int64_t* idx = (const int64_t*)region(sim, "hh_entry");
+        if (sim->mixed) CU(launch_gather<float>(a.Y + g * nhh, (const float*)region(sim, gname[g]), idx, nhh, sim->s));
+        else CU(launch_gather<double>(a.Y + g * nhh, (const double*)region(sim, gname[g]), idx, nhh, sim->s));
+    }
+    CU(cudaMemsetAsync(a.lam, 0, 8 * ncv, sim->s));
+    if (nhh > 0) CU(cudaMemsetAsync(a.ybar, 0, 24 * nhh, sim->s));
+    CU(cudaMemsetAsync(a.gacc, 0, 32 * ncv, sim->s));
+    CU(cudaMemsetAsync(a.cell_loss, 0, 8 * nc, sim->s));
+    // forward with checkpoints, then segment by segment backwards: recompute, reverse sweep
+    CU(cudaEventRecord(sim->t0[0], sim->s));
+    CU(launch_adj_forward(a, 0, n_steps, 0, sim->s));
+    const int64_t nck = (n_steps + checkpoint_every - 1) / checkpoint_every;
+    for (int64_t sgi = nck - 1; sgi >= 0; --sgi) {
+        const int64_t s0 = sgi * checkpoint_every, s1 = std::min<int64_t>(n_steps, s0 + checkpoint_every);
+        CU(launch_adj_forward(a, s0, s1, 1, sim->s));
+        CU(launch_adj_reverse(a, s0, s1, sim->s));
+    }
+    CU(launch_adj_reduce(a, sim->s));
+    CU(cudaEventRecord(sim->t1[0], sim->s));
+    std::vector<double> cl(nc);
+    if (nc > 0) CU(cudaMemcpyAsync(cl.data(), a.cell_loss, 8 * nc, cudaMemcpyDeviceToHost, sim->s));
+    CU(cudaStreamSynchronize(sim->s));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, sim->t0[0], sim->t1[0]));
+    sim->pending_time[0] = false;
+    sim->last_epoch_ms = ms;
+    sim->last_launches = 2 + 2 * nck;
+    double total = 0.0;
+    for (double x : cl) total += x;
+    *loss = total;
+    return sync_out(sim);
 }
 
 }  // extern "C"

@@ -198,3 +198,27 @@ class Simulation(Plan):
         ms, n = C.c_double(), C.c_int64()
         L.check(L.load().arb_last_timing(self.h, C.byref(ms), C.byref(n)), self.h)
         return ms.value, n.value
+
+    # --- discrete adjoint
+    def adjoint(self, n_steps, obs_cv, target, loss_scale, group_of_cv, n_groups, checkpoint_every=500):
+        """Loss and gradient over the next n_steps from the current state (arb_adjoint); the
+        state is left unchanged. target: [n_steps, n_obs] (host or device); returns
+        (loss float, grad float64 tensor [n_groups, 4] on the device)."""
+        torch = self.torch
+        lib = L.load()
+        n_steps, n_groups = int(n_steps), int(n_groups)
+        obs_cv = np.ascontiguousarray(obs_cv, np.int64)
+        group = np.ascontiguousarray(group_of_cv, np.int32)
+        tgt = torch.as_tensor(target, dtype=torch.float64).to(self.device).reshape(n_steps, obs_cv.size).contiguous()
+        nbytes = C.c_int64()
+        L.check(lib.arb_adjoint_workspace_bytes(self.h, n_steps, int(checkpoint_every), obs_cv.size, n_groups,
+                                                C.byref(nbytes)), self.h)
+        ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        aligned = (ws.data_ptr() + 255) & ~255
+        grad = torch.zeros((n_groups, 4), dtype=torch.float64, device=self.device)
+        loss = C.c_double()
+        L.check(lib.arb_adjoint(self.h, n_steps, int(checkpoint_every), obs_cv.size, _p(obs_cv),
+                                C.c_void_p(tgt.data_ptr()), float(loss_scale), _p(group), n_groups,
+                                C.c_void_p(aligned), nbytes.value, C.c_void_p(grad.data_ptr()), C.byref(loss)), self.h)
+        self._adj_keep = (ws, tgt)     # freed with the next call or the handle
+        return loss.value, grad
