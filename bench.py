@@ -34,6 +34,7 @@ WORKLOADS = {
     "ring": (1, "fp64"),
     "batched": (2, "fp64"),
     "mixed": (3, "mixed"),
+    "adjoint": (4, "fp64"),
 }
 
 
@@ -44,6 +45,20 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+# FP64 issue ceiling of a B300: 148 SMs x 2 FP64 FMA lanes per clock x 2032 MHz (the SM count
+# and maximum clock of the part; 2 per clock per SM is ncu's peak_sustained for
+# sm__sass_thread_inst_executed_op_dfma_pred_on). In FLOP/s (FMA = 2) this is 1.2 PFLOP/s /
+# 1000, i.e. the 1.2 TFLOP/s FP64 of the part.
+FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
+
+# FP64 thread instructions (DFMA + DMUL + DADD) the streamed epoch kernel executes per
+# CV-step, and its DRAM bytes per CV-step, on the batched workload: from the ncu capture of
+# 40,000 cells (profiles/stream_kernel_batched_40000cells.md), which has the same cell-size
+# mix, synapse and HH densities per CV as the full 65,536-cell workload.
+STREAM_FP64_PER_CV_STEP = {"batched": 20.0}
+STREAM_DRAM_BYTES_PER_CV_STEP = {}      # taken before the kernel's last change: not reported
 
 
 def algorithmic_bytes_per_cv_step(model, precision):
@@ -154,6 +169,106 @@ def run_reference(args, model, spec, precision, workload_name):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_inputs(model, spec):
+    """Loss inputs of the fitting workload: soma observations and the loss scale; the target
+    traces are those of the hidden parameter set (computed by the caller's forward path)."""
+    obs = model.cv_offset[:-1].copy()
+    K = spec.n_steps
+    group, ng = model.param_groups()
+    return obs, K, 1.0 / (K * obs.size), group, ng
+
+
+def run_adjoint(args, model, spec):
+    """One step = the loss and gradient of the whole run (n_steps time steps forward, then the
+    checkpointed reverse sweep) for all cells. Metric: compartment-steps of the run per second
+    of gradient evaluation."""
+    from inputs import make_config
+    obs, K, scale, group, ng = adjoint_inputs(model, spec)
+    tgt_model, _ = make_config(4, n_cells=model.n_cells, t_end=spec.t_end, variant="target")
+    rank, world, _ = dist_env()
+    name = "adjoint: %s, %d cells, %d CVs, %d steps of dt %.3f ms, checkpoint every %d steps, %d parameters" % (
+        spec.name, model.n_cells, model.n_cv, K, spec.dt, args.checkpoint_every, 4 * ng)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        from inputs.sample import submodel
+        cells = np.arange(min(model.n_cells, max(1, args.ref_cells)))
+        sm, ss, cv_old = submodel(model, spec, cells)
+        st, _, _ = submodel(tgt_model, spec, cells)
+        so = sm.cv_offset[:-1].copy()
+        _, target = oracle.simulate(st, ss, probes=so)
+        sg, sng = sm.param_groups()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.OracleSim(sm, spec.dt, spec.epoch_steps).adjoint(K, so, target, scale, sg, sng)
+        el = time.perf_counter() - t0
+        value = sm.n_cv * K * args.steps / el
+        print(json.dumps({
+            "impl": "reference", "metric": "compartment-steps/sec (gradient)", "value": value, "unit": "CV-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sampled_cells": int(cells.size)},
+            "cpu_baseline": {"value": value, "unit": "CV-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "%d of %d cells, whole run" % (cells.size, model.n_cells)},
+            "e2e": {"value": value, "unit": "CV-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_1901_07454_b300 as arb
+    # target traces of the hidden parameters: an input of the workload, made by the forward path
+    ts = arb.Simulation(tgt_model, dt=spec.dt, epoch_steps=spec.epoch_steps)
+    tr = ts.set_probes(obs, K)
+    ts.advance(spec.t_end)
+    target = tr.clone()
+    del ts
+    sim = arb.Simulation(model, dt=spec.dt, epoch_steps=spec.epoch_steps)
+    for _ in range(args.warmup):
+        sim.adjoint(K, obs, target, scale, group, ng, checkpoint_every=args.checkpoint_every)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss, grad = sim.adjoint(K, obs, target, scale, group, ng, checkpoint_every=args.checkpoint_every)
+        kern.append(sim.last_timing()[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot_ms = e0.elapsed_time(e1)
+    units = model.n_cv * K * args.steps
+    value = units / (tot_ms * 1e-3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        from inputs.sample import submodel
+        cells = np.arange(min(model.n_cells, 8))
+        sm, ss, _ = submodel(model, spec, cells)
+        sg, sng = sm.param_groups()
+        so = sm.cv_offset[:-1].copy()
+        tcpu = tr.cpu().numpy()[:, cells]
+        t0 = time.perf_counter()
+        oracle.OracleSim(sm, spec.dt, spec.epoch_steps).adjoint(K, so, tcpu, scale, sg, sng)
+        el = time.perf_counter() - t0
+        cpu = {"value": sm.n_cv * K / el, "unit": "CV-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d of %d cells, whole run (%d steps), %.1f s" % (cells.size, model.n_cells, K, el)}
+    print(json.dumps({
+        "metric": "compartment-steps/sec (gradient)", "value": value, "unit": "CV-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "cells": model.n_cells, "cvs": model.n_cv, "loss": loss,
+                   "l2": "working set (checkpoints and a 500-step segment, ~1.3 GB) larger than L2"},
+        "adjoint_kernels_ms_mean": sum(kern) / len(kern),
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": sim.last_timing()[1] * args.steps, "clocks": clk}), flush=True)
+
+
 def cpu_baseline(model, spec, budget_s):
     """Oracle on all host cores over a bounded sample: whole epochs of all cells until about
     budget_s seconds have passed (at least one epoch)."""
@@ -190,6 +305,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cells", type=int, default=0, help="use only this many cells of the workload (0 = all)")
     ap.add_argument("--scheme", default="implicit", choices=["implicit", "explicit"])
+    ap.add_argument("--checkpoint-every", type=int, default=500, help="adjoint workload: steps between checkpoints")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -198,6 +314,8 @@ def main():
     E_ms = None
     ncells = args.cells if args.cells > 0 else None
     model, spec = make_config(cfg, n_cells=ncells, t_end=None)
+    if args.workload == "adjoint":
+        return run_adjoint(args, model, spec)
     E = spec.epoch_steps
     # the run must cover warm-up + timed epochs: extend external inputs if needed
     need_t = (args.warmup + args.steps) * E * spec.dt
@@ -264,12 +382,30 @@ def main():
     value = units / (tot_ms * 1e-3)
     nspk = sim.num_spikes()
 
-    # roofline of the dominant kernel (the epoch kernel): algorithmic bytes per launch over
-    # its mean launch time (CUDA events around it on the library's stream)
+    # roofline of the dominant kernel (the epoch kernel), timed with CUDA events around it on
+    # the library's stream: FP64 issue (what binds it) and HBM (algorithmic bytes)
     bpc = algorithmic_bytes_per_cv_step(model, precision)
     kern_mean_ms = sum(kern_ms) / len(kern_ms)
     achieved = bpc * model.n_cv * E / (kern_mean_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    streamed = info["cells_per_pack"] == 32
+    kname = "arb_stream_kernel" if streamed else "arb_epoch_kernel"
+    cv_steps_launch = model.n_cv * E
+    fp64_per = STREAM_FP64_PER_CV_STEP.get(args.workload) if (streamed and precision == "fp64") else None
+    dram_per = STREAM_DRAM_BYTES_PER_CV_STEP.get(args.workload) if (streamed and precision == "fp64") else None
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+           "algorithmic_bytes_per_cv_step": bpc,
+           "traffic": dram_per * cv_steps_launch if dram_per else None}
+    if fp64_per is not None:
+        ach = fp64_per * cv_steps_launch / (kern_mean_ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_INST_PER_S, "unit": "FP64 inst/s",
+                    "frac": ach / FP64_PEAK_INST_PER_S, "traffic": hbm["traffic"],
+                    "peak_kind": "derived: 148 SMs x 2 FP64 FMA/clk x 2032 MHz",
+                    "fp64_inst_per_cv_step": fp64_per, "kernel": kname, "kernel_ms_mean": kern_mean_ms, "hbm": hbm}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "peak_kind": peak_kind, "kernel": kname, "kernel_ms_mean": kern_mean_ms,
+                    "algorithmic_bytes_per_cv_step": bpc}
 
     # end to end through the public API with host buffers: create + upload from host arrays,
     # per step advance one epoch and read all voltages and spikes back to the host
@@ -314,11 +450,9 @@ def main():
                        "dt_ms": spec.dt, "step": "one epoch (%d time steps) of all cells incl. spike exchange" % E,
                        "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],
                        "lane_efficiency": round(info["lane_efficiency"], 4), "smem_packs": info["smem_packs"],
+                       "max_pack_rows": info["max_pack_rows"], "split_cvs": info["split_cvs"],
                        "spikes": nspk, "wall_s": wall, "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "arb_epoch_kernel", "kernel_ms_mean": kern_mean_ms,
-                         "algorithmic_bytes_per_cv_step": bpc},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -9,11 +9,15 @@
 //   Vbar = (C/dt) lam_{k+1} + dL/dV^{k+1} + sum_gates dPhi/dV ybar,   lam_k = A(y^k)^{-1} Vbar,
 // and the parameter and gate adjoints follow from lam_k, V^k, V^{k+1} and y^k.
 //
-// Work is per cell and cells never interact, so every kernel runs one warp per cell over a
+// Work is per cell and cells never interact, so every kernel runs one block per cell over a
 // whole range of steps: the element-wise parts (membrane terms, gates and their derivatives,
-// gradient terms) are spread over the lanes, the tree elimination runs on lane 0. The forward
-// pass keeps a checkpoint of the state every `ckpt` steps; the reverse pass recomputes one
-// segment from its checkpoint, keeping every state, and sweeps it backwards.
+// gradient terms) are spread over the block's threads; the tree solve runs in shared memory
+// on the first warp, which takes the cell's unbranched chains level by level (leaf chains
+// first), one chain per lane, and hands each chain's elimination to its parent chain through
+// a per-chain slot. The forward pass keeps a checkpoint of the state every `ckpt` steps. The
+// backward pass goes segment by segment: each stage sweeps one segment backwards while other
+// blocks of the same launch recompute the previous segment from its checkpoint into the second
+// segment buffer, keeping every state and the gate-update derivatives the sweep will need.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -24,7 +28,7 @@
 namespace arbk {
 namespace {
 
-constexpr int kAdjWarps = 1;   // warps per block: one cell per block spreads small batches over all SMs
+constexpr int kAdjThreads = 128;   // threads per cell (block)
 
 // Conductance (uS) and conductance x reversal (nA) of CV i with the gates of one step.
 __device__ __forceinline__ void membrane(const AdjArgs& a, int64_t i, const double* Y, double& G, double& GE) {
@@ -41,43 +45,107 @@ __device__ __forceinline__ void membrane(const AdjArgs& a, int64_t i, const doub
     }
 }
 
-// In-place tree solve of one cell (lane 0): diagonal d, off-diagonal -sigma, right-hand side b;
-// the solution replaces b. Elimination from the highest local index to the root, then back
-// substitution (parent index < child index).
-__device__ void tree_solve(const AdjArgs& a, int64_t off, int64_t n) {
-    double* d = a.d + off;
-    double* b = a.b + off;
-    const int32_t* par = a.parent + off;
-    const double* sg = a.sig + off;
-    for (int64_t i = n - 1; i >= 1; --i) {
-        const int32_t p = par[i];
-        const double f = sg[i] / d[i];
-        d[p] -= f * sg[i];
-        b[p] += f * b[i];
+struct Smem {
+    double* d;    // [smem_cv] diagonal, then eliminated pivots
+    double* b;    // [smem_cv] right-hand side, then the solution
+    double* r;    // [smem_cv] 1 / eliminated pivot
+    double* cd;   // [smem_ch] a chain's elimination into its parent's diagonal
+    double* cb;   //           ... and right-hand side
+};
+
+__device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
+    extern __shared__ double adj_smem[];
+    Smem m;
+    m.d = adj_smem;
+    m.b = m.d + a.smem_cv;
+    m.r = m.b + a.smem_cv;
+    m.cd = m.r + a.smem_cv;
+    m.cb = m.cd + a.smem_ch;
+    return m;
+}
+
+// Tree solve of cell c in shared memory (first warp): symmetric matrix with diagonal sm.d and
+// off-diagonal -sigma between a CV and its parent; the solution replaces sm.b.
+// Elimination: chains level by level from the leaves; within a chain from its tail (the CV
+// farthest from the root, which first takes its child chains' eliminations) to its head,
+// whose elimination goes to the chain's slot. Back substitution: levels in reverse order, each
+// chain from its head (using its parent's solution) to its tail.
+__device__ void chain_solve(const AdjArgs& a, int c, int64_t off, int lane, const Smem& sm) {
+    const int64_t q0 = a.ch_ptr[c];
+    const int64_t l0 = a.lev_off[c];
+    const int nl = (int)(a.lev_off[c + 1] - l0) - 1;
+    const double* sig = a.sig + off;
+    for (int L = 0; L < nl; ++L) {
+        for (int64_t q = a.lev_bound[l0 + L] + lane; q < a.lev_bound[l0 + L + 1]; q += 32) {
+            const int64_t cs = a.ch_cv_ptr[q], ce = a.ch_cv_ptr[q + 1];
+            int x = a.ch_cvs[ce - 1];
+            double dx = sm.d[x], bx = sm.b[x];
+            for (int64_t k = a.ch_kid_ptr[q]; k < a.ch_kid_ptr[q + 1]; ++k) {
+                const int64_t j = a.ch_kids[k] - q0;
+                dx += sm.cd[j];
+                bx += sm.cb[j];
+            }
+            for (int64_t u = ce - 1; u > cs; --u) {
+                const int y = a.ch_cvs[u - 1];
+                const double sg = sig[x];
+                const double r = rcp_nr(dx);
+                sm.r[x] = r;
+                sm.b[x] = bx;
+                const double f = sg * r;
+                dx = sm.d[y] - f * sg;
+                bx = sm.b[y] + f * bx;
+                x = y;
+            }
+            const double r = rcp_nr(dx);
+            sm.r[x] = r;
+            sm.b[x] = bx;
+            if (a.parent[off + x] >= 0) {
+                const double sg = sig[x];
+                const double f = sg * r;
+                sm.cd[q - q0] = -f * sg;
+                sm.cb[q - q0] = f * bx;
+            }
+        }
+        __syncwarp();
     }
-    b[0] = b[0] / d[0];
-    for (int64_t i = 1; i < n; ++i) b[i] = (b[i] + sg[i] * b[par[i]]) / d[i];
+    for (int L = nl - 1; L >= 0; --L) {
+        for (int64_t q = a.lev_bound[l0 + L] + lane; q < a.lev_bound[l0 + L + 1]; q += 32) {
+            const int64_t cs = a.ch_cv_ptr[q], ce = a.ch_cv_ptr[q + 1];
+            int x = a.ch_cvs[cs];
+            const int32_t p = a.parent[off + x];
+            double v = (p >= 0) ? (sm.b[x] + sig[x] * sm.b[p]) * sm.r[x] : sm.b[x] * sm.r[x];
+            sm.b[x] = v;
+            for (int64_t u = cs + 1; u < ce; ++u) {
+                x = a.ch_cvs[u];
+                v = (sm.b[x] + sig[x] * v) * sm.r[x];
+                sm.b[x] = v;
+            }
+        }
+        __syncwarp();
+    }
 }
 
 // mode 0: steps [s0, s1) from the running state (a.V, a.Y), in place, with a checkpoint
 //         before every step that is a multiple of ckpt, and the loss;
-// mode 1: steps [s0, s1) from checkpoint s0 / ckpt, every state kept in the segment buffers.
-__global__ void __launch_bounds__(kAdjWarps * 32) k_adj_forward(AdjArgs a, int64_t s0, int64_t s1, int mode) {
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kAdjWarps + (threadIdx.x >> 5);
-    if (c >= a.n_cells) return;
+// mode 1: steps [s0, s1) from checkpoint s0 / ckpt, every state kept in segment buffer buf.
+__device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, int mode, int buf) {
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t off = a.off[c], n = a.off[c + 1] - off;
+    double* const segV = a.segV[buf];
+    double* const segY = a.segY[buf];
+    double* const segG = a.segG[buf];
     const int64_t nhh = a.n_hh;
+    const Smem sm = smem_of(a);
     if (mode == 1) {
         const double* cV = a.ckV + (s0 / a.ckpt) * a.n_cv;
         const double* cY = a.ckY + (s0 / a.ckpt) * 3 * nhh;
-        for (int64_t i = off + lane; i < off + n; i += 32) {
-            a.segV[i] = cV[i];
+        for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
+            segV[i] = cV[i];
             const int32_t j = a.hidx[i];
             if (j >= 0)
-                for (int g = 0; g < 3; ++g) a.segY[g * nhh + j] = cY[g * nhh + j];
+                for (int g = 0; g < 3; ++g) segY[g * nhh + j] = cY[g * nhh + j];
         }
-        __syncwarp();
+        __syncthreads();
     }
     double lsum = 0.0;
     for (int64_t s = s0; s < s1; ++s) {
@@ -91,7 +159,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_forward(AdjArgs a, int64
             if (s % a.ckpt == 0) {
                 double* cV = a.ckV + (s / a.ckpt) * a.n_cv;
                 double* cY = a.ckY + (s / a.ckpt) * 3 * nhh;
-                for (int64_t i = off + lane; i < off + n; i += 32) {
+                for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
                     cV[i] = a.V[i];
                     const int32_t j = a.hidx[i];
                     if (j >= 0)
@@ -99,29 +167,32 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_forward(AdjArgs a, int64
                 }
             }
         } else {
-            Vs = a.segV + (s - s0) * a.n_cv;
-            Ys = a.segY + (s - s0) * 3 * nhh;
+            Vs = segV + (s - s0) * a.n_cv;
+            Ys = segY + (s - s0) * 3 * nhh;
             Vd = const_cast<double*>(Vs) + a.n_cv;
             Yd = const_cast<double*>(Ys) + 3 * nhh;
         }
         // assemble A(y^s) and the right-hand side
-        for (int64_t i = off + lane; i < off + n; i += 32) {
+        for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
             double G, GE;
             membrane(a, i, Ys, G, GE);
-            a.d[i] = a.cdt[i] + G + a.dsig[i];
-            a.b[i] = a.cdt[i] * Vs[i] + GE;
+            sm.d[i - off] = a.cdt[i] + G + a.dsig[i];
+            sm.b[i - off] = a.cdt[i] * Vs[i] + GE;
         }
-        __syncwarp();
-        if (lane == 0) {
-            const double t = (double)(a.k0 + s) * a.dt;
-            for (int64_t q = a.st_ptr[c]; q < a.st_ptr[c + 1]; ++q)
-                if (a.st_on[q] <= t && t < a.st_on[q] + a.st_dur[q]) a.b[a.st_cv[q]] += a.st_amp[q];
-            tree_solve(a, off, n);
+        __syncthreads();
+        if (tid < 32) {
+            if (tid == 0) {
+                const double t = (double)(a.k0 + s) * a.dt;
+                for (int64_t q = a.st_ptr[c]; q < a.st_ptr[c + 1]; ++q)
+                    if (a.st_on[q] <= t && t < a.st_on[q] + a.st_dur[q]) sm.b[a.st_cv[q] - off] += a.st_amp[q];
+            }
+            __syncwarp();
+            chain_solve(a, c, off, lane, sm);
         }
-        __syncwarp();
+        __syncthreads();
         // new voltage, gates with it, loss
-        for (int64_t i = off + lane; i < off + n; i += 32) {
-            const double v = a.b[i];
+        for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
+            const double v = sm.b[i - off];
             Vd[i] = v;
             const int32_t j = a.hidx[i];
             if (j >= 0) {
@@ -129,6 +200,21 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_forward(AdjArgs a, int64
                 Yd[j] = gate(Ys[j], r.am, r.bm, a.dt);
                 Yd[nhh + j] = gate(Ys[nhh + j], r.ah, r.bh, a.dt);
                 Yd[2 * nhh + j] = gate(Ys[2 * nhh + j], r.an, r.bn, a.dt);
+                if (mode == 1) {
+                    // what the reverse sweep of this step needs from the gate update
+                    const Rates dr = hh_rate_derivs(v, r);
+                    const double dt = a.dt;
+                    const double em = exp(-dt * (r.am + r.bm));
+                    const double eh = exp(-dt * (r.ah + r.bh));
+                    const double en = exp(-dt * (r.an + r.bn));
+                    double* G6 = segG + (s - s0) * 6 * nhh;
+                    G6[j] = gate_dv(Ys[j], r.am, r.bm, dr.am, dr.bm, dt, em);
+                    G6[nhh + j] = gate_dv(Ys[nhh + j], r.ah, r.bh, dr.ah, dr.bh, dt, eh);
+                    G6[2 * nhh + j] = gate_dv(Ys[2 * nhh + j], r.an, r.bn, dr.an, dr.bn, dt, en);
+                    G6[3 * nhh + j] = em;
+                    G6[4 * nhh + j] = eh;
+                    G6[5 * nhh + j] = en;
+                }
             }
             if (mode == 0) {
                 const int32_t o = a.obs[i];
@@ -138,58 +224,61 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_forward(AdjArgs a, int64
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
     if (mode == 0) {
+        // fixed-order reduction: warps, then the warp sums in order
+        __shared__ double wsum[kAdjThreads / 32];
         for (int sh = 16; sh > 0; sh >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, sh);
-        if (lane == 0) a.cell_loss[c] += lsum;
+        if (lane == 0) wsum[tid >> 5] = lsum;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < kAdjThreads / 32; ++w) tot += wsum[w];
+            a.cell_loss[c] += tot;
+        }
     }
 }
 
-// Reverse sweep over the segment [s0, s1) held in the segment buffers.
-__global__ void __launch_bounds__(kAdjWarps * 32) k_adj_reverse(AdjArgs a, int64_t s0, int64_t s1) {
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kAdjWarps + (threadIdx.x >> 5);
-    if (c >= a.n_cells) return;
+// Reverse sweep over the segment [s0, s1) held in segment buffer buf.
+__device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, int buf) {
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t off = a.off[c], n = a.off[c + 1] - off;
+    const double* const segV = a.segV[buf];
+    const double* const segY = a.segY[buf];
+    const double* const segG = a.segG[buf];
     const int64_t nhh = a.n_hh, ncv = a.n_cv;
     const double dt = a.dt;
+    const Smem sm = smem_of(a);
     for (int64_t s = s1 - 1; s >= s0; --s) {
-        const double* V0 = a.segV + (s - s0) * ncv;
+        const double* V0 = segV + (s - s0) * ncv;
         const double* V1 = V0 + ncv;
-        const double* Y0 = a.segY + (s - s0) * 3 * nhh;
+        const double* Y0 = segY + (s - s0) * 3 * nhh;
         // Vbar = (C/dt) lam + dL/dV^{s+1} + dPhi/dV^T ybar; A(y^s); ybar <- dPhi/dy ybar
-        for (int64_t i = off + lane; i < off + n; i += 32) {
+        for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
             double G, GE;
             membrane(a, i, Y0, G, GE);
-            a.d[i] = a.cdt[i] + G + a.dsig[i];
+            sm.d[i - off] = a.cdt[i] + G + a.dsig[i];
             double vb = a.cdt[i] * a.lam[i];
             const int32_t o = a.obs[i];
             if (o >= 0) vb += 2.0 * a.loss_scale * (V1[i] - a.target[s * a.n_obs + o]);
             const int32_t j = a.hidx[i];
             if (j >= 0) {
-                const double v = V1[i];
-                const Rates r = hh_rates(v);
-                const Rates dr = hh_rate_derivs(v, r);
-                const double em = exp(-dt * (r.am + r.bm));
-                const double eh = exp(-dt * (r.ah + r.bh));
-                const double en = exp(-dt * (r.an + r.bn));
+                const double* G6 = segG + (s - s0) * 6 * nhh;
                 double* yb = a.ybar;
-                vb += gate_dv(Y0[j], r.am, r.bm, dr.am, dr.bm, dt, em) * yb[j]
-                    + gate_dv(Y0[nhh + j], r.ah, r.bh, dr.ah, dr.bh, dt, eh) * yb[nhh + j]
-                    + gate_dv(Y0[2 * nhh + j], r.an, r.bn, dr.an, dr.bn, dt, en) * yb[2 * nhh + j];
-                yb[j] *= em;
-                yb[nhh + j] *= eh;
-                yb[2 * nhh + j] *= en;
+                vb += G6[j] * yb[j] + G6[nhh + j] * yb[nhh + j] + G6[2 * nhh + j] * yb[2 * nhh + j];
+                yb[j] *= G6[3 * nhh + j];
+                yb[nhh + j] *= G6[4 * nhh + j];
+                yb[2 * nhh + j] *= G6[5 * nhh + j];
             }
-            a.b[i] = vb;
+            sm.b[i - off] = vb;
         }
-        __syncwarp();
-        if (lane == 0) tree_solve(a, off, n);
-        __syncwarp();
+        __syncthreads();
+        if (tid < 32) chain_solve(a, c, off, lane, sm);
+        __syncthreads();
         // lam_s; gradient terms; gate adjoint of y^s
-        for (int64_t i = off + lane; i < off + n; i += 32) {
-            const double lam = a.b[i];
+        for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
+            const double lam = sm.b[i - off];
             a.lam[i] = lam;
             const double v1 = V1[i];
             a.gacc[3 * ncv + i] += lam * (V0[i] - v1) / dt * (a.area[i] * 1e-5);
@@ -207,7 +296,24 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adj_reverse(AdjArgs a, int64
                 a.ybar[2 * nhh + j] += a.gk[j] * 4.0 * n2 * nn * lk;
             }
         }
-        __syncwarp();
+        __syncthreads();
+    }
+}
+
+// Forward pass with checkpoints and the loss: one block per cell.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_forward(AdjArgs a, int64_t s0, int64_t s1) {
+    forward_cell(a, blockIdx.x, s0, s1, 0, 0);
+}
+
+// One backward stage: blocks [0, n_cells) sweep segment [r0, r1) (buffer rbuf) backwards,
+// blocks [n_cells, 2 n_cells) recompute segment [f0, f1) into the other buffer meanwhile.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_stage(AdjArgs a, int64_t r0, int64_t r1, int rbuf,
+                                                           int64_t f0, int64_t f1) {
+    const int b = blockIdx.x;
+    if (b < a.n_cells) {
+        if (r1 > r0) reverse_cell(a, b, r0, r1, rbuf);
+    } else if (f1 > f0) {
+        forward_cell(a, b - a.n_cells, f0, f1, 1, rbuf ^ 1);
     }
 }
 
@@ -231,17 +337,25 @@ __global__ void k_adj_reduce(AdjArgs a) {
 
 }  // namespace
 
-int adj_blocks(int32_t n_cells) { return (n_cells + kAdjWarps - 1) / kAdjWarps; }
+size_t adj_smem_bytes(const AdjArgs& a) { return sizeof(double) * (3 * (size_t)a.smem_cv + 2 * (size_t)a.smem_ch); }
 
-cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, int mode, cudaStream_t s) {
+cudaError_t adj_prepare(const AdjArgs& a) {
+    const int bytes = (int)adj_smem_bytes(a);
+    cudaError_t e = cudaFuncSetAttribute(k_adj_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s) {
     if (a.n_cells == 0 || s1 <= s0) return cudaSuccess;
-    k_adj_forward<<<adj_blocks(a.n_cells), kAdjWarps * 32, 0, s>>>(a, s0, s1, mode);
+    k_adj_forward<<<a.n_cells, kAdjThreads, adj_smem_bytes(a), s>>>(a, s0, s1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_reverse(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s) {
-    if (a.n_cells == 0 || s1 <= s0) return cudaSuccess;
-    k_adj_reverse<<<adj_blocks(a.n_cells), kAdjWarps * 32, 0, s>>>(a, s0, s1);
+cudaError_t launch_adj_stage(const AdjArgs& a, int64_t r0, int64_t r1, int rbuf, int64_t f0, int64_t f1,
+                             cudaStream_t s) {
+    if (a.n_cells == 0) return cudaSuccess;
+    k_adj_stage<<<2 * a.n_cells, kAdjThreads, adj_smem_bytes(a), s>>>(a, r0, r1, rbuf, f0, f1);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,10 @@ enum : int32_t { kFlagPopMask = 0xFF, kFlagRemote = 0x100, kFlagRoot = 0x200 };
 constexpr int32_t kMbNone = 0x7FF;
 constexpr int kMbOutShift = 10;
 constexpr int kMbInShift = 21;
-constexpr int kStreamWarps = 8;        // warps per CTA of the streamed kernel (one CTA per SM)
+#ifndef ARB_STREAM_WARPS
+#define ARB_STREAM_WARPS 16
+#endif
+constexpr int kStreamWarps = ARB_STREAM_WARPS;   // warps per CTA of the streamed kernel (one CTA per SM)
 constexpr int kStreamRound = 8;        // rows per round in streamed shared packs
 
 // Event delivered inside one epoch, bucketed per owner lane and sorted by
@@ -238,14 +241,26 @@ struct AdjArgs {
     double* Y;                 // [3][n_hh]
     double* ckV;               // [n_ckpt][n_cv]
     double* ckY;               // [n_ckpt][3][n_hh]
-    double* segV;              // [ckpt+1][n_cv]
-    double* segY;              // [ckpt+1][3][n_hh]
-    double* d;                 // [n_cv] solve scratch
-    double* b;                 // [n_cv]
+    // two segment buffers (one is swept backwards while the next is recomputed)
+    double* segV[2];           // [ckpt+1][n_cv]
+    double* segY[2];           // [ckpt+1][3][n_hh]
+    double* segG[2];           // [ckpt][6][n_hh] per step: dPhi/dV of m, h, n and exp(-dt (alpha+beta))
+                               // of m, h, n, written by the recompute pass for the reverse sweep
     double* lam;               // [n_cv] solve result of the later step
     double* ybar;              // [3][n_hh]
     double* gacc;              // [4][n_cv] gradient per CV: gnabar, gkbar, gl, cm
     double* cell_loss;         // [n_cells]
+    // tree solve schedule: the unbranched chains of each cell, ordered by level (leaf chains
+    // level 0, a chain's level is one more than its highest child chain)
+    const int64_t* ch_ptr;     // [n_cells+1] chains of cell c (global chain indices)
+    const int64_t* lev_off;    // [n_cells+1] offsets into lev_bound
+    const int64_t* lev_bound;  // per cell: first chain of each level, then one past the last
+    const int64_t* ch_cv_ptr;  // [n_chains+1] range of the chain in ch_cvs
+    const int32_t* ch_cvs;     // cell-local CVs of each chain, head (nearest the root) first
+    const int64_t* ch_kid_ptr; // [n_chains+1] range of the chain's child chains in ch_kids
+    const int64_t* ch_kids;    // global chain indices
+    int32_t smem_cv;           // shared-memory slots per cell (largest cell)
+    int32_t smem_ch;           // largest chain count of a cell
     const int64_t* grp_ptr;    // [n_groups+1] CVs of each parameter group, ascending
     const int64_t* grp_cv;
     int32_t n_groups;

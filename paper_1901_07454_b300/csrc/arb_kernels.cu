@@ -18,16 +18,6 @@
 namespace arbk {
 
 
-// 1/x for the positive pivots of the implicit scheme: the hardware estimate (about 20 correct
-// bits) refined by one third-order step, r <- r + r (e + e^2) with e = 1 - x r, which triples
-// the number of correct bits (error e^3).
-__device__ __forceinline__ double rcp_nr(double x) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    const double e = fma(-x, r, 1.0);
-    return fma(r, fma(e, e, e), r);
-}
-
 // ------------------------------------------------------------------------------------------
 // The epoch kernel: a persistent grid; each warp takes packs from a work counter and runs
 // every time step of the epoch for the pack's cells.
@@ -574,8 +564,14 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     __syncwarp();
 }
 
-constexpr int kPF = 4;    // rows prefetched ahead in the streamed forward sweep
-constexpr int kPB = 16;   // rows prefetched ahead in the streamed back substitution (light rows)
+#ifndef ARB_STREAM_PF
+#define ARB_STREAM_PF 3
+#endif
+#ifndef ARB_STREAM_PB
+#define ARB_STREAM_PB 6
+#endif
+constexpr int kPF = ARB_STREAM_PF;   // rows prefetched ahead in the streamed forward sweep
+constexpr int kPB = ARB_STREAM_PB;   // rows prefetched ahead in the streamed back substitution (light rows)
 
 template <class MT, bool kImp, bool kShared>
 __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, int64_t k0, int nsteps, int lane) {

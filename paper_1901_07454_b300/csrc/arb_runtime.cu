@@ -40,9 +40,12 @@ template <class T>
 cudaError_t launch_gather(double* out, const T* src, const int64_t* idx, int64_t n, cudaStream_t s);
 template <class T>
 cudaError_t launch_scatter(T* dst, const double* src, const int64_t* idx, int64_t n, cudaStream_t s);
-cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, int mode, cudaStream_t s);
-cudaError_t launch_adj_reverse(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s);
+cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s);
+cudaError_t launch_adj_stage(const AdjArgs& a, int64_t r0, int64_t r1, int rbuf, int64_t f0, int64_t f1,
+                             cudaStream_t s);
 cudaError_t launch_adj_reduce(const AdjArgs& a, cudaStream_t s);
+cudaError_t adj_prepare(const AdjArgs& a);
+size_t adj_smem_bytes(const AdjArgs& a);
 
 }  // namespace arbk
 
@@ -2079,6 +2082,77 @@ struct AdjLayout {
     }
 };
 
+// Tree-solve schedule of the adjoint kernels: per cell, its unbranched chains (maximal runs
+// of CVs with one child each, head nearest the root) ordered by level.
+struct ChainPlan {
+    std::vector<int64_t> ch_ptr, lev_off, lev_bound, ch_cv_ptr, ch_kid_ptr, ch_kids;
+    std::vector<int32_t> ch_cvs;
+    int32_t max_cv = 0, max_ch = 0;
+};
+
+ChainPlan chain_plan(const arb_sim* sim) {
+    ChainPlan P;
+    const int32_t nc = sim->n_cells;
+    P.ch_ptr.assign(nc + 1, 0);
+    P.lev_off.assign(nc + 1, 0);
+    P.ch_cv_ptr.push_back(0);
+    P.ch_kid_ptr.push_back(0);
+    for (int32_t c = 0; c < nc; ++c) {
+        const int64_t off = sim->cv_offset[c];
+        const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
+        const int32_t* par = sim->parent.data() + off;
+        std::vector<int32_t> nch(n, 0), only(n, -1);
+        for (int32_t i = 1; i < n; ++i) { nch[par[i]]++; only[par[i]] = i; }
+        // chains, in ascending head order (a parent chain's head precedes its children's)
+        std::vector<std::vector<int32_t>> cvs;
+        std::vector<int32_t> chain_of_tail(n, -1), parent_chain;
+        for (int32_t h = 0; h < n; ++h) {
+            if (h != 0 && nch[par[h]] == 1) continue;   // continues its parent's chain
+            std::vector<int32_t> v{h};
+            int32_t x = h;
+            while (nch[x] == 1) { x = only[x]; v.push_back(x); }
+            chain_of_tail[x] = (int32_t)cvs.size();
+            parent_chain.push_back(h == 0 ? -1 : par[h]);   // parent CV for now
+            cvs.push_back(std::move(v));
+        }
+        const int32_t nq = (int32_t)cvs.size();
+        for (int32_t q = 0; q < nq; ++q)
+            if (parent_chain[q] >= 0) parent_chain[q] = chain_of_tail[parent_chain[q]];
+        std::vector<std::vector<int32_t>> kids(nq);
+        for (int32_t q = 0; q < nq; ++q)
+            if (parent_chain[q] >= 0) kids[parent_chain[q]].push_back(q);
+        std::vector<int32_t> level(nq, 0);
+        int32_t maxl = 0;
+        for (int32_t q = nq - 1; q >= 0; --q) {
+            for (int32_t k : kids[q]) level[q] = std::max(level[q], level[k] + 1);
+            maxl = std::max(maxl, level[q]);
+        }
+        std::vector<int32_t> order(nq);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return level[x] < level[y]; });
+        std::vector<int64_t> gidx(nq);
+        const int64_t q0 = (int64_t)P.ch_cv_ptr.size() - 1;
+        for (int32_t r = 0; r < nq; ++r) gidx[order[r]] = q0 + r;
+        P.lev_off[c] = (int64_t)P.lev_bound.size();
+        for (int32_t L = 0, r = 0; L <= maxl + 1; ++L) {
+            while (r < nq && level[order[r]] < L) ++r;
+            P.lev_bound.push_back(q0 + r);
+        }
+        for (int32_t r = 0; r < nq; ++r) {
+            const int32_t q = order[r];
+            for (int32_t x : cvs[q]) P.ch_cvs.push_back(x);
+            P.ch_cv_ptr.push_back((int64_t)P.ch_cvs.size());
+            for (int32_t k : kids[q]) P.ch_kids.push_back(gidx[k]);
+            P.ch_kid_ptr.push_back((int64_t)P.ch_kids.size());
+        }
+        P.ch_ptr[c + 1] = q0 + nq;
+        P.max_cv = std::max(P.max_cv, n);
+        P.max_ch = std::max(P.max_ch, nq);
+    }
+    P.lev_off[nc] = (int64_t)P.lev_bound.size();
+    return P;
+}
+
 AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t n_obs, int32_t n_groups) {
     (void)n_obs;
     const int64_t nc = sim->n_cells, ncv = sim->n_cv, nhh = (int64_t)sim->hh_cv.size(), nst = (int64_t)sim->st_cv.size();
@@ -2096,14 +2170,23 @@ AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t 
     L.add("Y", 24 * nhh);
     L.add("ckV", 8 * ncv * nck);
     L.add("ckY", 24 * nhh * nck);
-    L.add("segV", 8 * ncv * (seg + 1));
-    L.add("segY", 24 * nhh * (seg + 1));
-    for (const char* n : {"d", "b", "lam"}) L.add(n, 8 * ncv);
+    for (const char* n : {"segV0", "segV1"}) L.add(n, 8 * ncv * (seg + 1));
+    for (const char* n : {"segY0", "segY1"}) L.add(n, 24 * nhh * (seg + 1));
+    for (const char* n : {"segG0", "segG1"}) L.add(n, 48 * nhh * seg);
+    L.add("lam", 8 * ncv);
     L.add("ybar", 24 * nhh);
     L.add("gacc", 32 * ncv);
     L.add("cell_loss", 8 * nc);
     L.add("grp_ptr", 8 * ((int64_t)n_groups + 1));
     L.add("grp_cv", 8 * ncv);
+    // chain schedule: at most one chain per CV, at most n_cv + 1 level bounds per cell
+    L.add("ch_ptr", 8 * (nc + 1));
+    L.add("lev_off", 8 * (nc + 1));
+    L.add("lev_bound", 8 * (ncv + nc));
+    L.add("ch_cv_ptr", 8 * (ncv + 1));
+    L.add("ch_cvs", 4 * ncv);
+    L.add("ch_kid_ptr", 8 * (ncv + 1));
+    L.add("ch_kids", 8 * ncv);
     return L;
 }
 
@@ -2203,6 +2286,9 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
             st_amp[w] = sim->st_amp[q];
         }
     }
+    const ChainPlan CP = chain_plan(sim);
+    if (3 * (size_t)CP.max_cv + 2 * (size_t)CP.max_ch > (size_t)200 * 1024 / 8)
+        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve in shared memory (cells up to ~8,000 CVs)");
     arb_status st = sync_in(sim);
     if (st != ARB_OK) return st;
     char* base = (char*)workspace;
@@ -2221,7 +2307,14 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         (st = up("st_on", st_on.data(), 8 * nst)) != ARB_OK || (st = up("st_dur", st_dur.data(), 8 * nst)) != ARB_OK ||
         (st = up("st_amp", st_amp.data(), 8 * nst)) != ARB_OK || (st = up("obs", obs.data(), 4 * ncv)) != ARB_OK ||
         (st = up("grp_ptr", grp_ptr.data(), 8 * ((size_t)n_groups + 1))) != ARB_OK ||
-        (st = up("grp_cv", grp_cv.data(), 8 * grp_cv.size())) != ARB_OK)
+        (st = up("grp_cv", grp_cv.data(), 8 * grp_cv.size())) != ARB_OK ||
+        (st = up("ch_ptr", CP.ch_ptr.data(), 8 * CP.ch_ptr.size())) != ARB_OK ||
+        (st = up("lev_off", CP.lev_off.data(), 8 * CP.lev_off.size())) != ARB_OK ||
+        (st = up("lev_bound", CP.lev_bound.data(), 8 * CP.lev_bound.size())) != ARB_OK ||
+        (st = up("ch_cv_ptr", CP.ch_cv_ptr.data(), 8 * CP.ch_cv_ptr.size())) != ARB_OK ||
+        (st = up("ch_cvs", CP.ch_cvs.data(), 4 * CP.ch_cvs.size())) != ARB_OK ||
+        (st = up("ch_kid_ptr", CP.ch_kid_ptr.data(), 8 * CP.ch_kid_ptr.size())) != ARB_OK ||
+        (st = up("ch_kids", CP.ch_kids.data(), 8 * CP.ch_kids.size())) != ARB_OK)
         return st;
     AdjArgs a{};
     a.n_cells = (int32_t)nc;
@@ -2256,14 +2349,26 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.Y = (double*)L.at(base, "Y");
     a.ckV = (double*)L.at(base, "ckV");
     a.ckY = (double*)L.at(base, "ckY");
-    a.segV = (double*)L.at(base, "segV");
-    a.segY = (double*)L.at(base, "segY");
-    a.d = (double*)L.at(base, "d");
-    a.b = (double*)L.at(base, "b");
+    a.segV[0] = (double*)L.at(base, "segV0");
+    a.segV[1] = (double*)L.at(base, "segV1");
+    a.segY[0] = (double*)L.at(base, "segY0");
+    a.segY[1] = (double*)L.at(base, "segY1");
+    a.segG[0] = (double*)L.at(base, "segG0");
+    a.segG[1] = (double*)L.at(base, "segG1");
     a.lam = (double*)L.at(base, "lam");
     a.ybar = (double*)L.at(base, "ybar");
     a.gacc = (double*)L.at(base, "gacc");
     a.cell_loss = (double*)L.at(base, "cell_loss");
+    a.ch_ptr = (const int64_t*)L.at(base, "ch_ptr");
+    a.lev_off = (const int64_t*)L.at(base, "lev_off");
+    a.lev_bound = (const int64_t*)L.at(base, "lev_bound");
+    a.ch_cv_ptr = (const int64_t*)L.at(base, "ch_cv_ptr");
+    a.ch_cvs = (const int32_t*)L.at(base, "ch_cvs");
+    a.ch_kid_ptr = (const int64_t*)L.at(base, "ch_kid_ptr");
+    a.ch_kids = (const int64_t*)L.at(base, "ch_kids");
+    a.smem_cv = std::max<int32_t>(CP.max_cv, 1);
+    a.smem_ch = std::max<int32_t>(CP.max_ch, 1);
+    CU(adj_prepare(a));
     a.grp_ptr = (const int64_t*)L.at(base, "grp_ptr");
     a.grp_cv = (const int64_t*)L.at(base, "grp_cv");
     a.n_groups = n_groups;
@@ -2282,12 +2387,24 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     CU(cudaMemsetAsync(a.cell_loss, 0, 8 * nc, sim->s));
     // forward with checkpoints, then segment by segment backwards: recompute, reverse sweep
     CU(cudaEventRecord(sim->t0[0], sim->s));
-    CU(launch_adj_forward(a, 0, n_steps, 0, sim->s));
+    CU(launch_adj_forward(a, 0, n_steps, sim->s));
+    // segment g lives in buffer g % 2; each stage sweeps segment g backwards while the
+    // segment before it is recomputed from its checkpoint into the other buffer
     const int64_t nck = (n_steps + checkpoint_every - 1) / checkpoint_every;
-    for (int64_t sgi = nck - 1; sgi >= 0; --sgi) {
-        const int64_t s0 = sgi * checkpoint_every, s1 = std::min<int64_t>(n_steps, s0 + checkpoint_every);
-        CU(launch_adj_forward(a, s0, s1, 1, sim->s));
-        CU(launch_adj_reverse(a, s0, s1, sim->s));
+    auto seg = [&](int64_t g, int64_t& s0, int64_t& s1) {
+        s0 = g * checkpoint_every;
+        s1 = std::min<int64_t>(n_steps, s0 + checkpoint_every);
+    };
+    {
+        int64_t f0, f1;
+        seg(nck - 1, f0, f1);
+        CU(launch_adj_stage(a, 0, 0, (int)((nck - 1) % 2) ^ 1, f0, f1, sim->s));   // recompute only
+    }
+    for (int64_t g = nck - 1; g >= 0; --g) {
+        int64_t r0, r1, f0 = 0, f1 = 0;
+        seg(g, r0, r1);
+        if (g > 0) seg(g - 1, f0, f1);
+        CU(launch_adj_stage(a, r0, r1, (int)(g % 2), f0, f1, sim->s));
     }
     CU(launch_adj_reduce(a, sim->s));
     CU(cudaEventRecord(sim->t1[0], sim->s));
@@ -2298,7 +2415,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     CU(cudaEventElapsedTime(&ms, sim->t0[0], sim->t1[0]));
     sim->pending_time[0] = false;
     sim->last_epoch_ms = ms;
-    sim->last_launches = 2 + 2 * nck;
+    sim->last_launches = 3 + nck;
     double total = 0.0;
     for (double x : cl) total += x;
     *loss = total;

@@ -108,7 +108,7 @@ def test_autograd_function_and_a_descent_step():
     with torch.no_grad():
         step = 1e-3 * theta.abs() * torch.sign(theta.grad)
         L2 = arb.adjoint_loss(theta - step, m, group, obs, target, scale, K, spec.dt, 100)
-    assert float(L2) < float(L)
+    assert float(L2.detach()) < float(L.detach())
 
 
 def test_adjoint_full_size_sampled_cells():
