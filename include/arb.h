@@ -2,12 +2,12 @@
  * arb.h -- C ABI of the B300 batched cable-equation stepper.
  *
  * The library advances a batch of multicompartment neurons with the method of
- * arXiv 1901.07454 (Arbor), Sec. "Model": finite-volume cable equation per cell,
- * membrane currents at V(t), one implicit-Euler voltage step solved on each cell's
- * tree-shaped (Hines) matrix, then channel/synapse state updates with the new voltage,
- * threshold spike detection, and spike exchange once per minimum-delay epoch
- * (Sec. "Implementation", "Simulation workflow"). Every stage of a time step runs in the
- * library's own sm_103a CUDA kernels.
+ * arXiv 1901.07454 (Arbor), Sec. "Model": finite-volume cable equation per cell, membrane
+ * terms from the channel and synapse states at t, one implicit-Euler voltage step solved
+ * on each cell's tree-shaped (Hines) matrix, then channel/synapse state updates with the new
+ * voltage, threshold spike detection, and spike exchange once per minimum-delay epoch
+ * (Sec. "Implementation", "Simulation workflow"). It also computes the discrete adjoint of
+ * that step (arb_adjoint). Every stage runs in the library's own sm_103a CUDA kernels.
  *
  * Conventions for every entry point:
  *  - Units: mV, ms, um, uF/cm^2, Ohm*cm, S/cm^2 (channel densities), uS (synaptic
@@ -123,11 +123,12 @@ typedef struct {
  * capacities sized for typical runs. Never fails for a non-NULL argument. */
 arb_status arb_default_params(arb_params* p);
 
-/* Validates the model and prepares everything on the host (per-CV geometry; the constant
- * implicit-Euler matrix of Sec. "Model" and its Hines factorisation, since with a fixed dt and
- * all membrane current on the right-hand side only the right-hand side changes per step;
- * the packing of cells into warps and the solve schedule). Makes no CUDA call.
- * On success *out owns a handle that must be released with arb_destroy. */
+/* Validates the model and prepares everything on the host: per-CV geometry; the constant
+ * parts of the implicit-Euler system of Sec. "Model" (ARB_IMPLICIT: c/dt, the axial
+ * conductances and the constant diagonal, the membrane terms being added per step; ARB_EXPLICIT:
+ * the constant matrix and its Hines factorisation); the packing of cells into warps (one cell
+ * per lane, cells spread over lanes, or cells sharing a warp) with its solve schedule.
+ * Makes no CUDA call. On success *out owns a handle that must be released with arb_destroy. */
 arb_status arb_create(const arb_model* model, const arb_params* params, arb_sim** out);
 
 /* Releases the handle. Does not free the caller's workspace. NULL is ignored. */

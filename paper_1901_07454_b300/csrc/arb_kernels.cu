@@ -2,11 +2,11 @@
 //
 // One epoch (Sec. "Implementation", "Simulation workflow": cells advance independently for
 // an interval no longer than the minimum delay) is this fixed sequence of launches:
-//   k_epoch_begin -> k_ev_count -> k_ev_scan -> k_ev_scatter -> k_ev_sort   (event delivery lists)
-//   arb_epoch_kernel                                                         (all time steps)
-//   k_spike_expand -> k_epoch_end                                            (spike exchange)
-// Per-epoch values live in the device control block, so the sequence is captured once as a
-// CUDA graph and replayed for every epoch.
+//   k_epoch_begin -> k_ev_walk<count> -> k_ev_scan -> k_ev_walk<scatter> -> k_ev_sort   (event lists)
+//   arb_stream_kernel (streamed packs) or arb_epoch_kernel (tile packs)   (all time steps)
+//   k_spike_expand -> k_epoch_end                                         (spike exchange)
+// Per-epoch values live in the device control block, so the sequence is captured once (as
+// three CUDA graphs, timed between them) and replayed for every epoch.
 #include <cuda_runtime.h>
 
 #include <cmath>
