@@ -30,14 +30,26 @@ __device__ __forceinline__ float exprelr_f(float x) { return x == 0.0f ? 1.0f : 
 struct Rates { double am, bm, ah, bh, an, bn; };
 struct RatesF { float am, bm, ah, bh, an, bn; };
 
+// FP64 rates from three transcendentals instead of six: with x1 = -(v+40)/10,
+// exp(-(v+35)/10) = e^{x1} e^{1/2} and exp(-(v+55)/10) = e^{x1} e^{-3/2}, where e^{x1} = expm1(x1)
+// + 1 only ever enters a sum with 1 (so its absolute error, not its relative one, matters);
+// exp(-(v+65)/20) = exp(-(v+65)/80)^4. Near the removable point of alpha_n (|x2| < 0.1) its
+// expm1 is taken directly, since e^{x2} - 1 formed from e^{x1} would cancel there.
 __device__ __forceinline__ Rates hh_rates(double v) {
     Rates r;
-    r.am = exprelr_d((v + 40.0) * -0.1);
+    const double x1 = (v + 40.0) * -0.1;
+    const double em1 = expm1(x1);
+    r.am = x1 == 0.0 ? 1.0 : x1 / em1;
+    const double e80 = exp((v + 65.0) * -0.0125);
+    const double e40 = e80 * e80;
+    r.bn = 0.125 * e80;
+    r.ah = 0.07 * (e40 * e40);
     r.bm = 4.0 * exp((v + 65.0) * (-1.0 / 18.0));
-    r.ah = 0.07 * exp((v + 65.0) * -0.05);
-    r.bh = 1.0 / (1.0 + exp((v + 35.0) * -0.1));
-    r.an = 0.1 * exprelr_d((v + 55.0) * -0.1);
-    r.bn = 0.125 * exp((v + 65.0) * -0.0125);
+    const double ex1 = em1 + 1.0;
+    r.bh = 1.0 / fma(ex1, 1.6487212707001282, 1.0);            // e^{1/2}
+    const double x2 = (v + 55.0) * -0.1;
+    const double em2 = fabs(x2) < 0.1 ? expm1(x2) : fma(ex1, 0.22313016014842982, -1.0);   // e^{-3/2}
+    r.an = 0.1 * (x2 == 0.0 ? 1.0 : x2 / em2);
     return r;
 }
 

@@ -127,8 +127,12 @@ struct DevModel {
     double* V;                // voltages, tile layout
     double* Sg;               // S scratch for packs whose tiles live in global memory
     double* Rg;               // diagonal / e scratch of those packs (implicit scheme)
-    double* Gm;               // streamed packs: mechanism conductance per compact slot
-    double* Em;               // streamed packs: mechanism right-hand side per compact slot
+    double* Gm;               // streamed packs, per compact mechanism slot: the diagonal (implicit:
+                              // constant part + membrane conductance of the step)
+    double* Em;               // ... and the right-hand side terms (implicit: passive g E + membrane
+                              // g E + clamp current)
+    const double* cE;         // streamed packs, implicit: constant diagonal and right-hand side of
+    const double* cB;         // each compact slot (ce, cb of its entry), which Gm and Em start from
     // synapses (syn_rows * 32)
     const int32_t* syn_slot;  // tile slot of the synapse's CV, -1 padding
     const int32_t* syn_vs;    // where its voltage is read (on-chip V slot, or the tile slot)

@@ -443,9 +443,17 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
                                             bool update, int apply_step, bool terms, int& ev_i, int ev_end,
                                             int32_t& late, MT dt) {
     if (terms) {
+        // implicit: the slots start from the constant diagonal and right-hand side of their
+        // entry, so the forward sweep adds nothing for them
+        const double* cE = d.cE + pk.c_off;
+        const double* cB = d.cB + pk.c_off;
         for (int c = lane; c < pk.nvc; c += kWarp) {
-            if (kImp) Gm[c] = 0.0;
-            Em[c] = 0.0;
+            if (kImp) {
+                Gm[c] = __ldg(cE + c);
+                Em[c] = __ldg(cB + c);
+            } else {
+                Em[c] = 0.0;
+            }
         }
     }
     __syncwarp();
@@ -507,8 +515,12 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
             if (terms) {
                 if (c != cur) {
                     if (cur >= 0) {
-                        if (kImp) Gm[cur] = gsum;
-                        Em[cur] = esum;
+                        if (kImp) {
+                            Gm[cur] += gsum;
+                            Em[cur] += esum;
+                        } else {
+                            Em[cur] = esum;
+                        }
                     }
                     cur = c;
                     gsum = 0.0;
@@ -526,8 +538,12 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         }
     }
     if (terms && cur >= 0) {
-        if (kImp) Gm[cur] = gsum;
-        Em[cur] = esum;
+        if (kImp) {
+            Gm[cur] += gsum;
+            Em[cur] += esum;
+        } else {
+            Em[cur] = esum;
+        }
     }
     __syncwarp();
     for (int jh = 0; jh < pk.nhh_row; ++jh) {
@@ -638,7 +654,7 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
             double yprev = 0.0, kprev = 0.0, eprev = 0.0;
             // rows are fetched kPF ahead; the compact mechanism slot of a row is fetched 2*kPF
             // ahead so that the load of its terms never waits on the index load
-            double pv[kPF], pa[kPF], pb[kPF], pk_[kPF], pe[kPF], pg[kPF], pm[kPF];
+            double pv[kPF], pa[kPF], pb[kPF], pk_[kPF], pe[kPF], pm[kPF];
             int pf[kPF], pc[kPF];
             auto fetch_c = [&](int j) { return j < J ? __ldg(cm_ + (size_t)j * kWarp) : -1; };
             auto fetch = [&](int j, int u, int c) {
@@ -646,12 +662,17 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                 const size_t o = (size_t)(in ? j : 0) * kWarp;
                 pv[u] = in ? Vg[(in ? j : 0) * kWarp + lane] : 0.0;
                 pa[u] = in ? __ldg(ca + o) : 0.0;
-                pb[u] = in ? __ldg(cb + o) : 0.0;
                 pk_[u] = in ? __ldg(ck + o) : 0.0;
-                pe[u] = in ? __ldg(ce + o) : 1.0;
                 pf[u] = in ? __ldg(fl + o) : kFlagRoot;
-                pg[u] = (c >= 0 && kImp) ? Gm[c] : 0.0;
-                pm[u] = c >= 0 ? Em[c] : 0.0;
+                if constexpr (kImp) {
+                    // diagonal and right-hand side terms: the mechanism slot's, else the constants
+                    pe[u] = c >= 0 ? Gm[c] : (in ? __ldg(ce + o) : 1.0);
+                    pb[u] = c >= 0 ? Em[c] : (in ? __ldg(cb + o) : 0.0);
+                } else {
+                    pe[u] = in ? __ldg(ce + o) : 1.0;
+                    pb[u] = in ? __ldg(cb + o) : 0.0;
+                    pm[u] = c >= 0 ? Em[c] : 0.0;
+                }
             };
             {
                 int c0[kPF];
@@ -671,7 +692,8 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                             if (left == 0) { __syncwarp(); left = R; }
                             --left;
                         }
-                        const double V = pv[u], A = pa[u], Bc = pb[u], K = pk_[u], E = pe[u], G = pg[u], M = pm[u];
+                        const double V = pv[u], A = pa[u], Bc = pb[u], K = pk_[u], E = pe[u];
+                        const double M = kImp ? 0.0 : pm[u];
                         const int f = pf[u];
                         fetch(j + kPF, u, pc[u]);        // row j + kPF, its slot index is ready
                         pc[u] = fetch_c(j + 2 * kPF);    // slot index of row j + 2 kPF
@@ -679,8 +701,8 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                         const int mb_in = kShared ? (int)((unsigned)f >> kMbInShift) : kMbNone;
                         const int mb_out = kShared ? ((f >> kMbOutShift) & kMbNone) : kMbNone;
                         if constexpr (kImp) {
-                            double dd = fma(-kprev, eprev, E + G);
-                            double bb = fma(kprev, yprev, fma(A, V, Bc) + M);
+                            double dd = fma(-kprev, eprev, E);
+                            double bb = fma(kprev, yprev, fma(A, V, Bc));
                             if (kShared) {
                                 if (mb_in != kMbNone) { dd -= mbd[mb_in]; bb += mbb[mb_in]; }
                             } else {

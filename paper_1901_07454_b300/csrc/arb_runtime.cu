@@ -97,6 +97,7 @@ struct Plan {
     int cells_per_pack = 0;
     bool stream = false;                    // packs streamed from global memory (one cell per lane)
     int64_t c_total = 0;                    // streamed packs: compact mechanism slots
+    std::vector<double> cE, cB;             // streamed packs: ce, cb of each compact slot
     int32_t stack_depth = 1;                // streamed packs: deepest hand-over stack
     int64_t warp_smem = 32;                 // streamed packs: shared memory per warp (double2)
     int64_t split_cvs = -1;                 // streamed packs: cells above this size are spread
@@ -442,6 +443,7 @@ static void layout_regions(arb_sim* sim) {
         {"ca", 8 * ne}, {"cb", 8 * ne}, {"ck", 8 * ne}, {"ce", 8 * ne}, {"pslot", 4 * ne}, {"vmap", 4 * ne},
         {"V", 8 * ne}, {"Sg", 8 * std::max<int64_t>(pl.sg_total, 1)}, {"Rg", 8 * std::max<int64_t>(pl.sg_total, 1)},
         {"Gm", 8 * std::max<int64_t>(pl.c_total, 1)}, {"Em", 8 * std::max<int64_t>(pl.c_total, 1)},
+        {"cE", 8 * std::max<int64_t>(pl.c_total, 1)}, {"cB", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
         {"syn_e", 8 * pl.syn_rows * kWarp}, {"syn_decay", 8 * pl.syn_rows * kWarp}, {"syn_sc", 8 * pl.syn_rows * kWarp},
         {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_vs", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
@@ -508,6 +510,8 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.Sg = (double*)region(sim, "Sg");
     d.Rg = (double*)region(sim, "Rg");
     d.Gm = (double*)region(sim, "Gm");
+    d.cE = (const double*)region(sim, "cE");
+    d.cB = (const double*)region(sim, "cB");
     d.Em = (double*)region(sim, "Em");
     d.syn_slot = (const int32_t*)region(sim, "syn_slot");
     d.syn_vs = (const int32_t*)region(sim, "syn_vs");
@@ -1186,7 +1190,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 for (int64_t cv = sim->cv_offset[c]; cv < sim->cv_offset[c + 1]; ++cv)
                     if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = 0;
             for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
-                if (pl.vmap[t] >= 0) pl.vmap[t] = nvc++;
+                if (pl.vmap[t] >= 0) {
+                    pl.vmap[t] = nvc++;
+                    pl.cE.push_back(pl.ce[t]);
+                    pl.cB.push_back(pl.cb[t]);
+                }
             pd.nvc = nvc;
             pd.c_off = c_total;
             c_total += nvc;
@@ -1675,6 +1683,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("packs", pl.packs);
     UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot); UP("vmap", pl.vmap);
     UP("V", pl.V0);
+    UP("cE", pl.cE); UP("cB", pl.cB);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     UP("hh_slot", pl.hh_slot); UP("hh_vs", pl.hh_vs); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
     UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
