@@ -105,3 +105,27 @@ def test_bind_requires_device_pointer(arb):
     buf = (C.c_char * 1024)()
     st = arb.load().arb_bind_workspace(p.h, C.cast(buf, C.c_void_p), 1024)
     assert st != 0
+
+
+def test_adjoint_workspace_query_and_unbound_handle(arb):
+    lib = arb.load()
+    m, _ = make_config(4, n_cells=2, t_end=1.0)
+    p = arb.Plan(m)
+    group, ng = m.param_groups()
+
+    def ws(n_steps, ck):
+        b = C.c_int64()
+        assert lib.arb_adjoint_workspace_bytes(p.h, n_steps, ck, 2, ng, C.byref(b)) == 0
+        return b.value
+
+    # checkpoints grow with n_steps / ckpt, the two segment buffers with ckpt
+    assert ws(8000, 500) > ws(4000, 500) > 0
+    assert ws(8000, 100) < ws(8000, 500)
+    assert ws(8000, 1) > ws(8000, 100)
+    b = C.c_int64()
+    assert lib.arb_adjoint_workspace_bytes(p.h, 0, 500, 2, ng, C.byref(b)) == -1
+    assert lib.arb_adjoint_workspace_bytes(p.h, 10, 0, 2, ng, C.byref(b)) == -1
+    # without a bound workspace the call is refused before any CUDA work
+    loss = C.c_double()
+    rc = lib.arb_adjoint(p.h, 10, 5, 0, None, None, 1.0, None, 0, None, 0, None, C.byref(loss))
+    assert rc == -5 and b"bind" in lib.arb_last_error(p.h)

@@ -148,3 +148,35 @@ def test_adjoint_refuses_synapses_and_the_explicit_scheme():
         g2, n2 = m2.param_groups()
         arb.Simulation(m2, dt=0.025).adjoint(10, m2.cv_offset[:-1], np.zeros((10, m2.n_cells)), 1.0, g2, n2)
     assert "synapses" in str(ei.value)
+
+
+def test_adjoint_ragged_trees_passive_dendrites_partial_groups():
+    # HH soma and passive dendrites on ragged random trees (3 to 55 CVs per cell), a clamp,
+    # observations on the soma and one dendritic CV, and CVs left out of every group
+    import paper_1901_07454_b300 as arb
+    from inputs import small_tree_model
+    m = small_tree_model(8, n_cells=6, n_branches=7, cv_range=(1, 12), n_syn=0)
+    m.stim_cv = m.cv_offset[:-1].copy()
+    k = m.stim_cv.size
+    m.stim_t_on, m.stim_dur, m.stim_amp = np.full(k, 0.5), np.full(k, 1e9), np.linspace(0.05, 0.6, k)
+    m.__post_init__()
+    spec = SimSpec(dt=0.025, t_end=6.0, epoch_steps=400)
+    K = spec.n_steps
+    obs = np.concatenate([m.cv_offset[:-1], m.cv_offset[1:] - 1])
+    obs = np.unique(obs)
+    rng = np.random.default_rng(3)
+    target = -65.0 + 20.0 * rng.random((K, obs.size))
+    group, ng = m.param_groups()
+    group = group.copy()
+    group[rng.random(group.size) < 0.2] = -1
+    lo, go = oracle.OracleSim(m, spec.dt, 400).adjoint(K, obs, target, 1.0 / K, group, ng)
+    sim = arb.Simulation(m, dt=spec.dt)
+    lg, gg = sim.adjoint(K, obs, target, 1.0 / K, group, ng, checkpoint_every=37)
+    assert abs(lg - lo) <= 1e-10 * lo
+    gg = gg.cpu().numpy()
+    for p in range(4):
+        scale = max(np.max(np.abs(go[:, p])), 1e-300)
+        assert np.max(np.abs(gg[:, p] - go[:, p])) <= 1e-8 * scale, p
+    # no observations: zero loss, zero gradient
+    l0, g0 = sim.adjoint(10, np.zeros(0, np.int64), np.zeros((10, 0)), 1.0, group, ng)
+    assert l0 == 0.0 and not np.any(g0.cpu().numpy())
