@@ -4,7 +4,7 @@ A "step" of this benchmark is one epoch: the full hot path (event delivery, mech
 currents, implicit-Euler assembly, Hines solve, state update, threshold detection for every
 time step of the epoch, then the spike exchange) over all cells of the workload.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ring|batched|mixed|small]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ring|batched|mixed|small|dense|adjoint]
   python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
 
 Prints one JSON line (rank 0). With torchrun and N > 1 every rank runs its own replica of
@@ -35,7 +35,12 @@ WORKLOADS = {
     "batched": (2, "fp64"),
     "mixed": (3, "mixed"),
     "adjoint": (4, "fp64"),
+    "dense": (5, "fp64"),
 }
+
+# per-workload handle settings: the dense network shares one state per synapse group and holds
+# tens of millions of pending events
+SIM_KW = {"dense": dict(coalesce_synapses=True, event_capacity=1 << 26, bucket_capacity=1 << 26)}
 
 
 def peaks():
@@ -61,15 +66,18 @@ STREAM_FP64_PER_CV_STEP = {"batched": 17.9}
 STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 123.9}
 
 
-def algorithmic_bytes_per_cv_step(model, precision):
+def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
     """Streaming bytes one CV-step must move if nothing stayed on chip: V read+write (16),
     capacitance/dt (8), axial conductance to the parent (8), parent index (4); passive G (8) per
     passive CV; HH gates m,h,n read+write and three conductances (72 FP64, 36 FP32-mechanism)
-    per HH CV; per synapse g read+write and its CV index (20 FP64, 12 FP32)."""
+    per HH CV; per synapse state g read+write and its CV index (20 FP64, 12 FP32), where with
+    coalescing one state serves all synapses of a CV with equal tau and e."""
     n_cv = model.n_cv
     hh = np.asarray(model.hh_cv).size
     pas = np.asarray(model.pas_cv).size
     syn = model.n_syn
+    if coalesce and syn:
+        syn = np.unique(np.stack([model.syn_cv, model.syn_tau, model.syn_e], 1), axis=0).shape[0]
     mixed = precision == "mixed"
     total = 36.0 * n_cv + 8.0 * pas + (36.0 if mixed else 72.0) * hh + (12.0 if mixed else 20.0) * syn
     return total / n_cv
@@ -337,7 +345,8 @@ def main():
     import paper_1901_07454_b300 as arb
 
     sim = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
-                         cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
+                         cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
+                         **SIM_KW.get(args.workload, {}))
     sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
     info = sim.plan_info()
     stream = torch.cuda.current_stream()
@@ -384,7 +393,7 @@ def main():
 
     # roofline of the dominant kernel (the epoch kernel), timed with CUDA events around it on
     # the library's stream: FP64 issue (what binds it) and HBM (algorithmic bytes)
-    bpc = algorithmic_bytes_per_cv_step(model, precision)
+    bpc = algorithmic_bytes_per_cv_step(model, precision, SIM_KW.get(args.workload, {}).get("coalesce_synapses", False))
     kern_mean_ms = sum(kern_ms) / len(kern_ms)
     achieved = bpc * model.n_cv * E / (kern_mean_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
@@ -414,7 +423,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
-                              cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
+                              cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
+                              **SIM_KW.get(args.workload, {}))
         h2d = model_bytes(model)
         kk = 0
         ev_per_epoch = 0

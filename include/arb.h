@@ -68,6 +68,12 @@ typedef struct {
                                     over several lanes (chains scheduled in rounds, hand-overs
                                     through shared memory); 0 = threshold chosen by the library
                                     from the load of a warp slot, -1 = never spread */
+    int32_t coalesce_synapses;   /* 1: synapses on one CV with equal tau and e share one state
+                                    (their conductances add linearly, so the voltages agree up to
+                                    rounding); arb_get_state then reports each group's g on its
+                                    lowest-index synapse and 0 on the others, arb_set_state sums a
+                                    group's g. 0 (default): one state per synapse. */
+    int32_t reserved;            /* must be 0 */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */

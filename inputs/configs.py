@@ -149,11 +149,12 @@ def _truncated_normal(rng, mean, sd, n):
 
 
 def make_config(config: int, n_cells: int | None = None, t_end: float | None = None,
-                variant: str = "") -> tuple[Model, SimSpec]:
-    """Workload `config` (0..4); n_cells / t_end shrink it for tests; variant selects options.
+                variant: str = "", syn_per_cell: int | None = None) -> tuple[Model, SimSpec]:
+    """Workload `config` (0..5); n_cells / t_end shrink it for tests; variant selects options.
 
     variant "ring_active" (config 1): the stimulus on cell 0 is raised so that the ring fires.
     variant "target" (config 4): the hidden parameter set that produces the target traces.
+    syn_per_cell (config 5): synapses (and incoming connections) per cell, default 10,000.
     """
     if config == 0:
         n = 10 if n_cells is None else n_cells
@@ -273,6 +274,48 @@ def make_config(config: int, n_cells: int | None = None, t_end: float | None = N
         spec = SimSpec(dt=0.025, t_end=T, epoch_steps=400, name="adjoint-%d" % n)
         return m, spec
 
+    if config == 5:
+        # dense network after the paper's "10k connectivity" benchmark model: ring-model cells
+        # (about 130 compartments: 6-16 branches of 8-16 CVs, HH soma, passive dendrites),
+        # 10,000 excitatory exponential synapses per cell, each fed by one connection from a
+        # uniformly chosen other cell, delays U(10, 20) ms (minimum delay 10 ms), weights
+        # N(1e-6, 2e-7) uS; every cell is driven to spike synchronously at 50 Hz by a 1-ms, 2-nA
+        # pulse every 20 ms on CV 0 (the network input depolarises, up to about -40 mV, without
+        # adding spikes)
+        n = 4096 if n_cells is None else n_cells
+        T = 100.0 if t_end is None else t_end
+        nsyn = 10000 if syn_per_cell is None else int(syn_per_cell)
+        tb = _TreeBatch()
+        for blk in range((n + BLOCK - 1) // BLOCK):
+            rng = _rng(5, blk)
+            for _ in range(min(BLOCK, n - blk * BLOCK)):
+                nb = int(rng.integers(6, 17))
+                _random_cell_fixed(rng, nb, lambda k, r=rng: r.integers(8, 17, size=k), tb)
+        cv_offset, parent, length, radius, bcv = tb.expand()
+        hh_cv, pas_cv = _mechanisms_soma_hh(cv_offset, bcv)
+        rng = _rng(5, 9999)
+        syn_cv = _place_synapses(rng, cv_offset, nsyn)
+        m = _assemble(cv_offset, parent, length, radius, bcv, hh_cv, pas_cv, syn_cv)
+        nsyn_tot = n * nsyn
+        cell_of_syn = np.repeat(np.arange(n), nsyn)
+        if n > 1:
+            src = rng.integers(0, n - 1, size=nsyn_tot)
+            src = np.where(src >= cell_of_syn, src + 1, src)   # no self connections
+        else:
+            src = np.zeros(nsyn_tot, np.int64)
+        m.conn_src = src.astype(np.int32)
+        m.conn_dst_syn = np.arange(nsyn_tot, dtype=np.int64)
+        m.conn_delay = rng.uniform(10.0, 20.0, nsyn_tot)
+        m.conn_weight = _truncated_normal(rng, 1e-6, 2e-7, nsyn_tot)
+        pulses = np.arange(1.0, T, 20.0)
+        m.stim_cv = np.repeat(cv_offset[:-1], pulses.size)
+        m.stim_t_on = np.tile(pulses, n)
+        m.stim_dur = np.full(m.stim_cv.size, 1.0)
+        m.stim_amp = np.full(m.stim_cv.size, 2.0)
+        m.__post_init__()
+        spec = SimSpec(dt=0.025, t_end=T, epoch_steps=400, name="dense-%d" % n)
+        return m, spec
+
     raise ValueError("unknown config %r" % config)
 
 
@@ -298,7 +341,7 @@ def _assemble(cv_offset, parent, length, radius, bcv, hh_cv, pas_cv, syn_cv):
 
 
 def config_names():
-    return {0: "plain-small", 1: "plain-ring", 2: "batched", 3: "mixed", 4: "adjoint"}
+    return {0: "plain-small", 1: "plain-ring", 2: "batched", 3: "mixed", 4: "adjoint", 5: "dense"}
 
 
 def small_tree_model(seed: int, n_cells: int = 1, n_branches: int = 5, cv_range=(1, 6),

@@ -196,21 +196,28 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             Vd[i] = v;
             const int32_t j = a.hidx[i];
             if (j >= 0) {
-                const Rates r = hh_rates(v);
-                Yd[j] = gate(Ys[j], r.am, r.bm, a.dt);
-                Yd[nhh + j] = gate(Ys[nhh + j], r.ah, r.bh, a.dt);
-                Yd[2 * nhh + j] = gate(Ys[2 * nhh + j], r.an, r.bn, a.dt);
-                if (mode == 1) {
-                    // what the reverse sweep of this step needs from the gate update
-                    const Rates dr = hh_rate_derivs(v, r);
+                if (mode == 0) {
+                    const Rates r = hh_rates(v);
+                    Yd[j] = gate(Ys[j], r.am, r.bm, a.dt);
+                    Yd[nhh + j] = gate(Ys[nhh + j], r.ah, r.bh, a.dt);
+                    Yd[2 * nhh + j] = gate(Ys[2 * nhh + j], r.an, r.bn, a.dt);
+                } else {
+                    // the gate update, and what the reverse sweep of this step needs from it:
+                    // dPhi/dV and exp(-dt (alpha + beta)) of each gate
+                    Rates r, dr;
+                    hh_rates_derivs(v, r, dr);
                     const double dt = a.dt;
                     const double em = exp(-dt * (r.am + r.bm));
                     const double eh = exp(-dt * (r.ah + r.bh));
                     const double en = exp(-dt * (r.an + r.bn));
+                    const double xm = Ys[j], xh = Ys[nhh + j], xn = Ys[2 * nhh + j];
+                    Yd[j] = gate_e(xm, r.am, r.bm, em);
+                    Yd[nhh + j] = gate_e(xh, r.ah, r.bh, eh);
+                    Yd[2 * nhh + j] = gate_e(xn, r.an, r.bn, en);
                     double* G6 = segG + (s - s0) * 6 * nhh;
-                    G6[j] = gate_dv(Ys[j], r.am, r.bm, dr.am, dr.bm, dt, em);
-                    G6[nhh + j] = gate_dv(Ys[nhh + j], r.ah, r.bh, dr.ah, dr.bh, dt, eh);
-                    G6[2 * nhh + j] = gate_dv(Ys[2 * nhh + j], r.an, r.bn, dr.an, dr.bn, dt, en);
+                    G6[j] = gate_dv(xm, r.am, r.bm, dr.am, dr.bm, dt, em);
+                    G6[nhh + j] = gate_dv(xh, r.ah, r.bh, dr.ah, dr.bh, dt, eh);
+                    G6[2 * nhh + j] = gate_dv(xn, r.an, r.bn, dr.an, dr.bn, dt, en);
                     G6[3 * nhh + j] = em;
                     G6[4 * nhh + j] = eh;
                     G6[5 * nhh + j] = en;

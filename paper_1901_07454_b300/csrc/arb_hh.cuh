@@ -35,10 +35,10 @@ struct RatesF { float am, bm, ah, bh, an, bn; };
 // + 1 only ever enters a sum with 1 (so its absolute error, not its relative one, matters);
 // exp(-(v+65)/20) = exp(-(v+65)/80)^4. Near the removable point of alpha_n (|x2| < 0.1) its
 // expm1 is taken directly, since e^{x2} - 1 formed from e^{x1} would cancel there.
-__device__ __forceinline__ Rates hh_rates(double v) {
+__device__ __forceinline__ Rates hh_rates_em(double v, double& em1, double& em2) {
     Rates r;
     const double x1 = (v + 40.0) * -0.1;
-    const double em1 = expm1(x1);
+    em1 = expm1(x1);
     r.am = x1 == 0.0 ? 1.0 : x1 / em1;
     const double e80 = exp((v + 65.0) * -0.0125);
     const double e40 = e80 * e80;
@@ -48,9 +48,14 @@ __device__ __forceinline__ Rates hh_rates(double v) {
     const double ex1 = em1 + 1.0;
     r.bh = 1.0 / fma(ex1, 1.6487212707001282, 1.0);            // e^{1/2}
     const double x2 = (v + 55.0) * -0.1;
-    const double em2 = fabs(x2) < 0.1 ? expm1(x2) : fma(ex1, 0.22313016014842982, -1.0);   // e^{-3/2}
+    em2 = fabs(x2) < 0.1 ? expm1(x2) : fma(ex1, 0.22313016014842982, -1.0);   // e^{-3/2}
     r.an = 0.1 * (x2 == 0.0 ? 1.0 : x2 / em2);
     return r;
+}
+
+__device__ __forceinline__ Rates hh_rates(double v) {
+    double em1, em2;
+    return hh_rates_em(v, em1, em2);
 }
 
 __device__ __forceinline__ RatesF hh_rates(float v) {
@@ -68,6 +73,11 @@ __device__ __forceinline__ double gate(double x, double a, double b, double dt) 
     const double s = a + b;
     const double xinf = a / s;
     return xinf + (x - xinf) * exp(-dt * s);
+}
+// The same update with e = exp(-dt (a + b)) already formed.
+__device__ __forceinline__ double gate_e(double x, double a, double b, double e) {
+    const double xinf = a / (a + b);
+    return xinf + (x - xinf) * e;
 }
 __device__ __forceinline__ float gate(float x, float a, float b, float dt) {
     const float s = a + b;
@@ -90,6 +100,11 @@ __device__ __forceinline__ double exprelr_deriv_d(double x) {
     return (em - x * (em + 1.0)) / (em * em);
 }
 
+// d/dx of x / (e^x - 1) given em = e^x - 1 (the closed form, for |x| >= 0.1).
+__device__ __forceinline__ double exprelr_deriv_em(double x, double em) {
+    return (em - x * (em + 1.0)) / (em * em);
+}
+
 // dRates/dV (1/(ms mV)) given the rates at v.
 __device__ __forceinline__ Rates hh_rate_derivs(double v, const Rates& r) {
     Rates d;
@@ -100,6 +115,22 @@ __device__ __forceinline__ Rates hh_rate_derivs(double v, const Rates& r) {
     d.an = -0.01 * exprelr_deriv_d((v + 55.0) * -0.1);
     d.bn = r.bn * -0.0125;
     return d;
+}
+
+// Rates and their derivatives together: the derivatives of alpha_m and alpha_n reuse the
+// e^x - 1 of the rates where the closed form applies (|x| >= 0.1).
+__device__ __forceinline__ void hh_rates_derivs(double v, Rates& r, Rates& d) {
+    double em1, em2;
+    r = hh_rates_em(v, em1, em2);
+    const double x1 = (v + 40.0) * -0.1, x2 = (v + 55.0) * -0.1;
+    const double dm = fabs(x1) < 0.1 ? exprelr_deriv_d(x1) : exprelr_deriv_em(x1, em1);
+    const double dn = fabs(x2) < 0.1 ? exprelr_deriv_d(x2) : exprelr_deriv_em(x2, em2);
+    d.am = -0.1 * dm;
+    d.bm = r.bm * (-1.0 / 18.0);
+    d.ah = r.ah * -0.05;
+    d.bh = r.bh * (1.0 - r.bh) * 0.1;
+    d.an = -0.01 * dn;
+    d.bn = r.bn * -0.0125;
 }
 
 // d/dV of the exact gate update xinf + (x - xinf) exp(-dt s), s = a + b, at frozen V;

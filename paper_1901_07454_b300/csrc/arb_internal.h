@@ -89,7 +89,7 @@ struct Ctl {
     int64_t spk_lo;            // first spike of this epoch
     int64_t probe_k0;          // step at which probe row 0 is taken
     int64_t probe_max;         // probe rows available
-    int32_t pool_n[2];         // pending network events in pool 0 / 1
+    int64_t pool_n64[2];       // pending network events in pool 0 / 1 (may count past the capacity)
     int32_t parity;            // pool holding the events not yet delivered
     int32_t n_due;             // events delivered in this epoch
     int32_t pack_next;         // work counter of the persistent epoch kernel

@@ -896,7 +896,7 @@ __global__ void k_epoch_begin(EvArgs a) {
         }
         c->ext_hi = lo;
         c->spk_lo = c->n_spikes;
-        c->pool_n[c->parity ^ 1] = 0;
+        c->pool_n64[c->parity ^ 1] = 0;
         c->pack_next = 0;
         c->n_due = 0;
     }
@@ -908,7 +908,33 @@ __global__ void k_ev_walk(EvArgs a) {
     Ctl* c = a.ctl;
     const int par = c->parity;
     const int64_t k0 = c->k0, k1 = c->k1;
-    const int64_t n_pool = min((int64_t)c->pool_n[par], a.pool_cap);
+    const int64_t n_pool = min((int64_t)c->pool_n64[par], a.pool_cap);
+    if (!kScatter) {
+        // pending events not due in this epoch move to the other pool: one atomic per warp
+        const int lane = threadIdx.x & 31;
+        const PendEv* src = par ? a.pool[1] : a.pool[0];
+        PendEv* dst = par ? a.pool[0] : a.pool[1];
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        const int64_t n_round = (n_pool + 31) / 32 * 32;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+            PendEv e;
+            bool keep = false;
+            if (i < n_pool) {
+                e = src[i];
+                keep = e.step >= k1;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (m == 0) continue;
+            long long base = 0;
+            if (lane == 0) base = (long long)atomicAdd((unsigned long long*)&c->pool_n64[par ^ 1], (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) {
+                const int64_t pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < a.pool_cap) dst[pos] = e;
+                else atomicOr(&c->status, kStPoolOverflow);
+            }
+        }
+    }
     const int64_t n_ext = c->ext_hi - c->ext_lo;
     const int64_t total = n_pool + n_ext;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -917,14 +943,7 @@ __global__ void k_ev_walk(EvArgs a) {
         int32_t syn, src, idx;
         if (i < n_pool) {
             const PendEv e = (par ? a.pool[1] : a.pool[0])[i];
-            if (e.step >= k1) {
-                if (!kScatter) {           // not due yet: keep it for a later epoch
-                    const int pos = atomicAdd(&c->pool_n[par ^ 1], 1);
-                    if (pos < a.pool_cap) (par ? a.pool[0] : a.pool[1])[pos] = e;
-                    else atomicOr(&c->status, kStPoolOverflow);
-                }
-                continue;
-            }
+            if (e.step >= k1) continue;   // not due yet: kept by the pass below
             t = e.t; w = e.w; step = e.step; syn = e.syn; src = e.src; idx = e.idx;
         } else {
             const int64_t x = c->ext_lo + (i - n_pool);
@@ -984,15 +1003,42 @@ __device__ __forceinline__ bool ev_less(const EvRec& x, const EvRec& y) {
     return x.idx < y.idx;
 }
 
-// Per-owner insertion sort: lists are short (a few events per lane and epoch).
+// Per-owner sort of the epoch's events by (step, synapse row, t, source, index), which is a
+// total order. Short lists (a few events per lane and epoch on the batched workload) use an
+// insertion sort; long ones (dense networks: thousands per lane) an in-place heapsort.
 __global__ void k_ev_sort(EvArgs a) {
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_owner; o += gridDim.x * blockDim.x) {
         const int lo = a.off[o], hi = a.off[o + 1];
-        for (int i = lo + 1; i < hi; ++i) {
-            const EvRec x = a.rec[i];
-            int j = i - 1;
-            while (j >= lo && ev_less(x, a.rec[j])) { a.rec[j + 1] = a.rec[j]; --j; }
-            a.rec[j + 1] = x;
+        EvRec* r = a.rec + lo;
+        const int n = hi - lo;
+        if (n <= 48) {
+            for (int i = 1; i < n; ++i) {
+                const EvRec x = r[i];
+                int j = i - 1;
+                while (j >= 0 && ev_less(x, r[j])) { r[j + 1] = r[j]; --j; }
+                r[j + 1] = x;
+            }
+            continue;
+        }
+        auto sift = [&](int root, int end) {          // max-heap on [0, end)
+            const EvRec x = r[root];
+            int i = root;
+            for (;;) {
+                int ch = 2 * i + 1;
+                if (ch >= end) break;
+                if (ch + 1 < end && ev_less(r[ch], r[ch + 1])) ++ch;
+                if (!ev_less(x, r[ch])) break;
+                r[i] = r[ch];
+                i = ch;
+            }
+            r[i] = x;
+        };
+        for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
+        for (int end = n - 1; end > 0; --end) {
+            const EvRec t = r[0];
+            r[0] = r[end];
+            r[end] = t;
+            sift(0, end);
         }
     }
 }
@@ -1003,14 +1049,27 @@ __global__ void k_ev_sort(EvArgs a) {
 // its source (the connection table of Sec. "Implementation", grouped by source here), and each
 // resulting event waits in the pending pool for the epoch that contains its step.
 __global__ void k_spike_expand(SpkArgs a) {
+    // one warp per spike: lane 0 reserves the spike's whole fan-out in the pending pool with
+    // one atomic, the lanes write its events
     Ctl* c = a.ctl;
     const int par = c->parity;
     const int64_t k1 = c->k1;
     const int64_t lo = c->spk_lo, hi = min(c->n_spikes, a.spike_cap);
-    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    PendEv* out = par ? a.pool[0] : a.pool[1];
+    for (int64_t i = lo + warp; i < hi; i += nwarps) {
         const int32_t gid = a.spk_gid[i];
         const double ts = a.spk_t[i];
-        for (int64_t q = a.out_ptr[gid]; q < a.out_ptr[gid + 1]; ++q) {
+        const int64_t q0 = a.out_ptr[gid], deg = a.out_ptr[gid + 1] - q0;
+        if (deg == 0) continue;
+        int64_t base = 0;
+        if (lane == 0) base = atomicAdd((unsigned long long*)&c->pool_n64[par ^ 1], (unsigned long long)deg);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base + deg > a.pool_cap && lane == 0) atomicOr(&c->status, kStPoolOverflow);
+        for (int64_t k = lane; k < deg; k += 32) {
+            const int64_t q = q0 + k;
             PendEv e;
             e.t = __dadd_rn(ts, a.out_delay[q]);
             int64_t step = (int64_t)ceil(__ddiv_rn(e.t, a.dt));
@@ -1021,9 +1080,7 @@ __global__ void k_spike_expand(SpkArgs a) {
             e.src = gid;
             e.idx = a.out_idx[q];
             e.pad = 0;
-            const int pos = atomicAdd(&c->pool_n[par ^ 1], 1);
-            if (pos < a.pool_cap) (par ? a.pool[0] : a.pool[1])[pos] = e;
-            else atomicOr(&c->status, kStPoolOverflow);
+            if (base + k < a.pool_cap) out[base + k] = e;
         }
     }
 }
@@ -1033,7 +1090,7 @@ __global__ void k_epoch_end(Ctl* c, int64_t pool_cap) {
         c->k0 = c->k1;
         c->ext_lo = c->ext_hi;
         const int np = c->parity ^ 1;
-        if (c->pool_n[np] > pool_cap) c->pool_n[np] = (int32_t)pool_cap;
+        if (c->pool_n64[np] > pool_cap) c->pool_n64[np] = pool_cap;
         c->parity = np;
     }
 }
@@ -1044,13 +1101,13 @@ __global__ void k_epoch_end(Ctl* c, int64_t pool_cap) {
 template <class T>
 __global__ void k_gather(double* out, const T* src, const int64_t* idx, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (double)src[idx[i]];
+        out[i] = idx[i] >= 0 ? (double)src[idx[i]] : 0.0;
 }
 
 template <class T>
 __global__ void k_scatter(T* dst, const double* src, const int64_t* idx, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[idx[i]] = (T)src[i];
+        if (idx[i] >= 0) dst[idx[i]] = (T)src[i];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1091,7 +1148,7 @@ cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s) {
 }
 
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s) {
-    k_spike_expand<<<n_sm, 128, 0, s>>>(a);
+    k_spike_expand<<<4 * n_sm, 256, 0, s>>>(a);
     k_epoch_end<<<1, 32, 0, s>>>(a.ctl, a.pool_cap);
     return cudaGetLastError();
 }

@@ -119,6 +119,12 @@ struct arb_sim {
     std::vector<double> length, radius, cm, Ra;
     std::vector<int64_t> hh_cv, pas_cv, syn_cv, st_cv, det_cv;
     std::vector<double> gnabar, gkbar, gl, g_pas, e_pas, syn_tau, syn_e, st_on, st_dur, st_amp;
+    // synapse state units: one per synapse, or per (CV, tau, e) group when coalescing
+    bool coalesce = false;
+    std::vector<int32_t> syn_unit;          // model synapse -> unit
+    std::vector<int64_t> u_cv;
+    std::vector<double> u_tau, u_e;
+    std::vector<int32_t> u_rep;             // lowest-index synapse of the unit
     double threshold = -10.0;
     std::vector<int32_t> conn_src;
     std::vector<int64_t> conn_dst;
@@ -648,6 +654,47 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         !copy_d(m->n_syn, m->syn_e, sim->syn_e))
         return bad(sim->err.empty() ? "bad synapse arrays" : sim->err);
     for (double tau : sim->syn_tau) if (!(tau > 0)) return bad("synapse tau must be > 0");
+    if (p.coalesce_synapses != 0 && p.coalesce_synapses != 1) return bad("coalesce_synapses must be 0 or 1");
+    if (p.reserved != 0) return bad("reserved must be 0");
+    sim->coalesce = p.coalesce_synapses == 1;
+    {
+        const int64_t ns = (int64_t)sim->syn_cv.size();
+        sim->syn_unit.assign(ns, 0);
+        if (sim->coalesce) {
+            std::vector<int32_t> ord(ns);
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+                if (sim->syn_cv[x] != sim->syn_cv[y]) return sim->syn_cv[x] < sim->syn_cv[y];
+                if (sim->syn_tau[x] != sim->syn_tau[y]) return sim->syn_tau[x] < sim->syn_tau[y];
+                return sim->syn_e[x] < sim->syn_e[y];
+            });
+            std::vector<int32_t> unit_of_sorted(ns);
+            int32_t nu = 0;
+            for (int64_t r = 0; r < ns; ++r) {
+                const int32_t x = ord[r];
+                if (r > 0) {
+                    const int32_t y = ord[r - 1];
+                    if (sim->syn_cv[x] != sim->syn_cv[y] || sim->syn_tau[x] != sim->syn_tau[y] || sim->syn_e[x] != sim->syn_e[y]) ++nu;
+                }
+                sim->syn_unit[x] = nu;
+            }
+            nu = ns > 0 ? nu + 1 : 0;
+            sim->u_rep.assign(nu, INT32_MAX);
+            for (int64_t i = 0; i < ns; ++i) sim->u_rep[sim->syn_unit[i]] = std::min<int32_t>(sim->u_rep[sim->syn_unit[i]], (int32_t)i);
+        } else {
+            std::iota(sim->syn_unit.begin(), sim->syn_unit.end(), 0);
+            sim->u_rep = sim->syn_unit;
+        }
+        const size_t nu = sim->u_rep.size();
+        sim->u_cv.resize(nu);
+        sim->u_tau.resize(nu);
+        sim->u_e.resize(nu);
+        for (size_t u = 0; u < nu; ++u) {
+            sim->u_cv[u] = sim->syn_cv[sim->u_rep[u]];
+            sim->u_tau[u] = sim->syn_tau[sim->u_rep[u]];
+            sim->u_e[u] = sim->syn_e[sim->u_rep[u]];
+        }
+    }
     if (m->n_syn > INT32_MAX / 2) return bad("too many synapses");
     if (!copy_idx(m->n_stim, m->stim_cv, sim->st_cv, "stim") || !copy_d(m->n_stim, m->stim_t_on, sim->st_on) ||
         !copy_d(m->n_stim, m->stim_dur, sim->st_dur) || !copy_d(m->n_stim, m->stim_amp, sim->st_amp))
@@ -780,12 +827,12 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     const int64_t mtb = sim->mixed ? 4 : 8;
     Plan& pl = sim->plan;
     pl.tile_doubles = (int)(budget / 8);
-    const int32_t nsyn_all = (int32_t)sim->syn_cv.size();
+    const int32_t nsyn_all = (int32_t)sim->u_cv.size();     // synapse state units
     std::vector<int32_t> cell_of(ncv);
     for (int32_t c = 0; c < nc; ++c)
         for (int64_t i = sim->cv_offset[c]; i < sim->cv_offset[c + 1]; ++i) cell_of[i] = c;
     std::vector<std::vector<int32_t>> cell_syn(nc), cell_hh(nc), cell_st(nc);
-    for (int32_t i = 0; i < nsyn_all; ++i) cell_syn[cell_of[sim->syn_cv[i]]].push_back(i);
+    for (int32_t i = 0; i < nsyn_all; ++i) cell_syn[cell_of[sim->u_cv[i]]].push_back(i);
     for (size_t i = 0; i < sim->hh_cv.size(); ++i) cell_hh[cell_of[sim->hh_cv[i]]].push_back((int32_t)i);
     for (size_t i = 0; i < sim->st_cv.size(); ++i) cell_st[cell_of[sim->st_cv[i]]].push_back((int32_t)i);
     std::vector<char> cv_has_mech(ncv, 0);
@@ -835,7 +882,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
             G.hh.insert(G.hh.end(), cell_hh[c].begin(), cell_hh[c].end());
         }
-        assign_grouped(sy, sim->syn_cv, G.syn_l);
+        assign_grouped(sy, sim->u_cv, G.syn_l);
         assign_grouped(st, sim->st_cv, G.st_l);
         for (int l = 0; l < 32; ++l) {
             G.nsyn_row = std::max<int64_t>(G.nsyn_row, (int64_t)G.syn_l[l].size());
@@ -1097,7 +1144,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
                 hh_l[pi].insert(hh_l[pi].end(), cell_hh[c].begin(), cell_hh[c].end());
             }
-            assign_grouped(sy, sim->syn_cv, syn_l[pi]);
+            assign_grouped(sy, sim->u_cv, syn_l[pi]);
             assign_grouped(st, sim->st_cv, st_l[pi]);
             row0 += J;
         }
@@ -1286,11 +1333,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 for (size_t rr = 0; rr < v.size(); ++rr) {
                     const int32_t i = v[rr];
                     const int64_t q = ((int64_t)pd.syn_row0 + (int64_t)rr) * kWarp + l;
-                    const int64_t cv = sim->syn_cv[i];
+                    const int64_t cv = sim->u_cv[i];
                     pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
                     pl.syn_vs[q] = pl.vmap[pl.cv_tile[cv]];
-                    pl.syn_e[q] = sim->syn_e[i];
-                    pl.syn_decay[q] = std::exp(-p.dt / sim->syn_tau[i]);
+                    pl.syn_e[q] = sim->u_e[i];
+                    pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
                     pl.syn_sc[q] = invd[cv];
                     pl.syn_entry[i] = q;
                     pl.syn_owner[i] = pi * kWarp + l;
@@ -1496,11 +1543,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             for (size_t r = 0; r < v.size(); ++r) {
                 const int32_t i = v[r];
                 const int64_t q = ((int64_t)pd.syn_row0 + (int64_t)r) * kWarp + l;
-                const int64_t cv = sim->syn_cv[i];
+                const int64_t cv = sim->u_cv[i];
                 pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
                 pl.syn_vs[q] = vread(cv);
-                pl.syn_e[q] = sim->syn_e[i];
-                pl.syn_decay[q] = std::exp(-p.dt / sim->syn_tau[i]);
+                pl.syn_e[q] = sim->u_e[i];
+                pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
                 pl.syn_sc[q] = invd[cv];
                 pl.syn_entry[i] = q;
                 pl.syn_owner[i] = pi * kWarp + l;
@@ -1535,6 +1582,23 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         }
     }
     }   // tile packs
+
+    // per model synapse: the owner lane and row of its unit (events go there), and the state
+    // entry for the unit's lowest-index synapse only (-1 for the others)
+    {
+        const int64_t ns = (int64_t)sim->syn_cv.size();
+        std::vector<int64_t> entry(ns, -1);
+        std::vector<int32_t> owner(ns, 0), js(ns, 0);
+        for (int64_t i = 0; i < ns; ++i) {
+            const int32_t u = sim->syn_unit[i];
+            owner[i] = pl.syn_owner[u];
+            js[i] = pl.syn_js[u];
+            if (sim->u_rep[u] == i) entry[i] = pl.syn_entry[u];
+        }
+        pl.syn_entry.swap(entry);
+        pl.syn_owner.swap(owner);
+        pl.syn_js.swap(js);
+    }
 
     // initial gates
     {
@@ -1996,7 +2060,10 @@ arb_status arb_set_probes(arb_sim* sim, int64_t n, const int64_t* cv, double* de
 }
 
 static arb_status upload_mech_state(arb_sim* sim, const std::vector<double>& m, const std::vector<double>& h,
-                                    const std::vector<double>& n, const std::vector<double>& g) {
+                                    const std::vector<double>& n, const std::vector<double>& g_in) {
+    // one state per unit: the unit's lowest-index synapse carries the sum over the unit
+    std::vector<double> g(g_in.size(), 0.0);
+    for (size_t i = 0; i < g_in.size(); ++i) g[sim->u_rep[sim->syn_unit[i]]] += g_in[i];
     double* scr = (double*)region(sim, "scratch");
     const int64_t nhh = (int64_t)sim->hh_cv.size(), nsyn = (int64_t)sim->syn_cv.size();
     const int64_t* hidx = (const int64_t*)region(sim, "hh_entry");

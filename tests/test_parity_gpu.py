@@ -138,6 +138,19 @@ def test_batched_full_size_sampled_cells():
     assert rel_err(g["V"][cv_old], o["V"]) <= TOL
 
 
+def test_mixed_full_size_sampled_cells():
+    # the 65,536-cell mixed workload (FP32 mechanisms) in the benchmark's launch configuration;
+    # sampled cells against the FP64 oracle, open loop over the first millisecond
+    m, spec = make_config(3, t_end=1.0)
+    g = run_gpu(m, spec, precision="mixed")
+    rng = np.random.default_rng(1)
+    cells = np.unique(np.concatenate([rng.choice(1024, 24, replace=False),
+                                      np.argsort(np.diff(m.cv_offset))[-4:]]))
+    sm, ss, cv_old = submodel(m, spec, cells)
+    o = run_oracle(sm, ss)
+    assert np.max(np.abs(g["V"][cv_old] - o["V"])) <= 1e-3
+
+
 def test_epoch_length_and_advance_chunks_are_bitwise_neutral():
     m, spec = make_config(1, n_cells=24, t_end=40.0)
     a = run_gpu(m, spec)
@@ -237,3 +250,61 @@ def test_nonfinite_is_reported():
     with pytest.raises(arb.ArbError) as ei:
         sim.advance(100.0)
     assert "NONFINITE" in str(ei.value)
+
+
+@pytest.mark.parametrize("kpp", [0, 32])
+def test_coalesced_synapses_match_the_oracle(kpp):
+    # many synapses per CV (three time constants, two reversals): coalesced states must give the
+    # per-synapse oracle's voltages, and the state read-back carries each group's summed g
+    import paper_1901_07454_b300 as arb
+    m = small_tree_model(13, n_cells=20, n_branches=6, cv_range=(2, 9), n_syn=60)
+    rng = np.random.default_rng(9)
+    m.syn_tau = rng.choice([1.0, 2.0, 5.0], m.n_syn)
+    m.syn_e = rng.choice([0.0, -70.0], m.n_syn)
+    m.stim_cv = m.cv_offset[:-1:2].copy()
+    k = m.stim_cv.size
+    m.stim_t_on, m.stim_dur, m.stim_amp = np.full(k, 1.0), np.full(k, 8.0), np.linspace(0.1, 0.8, k)
+    m.__post_init__()
+    syn, t, w = _with_events(m, 4, 60.0, 20.0, w=0.01)
+    spec = SimSpec(dt=0.025, t_end=20.0, epoch_steps=40, ev_syn=syn, ev_t=t, ev_w=w)
+    g = run_gpu(m, spec, probes=m.cv_offset[:-1], cells_per_pack=kpp, coalesce_synapses=True)
+    o = run_oracle(m, spec, probes=m.cv_offset[:-1])
+    assert rel_err(g["V"], o["V"]) <= TOL
+    compare_spikes(g["spikes"], o["spikes"])
+    # g per (CV, tau, e) group, reported on the group's lowest-index synapse
+    key = np.stack([m.syn_cv, m.syn_tau, m.syn_e], 1)
+    _, first, unit = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    og = o["sim"].get_state()["g"]
+    want = np.zeros(m.n_syn)
+    np.add.at(want, first[unit.ravel()], og)
+    got = g["sim"].get_state()["g"]
+    assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.max(np.abs(want)))
+    assert np.count_nonzero(got) <= first.size
+    # setting a state sums each group: the same state read back
+    st = g["sim"].get_state()
+    g["sim"].set_state(st)
+    assert np.array_equal(g["sim"].get_state()["g"], got)
+
+
+def test_dense_network_closed_loop_small():
+    # the dense workload at 128 cells x 1,000 synapses: synchronous 50 Hz firing, every spike
+    # fans out to ~1,000 synapses with delays of 10-20 ms
+    m, spec = make_config(5, n_cells=128, syn_per_cell=1000, t_end=60.0)
+    probes = m.cv_offset[:-1]
+    o = run_oracle(m, spec, probes=probes)
+    for co in (True, False):
+        g = run_gpu(m, spec, probes=probes, coalesce_synapses=co)
+        compare_spikes(g["spikes"], o["spikes"])
+        assert rel_err(g["V"], o["V"]) <= TOL
+        assert rel_err(g["trace"], o["trace"]) <= trace_bar(TOL, oracle_spread(m, spec, probes))
+    assert len(o["spikes"][1]) == 3 * m.n_cells
+
+
+def test_dense_full_size_two_epochs():
+    # 4,096 cells x 10,000 synapses (41M connections) in the benchmark's configuration: the
+    # synchronous spikes of the first epoch deliver ~41M events into the second
+    m, spec = make_config(5, t_end=20.0)
+    g = run_gpu(m, spec, coalesce_synapses=True, event_capacity=1 << 26, bucket_capacity=1 << 26)
+    o = run_oracle(m, spec)
+    compare_spikes(g["spikes"], o["spikes"])
+    assert rel_err(g["V"], o["V"]) <= TOL
