@@ -190,6 +190,7 @@ struct EvArgs {
     int32_t* counts;
     int32_t* off;
     EvRec* rec;
+    EvRec* tmp;               // [bucket_cap] scratch of the long-list sort
     int64_t bucket_cap;
     int32_t n_owner;
     int32_t epoch_steps;

@@ -1004,42 +1004,109 @@ __device__ __forceinline__ bool ev_less(const EvRec& x, const EvRec& y) {
 }
 
 // Per-owner sort of the epoch's events by (step, synapse row, t, source, index), which is a
-// total order. Short lists (a few events per lane and epoch on the batched workload) use an
-// insertion sort; long ones (dense networks: thousands per lane) an in-place heapsort.
+// total order. Short lists (a few events per lane and epoch on the batched workload) are sorted
+// here by one thread each with an insertion sort; long ones are left to k_ev_sort_long.
+constexpr int kEvShort = 48;
 __global__ void k_ev_sort(EvArgs a) {
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_owner; o += gridDim.x * blockDim.x) {
-        const int lo = a.off[o], hi = a.off[o + 1];
-        EvRec* r = a.rec + lo;
+        const int lo = a.off[o], hi = min(a.off[o + 1], (int)min((int64_t)INT32_MAX, a.bucket_cap));
         const int n = hi - lo;
-        if (n <= 48) {
-            for (int i = 1; i < n; ++i) {
-                const EvRec x = r[i];
-                int j = i - 1;
-                while (j >= 0 && ev_less(x, r[j])) { r[j + 1] = r[j]; --j; }
-                r[j + 1] = x;
+        if (n > kEvShort) continue;
+        EvRec* r = a.rec + lo;
+        for (int i = 1; i < n; ++i) {
+            const EvRec x = r[i];
+            int j = i - 1;
+            while (j >= 0 && ev_less(x, r[j])) { r[j + 1] = r[j]; --j; }
+            r[j + 1] = x;
+        }
+    }
+}
+
+// Long per-owner lists (dense networks: thousands of events per lane and epoch), one block per
+// list: the records are copied to a scratch buffer, counting-sorted by step (the block's threads
+// histogram and scatter record indices in shared memory), each step's bucket is
+// insertion-sorted by the full key, and the records are gathered back in order. Lists that do
+// not fit are heap-sorted in place by one thread.
+constexpr int kEvLongMax = 16384;      // indices staged per list
+constexpr int kEvLongSteps = 4096;     // histogram bins (epoch steps) in shared memory
+__global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
+    extern __shared__ int ev_smem[];
+    int* sidx = ev_smem;                                           // [kEvLongMax]
+    int* hist = sidx + kEvLongMax;                                 // [kEvLongSteps + 1]
+    int* cur = hist + kEvLongSteps + 1;                            // [kEvLongSteps]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int E = a.epoch_steps;
+    for (int o = blockIdx.x; o < a.n_owner; o += gridDim.x) {
+        const int lo = a.off[o], hi = min(a.off[o + 1], (int)min((int64_t)INT32_MAX, a.bucket_cap));
+        const int n = hi - lo;
+        if (n <= kEvShort) continue;                               // uniform across the block
+        EvRec* r = a.rec + lo;
+        EvRec* t = a.tmp + lo;
+        if (n > kEvLongMax || E > kEvLongSteps) {
+            if (tid == 0) {
+                auto sift = [&](int root, int end) {               // max-heap on [0, end)
+                    const EvRec x = r[root];
+                    int i = root;
+                    for (;;) {
+                        int ch = 2 * i + 1;
+                        if (ch >= end) break;
+                        if (ch + 1 < end && ev_less(r[ch], r[ch + 1])) ++ch;
+                        if (!ev_less(x, r[ch])) break;
+                        r[i] = r[ch];
+                        i = ch;
+                    }
+                    r[i] = x;
+                };
+                for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
+                for (int end = n - 1; end > 0; --end) {
+                    const EvRec x = r[0];
+                    r[0] = r[end];
+                    r[end] = x;
+                    sift(0, end);
+                }
             }
+            __syncthreads();
             continue;
         }
-        auto sift = [&](int root, int end) {          // max-heap on [0, end)
-            const EvRec x = r[root];
-            int i = root;
-            for (;;) {
-                int ch = 2 * i + 1;
-                if (ch >= end) break;
-                if (ch + 1 < end && ev_less(r[ch], r[ch + 1])) ++ch;
-                if (!ev_less(x, r[ch])) break;
-                r[i] = r[ch];
-                i = ch;
-            }
-            r[i] = x;
-        };
-        for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
-        for (int end = n - 1; end > 0; --end) {
-            const EvRec t = r[0];
-            r[0] = r[end];
-            r[end] = t;
-            sift(0, end);
+        for (int i = tid; i <= E; i += nt) hist[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) {
+            const EvRec x = r[i];
+            t[i] = x;
+            atomicAdd(&hist[min(max(x.step_rel, 0), E - 1) + 1], 1);
         }
+        __syncthreads();
+        if (tid < 32) {                                            // bucket starts: warp scan in chunks
+            int carry = 0;
+            for (int base = 1; base <= E; base += 32) {
+                const int i = base + tid;
+                int v = i <= E ? hist[i] : 0;
+                for (int sh = 1; sh < 32; sh <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, v, sh);
+                    if (tid >= sh) v += u;
+                }
+                if (i <= E) hist[i] = v + carry;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < E; i += nt) cur[i] = hist[i];
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) sidx[atomicAdd(&cur[min(max(t[i].step_rel, 0), E - 1)], 1)] = i;
+        __syncthreads();
+        for (int b = tid; b < E; b += nt) {                        // order inside each step
+            const int b0 = hist[b], b1 = hist[b + 1];
+            for (int i = b0 + 1; i < b1; ++i) {
+                const int x = sidx[i];
+                const EvRec xr = t[x];
+                int j = i - 1;
+                while (j >= b0 && ev_less(xr, t[sidx[j]])) { sidx[j + 1] = sidx[j]; --j; }
+                sidx[j + 1] = x;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) r[i] = t[sidx[i]];
+        __syncthreads();
     }
 }
 
@@ -1137,6 +1204,13 @@ template cudaError_t launch_epoch<float>(const DevModel<float>&, bool, int, int,
 template cudaError_t epoch_occupancy<double>(bool, int, int, int*);
 template cudaError_t epoch_occupancy<float>(bool, int, int, int*);
 
+size_t ev_sort_long_smem() { return sizeof(int) * (kEvLongMax + 2 * kEvLongSteps + 1); }
+
+// Kernel attributes the event launches need, set once before they are captured.
+cudaError_t events_prepare() {
+    return cudaFuncSetAttribute(k_ev_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ev_sort_long_smem());
+}
+
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s) {
     const int owner_blocks = max(1, min(4 * n_sm, (a.n_owner + 255) / 256));
     k_epoch_begin<<<owner_blocks, 256, 0, s>>>(a);
@@ -1144,6 +1218,7 @@ cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s) {
     k_ev_scan<<<1, 1024, 0, s>>>(a);
     k_ev_walk<true><<<2 * n_sm, 256, 0, s>>>(a);
     k_ev_sort<<<owner_blocks, 256, 0, s>>>(a);
+    k_ev_sort_long<<<4 * n_sm, 256, ev_sort_long_smem(), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int wa
 template <class MT>
 cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm);
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
+cudaError_t events_prepare();
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s);
 template <class T>
 cudaError_t launch_gather(double* out, const T* src, const int64_t* idx, int64_t n, cudaStream_t s);
@@ -460,7 +461,7 @@ static void layout_regions(arb_sim* sim) {
         {"det_slot", 4 * nowner}, {"det_gid", 4 * nowner},
         {"probe_slot", 4 * std::max<int64_t>(sim->n_cv, 1)}, {"probe_col", 4 * std::max<int64_t>(sim->n_cv, 1)},
         {"ev_off", 4 * (nowner + 1)}, {"counts", 4 * std::max<int64_t>(nowner, 1)},
-        {"ev", sizeof(EvRec) * p.bucket_capacity},
+        {"ev", sizeof(EvRec) * p.bucket_capacity}, {"ev_tmp", sizeof(EvRec) * p.bucket_capacity},
         {"pool0", sizeof(PendEv) * p.event_capacity}, {"pool1", sizeof(PendEv) * p.event_capacity},
         {"ext_step", 8 * p.ext_event_capacity}, {"ext_t", 8 * p.ext_event_capacity}, {"ext_w", 8 * p.ext_event_capacity},
         {"ext_syn", 4 * p.ext_event_capacity}, {"ext_idx", 4 * p.ext_event_capacity},
@@ -1787,6 +1788,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     a.counts = (int32_t*)region(sim, "counts");
     a.off = (int32_t*)region(sim, "ev_off");
     a.rec = (EvRec*)region(sim, "ev");
+    a.tmp = (EvRec*)region(sim, "ev_tmp");
     a.bucket_cap = sim->prm.bucket_capacity;
     a.n_owner = (int32_t)(pl.packs.size() * kWarp);
     a.epoch_steps = sim->epoch_steps;
@@ -1804,6 +1806,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     b.pool[1] = a.pool[1];
     b.pool_cap = sim->prm.event_capacity;
     b.dt = sim->prm.dt;
+    CU(events_prepare());
     // launch shape of the persistent epoch kernel
     if (pl.stream) {
         // fewer warps per CTA when one warp's stack or mailbox is large
