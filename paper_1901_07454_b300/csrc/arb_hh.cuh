@@ -8,9 +8,11 @@
 
 namespace arbk {
 
-// 1/x for the positive pivots of the implicit scheme: the hardware estimate (about 20 correct
-// bits) refined by one third-order step, r <- r + r (e + e^2) with e = 1 - x r, which triples
-// the number of correct bits (error e^3).
+// 1/x (pivots of the implicit scheme, and the quotients of the FP64 HH rates and gate
+// updates): the hardware estimate (about 20 correct bits) refined by one third-order step,
+// r <- r + r (e + e^2) with e = 1 - x r, which triples the number of correct bits (error e^3),
+// so the result is within an ulp or so of 1/x. x must be nonzero with |x| between about 1e-300
+// and 1e300 (the estimate flushes subnormal results to zero); the callers' values are.
 __device__ __forceinline__ double rcp_nr(double x) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
@@ -39,17 +41,17 @@ __device__ __forceinline__ Rates hh_rates_em(double v, double& em1, double& em2)
     Rates r;
     const double x1 = (v + 40.0) * -0.1;
     em1 = expm1(x1);
-    r.am = x1 == 0.0 ? 1.0 : x1 / em1;
+    r.am = x1 == 0.0 ? 1.0 : x1 * rcp_nr(em1);
     const double e80 = exp((v + 65.0) * -0.0125);
     const double e40 = e80 * e80;
     r.bn = 0.125 * e80;
     r.ah = 0.07 * (e40 * e40);
     r.bm = 4.0 * exp((v + 65.0) * (-1.0 / 18.0));
     const double ex1 = em1 + 1.0;
-    r.bh = 1.0 / fma(ex1, 1.6487212707001282, 1.0);            // e^{1/2}
+    r.bh = rcp_nr(fma(ex1, 1.6487212707001282, 1.0));          // e^{1/2}
     const double x2 = (v + 55.0) * -0.1;
     em2 = fabs(x2) < 0.1 ? expm1(x2) : fma(ex1, 0.22313016014842982, -1.0);   // e^{-3/2}
-    r.an = 0.1 * (x2 == 0.0 ? 1.0 : x2 / em2);
+    r.an = 0.1 * (x2 == 0.0 ? 1.0 : x2 * rcp_nr(em2));
     return r;
 }
 
@@ -71,12 +73,12 @@ __device__ __forceinline__ RatesF hh_rates(float v) {
 
 __device__ __forceinline__ double gate(double x, double a, double b, double dt) {
     const double s = a + b;
-    const double xinf = a / s;
+    const double xinf = a * rcp_nr(s);
     return xinf + (x - xinf) * exp(-dt * s);
 }
 // The same update with e = exp(-dt (a + b)) already formed.
 __device__ __forceinline__ double gate_e(double x, double a, double b, double e) {
-    const double xinf = a / (a + b);
+    const double xinf = a * rcp_nr(a + b);
     return xinf + (x - xinf) * e;
 }
 __device__ __forceinline__ float gate(float x, float a, float b, float dt) {
