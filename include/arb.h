@@ -225,8 +225,16 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
                        const int32_t* group_of_cv, int32_t n_groups, void* workspace,
                        int64_t workspace_bytes, double* grad, double* loss);
 
+/* The library's own FP64 elementary functions, evaluated element-wise on caller-owned DEVICE
+ * arrays (asynchronous on `stream`), for validation: ARB_FN_EXP y[i] = exp(x[i]) (table-driven,
+ * Tang's method; |x| < 700), ARB_FN_EXPM1 y[i] = exp(x[i]) - 1, ARB_FN_HH_RATES y[6 i .. 6 i + 5]
+ * = alpha_m, beta_m, alpha_h, beta_h, alpha_n, beta_n (1/ms) at V = x[i] mV, as the FP64
+ * kernels compute them. The paper has no counterpart. Errors via arb_last_error(NULL). */
+enum { ARB_FN_EXP = 0, ARB_FN_EXPM1 = 1, ARB_FN_HH_RATES = 2 };
+arb_status arb_math_eval(int32_t fn, int64_t n, const double* x, double* y, void* stream);
+
 /* Message of the last failing call on this handle; with NULL, of the last failing call on
- * this thread that has no handle (arb_create, arb_solve_trees_noalloc). */
+ * this thread that has no handle (arb_create, arb_solve_trees_noalloc, arb_math_eval). */
 const char* arb_last_error(const arb_sim* sim);
 
 /* Tree solve that allocates no memory. The paper has no counterpart to this entry point; it

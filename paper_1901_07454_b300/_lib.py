@@ -21,7 +21,7 @@ EXPORTED = ["arb_default_params", "arb_create", "arb_destroy", "arb_workspace_by
             "arb_enqueue_events", "arb_advance", "arb_time", "arb_read_voltage", "arb_num_spikes",
             "arb_read_spikes", "arb_set_probes", "arb_get_state", "arb_set_state", "arb_plan_info",
             "arb_last_timing", "arb_last_error", "arb_solve_trees_noalloc", "arb_adjoint_workspace_bytes",
-            "arb_adjoint"]
+            "arb_adjoint", "arb_math_eval"]
 
 
 class arb_params(C.Structure):
@@ -84,6 +84,7 @@ def load():
         "arb_solve_trees_noalloc": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, vp]),
         "arb_adjoint_workspace_bytes": (i32, [vp, i64, i32, i64, i32, C.POINTER(i64)]),
         "arb_adjoint": (i32, [vp, i64, i32, i64, vp, vp, dbl, vp, i32, vp, i64, vp, C.POINTER(dbl)]),
+        "arb_math_eval": (i32, [i32, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -207,9 +207,9 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                     Rates r, dr;
                     hh_rates_derivs(v, r, dr);
                     const double dt = a.dt;
-                    const double em = exp(-dt * (r.am + r.bm));
-                    const double eh = exp(-dt * (r.ah + r.bh));
-                    const double en = exp(-dt * (r.an + r.bn));
+                    const double em = gate_decay(r.am, r.bm, dt);
+                    const double eh = gate_decay(r.ah, r.bh, dt);
+                    const double en = gate_decay(r.an, r.bn, dt);
                     const double xm = Ys[j], xh = Ys[nhh + j], xn = Ys[2 * nhh + j];
                     Yd[j] = gate_e(xm, r.am, r.bm, em);
                     Yd[nhh + j] = gate_e(xh, r.ah, r.bh, eh);

@@ -6,6 +6,8 @@
 
 #include <cmath>
 
+#include "arb_exp_table.h"
+
 namespace arbk {
 
 // 1/x (pivots of the implicit scheme, and the quotients of the FP64 HH rates and gate
@@ -20,6 +22,31 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return fma(r, fma(e, e, e), r);
 }
 
+
+// exp(x) for |x| < 700 by Tang's table-driven method (ACM TOMS 15(2), 1989): x = k ln2/64 + r
+// with k = 64 m + j and |r| <= ln2/128, exp(x) = 2^m 2^(j/64) exp(r); exp(r) - 1 is its
+// Taylor polynomial to r^5 (the first omitted term is below 4e-17 there), 2^(j/64) comes from a
+// 64-entry table and 2^m is added to the exponent field. 10 FP64 operations; within about an
+// ulp of exp(x).
+__device__ __forceinline__ double exp_t(double x) {
+    const double kShift = 6755399441055744.0;          // 1.5 * 2^52: adding it rounds to an integer
+    const double t = fma(x, kExpInvLn2x64, kShift);
+    const int k = __double2loint(t);                    // the rounded integer, two's complement
+    const double kd = t - kShift;
+    double r = fma(-kd, kExpLn2Hi, x);
+    r = fma(-kd, kExpLn2Lo, r);
+    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(r, q, 1.0 / 6.0);
+    q = fma(r, q, 0.5);
+    q = fma(r, q, 1.0);
+    const double T = __ldg(&kExpTable[k & 63]);
+    const double y = fma(T, r * q, T);
+    return __hiloint2double(__double2hiint(y) + ((k >> 6) << 20), __double2loint(y));
+}
+
+// e^x - 1: the library's expm1 where |x| < 0.1 (where e^x - 1 would cancel), else exp_t - 1
+// (relative error of the difference at most ~10 ulp there).
+__device__ __forceinline__ double expm1_t(double x) { return fabs(x) < 0.1 ? expm1(x) : exp_t(x) - 1.0; }
 
 // ------------------------------------------------------------------------------------------
 // Hodgkin-Huxley rates (1/ms) and exact gate update at frozen V, in the precision MT.
@@ -40,13 +67,13 @@ struct RatesF { float am, bm, ah, bh, an, bn; };
 __device__ __forceinline__ Rates hh_rates_em(double v, double& em1, double& em2) {
     Rates r;
     const double x1 = (v + 40.0) * -0.1;
-    em1 = expm1(x1);
+    em1 = expm1_t(x1);
     r.am = x1 == 0.0 ? 1.0 : x1 * rcp_nr(em1);
-    const double e80 = exp((v + 65.0) * -0.0125);
+    const double e80 = exp_t((v + 65.0) * -0.0125);
     const double e40 = e80 * e80;
     r.bn = 0.125 * e80;
     r.ah = 0.07 * (e40 * e40);
-    r.bm = 4.0 * exp((v + 65.0) * (-1.0 / 18.0));
+    r.bm = 4.0 * exp_t((v + 65.0) * (-1.0 / 18.0));
     const double ex1 = em1 + 1.0;
     r.bh = rcp_nr(fma(ex1, 1.6487212707001282, 1.0));          // e^{1/2}
     const double x2 = (v + 55.0) * -0.1;
@@ -71,10 +98,12 @@ __device__ __forceinline__ RatesF hh_rates(float v) {
     return r;
 }
 
+// exp(-dt (a + b)): the decay factor of a gate over one step at frozen V.
+__device__ __forceinline__ double gate_decay(double a, double b, double dt) { return exp_t(-dt * (a + b)); }
+
 __device__ __forceinline__ double gate(double x, double a, double b, double dt) {
-    const double s = a + b;
-    const double xinf = a * rcp_nr(s);
-    return xinf + (x - xinf) * exp(-dt * s);
+    const double xinf = a * rcp_nr(a + b);
+    return xinf + (x - xinf) * gate_decay(a, b, dt);
 }
 // The same update with e = exp(-dt (a + b)) already formed.
 __device__ __forceinline__ double gate_e(double x, double a, double b, double e) {
