@@ -847,6 +847,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         std::array<std::vector<int32_t>, 32> syn_l, st_l;
         std::vector<int32_t> hh;
         int64_t nsyn_row = 0, nhh_row = 0, nst_row = 0, nvc = 0;
+        int64_t bytes = 0;   // shared-memory tile
         bool smem = false;
         double cost = 0;
     };
@@ -919,6 +920,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         }
         G.nvc = nvc;
         const int64_t bytes = 8 * (J * 32 * (sim->implicit ? 2 : 1) + nvc) + mtb * 32 * (G.nsyn_row + 3 * G.nhh_row);
+        G.bytes = bytes;
         G.smem = bytes <= budget && nvc < 0xFFFF && J * 32 <= 0xFFFF;
         G.cost = 3.0 * (double)J + 260.0 * (double)G.nhh_row + 4.0 * (double)G.nsyn_row;
         return G;
@@ -947,6 +949,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             place(g, kpp == 32, out);
         }
     };
+    // estimated per-SM work of a set of groups: longest-processing-time assignment to the SMs
+    // (a static model; Python's autotune_packing times the candidates on the GPU instead)
     auto lpt_cost = [&](const std::vector<Group>& gs) {
         std::vector<double> c;
         double mx = 0;
@@ -1374,6 +1378,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         }
     } else {
     if (groups.empty() && nc > 0) build_k(kpp, groups);
+    {   // per-warp tile: the largest shared-memory pack's need, so that more warps fit an SM
+        int64_t need = 0;
+        for (const Group& G : groups) if (G.smem) need = std::max(need, G.bytes);
+        if (need > 0) pl.tile_doubles = (int)(((need + 31) & ~(int64_t)31) / 8);
+    }
     const int32_t npk = (int32_t)groups.size();
     // the persistent kernel takes packs in this order: most work first
     std::stable_sort(groups.begin(), groups.end(), [](const Group& x, const Group& y) { return x.cost > y.cost; });

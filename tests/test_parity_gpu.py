@@ -308,3 +308,16 @@ def test_dense_full_size_two_epochs():
     o = run_oracle(m, spec)
     compare_spikes(g["spikes"], o["spikes"])
     assert rel_err(g["V"], o["V"]) <= TOL
+
+
+def test_autotuned_packing_is_timed_and_keeps_parity():
+    import paper_1901_07454_b300 as arb
+    m, spec = make_config(1, n_cells=96, t_end=10.0)
+    best, times = arb.autotune_packing(m, dt=spec.dt, epoch_steps=spec.epoch_steps,
+                                       candidates=[dict(cells_per_pack=k) for k in (8, 2, 32)], epochs=1)
+    assert len(times) == 3 and all(t > 0 for t in times.values())
+    assert best["cells_per_pack"] in (8, 2, 32)
+    assert times[tuple(sorted(best.items()))] == min(times.values())
+    g = run_gpu(m, spec, **best)
+    o = run_oracle(m, spec)
+    assert rel_err(g["V"], o["V"]) <= TOL
