@@ -448,11 +448,19 @@ def main():
         h2d = model_bytes(model)
         kk = 0
         ev_per_epoch = 0
+        ev_sorted = bool(np.all(np.diff(spec.ev_t) >= 0))
         for i in range(args.steps):
             lo, hi = kk * spec.dt, (kk + E) * spec.dt
-            sel = (spec.ev_t >= lo) & (spec.ev_t < hi) if i > 0 else (spec.ev_t < hi)
+            if ev_sorted:      # the epoch's events are a contiguous run of the time-sorted list
+                a = 0 if i == 0 else int(np.searchsorted(spec.ev_t, lo, "left"))
+                b = int(np.searchsorted(spec.ev_t, hi, "left"))
+                sel = slice(a, b)
+                n_sel = b - a
+            else:
+                sel = (spec.ev_t >= lo) & (spec.ev_t < hi) if i > 0 else (spec.ev_t < hi)
+                n_sel = int(sel.sum())
             sim2.enqueue(spec.ev_syn[sel], spec.ev_t[sel], spec.ev_w[sel])
-            ev_per_epoch += int(sel.sum())
+            ev_per_epoch += n_sel
             kk += E
             sim2.advance(kk * spec.dt)
             g, ts = sim2.spikes()

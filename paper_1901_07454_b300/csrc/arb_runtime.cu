@@ -20,6 +20,7 @@
 #include <queue>
 #include <unordered_map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/arb.h"
@@ -65,15 +66,33 @@ struct ExtEvent {
     int32_t idx;
 };
 
+// Allocator that leaves trivially constructible elements uninitialised, so that the large host
+// arrays of a plan can be filled by several threads (the first touch of their pages then runs
+// in parallel).
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind { using other = UninitAlloc<U>; };
+    UninitAlloc() = default;
+    template <class U>
+    UninitAlloc(const UninitAlloc<U>&) {}
+    template <class U>
+    void construct(U* p) noexcept { ::new ((void*)p) U; }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
+};
+template <class T>
+using hvec = std::vector<T, UninitAlloc<T>>;
+
 struct Plan {
     std::vector<PackDesc> packs;
     int64_t total_rows = 0;
-    std::vector<double> ca, cb, ck, ce;     // total_rows*32
-    std::vector<int32_t> pslot;
-    std::vector<int32_t> vmap;              // on-chip voltage slots (own | parent << 16)
-    std::vector<double> V0;                 // initial voltage per tile entry
-    std::vector<int64_t> cv_tile;           // model CV -> global tile index
-    std::vector<int32_t> cv_pack;           // model CV -> pack
+    hvec<double> ca, cb, ck, ce;            // total_rows*32
+    hvec<int32_t> pslot;
+    hvec<int32_t> vmap;                     // on-chip voltage slots (own | parent << 16)
+    hvec<double> V0;                        // initial voltage per tile entry
+    hvec<int64_t> cv_tile;                  // model CV -> global tile index
+    hvec<int32_t> cv_pack;                  // model CV -> pack
     // synapses
     int64_t syn_rows = 0;
     std::vector<int32_t> syn_slot, syn_vs;
@@ -116,8 +135,8 @@ struct arb_sim {
     int32_t n_cells = 0;
     int64_t n_cv = 0;
     std::vector<int64_t> cv_offset;
-    std::vector<int32_t> parent;
-    std::vector<double> length, radius, cm, Ra;
+    hvec<int32_t> parent;
+    hvec<double> length, radius, cm, Ra;
     std::vector<int64_t> hh_cv, pas_cv, syn_cv, st_cv, det_cv;
     std::vector<double> gnabar, gkbar, gl, g_pas, e_pas, syn_tau, syn_e, st_on, st_dur, st_amp;
     // synapse state units: one per synapse, or per (CV, tau, e) group when coalescing
@@ -191,6 +210,39 @@ arb_status fail(arb_sim* s, arb_status st, const std::string& msg) {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// Runs fn(i) for i in [0, n) on the host's hardware threads (contiguous chunks; fn must only
+// write data owned by its index).
+template <class F>
+void parallel_for(int64_t n, F fn) {
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>(hw, std::max<int64_t>(1, n / 64));
+    if (nt <= 1) {
+        for (int64_t i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (int64_t t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+            for (int64_t i = lo; i < hi; ++i) fn(i);
+        });
+    for (auto& x : th) x.join();
+}
+
+// v = n copies of val, written in parallel.
+template <class T, class A>
+void par_assign(std::vector<T, A>& v, int64_t n, T val) {
+    v.clear();
+    v.resize((size_t)n);
+    constexpr int64_t kChunk = 1 << 16;
+    T* p = v.data();
+    parallel_for((n + kChunk - 1) / kChunk, [&](int64_t c) {
+        const int64_t lo = c * kChunk, hi = std::min<int64_t>(n, lo + kChunk);
+        for (int64_t i = lo; i < hi; ++i) p[i] = val;
+    });
+}
+
 // Steady state of the Hodgkin-Huxley gates at voltage v (classic rates, 1/ms).
 void hh_steady(double v, double& m, double& h, double& n) {
     auto exr = [](double x) { return x == 0.0 ? 1.0 : x / std::expm1(x); };
@@ -205,12 +257,12 @@ void hh_steady(double v, double& m, double& h, double& n) {
 // Per-CV membrane area (um^2), capacitance (nF) and axial conductance to the parent (uS):
 // each CV is a cylinder; the conductance between a CV and its parent is that of the two half
 // cylinders between their centres in series (Sec. "Model", Eq. discrete-v).
-void cv_geometry(const arb_sim* sim, std::vector<double>& area, std::vector<double>& cap, std::vector<double>& sigma) {
+void cv_geometry(const arb_sim* sim, hvec<double>& area, hvec<double>& cap, hvec<double>& sigma) {
     const int64_t ncv = sim->n_cv;
-    area.assign(ncv, 0.0);
-    cap.assign(ncv, 0.0);
-    sigma.assign(ncv, 0.0);
-    for (int32_t c = 0; c < sim->n_cells; ++c) {
+    par_assign(area, ncv, 0.0);
+    par_assign(cap, ncv, 0.0);
+    par_assign(sigma, ncv, 0.0);
+    parallel_for(sim->n_cells, [&](int64_t c) {
         const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
         for (int64_t i = 0; i < n; ++i) {
             const int64_t g = off + i;
@@ -225,7 +277,7 @@ void cv_geometry(const arb_sim* sim, std::vector<double>& area, std::vector<doub
                 sigma[g] = 1.0 / (half_i + half_p);       // uS
             }
         }
-    }
+    });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -492,12 +544,12 @@ static char* region(arb_sim* sim, const char* name) {
     return nullptr;
 }
 
-template <class T>
-static arb_status up(arb_sim* sim, const char* name, const std::vector<T>& v) {
+template <class V>
+static arb_status up(arb_sim* sim, const char* name, const V& v) {
     if (v.empty()) return ARB_OK;
     char* dst = region(sim, name);
     if (!dst) return fail(sim, ARB_E_STATE, std::string("internal: no region ") + name);
-    CU(cudaMemcpyAsync(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, sim->s));
+    CU(cudaMemcpyAsync(dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice, sim->s));
     return ARB_OK;
 }
 
@@ -616,22 +668,39 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     sim->n_cv = ncv;
     if (ncv > (int64_t)INT32_MAX / 2) return bad("too many CVs");
     if (ncv > 0 && (!m->parent || !m->length_um || !m->radius_um || !m->cm || !m->Ra)) return bad("morphology array is NULL");
-    sim->parent.assign(m->parent, m->parent + ncv);
-    sim->length.assign(m->length_um, m->length_um + ncv);
-    sim->radius.assign(m->radius_um, m->radius_um + ncv);
-    sim->cm.assign(m->cm, m->cm + ncv);
-    sim->Ra.assign(m->Ra, m->Ra + ncv);
-    for (int32_t c = 0; c < nc; ++c) {
+    sim->parent.resize(ncv);
+    sim->length.resize(ncv);
+    sim->radius.resize(ncv);
+    sim->cm.resize(ncv);
+    sim->Ra.resize(ncv);
+    // copy and check cell by cell in parallel; the first failing cell (lowest index) is reported
+    std::vector<int64_t> bad_at(nc, -1);        // local index of the first bad CV, or -1
+    std::vector<char> bad_kind(nc, 0);          // 1 root, 2 parent order, 3 geometry
+    parallel_for(nc, [&](int64_t c) {
         const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
-        if (sim->parent[off] != -1) return bad("cell " + std::to_string(c) + ": first CV must have parent -1");
-        for (int64_t i = 1; i < n; ++i) {
-            const int32_t pi = sim->parent[off + i];
-            if (pi < 0 || pi >= i) return bad("cell " + std::to_string(c) + ": parent of local CV " + std::to_string(i) + " must be in [0, i)");
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t g = off + i;
+            sim->parent[g] = m->parent[g];
+            sim->length[g] = m->length_um[g];
+            sim->radius[g] = m->radius_um[g];
+            sim->cm[g] = m->cm[g];
+            sim->Ra[g] = m->Ra[g];
+            const int32_t pi = sim->parent[g];
+            char k = 0;
+            if (i == 0 ? pi != -1 : (pi < 0 || pi >= i)) k = i == 0 ? 1 : 2;
+            else if (!finite_pos(sim->length[g]) || !finite_pos(sim->radius[g]) || !finite_pos(sim->cm[g]) ||
+                     !finite_pos(sim->Ra[g]))
+                k = 3;
+            if (k && bad_at[c] < 0) { bad_at[c] = i; bad_kind[c] = k; }
         }
+    });
+    for (int32_t c = 0; c < nc; ++c) {
+        if (bad_at[c] < 0) continue;
+        const int64_t i = bad_at[c];
+        if (bad_kind[c] == 1) return bad("cell " + std::to_string(c) + ": first CV must have parent -1");
+        if (bad_kind[c] == 2) return bad("cell " + std::to_string(c) + ": parent of local CV " + std::to_string(i) + " must be in [0, i)");
+        return bad("CV " + std::to_string(sim->cv_offset[c] + i) + ": length, radius, cm and Ra must be finite and > 0");
     }
-    for (int64_t i = 0; i < ncv; ++i)
-        if (!finite_pos(sim->length[i]) || !finite_pos(sim->radius[i]) || !finite_pos(sim->cm[i]) || !finite_pos(sim->Ra[i]))
-            return bad("CV " + std::to_string(i) + ": length, radius, cm and Ra must be finite and > 0");
     auto copy_idx = [&](int64_t n, const int64_t* src, std::vector<int64_t>& dst, const char* what) -> bool {
         if (n < 0 || (n > 0 && !src)) return false;
         dst.assign(src, src + n);
@@ -744,7 +813,9 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         return bad("epoch of " + std::to_string(sim->epoch_steps) + " steps is longer than the minimum delay");
 
     // ------------------------------------------------------------------ discretisation
-    std::vector<double> area, cap, sigma, Glin(ncv, 0.0), GElin(ncv, 0.0);
+    hvec<double> area, cap, sigma, Glin, GElin;
+    par_assign(Glin, ncv, 0.0);
+    par_assign(GElin, ncv, 0.0);
     cv_geometry(sim, area, cap, sigma);
     for (size_t i = 0; i < sim->pas_cv.size(); ++i) {
         const int64_t cv = sim->pas_cv[i];
@@ -764,10 +835,16 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
 
     // ------------------------------------------------------------------ factorisation
     std::vector<CellOrder> ord(nc);
-    std::vector<double> invd(ncv), ck(ncv, 0.0), ce(ncv, 0.0), ca(ncv), cb(ncv);
+    hvec<double> invd, ck, ce, ca, cb;
+    par_assign(invd, ncv, 0.0);
+    par_assign(ck, ncv, 0.0);
+    par_assign(ce, ncv, 0.0);
+    par_assign(ca, ncv, 0.0);
+    par_assign(cb, ncv, 0.0);
     {
-        std::vector<double> dd;
-        for (int32_t c = 0; c < nc; ++c) {
+        // cells are independent: each thread orders and factorises whole cells
+        parallel_for(nc, [&](int64_t c) {
+            std::vector<double> dd;
             const int64_t off = sim->cv_offset[c];
             const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
             ord[c] = dfs_order(sim->parent.data() + off, n);
@@ -812,7 +889,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     ce[g] += sigma[g];
                     ce[off + o.dfs[o.dpar[q]]] += sigma[g];
                 }
-        }
+        });
     }
 
     // ------------------------------------------------------------------ packing
@@ -1120,8 +1197,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         });
         const int32_t npk = (int32_t)sg.size();
         pl.packs.resize(npk);
-        pl.cv_tile.assign(ncv, -1);
-        pl.cv_pack.assign(ncv, -1);
+        par_assign(pl.cv_tile, ncv, (int64_t)-1);
+        par_assign(pl.cv_pack, ncv, (int32_t)-1);
         std::vector<std::array<std::vector<int32_t>, 32>> syn_l(npk), st_l(npk);
         std::vector<std::vector<int32_t>> hh_l(npk);
         int64_t row0 = 0;
@@ -1160,13 +1237,13 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             if (pl.cv_tile[cv] < 0) return bad("internal error: a CV was not placed");
         pl.lane_eff = row0 > 0 ? (double)ncv / (double)ne : 1.0;
         pl.sg_total = ne;
-        pl.ca.assign(ne, 0.0);
-        pl.cb.assign(ne, 0.0);
-        pl.ck.assign(ne, 0.0);
-        pl.ce.assign(ne, sim->implicit ? 1.0 : 0.0);
-        pl.pslot.assign(ne, kFlagRoot);   // flags; padding behaves like an isolated root
-        pl.vmap.assign(ne, -1);           // compact mechanism slot
-        pl.V0.assign(ne, 0.0);
+        par_assign(pl.ca, ne, 0.0);
+        par_assign(pl.cb, ne, 0.0);
+        par_assign(pl.ck, ne, 0.0);
+        par_assign(pl.ce, ne, sim->implicit ? 1.0 : 0.0);
+        par_assign(pl.pslot, ne, (int32_t)kFlagRoot);   // flags; padding behaves like an isolated root
+        par_assign(pl.vmap, ne, (int32_t)-1);           // compact mechanism slot
+        par_assign(pl.V0, ne, 0.0);
         const uint32_t mb_out_mask = (uint32_t)kMbNone << kMbOutShift, mb_in_mask = (uint32_t)kMbNone << kMbInShift;
         for (int32_t pi = 0; pi < npk; ++pi)
             if (sg[pi].shared) {
@@ -1177,54 +1254,53 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         // per-entry constants; flags from the layout: an entry whose parent is not the next row
         // of its lane hands over (stack or mailbox)
         std::vector<int32_t> nmb(npk, 0);
-        std::unordered_map<int64_t, int32_t> mslot;   // parent entry -> mailbox slot (shared packs)
-        for (int32_t c = 0; c < nc; ++c) {
-            const int64_t off = sim->cv_offset[c];
-            for (int64_t i = 0; i < ncv_of[c]; ++i) {
-                const int64_t g = off + i;
-                const int64_t t = pl.cv_tile[g];
-                pl.ca[t] = ca[g];
-                pl.cb[t] = cb[g];
-                pl.ck[t] = ck[g];
-                pl.ce[t] = ce[g];
-                pl.V0[t] = -65.0;
-            }
-        }
-        for (int32_t c = 0; c < nc; ++c) {
-            const int64_t off = sim->cv_offset[c];
-            const int32_t pi = pl.cv_pack[off];
+        std::vector<char> err(npk, 0);     // 1: a CV with more than 255 handed-over children, 2: mailbox full
+        parallel_for(npk, [&](int64_t pi) {   // packs own disjoint entries
             const bool shared = sg[pi].shared;
-            for (int64_t i = 0; i < ncv_of[c]; ++i) {
-                const int64_t g = off + i;
-                const int64_t t = pl.cv_tile[g];
-                int32_t& f = pl.pslot[t];   // parents come before children: their counts and "in" slots are kept
-                f &= shared ? (int32_t)mb_in_mask : kFlagPopMask;
-                if (shared) f |= (int32_t)mb_out_mask;
-                if (sim->parent[g] < 0) {
-                    f |= kFlagRoot;
-                    continue;
+            for (int32_t c : sg[pi].cells) {
+                const int64_t off = sim->cv_offset[c];
+                for (int64_t i = 0; i < ncv_of[c]; ++i) {
+                    const int64_t g = off + i;
+                    const int64_t t = pl.cv_tile[g];
+                    pl.ca[t] = ca[g];
+                    pl.cb[t] = cb[g];
+                    pl.ck[t] = ck[g];
+                    pl.ce[t] = ce[g];
+                    pl.V0[t] = -65.0;
                 }
-                const int64_t tp = pl.cv_tile[off + sim->parent[g]];
-                if (tp == t + kWarp) continue;   // parent is the next row of this lane
-                f |= kFlagRemote;
-                int32_t& fp = pl.pslot[tp];
-                if (!shared) {
-                    if ((fp & kFlagPopMask) == kFlagPopMask) return bad("a CV has more than 255 handed-over children");
-                    fp += 1;
-                } else {
-                    auto it = mslot.find(tp);
-                    uint32_t s;
-                    if (it == mslot.end()) {
-                        s = (uint32_t)nmb[pi]++;
-                        if (s >= (uint32_t)kMbNone) return bad("internal error: mailbox overflow");
-                        mslot.emplace(tp, (int32_t)s);
-                        fp = (int32_t)(((uint32_t)fp & ~mb_in_mask) | (s << kMbInShift));
-                    } else {
-                        s = (uint32_t)it->second;
+                for (int64_t i = 0; i < ncv_of[c]; ++i) {
+                    const int64_t g = off + i;
+                    const int64_t t = pl.cv_tile[g];
+                    int32_t& f = pl.pslot[t];   // parents come before children: their counts and "in" slots are kept
+                    f &= shared ? (int32_t)mb_in_mask : kFlagPopMask;
+                    if (shared) f |= (int32_t)mb_out_mask;
+                    if (sim->parent[g] < 0) {
+                        f |= kFlagRoot;
+                        continue;
                     }
-                    f = (int32_t)(((uint32_t)f & ~mb_out_mask) | (s << kMbOutShift));
+                    const int64_t tp = pl.cv_tile[off + sim->parent[g]];
+                    if (tp == t + kWarp) continue;   // parent is the next row of this lane
+                    f |= kFlagRemote;
+                    int32_t& fp = pl.pslot[tp];
+                    if (!shared) {
+                        if ((fp & kFlagPopMask) == kFlagPopMask) { err[pi] = 1; return; }
+                        fp += 1;
+                    } else {
+                        // the parent's "in" slot, assigned by its first handed-over child
+                        uint32_t sl = (uint32_t)fp >> kMbInShift;
+                        if (sl == (uint32_t)kMbNone) {
+                            sl = (uint32_t)nmb[pi]++;
+                            if (sl >= (uint32_t)kMbNone) { err[pi] = 2; return; }
+                            fp = (int32_t)(((uint32_t)fp & ~mb_in_mask) | (sl << kMbInShift));
+                        }
+                        f = (int32_t)(((uint32_t)f & ~mb_out_mask) | (sl << kMbOutShift));
+                    }
                 }
             }
+        });
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            if (err[pi] == 1) return bad("a CV has more than 255 handed-over children");
+            if (err[pi] == 2) return bad("internal error: mailbox overflow");
         }
         // compact mechanism slots; stack depths (one cell per lane) and the round rule of the
         // mailbox (cells over several lanes)
@@ -1255,7 +1331,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 max_mb = std::max(max_mb, nmb[pi]);
                 // a hand-over between lanes crosses a round boundary (both sweeps), and within a
                 // round at most one lane adds to a given slot
-                std::unordered_map<int64_t, int> writer;   // round * 2048 + slot -> lane
+                std::vector<int32_t> w_round(pd.nmb, -1), w_lane(pd.nmb, -1);   // last writer of each slot
                 for (int32_t j = 0; j < pd.nrow; ++j)
                     for (int l = 0; l < kWarp; ++l) {
                         const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
@@ -1264,11 +1340,10 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                             return bad("internal error: mailbox slot out of range");
                         if (!(f & kFlagRemote) || (f & kFlagRoot)) continue;
                         if (so == kMbNone) return bad("internal error: hand-over without a mailbox slot");
-                        const int32_t s = so;
-                        const int64_t key = (int64_t)(j / kStreamRound) * 2048 + s;
-                        auto w = writer.find(key);
-                        if (w != writer.end() && w->second != l) return bad("internal error: two lanes add to one mailbox slot in a round");
-                        writer[key] = l;
+                        const int32_t rd = j / kStreamRound;
+                        if (w_round[so] == rd && w_lane[so] != l) return bad("internal error: two lanes add to one mailbox slot in a round");
+                        w_round[so] = rd;
+                        w_lane[so] = l;
                     }
                 for (int32_t c : sg[pi].cells)
                     for (int64_t cv = sim->cv_offset[c] + 1; cv < sim->cv_offset[c + 1]; ++cv) {
@@ -1388,8 +1463,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     std::stable_sort(groups.begin(), groups.end(), [](const Group& x, const Group& y) { return x.cost > y.cost; });
 
     pl.packs.resize(npk);
-    pl.cv_tile.assign(ncv, -1);
-    pl.cv_pack.assign(ncv, -1);
+    par_assign(pl.cv_tile, ncv, (int64_t)-1);
+    par_assign(pl.cv_pack, ncv, (int32_t)-1);
     int64_t row0 = 0, cvs_placed = 0, syn_rows = 0, hh_rows = 0, st_rows = 0;
     for (int32_t pi = 0; pi < npk; ++pi) {
         PackDesc& pd = pl.packs[pi];
@@ -1429,13 +1504,13 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     pl.lane_eff = pl.total_rows > 0 ? (double)ncv / (double)(pl.total_rows * kWarp) : 1.0;
     const int64_t ne = pl.total_rows * kWarp;
     if (ne > INT32_MAX) return bad("model too large for one handle");
-    pl.ca.assign(ne, 0.0);
-    pl.cb.assign(ne, 0.0);
-    pl.ck.assign(ne, 0.0);
-    pl.ce.assign(ne, sim->implicit ? 1.0 : 0.0);   // padding: unit diagonal keeps the pivots finite
-    pl.pslot.assign(ne, -2);
-    pl.vmap.assign(ne, -1);
-    pl.V0.assign(ne, 0.0);
+    par_assign(pl.ca, ne, 0.0);
+    par_assign(pl.cb, ne, 0.0);
+    par_assign(pl.ck, ne, 0.0);
+    par_assign(pl.ce, ne, sim->implicit ? 1.0 : 0.0);   // padding: unit diagonal keeps the pivots finite
+    par_assign(pl.pslot, ne, (int32_t)-2);
+    par_assign(pl.vmap, ne, (int32_t)-1);
+    par_assign(pl.V0, ne, 0.0);
     for (int32_t c = 0; c < nc; ++c) {
         const int64_t off = sim->cv_offset[c];
         const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
@@ -2335,9 +2410,9 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
             if (group_of_cv[i] >= 0) grp_cv[fill[group_of_cv[i]]++] = i;
     }
     const double dt = sim->prm.dt;
-    std::vector<double> area, cap, sigma;
+    hvec<double> area, cap, sigma;
     cv_geometry(sim, area, cap, sigma);
-    std::vector<double> cdt(ncv), dsig(sigma), glin(ncv, 0.0), gelin(ncv, 0.0);
+    std::vector<double> cdt(ncv), dsig(sigma.begin(), sigma.end()), glin(ncv, 0.0), gelin(ncv, 0.0);
     for (int64_t i = 0; i < ncv; ++i) cdt[i] = cap[i] / dt;
     for (int32_t c = 0; c < nc; ++c)
         for (int64_t i = sim->cv_offset[c] + 1; i < sim->cv_offset[c + 1]; ++i) dsig[sim->cv_offset[c] + sim->parent[i]] += sigma[i];
