@@ -53,7 +53,6 @@ __device__ __forceinline__ double expm1_t(double x) { return fabs(x) < 0.1 ? exp
 // The model (classic squid axon at 6.3 degC) is the one named by the paper's benchmark
 // (Sec. "Benchmarks", "Models": Hodgkin-Huxley soma, passive dendrites).
 
-__device__ __forceinline__ double exprelr_d(double x) { return x == 0.0 ? 1.0 : x / expm1(x); }
 __device__ __forceinline__ float exprelr_f(float x) { return x == 0.0f ? 1.0f : x / expm1f(x); }
 
 struct Rates { double am, bm, ah, bh, an, bn; };
@@ -134,18 +133,6 @@ __device__ __forceinline__ double exprelr_deriv_d(double x) {
 // d/dx of x / (e^x - 1) given em = e^x - 1 (the closed form, for |x| >= 0.1).
 __device__ __forceinline__ double exprelr_deriv_em(double x, double em) {
     return (em - x * (em + 1.0)) / (em * em);
-}
-
-// dRates/dV (1/(ms mV)) given the rates at v.
-__device__ __forceinline__ Rates hh_rate_derivs(double v, const Rates& r) {
-    Rates d;
-    d.am = -0.1 * exprelr_deriv_d((v + 40.0) * -0.1);
-    d.bm = r.bm * (-1.0 / 18.0);
-    d.ah = r.ah * -0.05;
-    d.bh = r.bh * (1.0 - r.bh) * 0.1;
-    d.an = -0.01 * exprelr_deriv_d((v + 55.0) * -0.1);
-    d.bn = r.bn * -0.0125;
-    return d;
 }
 
 // Rates and their derivatives together: the derivatives of alpha_m and alpha_n reuse the
