@@ -74,6 +74,7 @@ def lib():
         L.orc_set_state.argtypes = [vp, vp, vp, vp, vp, vp]
         L.orc_record_delivered.argtypes = [vp, i32]
         L.orc_set_explicit.argtypes = [vp, i32]
+        L.orc_set_exact_events.argtypes = [vp, i32]
         L.orc_num_delivered.restype = i64
         L.orc_num_delivered.argtypes = [vp]
         L.orc_get_delivered.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -163,9 +164,10 @@ class OracleSim:
     """FP64 CPU simulation of a Model; mirrors the library's create/enqueue/advance/read cycle."""
 
     def __init__(self, model, dt: float, epoch_steps: int, nthreads: int = 0, record_delivered=False,
-                 explicit=False):
+                 explicit=False, exact_events=False):
         """explicit=False: fully implicit voltage step (membrane conductance on the diagonal);
-        explicit=True: the printed linear system with the membrane current at V(t)."""
+        explicit=True: the printed linear system with the membrane current at V(t).
+        exact_events=True: steps are cut at the times of the events inside them."""
         self.model = model
         self.dt = float(dt)
         self.epoch_steps = int(epoch_steps)
@@ -175,6 +177,8 @@ class OracleSim:
             lib().orc_record_delivered(self.h, 1)
         if explicit:
             lib().orc_set_explicit(self.h, 1)
+        if exact_events:
+            lib().orc_set_exact_events(self.h, 1)
         self._probe_buf = None
 
     def __del__(self):
@@ -260,10 +264,11 @@ class OracleSim:
         return dict(syn=syn, t=t, w=w, step=step, src=src, idx=idx)
 
 
-def simulate(model, spec, nthreads: int = 0, probes=None, record_delivered=False, n_steps=None, explicit=False):
+def simulate(model, spec, nthreads: int = 0, probes=None, record_delivered=False, n_steps=None, explicit=False,
+             exact_events=False):
     """Run a whole SimSpec (or its first n_steps); returns (sim, probe trace or None)."""
     steps = spec.n_steps if n_steps is None else int(n_steps)
-    sim = OracleSim(model, spec.dt, spec.epoch_steps or 400, nthreads, record_delivered, explicit)
+    sim = OracleSim(model, spec.dt, spec.epoch_steps or 400, nthreads, record_delivered, explicit, exact_events)
     sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
     trace = sim.set_probes(probes, steps) if probes is not None else None
     sim.run_steps(steps)

@@ -37,6 +37,11 @@
  * Readings where the paper is silent: events at t_e are applied at the start of step
  * ceil(t_e/dt); the spike time is the linear interpolation of the upward crossing inside the
  * step; t_k = k*dt is formed as a product, never accumulated.
+ * Exact event times (optional): as Sec. "Model" describes, the time step is shortened so that
+ * every synapse update falls at the start of an integration step: a step whose interval holds
+ * events at t_e > t_k is cut at each distinct t_e, each piece is an integration step of its own
+ * length (implicit voltage step, gate and synapse updates, clamp sampled at its start, threshold
+ * crossing interpolated inside it), and the events at t_e are applied between the pieces.
  *
  * Units: mV, ms, um, nF, uS, nA (nF/ms = uS, uS*mV = nA).
  */
@@ -188,6 +193,7 @@ typedef struct {
     orc_model m;
     double dt;
     int explicit_current;    /* 1: membrane current at V(t) on the right-hand side */
+    int exact_events;        /* 1: steps are cut at event times (events in step floor(t_e/dt)) */
     int64_t epoch_steps;
     int nthreads;
     int64_t k;               /* steps taken */
@@ -284,7 +290,15 @@ static void queue_sort(orc_queue* q) {
     if (q->n - q->head > 1) qsort(q->ev + q->head, (size_t)(q->n - q->head), sizeof(orc_event), cmp_event);
 }
 
-static int64_t event_step(double t, double dt) { return (int64_t)ceil(t / dt); }
+/* Step of an event: fixed-step rule, applied at the start of step ceil(t/dt); exact rule,
+ * the step j with j*dt <= t < (j+1)*dt on the grid of products k*dt that the steps use. */
+static int64_t event_step(const orc_sim* s, double t) {
+    if (!s->exact_events) return (int64_t)ceil(t / s->dt);
+    int64_t j = (int64_t)floor(t / s->dt);
+    while ((double)(j + 1) * s->dt <= t) ++j;
+    while ((double)j * s->dt > t) --j;
+    return j;
+}
 
 orc_sim* orc_create(const orc_model* m, double dt, int64_t epoch_steps, int nthreads) {
     orc_sim* s = (orc_sim*)xcalloc(1, sizeof(orc_sim));
@@ -368,13 +382,14 @@ void orc_destroy(orc_sim* s) {
 
 void orc_record_delivered(orc_sim* s, int on) { s->record_delivered = on; }
 void orc_set_explicit(orc_sim* s, int on) { s->explicit_current = on; }
+void orc_set_exact_events(orc_sim* s, int on) { s->exact_events = on; }
 
 /* External events: applied at the start of step ceil(t/dt). Returns -1 if one lies in the past. */
 int orc_enqueue(orc_sim* s, int64_t n, const int64_t* syn, const double* t, const double* w) {
     for (int64_t i = 0; i < n; ++i) {
         orc_event e;
         e.t = t[i]; e.w = w[i]; e.syn = syn[i]; e.src = -1; e.idx = s->n_ext++;
-        e.step = event_step(t[i], s->dt);
+        e.step = event_step(s, t[i]);
         if (e.step < s->k || syn[i] < 0 || syn[i] >= s->m.n_syn) return -1;
         queue_push(&s->q[s->syn_cell[syn[i]]], &e);
     }
@@ -395,19 +410,14 @@ void orc_set_probes(orc_sim* s, int64_t n, const int64_t* cv, double* trace, int
     s->probe_max = max_steps;
 }
 
-/* One step t_k -> t_{k+1} of one cell, in the order of the operator splitting. */
-static void step_cell(orc_sim* s, int32_t c, int64_t k, double* I, double* d, double* a, double* b, double* Vn) {
-    const orc_model* m = &s->m;
-    const double dt = s->dt;
-    const int64_t off = m->cv_offset[c], n = m->cv_offset[c + 1] - off;
-    const double t = (double)k * dt;
-    double* V = s->V + off;
-    const int32_t* par = m->parent + off;
-
-    /* 1. events due at this step change the synapse state */
+/* Delivers the queued events of cell c that are due: those of earlier steps (late: an error),
+ * and those of step k at times up to t_upto (all of step k with the fixed-step rule). */
+static void deliver(orc_sim* s, int32_t c, int64_t k, double t_upto) {
     orc_queue* q = &s->q[c];
-    while (q->head < q->n && q->ev[q->head].step <= k) {
-        orc_event* e = &q->ev[q->head++];
+    while (q->head < q->n) {
+        orc_event* e = &q->ev[q->head];
+        if (e->step > k || (e->step == k && s->exact_events && e->t > t_upto)) break;
+        q->head++;
         if (e->step < k) s->error = 1;          /* late event: cannot happen by construction */
         s->syn_g[e->syn] += e->w;
         if (s->record_delivered) {
@@ -418,7 +428,17 @@ static void step_cell(orc_sim* s, int32_t c, int64_t k, double* I, double* d, do
             s->cell_deliv[c][s->cell_ndeliv[c]++] = *e;
         }
     }
+}
 
+/* One integration step of cell c from t0 over h (h = dt, or the piece of a step between event
+ * times), in the order of the operator splitting. */
+static void substep(orc_sim* s, int32_t c, double t0, double h, double* I, double* d, double* a, double* b, double* Vn) {
+    const orc_model* m = &s->m;
+    const int64_t off = m->cv_offset[c], n = m->cv_offset[c + 1] - off;
+    const double t = t0;
+    const double dt = h;
+    double* V = s->V + off;
+    const int32_t* par = m->parent + off;
     /* 2. membrane terms with the states at t_k: conductance g_i (uS) and g_i*E (nA) per CV for
      *    the implicit step, or the outward current I_i (nA) at V(t_k) for the explicit one;
      *    injected current Iinj (nA, depolarising) active at t_k */
@@ -517,8 +537,38 @@ static void step_cell(orc_sim* s, int32_t c, int64_t k, double* I, double* d, do
         s->syn_g[y] *= exp(-dt / m->syn_tau[y]);
     }
 
+}
+
+/* One step t_k -> t_{k+1} of one cell. With exact event times the step is cut at the times of
+ * the events that fall inside it (Sec. "Model": the time step is shortened so that every
+ * synapse update happens at the start of an integration step); otherwise events are applied at
+ * the start of step ceil(t_e/dt). */
+static void step_cell(orc_sim* s, int32_t c, int64_t k, double* I, double* d, double* a, double* b, double* Vn) {
+    const orc_model* m = &s->m;
+    const int64_t off = m->cv_offset[c];
+    const double t = (double)k * s->dt;
+    deliver(s, c, k, t);
+    if (!s->exact_events) {
+        substep(s, c, t, s->dt, I, d, a, b, Vn);
+    } else {
+        const double t_end = (double)(k + 1) * s->dt;
+        orc_queue* q = &s->q[c];
+        double cur = t;
+        for (;;) {
+            double next = t_end;
+            if (q->head < q->n && q->ev[q->head].step == k && q->ev[q->head].t < t_end) next = q->ev[q->head].t;
+            /* an uncut step is a step of dt (not t_end - t_k, which differs in the last bit) */
+            const double h = (cur == t && next >= t_end) ? s->dt : next - cur;
+            substep(s, c, cur, h, I, d, a, b, Vn);
+            if (next >= t_end) break;
+            deliver(s, c, k, next);
+            cur = next;
+        }
+    }
+
     /* probes record V(t_{k+1}) */
     if (s->n_probe > 0 && k >= s->probe_k0 && k - s->probe_k0 < s->probe_max) {
+        const double* V = s->V + off;
         double* row = s->probe_trace + (k - s->probe_k0) * s->n_probe;
         for (int64_t j = s->probe_ptr[c]; j < s->probe_ptr[c + 1]; ++j) {
             int64_t p = s->probe_list[j];
@@ -580,7 +630,7 @@ int orc_run(orc_sim* s, int64_t n_steps) {
                 e.syn = m->conn_dst_syn[ci];
                 e.src = src;
                 e.idx = ci;
-                e.step = event_step(e.t, s->dt);
+                e.step = event_step(s, e.t);
                 if (e.step < k1) e.step = k1;    /* never before the next epoch */
                 queue_push(&s->q[s->syn_cell[e.syn]], &e);
             }

@@ -327,6 +327,65 @@ def test_p7_single_synapse_event_recurrence(oracle_lib, explicit):
     assert abs(tr[s - 1, 0] + 65.0) < 1e-9 and tr[s, 0] - tr[s - 1, 0] > 1e-3
 
 
+def test_p7_exact_event_times_cut_the_step(oracle_lib):
+    # exact event times (the step is shortened at the event, Sec. "Model"): inside step
+    # floor(te/dt) the cell takes an implicit step to te, the synapse jumps, then the rest
+    m = _single_cv(g_pas=1e-4, e_pas=-65.0, n_syn=1)
+    area = 2 * math.pi * 5.0 * 20.0
+    C = 1.0 * area * 1e-5
+    G = 1e-4 * area * 1e-2
+    dt, w, tau = 0.025, 0.004, 2.0
+    te = [1.2345, 1.2405, 3.0]          # two events inside one step, one on a step boundary
+    sim = oracle_lib.OracleSim(m, dt, 40, exact_events=True)
+    sim.enqueue([0, 0, 0], te, [w, w, w])
+    tr = sim.set_probes([0], 400)
+    sim.run_steps(400)
+
+    def step(V, g, h):
+        V = (C / h * V + G * -65.0 + g * 0.0) / (C / h + G + g)
+        return V, g * math.exp(-h / tau)
+
+    V, g = -65.0, 0.0
+    ref = []
+    for k in range(400):
+        t0, t1 = k * dt, (k + 1) * dt
+        cur = t0
+        for e in te:                       # events at the start of the step
+            if e == t0:
+                g += w
+        for e in sorted(x for x in te if t0 < x < t1):
+            V, g = step(V, g, e - cur)
+            g += w
+            cur = e
+        V, g = step(V, g, t1 - cur)
+        ref.append(V)
+    ref = np.array(ref)
+    assert np.max(np.abs(tr[:, 0] - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # the first event already moves V inside its own step (with the fixed-step rule it would
+    # not before the next step)
+    s = math.floor(te[0] / dt)
+    assert abs(tr[s - 1, 0] + 65.0) < 1e-9 and tr[s, 0] - tr[s - 1, 0] > 1e-4
+
+
+def test_exact_and_fixed_rules_agree_on_step_boundaries(oracle_lib):
+    # events exactly on step boundaries: cutting at event times changes nothing
+    m = small_tree_model(3, n_cells=6, n_branches=5, cv_range=(1, 8), n_syn=3)
+    rng = np.random.default_rng(2)
+    k = rng.integers(1, 600, 200)
+    t = k * 0.025
+    keep = (t / 0.025) == k          # boundary times whose quotient is exact: both rules give step k
+    t, n = t[keep][:40], min(40, int(keep.sum()))
+    syn = rng.integers(0, m.n_syn, n)
+    w = np.full(n, 0.02)
+    outs = []
+    for exact in (False, True):
+        sim = oracle_lib.OracleSim(m, 0.025, 40, exact_events=exact)
+        sim.enqueue(syn, t, w)
+        sim.run_steps(800)
+        outs.append(sim.voltage())
+    assert np.array_equal(outs[0], outs[1])
+
+
 # ---------------------------------------------------------------- P8: spike interpolation
 def test_p8_threshold_crossing_time_on_linear_ramp(oracle_lib):
     m = _single_cv(g_pas=0.0)
