@@ -328,6 +328,8 @@ def main():
     ap.add_argument("--scheme", default="implicit", choices=["implicit", "explicit"])
     ap.add_argument("--checkpoint-every", type=int, default=500, help="adjoint workload: steps between checkpoints")
     ap.add_argument("--no-autotune", action="store_true", help="small-batch workloads: keep the static packing")
+    ap.add_argument("--exact-events", action="store_true",
+                    help="cut steps at event times (one cell per lane) instead of applying events at step starts")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -359,6 +361,9 @@ def main():
     import paper_1901_07454_b300 as arb
 
     sim_kw = dict(SIM_KW.get(args.workload, {}))
+    if args.exact_events:
+        sim_kw["exact_events"] = True
+        args.no_autotune = True
     tuned = None
     if args.cells_per_pack == 0 and args.workload != "batched" and not args.no_autotune:
         # small batches: time candidate packings on the GPU first (not part of the timed run)
@@ -420,8 +425,9 @@ def main():
     streamed = info["cells_per_pack"] == 32
     kname = "arb_stream_kernel" if streamed else "arb_epoch_kernel"
     cv_steps_launch = model.n_cv * E
-    fp64_per = STREAM_FP64_PER_CV_STEP.get(args.workload) if (streamed and precision == "fp64") else None
-    dram_per = STREAM_DRAM_BYTES_PER_CV_STEP.get(args.workload) if (streamed and precision == "fp64") else None
+    counted = streamed and precision == "fp64" and not args.exact_events   # the kernel the ncu counts are of
+    fp64_per = STREAM_FP64_PER_CV_STEP.get(args.workload) if counted else None
+    dram_per = STREAM_DRAM_BYTES_PER_CV_STEP.get(args.workload) if counted else None
     hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
            "algorithmic_bytes_per_cv_step": bpc,
            "traffic": dram_per * cv_steps_launch if dram_per else None}
@@ -444,7 +450,7 @@ def main():
         t0 = time.perf_counter()
         sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
                               cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
-                              **SIM_KW.get(args.workload, {}))
+                              **sim_kw)
         h2d = model_bytes(model)
         kk = 0
         ev_per_epoch = 0
@@ -483,7 +489,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f64 solve / f32 mechanisms", "data": "synthetic",
-            "scheme": args.scheme,
+            "scheme": args.scheme, "event_timing": "exact" if args.exact_events else "step start",
             "config": {"workload": workload_name, "cells": model.n_cells, "cvs": model.n_cv, "epoch_steps": E,
                        "dt_ms": spec.dt, "step": "one epoch (%d time steps) of all cells incl. spike exchange" % E,
                        "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],

@@ -54,6 +54,9 @@ enum { ARB_FP64 = 0, ARB_MIXED = 1 };
  *   dt * g / c > 2 in a compartment, which happens in small cells under synaptic bursts. */
 enum { ARB_IMPLICIT = 0, ARB_EXPLICIT = 1 };
 
+/* When events take effect (arb_params.event_timing). */
+enum { ARB_EVENTS_STEP_START = 0, ARB_EVENTS_EXACT = 1 };
+
 /* Run settings. Fill with arb_default_params, then override. */
 typedef struct {
     double dt;                   /* time step, ms (> 0) */
@@ -73,7 +76,12 @@ typedef struct {
                                     rounding); arb_get_state then reports each group's g on its
                                     lowest-index synapse and 0 on the others, arb_set_state sums a
                                     group's g. 0 (default): one state per synapse. */
-    int32_t reserved;            /* must be 0 */
+    int32_t event_timing;        /* ARB_EVENTS_STEP_START (default): an event at t is applied at
+                                    the start of step ceil(t/dt). ARB_EVENTS_EXACT: as in Sec.
+                                    "Model", a step is cut at the times of the events inside it
+                                    (each cell its own), every piece an implicit step of its own
+                                    length; needs ARB_IMPLICIT and ARB_FP64 and runs one cell per
+                                    lane (cells_per_pack 0 or 32, split_cvs 0 or -1). */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libarb_b300.so")
 ARB_OK, ARB_E_ARG, ARB_E_CUDA, ARB_E_OVERFLOW, ARB_E_NONFINITE, ARB_E_STATE, ARB_E_NOMEM = 0, -1, -2, -3, -4, -5, -6
 ARB_FP64, ARB_MIXED = 0, 1
 ARB_IMPLICIT, ARB_EXPLICIT = 0, 1
+ARB_EVENTS_STEP_START, ARB_EVENTS_EXACT = 0, 1
 STATUS_NAMES = {0: "ARB_OK", -1: "ARB_E_ARG", -2: "ARB_E_CUDA", -3: "ARB_E_OVERFLOW", -4: "ARB_E_NONFINITE",
                 -5: "ARB_E_STATE", -6: "ARB_E_NOMEM"}
 
@@ -28,7 +29,7 @@ class arb_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("epoch_steps", C.c_int32), ("precision", C.c_int32),
                 ("cells_per_pack", C.c_int32), ("smem_budget", C.c_int32),
                 ("scheme", C.c_int32), ("split_cvs", C.c_int32),
-                ("coalesce_synapses", C.c_int32), ("reserved", C.c_int32),
+                ("coalesce_synapses", C.c_int32), ("event_timing", C.c_int32),
                 ("event_capacity", C.c_int64), ("ext_event_capacity", C.c_int64),
                 ("spike_capacity", C.c_int64), ("bucket_capacity", C.c_int64), ("stream", C.c_void_p)]
 

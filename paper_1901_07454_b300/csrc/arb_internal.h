@@ -1,5 +1,6 @@
 // Internal types shared by the host runtime (arb_runtime.cu) and the kernels (arb_kernels.cu).
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace arbk {
@@ -173,6 +174,11 @@ struct DevModel {
     Ctl* ctl;
     double dt;
     double threshold;
+    int32_t exact;            // 1: steps are cut at event times (one cell per lane, own mechanisms)
+    int32_t pad_exact;
+    const double* syn_ntau;   // per synapse row entry: -1/tau (exact event times)
+    const int32_t* slot_lo;   // exact event times: per lane (owner), its range of compact slots
+    const int32_t* slot_hi;
 };
 
 // Arguments of the event-delivery kernels.
@@ -194,10 +200,14 @@ struct EvArgs {
     int64_t bucket_cap;
     int32_t n_owner;
     int32_t epoch_steps;
+    int32_t time_major;       // 1: order within a step by time first (exact event times)
+    int32_t pad_tm;
 };
 
 // Arguments of the spike-exchange kernel.
 struct SpkArgs {
+    int32_t exact;            // 1: an event belongs to the step j with j*dt <= t < (j+1)*dt
+    int32_t pad_exact;
     Ctl* ctl;
     const int32_t* spk_gid;
     const double* spk_t;
@@ -211,6 +221,17 @@ struct SpkArgs {
     int64_t pool_cap;
     double dt;
 };
+
+// Step of an event at time t (ms). Fixed-step rule: the event is applied at the start of step
+// ceil(t/dt). Exact event times: the step j with j*dt <= t < (j+1)*dt, on the grid of the
+// products k*dt that the step times are formed from.
+__host__ __device__ inline int64_t event_step(double t, double dt, bool exact) {
+    if (!exact) return (int64_t)ceil(t / dt);
+    int64_t j = (int64_t)floor(t / dt);
+    while ((double)(j + 1) * dt <= t) ++j;
+    while ((double)j * dt > t) --j;
+    return j;
+}
 
 // Discrete adjoint (model order: CVs of a cell contiguous, parent index below the child's).
 // Per-step state: V [n_cv] and the gates Y [3][n_hh] (m, h, n of HH instance j).

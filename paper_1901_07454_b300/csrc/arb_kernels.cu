@@ -11,6 +11,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "arb_hh.cuh"
 #include "arb_internal.h"
@@ -837,6 +838,238 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
     __syncwarp();
 }
 
+// ------------------------------------------------------------------------------------------
+// Streamed packs with exact event times (Sec. "Model": the time step is shortened so that every
+// synapse update falls at the start of an integration step). One cell per lane, and each lane's
+// synapses, HH instances and clamps on that lane, so that every lane cuts its own steps: a step
+// of the lane's cell is a sequence of pieces [cur, next], next being the next event time inside
+// the step or the step's end, each piece an implicit step of its own length h (c/h on the
+// diagonal, gates and synapses advanced over h, clamps sampled at cur). Lanes with fewer pieces
+// keep their state while the others go on. Events are listed per lane by (step, time, row).
+
+__device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack, int64_t k0, int nsteps, int lane) {
+    const PackDesc pk = d.packs[p];
+    const int J = pk.nrow;
+    double* Vg = d.V + (size_t)pk.row0 * kWarp;
+    double* Bs = d.Sg + pk.sg_off;
+    double* Rs = d.Rg + pk.sg_off;
+    double* Gm = d.Gm + pk.c_off;
+    double* Em = d.Em + pk.c_off;
+    double* gS = d.syn_g + (size_t)pk.syn_row0 * kWarp;
+    double* mS = d.hh_m + (size_t)pk.hh_row0 * kWarp;
+    double* hS = d.hh_h + (size_t)pk.hh_row0 * kWarp;
+    double* nS = d.hh_n + (size_t)pk.hh_row0 * kWarp;
+    const size_t e0 = (size_t)pk.row0 * kWarp + lane;
+    const double* __restrict__ ca = d.ca + e0;
+    const double* __restrict__ cb = d.cb + e0;
+    const double* __restrict__ ck = d.ck + e0;
+    const double* __restrict__ ce = d.ce + e0;
+    const int32_t* __restrict__ fl = d.pslot + e0;
+    const int32_t* __restrict__ cm_ = d.vmap + e0;
+    double2* stk = stack;
+    const int owner = p * kWarp + lane;
+    int ev_i = d.ev_off[owner];
+    const int ev_end = d.ev_off[owner + 1];
+    const int s_lo = d.slot_lo[owner], s_hi = d.slot_hi[owner];
+    const double dt = d.dt;
+    int32_t late = 0;
+    bool bad = false;
+
+    // the lane's events of step `step` up to time t_max are added to the rows they target; the
+    // constant parts of the lane's mechanism slots are restored and the terms of the next piece
+    // summed when `terms`; gates and synapses advance over h when `update`
+    auto mech = [&](double h, int step, double t_max, bool update, bool terms) {
+        if (terms)
+            for (int c = s_lo; c < s_hi; ++c) {
+                Gm[c] = __ldg(d.cE + pk.c_off + c);
+                Em[c] = __ldg(d.cB + pk.c_off + c);
+            }
+        while (step >= 0 && ev_i < ev_end && d.ev[ev_i].step_rel < step) { ++ev_i; late = 1; }
+        for (int js = 0; js < pk.nsyn_row; ++js) {
+            const size_t q = (size_t)(pk.syn_row0 + js) * kWarp + lane;
+            const int sl = __ldg(d.syn_slot + q);
+            if (sl < 0) continue;
+            double g = gS[js * kWarp + lane];
+            if (update) g *= (h == dt) ? __ldg(d.syn_decay + q) : exp_t(h * __ldg(d.syn_ntau + q));
+            while (step >= 0 && ev_i < ev_end) {
+                const EvRec r = d.ev[ev_i];
+                if (r.step_rel != step || r.t > t_max || r.js != js) break;
+                g += r.w;
+                ++ev_i;
+            }
+            gS[js * kWarp + lane] = g;
+            if (terms) {
+                const int c = __ldg(d.syn_vs + q);
+                Gm[c] += g;
+                Em[c] = fma(g, __ldg(d.syn_e + q), Em[c]);
+            }
+        }
+        for (int jh = 0; jh < pk.nhh_row; ++jh) {
+            const size_t q = (size_t)(pk.hh_row0 + jh) * kWarp + lane;
+            const int sl = __ldg(d.hh_slot + q);
+            if (sl < 0) continue;
+            const int idx = jh * kWarp + lane;
+            double m = mS[idx], hh = hS[idx], n = nS[idx];
+            if (update) {
+                const Rates r = hh_rates(Vg[sl]);
+                m = gate(m, r.am, r.bm, h);
+                hh = gate(hh, r.ah, r.bh, h);
+                n = gate(n, r.an, r.bn, h);
+                mS[idx] = m;
+                hS[idx] = hh;
+                nS[idx] = n;
+            }
+            if (terms) {
+                const int c = __ldg(d.hh_vs + q);
+                const double n2 = n * n;
+                const double gna = __ldg(d.hh_gna + q) * (m * m * m * hh);
+                const double gk = __ldg(d.hh_gk + q) * (n2 * n2);
+                Gm[c] += gna + gk;
+                Em[c] += gna * kENa + gk * kEK;
+            }
+        }
+    };
+
+    mech(dt, 0, (double)k0 * dt, false, true);   // terms of the first piece; events at its start
+
+    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const double thr = d.threshold;
+    const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
+    const bool probing = pk.npr > 0 && probe_max > 0;
+
+    for (int s = 0; s < nsteps; ++s) {
+        const int64_t k = k0 + s;
+        const double t0 = (double)k * dt, t1 = (double)(k + 1) * dt;
+        const bool last = (s + 1) == nsteps;
+        double cur = t0;
+        bool done = false;
+        for (;;) {
+            const bool act = !done;
+            if (!__any_sync(0xffffffffu, act)) break;
+            double next = t1;
+            if (act && ev_i < ev_end) {
+                const EvRec r = d.ev[ev_i];
+                if (r.step_rel == s && r.t < t1) next = r.t;
+            }
+            // an uncut step is a step of dt (t1 - t0 can differ from dt in the last bit)
+            const double h = (cur == t0 && next >= t1) ? dt : next - cur;
+            const double scale = act ? dt / h : 1.0;         // c/h = (c/dt) * scale
+            if (act)
+                for (int js = 0; js < pk.nst_row; ++js) {
+                    const size_t q = (size_t)(pk.st_row0 + js) * kWarp + lane;
+                    const int c = __ldg(d.st_slot + q);
+                    if (c >= 0 && __ldg(d.st_on + q) <= cur && cur < __ldg(d.st_off + q)) Em[c] += __ldg(d.st_amp + q);
+                }
+            const double v0 = (act && det >= 0) ? Vg[det] : 0.0;
+            // forward elimination, leaves to root
+            {
+                int sp = 0;
+                double yprev = 0.0, kprev = 0.0, eprev = 0.0;
+                for (int j = 0; j < J; ++j) {
+                    const size_t o = (size_t)j * kWarp;
+                    const int c = __ldg(cm_ + o);
+                    const int f = __ldg(fl + o);
+                    const double K = __ldg(ck + o);
+                    double A = __ldg(ca + o);
+                    double E = c >= 0 ? Gm[c] : __ldg(ce + o);
+                    const double B = c >= 0 ? Em[c] : __ldg(cb + o);
+                    if (scale != 1.0) {
+                        E = fma(A, scale - 1.0, E);
+                        A *= scale;
+                    }
+                    const double V = Vg[j * kWarp + lane];
+                    double dd = fma(-kprev, eprev, E);
+                    double bb = fma(kprev, yprev, fma(A, V, B));
+                    for (int qq = f & kFlagPopMask; qq > 0; --qq) {
+                        const double2 c2 = stk[(--sp) * kWarp + lane];
+                        dd -= c2.x;
+                        bb += c2.y;
+                    }
+                    const double r = rcp_nr(dd);
+                    const double uu = r * bb;
+                    const double ee = K * r;
+                    if (act) {
+                        Bs[j * kWarp + lane] = uu;
+                        Rs[j * kWarp + lane] = ee;
+                    }
+                    const bool remote = (f & kFlagRemote) != 0;
+                    if (remote && !(f & kFlagRoot)) stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                    kprev = remote ? 0.0 : K;
+                    eprev = ee;
+                    yprev = uu;
+                }
+            }
+            // back substitution, root to leaves
+            {
+                int sp = 0;
+                double vnext = 0.0;
+                for (int j = J - 1; j >= 0; --j) {
+                    const int f = __ldg(fl + (size_t)j * kWarp);
+                    const double U = Bs[j * kWarp + lane], X = Rs[j * kWarp + lane];
+                    double vp;
+                    if (f & kFlagRoot) vp = 0.0;
+                    else if (f & kFlagRemote) vp = stk[(--sp) * kWarp + lane].x;
+                    else vp = vnext;
+                    const double v = fma(X, vp, U);
+                    for (int qq = f & kFlagPopMask; qq > 0; --qq) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                    if (act) {
+                        Vg[j * kWarp + lane] = v;
+                        if (last) bad |= !isfinite(v);
+                    }
+                    vnext = v;
+                }
+            }
+            // state over h; events at `next` (inside the step) or at the next step's start; terms
+            if (act) {
+                const bool end = next >= t1;
+                if (!end) mech(h, s, next, true, true);
+                else mech(h, last ? -1 : s + 1, t1, true, !last);
+            }
+            bool spk = false;
+            double ts = 0.0;
+            if (act && det >= 0) {
+                const double v1 = Vg[det];
+                if (v0 < thr && v1 >= thr) {
+                    spk = true;
+                    ts = __dadd_rn(cur, __dmul_rn(h, __ddiv_rn(__dsub_rn(thr, v0), __dsub_rn(v1, v0))));
+                }
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, spk);
+            if (ball) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd((unsigned long long*)&d.ctl->n_spikes, (unsigned long long)__popc(ball));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (spk) {
+                    const int64_t pos = (int64_t)base + __popc(ball & ((1u << lane) - 1u));
+                    if (pos < d.spike_cap) {
+                        d.spk_gid[pos] = d.det_gid[owner];
+                        d.spk_t[pos] = ts;
+                    } else {
+                        atomicOr(&d.ctl->status, kStSpikeOverflow);
+                    }
+                }
+            }
+            if (act) {
+                cur = next;
+                done = next >= t1;
+            }
+        }
+        __syncwarp();
+        if (probing) {
+            const int64_t prow = k - probe_k0;
+            if (prow >= 0 && prow < probe_max)
+                for (int q = lane; q < pk.npr; q += kWarp)
+                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+        }
+        __syncwarp();
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    const bool any_late = __any_sync(0xffffffffu, late != 0);
+    if (lane == 0 && (any_bad || any_late))
+        atomicOr(&d.ctl->status, (any_bad ? kStNonFinite : 0) | (any_late ? kStLateEvent : 0));
+    __syncwarp();
+}
+
 template <class MT, bool kImp>
 __global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(DevModel<MT> d, int warp_smem_double2) {
     extern __shared__ double2 stk_smem[];
@@ -850,6 +1083,12 @@ __global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(Dev
         if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= d.n_packs) break;
+        if constexpr (std::is_same<MT, double>::value && kImp) {
+            if (d.exact) {
+                run_pack_exact(d, p, stack, k0, nsteps, lane);
+                continue;
+            }
+        }
         if (d.packs[p].round_rows > 0) run_pack_stream<MT, kImp, true>(d, p, stack, k0, nsteps, lane);
         else run_pack_stream<MT, kImp, false>(d, p, stack, k0, nsteps, lane);
     }
@@ -995,8 +1234,9 @@ __global__ void __launch_bounds__(1024) k_ev_scan(EvArgs a) {
     }
 }
 
-__device__ __forceinline__ bool ev_less(const EvRec& x, const EvRec& y) {
+__device__ __forceinline__ bool ev_less(const EvRec& x, const EvRec& y, bool time_major) {
     if (x.step_rel != y.step_rel) return x.step_rel < y.step_rel;
+    if (time_major && x.t != y.t) return x.t < y.t;
     if (x.js != y.js) return x.js < y.js;
     if (x.t != y.t) return x.t < y.t;
     if (x.src != y.src) return x.src < y.src;
@@ -1016,7 +1256,7 @@ __global__ void k_ev_sort(EvArgs a) {
         for (int i = 1; i < n; ++i) {
             const EvRec x = r[i];
             int j = i - 1;
-            while (j >= 0 && ev_less(x, r[j])) { r[j + 1] = r[j]; --j; }
+            while (j >= 0 && ev_less(x, r[j], a.time_major)) { r[j + 1] = r[j]; --j; }
             r[j + 1] = x;
         }
     }
@@ -1050,8 +1290,8 @@ __global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
                     for (;;) {
                         int ch = 2 * i + 1;
                         if (ch >= end) break;
-                        if (ch + 1 < end && ev_less(r[ch], r[ch + 1])) ++ch;
-                        if (!ev_less(x, r[ch])) break;
+                        if (ch + 1 < end && ev_less(r[ch], r[ch + 1], a.time_major)) ++ch;
+                        if (!ev_less(x, r[ch], a.time_major)) break;
                         r[i] = r[ch];
                         i = ch;
                     }
@@ -1100,7 +1340,7 @@ __global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
                 const int x = sidx[i];
                 const EvRec xr = t[x];
                 int j = i - 1;
-                while (j >= b0 && ev_less(xr, t[sidx[j]])) { sidx[j + 1] = sidx[j]; --j; }
+                while (j >= b0 && ev_less(xr, t[sidx[j]], a.time_major)) { sidx[j + 1] = sidx[j]; --j; }
                 sidx[j + 1] = x;
             }
         }
@@ -1139,7 +1379,7 @@ __global__ void k_spike_expand(SpkArgs a) {
             const int64_t q = q0 + k;
             PendEv e;
             e.t = __dadd_rn(ts, a.out_delay[q]);
-            int64_t step = (int64_t)ceil(__ddiv_rn(e.t, a.dt));
+            int64_t step = event_step(e.t, a.dt, a.exact != 0);
             if (step < k1) step = k1;
             e.step = step;
             e.w = a.out_w[q];

@@ -96,7 +96,7 @@ struct Plan {
     // synapses
     int64_t syn_rows = 0;
     std::vector<int32_t> syn_slot, syn_vs;
-    std::vector<double> syn_e, syn_decay, syn_sc;
+    std::vector<double> syn_e, syn_decay, syn_sc, syn_ntau;
     std::vector<int64_t> syn_entry;         // model synapse -> entry
     std::vector<int32_t> syn_owner, syn_js;
     // HH
@@ -118,6 +118,7 @@ struct Plan {
     bool stream = false;                    // packs streamed from global memory (one cell per lane)
     int64_t c_total = 0;                    // streamed packs: compact mechanism slots
     std::vector<double> cE, cB;             // streamed packs: ce, cb of each compact slot
+    std::vector<int32_t> slot_lo, slot_hi;  // exact event times: each lane's range of compact slots
     int32_t stack_depth = 1;                // streamed packs: deepest hand-over stack
     int64_t warp_smem = 32;                 // streamed packs: shared memory per warp (double2)
     int64_t split_cvs = -1;                 // streamed packs: cells above this size are spread
@@ -141,6 +142,7 @@ struct arb_sim {
     std::vector<double> gnabar, gkbar, gl, g_pas, e_pas, syn_tau, syn_e, st_on, st_dur, st_amp;
     // synapse state units: one per synapse, or per (CV, tau, e) group when coalescing
     bool coalesce = false;
+    bool exact = false;                     // steps cut at event times
     std::vector<int32_t> syn_unit;          // model synapse -> unit
     std::vector<int64_t> u_cv;
     std::vector<double> u_tau, u_e;
@@ -505,6 +507,7 @@ static void layout_regions(arb_sim* sim) {
         {"cE", 8 * std::max<int64_t>(pl.c_total, 1)}, {"cB", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
         {"syn_e", 8 * pl.syn_rows * kWarp}, {"syn_decay", 8 * pl.syn_rows * kWarp}, {"syn_sc", 8 * pl.syn_rows * kWarp},
+        {"syn_ntau", 8 * pl.syn_rows * kWarp}, {"slot_lo", 4 * std::max<int64_t>(nowner, 1)}, {"slot_hi", 4 * std::max<int64_t>(nowner, 1)},
         {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_vs", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
         {"hh_gk", 8 * pl.hh_rows * kWarp}, {"hh_m", mt * pl.hh_rows * kWarp}, {"hh_h", mt * pl.hh_rows * kWarp},
         {"hh_n", mt * pl.hh_rows * kWarp},
@@ -576,6 +579,10 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.syn_vs = (const int32_t*)region(sim, "syn_vs");
     d.syn_g = (MT*)region(sim, "syn_g");
     d.syn_e = (const double*)region(sim, "syn_e");
+    d.syn_ntau = (const double*)region(sim, "syn_ntau");
+    d.slot_lo = (const int32_t*)region(sim, "slot_lo");
+    d.slot_hi = (const int32_t*)region(sim, "slot_hi");
+    d.exact = sim->exact ? 1 : 0;
     d.syn_decay = (const double*)region(sim, "syn_decay");
     d.syn_sc = (const double*)region(sim, "syn_sc");
     d.hh_slot = (const int32_t*)region(sim, "hh_slot");
@@ -725,7 +732,13 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         return bad(sim->err.empty() ? "bad synapse arrays" : sim->err);
     for (double tau : sim->syn_tau) if (!(tau > 0)) return bad("synapse tau must be > 0");
     if (p.coalesce_synapses != 0 && p.coalesce_synapses != 1) return bad("coalesce_synapses must be 0 or 1");
-    if (p.reserved != 0) return bad("reserved must be 0");
+    if (p.event_timing != ARB_EVENTS_STEP_START && p.event_timing != ARB_EVENTS_EXACT)
+        return bad("event_timing must be ARB_EVENTS_STEP_START or ARB_EVENTS_EXACT");
+    sim->exact = p.event_timing == ARB_EVENTS_EXACT;
+    if (sim->exact && (p.scheme != ARB_IMPLICIT || p.precision != ARB_FP64))
+        return bad("exact event times need the implicit scheme and FP64");
+    if (sim->exact && ((p.cells_per_pack != 0 && p.cells_per_pack != 32) || p.split_cvs > 0))
+        return bad("exact event times run one cell per lane: cells_per_pack must be 0 or 32 and split_cvs 0 or -1");
     sim->coalesce = p.coalesce_synapses == 1;
     {
         const int64_t ns = (int64_t)sim->syn_cv.size();
@@ -1041,7 +1054,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         return std::max(ms, mx);
     };
     std::vector<Group> groups;
-    int kpp = p.cells_per_pack;
+    int kpp = sim->exact ? 32 : p.cells_per_pack;
     if (kpp == 0) {
         if (nc >= 32 * wpc * n_sm) {
             kpp = 32;
@@ -1147,7 +1160,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         };
         std::vector<double> ucost;
         for (int32_t i = 0; i < nc; i += 32) ucost.push_back((double)ncv_of[by_size[i]]);
-        int64_t split = p.split_cvs;
+        int64_t split = sim->exact ? -1 : p.split_cvs;
         if (split == 0) {
             // choose the threshold with the smallest estimated makespan over the warp slots
             double sumJ = 0;
@@ -1226,8 +1239,19 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
                 hh_l[pi].insert(hh_l[pi].end(), cell_hh[c].begin(), cell_hh[c].end());
             }
-            assign_grouped(sy, sim->u_cv, syn_l[pi]);
-            assign_grouped(st, sim->st_cv, st_l[pi]);
+            if (!sim->exact) {
+                assign_grouped(sy, sim->u_cv, syn_l[pi]);
+                assign_grouped(st, sim->st_cv, st_l[pi]);
+            } else {
+                // every lane holds its own cell's synapses (by CV) and clamps
+                for (size_t l = 0; l < G.cells.size(); ++l) {
+                    const int32_t c = G.cells[l];
+                    syn_l[pi][l] = cell_syn[c];
+                    std::stable_sort(syn_l[pi][l].begin(), syn_l[pi][l].end(),
+                                     [&](int32_t x, int32_t y) { return sim->u_cv[x] < sim->u_cv[y]; });
+                    st_l[pi][l] = cell_st[c];
+                }
+            }
             row0 += J;
         }
         pl.total_rows = row0;
@@ -1310,6 +1334,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         for (int64_t cv : sim->st_cv) mech[cv] = 1;
         int64_t c_total = 0;
         int32_t max_depth = 1, max_mb = 0;
+        pl.slot_lo.assign((size_t)npk * kWarp, 0);
+        pl.slot_hi.assign((size_t)npk * kWarp, 0);
         for (int32_t pi = 0; pi < npk; ++pi) {
             PackDesc& pd = pl.packs[pi];
             const int64_t base = (int64_t)pd.row0 * kWarp;
@@ -1317,12 +1343,28 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             for (int32_t c : sg[pi].cells)
                 for (int64_t cv = sim->cv_offset[c]; cv < sim->cv_offset[c + 1]; ++cv)
                     if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = 0;
-            for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
-                if (pl.vmap[t] >= 0) {
-                    pl.vmap[t] = nvc++;
-                    pl.cE.push_back(pl.ce[t]);
-                    pl.cB.push_back(pl.cb[t]);
+            if (!sim->exact) {
+                for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
+                    if (pl.vmap[t] >= 0) {
+                        pl.vmap[t] = nvc++;
+                        pl.cE.push_back(pl.ce[t]);
+                        pl.cB.push_back(pl.cb[t]);
+                    }
+            } else {
+                // lane by lane, so that each lane's slots are one range of its own
+                for (int l = 0; l < kWarp; ++l) {
+                    pl.slot_lo[(size_t)pi * kWarp + l] = nvc;
+                    for (int32_t j = 0; j < pd.nrow; ++j) {
+                        const int64_t t = base + (int64_t)j * kWarp + l;
+                        if (pl.vmap[t] >= 0) {
+                            pl.vmap[t] = nvc++;
+                            pl.cE.push_back(pl.ce[t]);
+                            pl.cB.push_back(pl.cb[t]);
+                        }
+                    }
+                    pl.slot_hi[(size_t)pi * kWarp + l] = nvc;
                 }
+            }
             pd.nvc = nvc;
             pd.c_off = c_total;
             c_total += nvc;
@@ -1392,14 +1434,21 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             size_t ms = 0, mt = 0;
             for (int l = 0; l < 32; ++l) { ms = std::max(ms, syn_l[pi][l].size()); mt = std::max(mt, st_l[pi][l].size()); }
             pd.syn_row0 = (int32_t)syn_rows; pd.nsyn_row = (int32_t)ms; syn_rows += (int64_t)ms;
-            pd.hh_row0 = (int32_t)hh_rows; pd.nhh_row = (int32_t)((hh_l[pi].size() + 31) / 32); hh_rows += pd.nhh_row;
+            pd.hh_row0 = (int32_t)hh_rows;
+            if (!sim->exact) {
+                pd.nhh_row = (int32_t)((hh_l[pi].size() + 31) / 32);
+            } else {                    // each lane's own cell's instances, one per row
+                pd.nhh_row = 0;
+                for (int32_t c : sg[pi].cells) pd.nhh_row = std::max<int32_t>(pd.nhh_row, (int32_t)cell_hh[c].size());
+            }
+            hh_rows += pd.nhh_row;
             pd.st_row0 = (int32_t)st_rows; pd.nst_row = (int32_t)mt; st_rows += (int64_t)mt;
         }
         pl.syn_rows = syn_rows; pl.hh_rows = hh_rows; pl.st_rows = st_rows;
         pl.syn_entry.assign(nsyn_all, -1); pl.syn_owner.assign(nsyn_all, 0); pl.syn_js.assign(nsyn_all, 0);
         pl.hh_entry.assign(sim->hh_cv.size(), -1);
         pl.syn_slot.assign(syn_rows * kWarp, -1); pl.syn_vs.assign(syn_rows * kWarp, -1);
-        pl.syn_e.assign(syn_rows * kWarp, 0.0); pl.syn_decay.assign(syn_rows * kWarp, 0.0); pl.syn_sc.assign(syn_rows * kWarp, 0.0);
+        pl.syn_e.assign(syn_rows * kWarp, 0.0); pl.syn_decay.assign(syn_rows * kWarp, 0.0); pl.syn_ntau.assign(syn_rows * kWarp, 0.0); pl.syn_sc.assign(syn_rows * kWarp, 0.0);
         pl.hh_slot.assign(hh_rows * kWarp, -1); pl.hh_vs.assign(hh_rows * kWarp, -1);
         pl.hh_sc.assign(hh_rows * kWarp, 0.0); pl.hh_gna.assign(hh_rows * kWarp, 0.0); pl.hh_gk.assign(hh_rows * kWarp, 0.0);
         pl.st_slot.assign(st_rows * kWarp, -1); pl.st_sc.assign(st_rows * kWarp, 0.0);
@@ -1418,6 +1467,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     pl.syn_vs[q] = pl.vmap[pl.cv_tile[cv]];
                     pl.syn_e[q] = sim->u_e[i];
                     pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
+                    pl.syn_ntau[q] = -1.0 / sim->u_tau[i];
                     pl.syn_sc[q] = invd[cv];
                     pl.syn_entry[i] = q;
                     pl.syn_owner[i] = pi * kWarp + l;
@@ -1435,9 +1485,19 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     pl.st_amp[q] = sim->st_amp[i];
                 }
             }
-            for (size_t rr = 0; rr < hh_l[pi].size(); ++rr) {
-                const int32_t i = hh_l[pi][rr];
-                const int64_t q = ((int64_t)pd.hh_row0 + (int64_t)(rr / 32)) * kWarp + (int64_t)(rr % 32);
+            std::vector<std::pair<int32_t, int64_t>> hh_at;   // (instance, entry)
+            if (!sim->exact) {
+                for (size_t rr = 0; rr < hh_l[pi].size(); ++rr)
+                    hh_at.push_back({hh_l[pi][rr], ((int64_t)pd.hh_row0 + (int64_t)(rr / 32)) * kWarp + (int64_t)(rr % 32)});
+            } else {
+                for (size_t l = 0; l < sg[pi].cells.size(); ++l) {
+                    const auto& v = cell_hh[sg[pi].cells[l]];
+                    for (size_t rr = 0; rr < v.size(); ++rr) hh_at.push_back({v[rr], ((int64_t)pd.hh_row0 + (int64_t)rr) * kWarp + (int64_t)l});
+                }
+            }
+            for (const auto& hq : hh_at) {
+                const int32_t i = hq.first;
+                const int64_t q = hq.second;
                 const int64_t cv = sim->hh_cv[i];
                 pl.hh_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
                 pl.hh_vs[q] = pl.vmap[pl.cv_tile[cv]];
@@ -1604,7 +1664,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     pl.syn_slot.assign(syn_rows * kWarp, -1);
     pl.syn_vs.assign(syn_rows * kWarp, -1);
     pl.syn_e.assign(syn_rows * kWarp, 0.0);
-    pl.syn_decay.assign(syn_rows * kWarp, 0.0);
+    pl.syn_decay.assign(syn_rows * kWarp, 0.0); pl.syn_ntau.assign(syn_rows * kWarp, 0.0);
     pl.syn_sc.assign(syn_rows * kWarp, 0.0);
     pl.hh_slot.assign(hh_rows * kWarp, -1);
     pl.hh_vs.assign(hh_rows * kWarp, -1);
@@ -1633,6 +1693,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 pl.syn_vs[q] = vread(cv);
                 pl.syn_e[q] = sim->u_e[i];
                 pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
+                    pl.syn_ntau[q] = -1.0 / sim->u_tau[i];
                 pl.syn_sc[q] = invd[cv];
                 pl.syn_entry[i] = q;
                 pl.syn_owner[i] = pi * kWarp + l;
@@ -1833,6 +1894,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot); UP("vmap", pl.vmap);
     UP("V", pl.V0);
     UP("cE", pl.cE); UP("cB", pl.cB);
+    UP("syn_ntau", pl.syn_ntau); UP("slot_lo", pl.slot_lo); UP("slot_hi", pl.slot_hi);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     UP("hh_slot", pl.hh_slot); UP("hh_vs", pl.hh_vs); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
     UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
@@ -1876,6 +1938,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     a.bucket_cap = sim->prm.bucket_capacity;
     a.n_owner = (int32_t)(pl.packs.size() * kWarp);
     a.epoch_steps = sim->epoch_steps;
+    a.time_major = sim->exact ? 1 : 0;
     SpkArgs& b = sim->spk_args;
     b.ctl = a.ctl;
     b.spk_gid = (const int32_t*)region(sim, "spk_gid");
@@ -1890,6 +1953,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     b.pool[1] = a.pool[1];
     b.pool_cap = sim->prm.event_capacity;
     b.dt = sim->prm.dt;
+    b.exact = sim->exact ? 1 : 0;
     CU(events_prepare());
     // launch shape of the persistent epoch kernel
     if (pl.stream) {
@@ -1931,7 +1995,7 @@ arb_status arb_enqueue_events(arb_sim* sim, int64_t n, const int64_t* syn, const
     for (int64_t i = 0; i < n; ++i) {
         if (syn[i] < 0 || syn[i] >= nsyn) return fail(sim, ARB_E_ARG, "event synapse index out of range");
         if (!std::isfinite(t[i]) || !std::isfinite(w[i])) return fail(sim, ARB_E_ARG, "event time and weight must be finite");
-        const int64_t step = (int64_t)std::ceil(t[i] / sim->prm.dt);
+        const int64_t step = event_step(t[i], sim->prm.dt, sim->exact);
         if (step < sim->k) return fail(sim, ARB_E_ARG, "event time lies before the current time");
     }
     if (sim->ext_counter + n > INT32_MAX) return fail(sim, ARB_E_OVERFLOW, "too many external events over the run");
@@ -1941,7 +2005,7 @@ arb_status arb_enqueue_events(arb_sim* sim, int64_t n, const int64_t* syn, const
         e.w = w[i];
         e.syn = (int32_t)syn[i];
         e.idx = (int32_t)(sim->ext_counter++);
-        e.step = (int64_t)std::ceil(t[i] / sim->prm.dt);
+        e.step = event_step(t[i], sim->prm.dt, sim->exact);
         sim->ext.push_back(e);
     }
     if (n > 0) sim->ext_dirty = true;

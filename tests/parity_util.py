@@ -30,10 +30,10 @@ def run_gpu(model, spec, n_steps=None, probes=None, advance_every=None, **kw):
     return out
 
 
-def run_oracle(model, spec, n_steps=None, probes=None, nthreads=0, scheme="implicit"):
+def run_oracle(model, spec, n_steps=None, probes=None, nthreads=0, scheme="implicit", exact=False):
     steps = spec.n_steps if n_steps is None else int(n_steps)
     sim, trace = oracle.simulate(model, spec, nthreads=nthreads, probes=probes, n_steps=steps,
-                                 explicit=(scheme == "explicit"))
+                                 explicit=(scheme == "explicit"), exact_events=exact)
     return dict(V=sim.voltage(), spikes=sim.spikes(), trace=trace, sim=sim)
 
 
@@ -116,10 +116,10 @@ def renumbered(model):
     return m, new_of_old
 
 
-def oracle_spread(model, spec, probes, scheme="implicit", n_steps=None):
+def oracle_spread(model, spec, probes, scheme="implicit", n_steps=None, exact=False):
     """Disagreement between two equally valid FP64 oracle runs that round differently at every
     step (original vs renumbered CVs): max over the probe trace of |dV| / max(|V|, 1 mV)."""
-    a = run_oracle(model, spec, n_steps=n_steps, probes=probes, scheme=scheme)
+    a = run_oracle(model, spec, n_steps=n_steps, probes=probes, scheme=scheme, exact=exact)
     m2, new_of_old = renumbered(model)
-    b = run_oracle(m2, spec, n_steps=n_steps, probes=new_of_old[np.asarray(probes)], scheme=scheme)
+    b = run_oracle(m2, spec, n_steps=n_steps, probes=new_of_old[np.asarray(probes)], scheme=scheme, exact=exact)
     return rel_err(b["trace"], a["trace"])

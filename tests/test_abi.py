@@ -129,3 +129,12 @@ def test_adjoint_workspace_query_and_unbound_handle(arb):
     loss = C.c_double()
     rc = lib.arb_adjoint(p.h, 10, 5, 0, None, None, 1.0, None, 0, None, 0, None, C.byref(loss))
     assert rc == -5 and b"bind" in lib.arb_last_error(p.h)
+
+
+def test_exact_event_times_validation_and_plan(arb):
+    m = small_tree_model(1, n_cells=40, n_branches=5, cv_range=(2, 8), n_syn=3)
+    info = arb.Plan(m, exact_events=True).plan_info()
+    assert info["cells_per_pack"] == 32 and info["split_cvs"] == -1
+    _expect_error(arb, m, "exact event times", exact_events=True, scheme="explicit")
+    _expect_error(arb, m, "exact event times", exact_events=True, precision="mixed")
+    _expect_error(arb, m, "one cell per lane", exact_events=True, cells_per_pack=8)
