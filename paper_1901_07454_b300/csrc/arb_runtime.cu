@@ -138,8 +138,8 @@ struct arb_sim {
     std::vector<int64_t> cv_offset;
     hvec<int32_t> parent;
     hvec<double> length, radius, cm, Ra;
-    std::vector<int64_t> hh_cv, pas_cv, syn_cv, st_cv, det_cv;
-    std::vector<double> gnabar, gkbar, gl, g_pas, e_pas, syn_tau, syn_e, st_on, st_dur, st_amp;
+    hvec<int64_t> hh_cv, pas_cv, syn_cv, st_cv, det_cv;
+    hvec<double> gnabar, gkbar, gl, g_pas, e_pas, syn_tau, syn_e, st_on, st_dur, st_amp;
     // synapse state units: one per synapse, or per (CV, tau, e) group when coalescing
     bool coalesce = false;
     bool exact = false;                     // steps cut at event times
@@ -708,18 +708,34 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         if (bad_kind[c] == 2) return bad("cell " + std::to_string(c) + ": parent of local CV " + std::to_string(i) + " must be in [0, i)");
         return bad("CV " + std::to_string(sim->cv_offset[c] + i) + ": length, radius, cm and Ra must be finite and > 0");
     }
-    auto copy_idx = [&](int64_t n, const int64_t* src, std::vector<int64_t>& dst, const char* what) -> bool {
-        if (n < 0 || (n > 0 && !src)) return false;
-        dst.assign(src, src + n);
-        for (int64_t i = 0; i < n; ++i)
-            if (dst[i] < 0 || dst[i] >= ncv) { sim->err = std::string(what) + " CV index out of range"; return false; }
+    // copies in parallel chunks; false when an element fails the check
+    auto par_copy = [&](int64_t n, const auto* src, auto& dst, auto ok) -> bool {
+        dst.resize((size_t)n);
+        constexpr int64_t kChunk = 1 << 16;
+        const int64_t nch = (n + kChunk - 1) / kChunk;
+        std::vector<char> bad_chunk(nch, 0);
+        auto* d = dst.data();
+        parallel_for(nch, [&](int64_t ch) {
+            const int64_t lo = ch * kChunk, hi = std::min<int64_t>(n, lo + kChunk);
+            for (int64_t i = lo; i < hi; ++i) {
+                d[i] = src[i];
+                if (!ok(d[i])) bad_chunk[ch] = 1;
+            }
+        });
+        for (char b : bad_chunk) if (b) return false;
         return true;
     };
-    auto copy_d = [&](int64_t n, const double* src, std::vector<double>& dst) -> bool {
-        if (n > 0 && !src) return false;
-        dst.assign(src, src + n);
-        for (double x : dst) if (!std::isfinite(x)) return false;
+    auto copy_idx = [&](int64_t n, const int64_t* src, hvec<int64_t>& dst, const char* what) -> bool {
+        if (n < 0 || (n > 0 && !src)) return false;
+        if (!par_copy(n, src, dst, [&](int64_t x) { return x >= 0 && x < ncv; })) {
+            sim->err = std::string(what) + " CV index out of range";
+            return false;
+        }
         return true;
+    };
+    auto copy_d = [&](int64_t n, const double* src, hvec<double>& dst) -> bool {
+        if (n < 0 || (n > 0 && !src)) return false;
+        return par_copy(n, src, dst, [](double x) { return std::isfinite(x); });
     };
     if (!copy_idx(m->n_hh, m->hh_cv, sim->hh_cv, "hh") || !copy_d(m->n_hh, m->gnabar, sim->gnabar) ||
         !copy_d(m->n_hh, m->gkbar, sim->gkbar) || !copy_d(m->n_hh, m->gl, sim->gl))
@@ -943,7 +959,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     };
     // lanes of grouped items: items on one CV stay on one lane (no two lanes update one slot in
     // a loop); groups by CV, largest first, onto the least loaded lane
-    auto assign_grouped = [&](const std::vector<int32_t>& items, const std::vector<int64_t>& item_cv,
+    auto assign_grouped = [&](const std::vector<int32_t>& items, const int64_t* item_cv,
                               std::array<std::vector<int32_t>, 32>& lanes) {
         for (auto& v : lanes) v.clear();
         std::vector<int32_t> it = items;
@@ -974,8 +990,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             st.insert(st.end(), cell_st[c].begin(), cell_st[c].end());
             G.hh.insert(G.hh.end(), cell_hh[c].begin(), cell_hh[c].end());
         }
-        assign_grouped(sy, sim->u_cv, G.syn_l);
-        assign_grouped(st, sim->st_cv, G.st_l);
+        assign_grouped(sy, sim->u_cv.data(), G.syn_l);
+        assign_grouped(st, sim->st_cv.data(), G.st_l);
         for (int l = 0; l < 32; ++l) {
             G.nsyn_row = std::max<int64_t>(G.nsyn_row, (int64_t)G.syn_l[l].size());
             G.nst_row = std::max<int64_t>(G.nst_row, (int64_t)G.st_l[l].size());
@@ -1184,6 +1200,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         {
             std::vector<int32_t> big, rest;
             for (int32_t c : by_size) ((split > 0 && ncv_of[c] > split) ? big : rest).push_back(c);
+            std::vector<std::vector<int32_t>> cand;   // greedy groups of large cells
             size_t i = 0;
             while (i < big.size()) {
                 std::vector<int32_t> g;
@@ -1195,8 +1212,13 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     sum += n;
                     ++i;
                 }
-                place_shared(g, split, sg);
+                cand.push_back(std::move(g));
             }
+            // schedule the groups on host threads; the results keep the groups' order
+            std::vector<std::vector<SGroup>> placed(cand.size());
+            parallel_for((int64_t)cand.size(), [&](int64_t k) { place_shared(cand[k], split, placed[k]); });
+            for (auto& v : placed)
+                for (auto& G : v) sg.push_back(std::move(G));
             for (size_t r = 0; r < rest.size(); r += 32) {
                 SGroup G;
                 G.cells.assign(rest.begin() + r, rest.begin() + std::min(rest.size(), r + 32));
@@ -1214,10 +1236,12 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         par_assign(pl.cv_pack, ncv, (int32_t)-1);
         std::vector<std::array<std::vector<int32_t>, 32>> syn_l(npk), st_l(npk);
         std::vector<std::vector<int32_t>> hh_l(npk);
-        int64_t row0 = 0;
-        for (int32_t pi = 0; pi < npk; ++pi) {
+        std::vector<int64_t> prow0(npk + 1, 0);        // first row of each pack
+        for (int32_t pi = 0; pi < npk; ++pi) prow0[pi + 1] = prow0[pi] + (int64_t)sg[pi].rows.rows.size();
+        parallel_for(npk, [&](int64_t pi) {          // packs own their rows, CVs and lists
             const SGroup& G = sg[pi];
             const int32_t J = (int32_t)G.rows.rows.size();
+            const int64_t row0 = prow0[pi];
             PackDesc& pd = pl.packs[pi];
             std::memset(&pd, 0, sizeof(pd));
             pd.row0 = (int32_t)row0;
@@ -1240,8 +1264,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 hh_l[pi].insert(hh_l[pi].end(), cell_hh[c].begin(), cell_hh[c].end());
             }
             if (!sim->exact) {
-                assign_grouped(sy, sim->u_cv, syn_l[pi]);
-                assign_grouped(st, sim->st_cv, st_l[pi]);
+                assign_grouped(sy, sim->u_cv.data(), syn_l[pi]);
+                assign_grouped(st, sim->st_cv.data(), st_l[pi]);
             } else {
                 // every lane holds its own cell's synapses (by CV) and clamps
                 for (size_t l = 0; l < G.cells.size(); ++l) {
@@ -1252,8 +1276,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     st_l[pi][l] = cell_st[c];
                 }
             }
-            row0 += J;
-        }
+        });
+        const int64_t row0 = prow0[npk];
         pl.total_rows = row0;
         const int64_t ne = row0 * kWarp;
         if (ne > INT32_MAX) return bad("model too large for one handle");
@@ -1336,7 +1360,10 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         int32_t max_depth = 1, max_mb = 0;
         pl.slot_lo.assign((size_t)npk * kWarp, 0);
         pl.slot_hi.assign((size_t)npk * kWarp, 0);
-        for (int32_t pi = 0; pi < npk; ++pi) {
+        // per pack, in parallel: pack-relative compact slots, and the checks of its schedule
+        std::vector<int32_t> p_nvc(npk, 0), p_depth(npk, 0);
+        std::vector<char> p_err(npk, 0);
+        parallel_for(npk, [&](int64_t pi) {
             PackDesc& pd = pl.packs[pi];
             const int64_t base = (int64_t)pd.row0 * kWarp;
             int32_t nvc = 0;
@@ -1345,32 +1372,21 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = 0;
             if (!sim->exact) {
                 for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
-                    if (pl.vmap[t] >= 0) {
-                        pl.vmap[t] = nvc++;
-                        pl.cE.push_back(pl.ce[t]);
-                        pl.cB.push_back(pl.cb[t]);
-                    }
+                    if (pl.vmap[t] >= 0) pl.vmap[t] = nvc++;
             } else {
                 // lane by lane, so that each lane's slots are one range of its own
                 for (int l = 0; l < kWarp; ++l) {
                     pl.slot_lo[(size_t)pi * kWarp + l] = nvc;
                     for (int32_t j = 0; j < pd.nrow; ++j) {
                         const int64_t t = base + (int64_t)j * kWarp + l;
-                        if (pl.vmap[t] >= 0) {
-                            pl.vmap[t] = nvc++;
-                            pl.cE.push_back(pl.ce[t]);
-                            pl.cB.push_back(pl.cb[t]);
-                        }
+                        if (pl.vmap[t] >= 0) pl.vmap[t] = nvc++;
                     }
                     pl.slot_hi[(size_t)pi * kWarp + l] = nvc;
                 }
             }
-            pd.nvc = nvc;
-            pd.c_off = c_total;
-            c_total += nvc;
+            p_nvc[pi] = nvc;
             if (sg[pi].shared) {
                 pd.nmb = nmb[pi];
-                max_mb = std::max(max_mb, nmb[pi]);
                 // a hand-over between lanes crosses a round boundary (both sweeps), and within a
                 // round at most one lane adds to a given slot
                 std::vector<int32_t> w_round(pd.nmb, -1), w_lane(pd.nmb, -1);   // last writer of each slot
@@ -1378,12 +1394,14 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     for (int l = 0; l < kWarp; ++l) {
                         const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
                         const int32_t so = (f >> kMbOutShift) & kMbNone, si = (int32_t)((uint32_t)f >> kMbInShift);
-                        if ((so != kMbNone && so >= pd.nmb) || (si != kMbNone && si >= pd.nmb) || (f & kFlagPopMask))
-                            return bad("internal error: mailbox slot out of range");
+                        if ((so != kMbNone && so >= pd.nmb) || (si != kMbNone && si >= pd.nmb) || (f & kFlagPopMask)) {
+                            p_err[pi] = 1;
+                            return;
+                        }
                         if (!(f & kFlagRemote) || (f & kFlagRoot)) continue;
-                        if (so == kMbNone) return bad("internal error: hand-over without a mailbox slot");
+                        if (so == kMbNone) { p_err[pi] = 2; return; }
                         const int32_t rd = j / kStreamRound;
-                        if (w_round[so] == rd && w_lane[so] != l) return bad("internal error: two lanes add to one mailbox slot in a round");
+                        if (w_round[so] == rd && w_lane[so] != l) { p_err[pi] = 3; return; }
                         w_round[so] = rd;
                         w_lane[so] = l;
                     }
@@ -1391,13 +1409,14 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     for (int64_t cv = sim->cv_offset[c] + 1; cv < sim->cv_offset[c + 1]; ++cv) {
                         const int64_t t = pl.cv_tile[cv], tp = pl.cv_tile[sim->cv_offset[c] + sim->parent[cv]];
                         if (t % kWarp == tp % kWarp) {
-                            if (tp <= t) return bad("internal error: parent before child on a lane");
+                            if (tp <= t) { p_err[pi] = 4; return; }
                         } else if ((t / kWarp - pd.row0) / kStreamRound >= (tp / kWarp - pd.row0) / kStreamRound) {
-                            return bad("internal error: cross-lane hand-over inside one round");
+                            p_err[pi] = 5;
+                            return;
                         }
                     }
                 pd.stack = 0;
-                continue;
+                return;
             }
             int32_t depth = 0;
             for (int l = 0; l < kWarp; ++l) {
@@ -1405,7 +1424,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 for (int32_t j = 0; j < pd.nrow; ++j) {                 // forward
                     const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
                     sp -= f & kFlagPopMask;
-                    if (sp < 0) return bad("internal error: hand-over stack underflow");
+                    if (sp < 0) { p_err[pi] = 6; return; }
                     if ((f & kFlagRemote) && !(f & kFlagRoot)) ++sp;
                     depth = std::max(depth, sp);
                 }
@@ -1413,14 +1432,40 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 for (int32_t j = pd.nrow - 1; j >= 0; --j) {            // backward
                     const int32_t f = pl.pslot[base + (int64_t)j * kWarp + l];
                     if ((f & kFlagRemote) && !(f & kFlagRoot)) --sp;
-                    if (sp < 0) return bad("internal error: voltage stack underflow");
+                    if (sp < 0) { p_err[pi] = 7; return; }
                     sp += f & kFlagPopMask;
                     depth = std::max(depth, sp);
                 }
             }
             pd.stack = depth;
-            max_depth = std::max(max_depth, depth);
+            p_depth[pi] = depth;
+        });
+        static const char* const kPlanErr[] = {"", "mailbox slot out of range", "hand-over without a mailbox slot",
+                                               "two lanes add to one mailbox slot in a round", "parent before child on a lane",
+                                               "cross-lane hand-over inside one round", "hand-over stack underflow",
+                                               "voltage stack underflow"};
+        for (int32_t pi = 0; pi < npk; ++pi)
+            if (p_err[pi]) return bad(std::string("internal error: ") + kPlanErr[(int)p_err[pi]]);
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            PackDesc& pd = pl.packs[pi];
+            pd.nvc = p_nvc[pi];
+            pd.c_off = c_total;
+            c_total += p_nvc[pi];
+            max_depth = std::max(max_depth, p_depth[pi]);
+            if (sg[pi].shared) max_mb = std::max(max_mb, nmb[pi]);
         }
+        // constant diagonal and right-hand side of every compact slot
+        pl.cE.assign(c_total, 0.0);
+        pl.cB.assign(c_total, 0.0);
+        parallel_for(npk, [&](int64_t pi) {
+            const PackDesc& pd = pl.packs[pi];
+            const int64_t base = (int64_t)pd.row0 * kWarp;
+            for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
+                if (pl.vmap[t] >= 0) {
+                    pl.cE[pd.c_off + pl.vmap[t]] = pl.ce[t];
+                    pl.cB[pd.c_off + pl.vmap[t]] = pl.cb[t];
+                }
+        });
         pl.c_total = c_total;
         pl.stack_depth = max_depth;
         pl.warp_smem = std::max<int64_t>((int64_t)max_depth * kWarp, ((int64_t)3 * max_mb + 1) / 2);
@@ -1454,7 +1499,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         pl.st_slot.assign(st_rows * kWarp, -1); pl.st_sc.assign(st_rows * kWarp, 0.0);
         pl.st_on.assign(st_rows * kWarp, 0.0); pl.st_off.assign(st_rows * kWarp, 0.0); pl.st_amp.assign(st_rows * kWarp, 0.0);
         pl.det_slot.assign((size_t)npk * kWarp, -1); pl.det_gid.assign((size_t)npk * kWarp, -1);
-        for (int32_t pi = 0; pi < npk; ++pi) {
+        parallel_for(npk, [&](int64_t pi) {          // packs own their rows and instances
             const PackDesc& pd = pl.packs[pi];
             const int64_t base = (int64_t)pd.row0 * kWarp;
             for (int l = 0; l < 32; ++l) {
@@ -1470,7 +1515,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     pl.syn_ntau[q] = -1.0 / sim->u_tau[i];
                     pl.syn_sc[q] = invd[cv];
                     pl.syn_entry[i] = q;
-                    pl.syn_owner[i] = pi * kWarp + l;
+                    pl.syn_owner[i] = (int32_t)(pi * kWarp + l);
                     pl.syn_js[i] = (int32_t)rr;
                 }
                 const auto& w = st_l[pi][l];
@@ -1510,7 +1555,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 pl.det_slot[(size_t)pi * kWarp + dd] = (int32_t)(pl.cv_tile[sim->det_cv[sg[pi].cells[dd]]] - base);
                 pl.det_gid[(size_t)pi * kWarp + dd] = sg[pi].cells[dd];
             }
-        }
+        });
     } else {
     if (groups.empty() && nc > 0) build_k(kpp, groups);
     {   // per-warp tile: the largest shared-memory pack's need, so that more warps fit an SM
