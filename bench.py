@@ -454,6 +454,7 @@ def main():
         h2d = model_bytes(model)
         kk = 0
         ev_per_epoch = 0
+        spk_read = 0
         ev_sorted = bool(np.all(np.diff(spec.ev_t) >= 0))
         for i in range(args.steps):
             lo, hi = kk * spec.dt, (kk + E) * spec.dt
@@ -469,15 +470,16 @@ def main():
             ev_per_epoch += n_sel
             kk += E
             sim2.advance(kk * spec.dt)
-            g, ts = sim2.spikes()
+            g, ts = sim2.new_spikes()
+            spk_read += g.size
         v = sim2.voltage()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e = {"value": model.n_cv * E * args.steps / el, "unit": "CV-steps/s",
                "h2d_bytes_per_step": int(h2d / args.steps + 28 * ev_per_epoch / args.steps + 8),
-               "d2h_bytes_per_step": int(8 * model.n_cv / args.steps + 12 * nspk / max(1, args.steps) + 16),
+               "d2h_bytes_per_step": int(8 * model.n_cv / args.steps + 12 * spk_read / args.steps + 16),
                "includes": "handle creation and model upload from host arrays; per step: that epoch's "
-                           "external events from host, advance one epoch, spikes to host; all voltages to host at the end"}
+                           "external events from host, advance one epoch, that epoch's spikes to host; all voltages to host at the end"}
         del sim2
 
     if rank == 0:

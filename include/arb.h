@@ -182,6 +182,16 @@ arb_status arb_num_spikes(arb_sim* sim, int64_t* n);
 /* Copies up to cap recorded spikes (host arrays), sorted by (time, gid); *n_out = count. */
 arb_status arb_read_spikes(arb_sim* sim, int32_t* gid, double* t, int64_t cap, int64_t* n_out);
 
+/* Copies up to cap of the spikes recorded after the first `first` ones (host arrays), sorted
+ * by (time, gid); *n_out = count (0 when first >= the number recorded). Spikes are recorded in
+ * the order of the advance calls that found them and every spike of one call is later than
+ * every spike of an earlier call, so reading from the count arb_num_spikes gave before an
+ * advance returns exactly that advance's spikes, and successive reads concatenate into the
+ * sorted list arb_read_spikes returns: per-epoch export costs O(new spikes). first < 0 gives
+ * ARB_E_ARG. */
+arb_status arb_read_spikes_from(arb_sim* sim, int64_t first, int32_t* gid, double* t, int64_t cap,
+                                int64_t* n_out);
+
 /* Records V(t_{k+1}) at n CVs after every step k, starting with the next step, into the
  * device array trace[max_steps][n] (row r = the r-th step after this call). Steps beyond
  * max_steps are not recorded. n = 0 switches probes off. cv: host array. */

@@ -2194,25 +2194,31 @@ arb_status arb_num_spikes(arb_sim* sim, int64_t* n) {
     return ARB_OK;
 }
 
-arb_status arb_read_spikes(arb_sim* sim, int32_t* gid, double* t, int64_t cap, int64_t* n_out) {
-    if (!sim || !n_out || cap < 0 || (cap > 0 && (!gid || !t))) return ARB_E_ARG;
+arb_status arb_read_spikes_from(arb_sim* sim, int64_t first, int32_t* gid, double* t, int64_t cap,
+                                int64_t* n_out) {
+    if (!sim || !n_out || first < 0 || cap < 0 || (cap > 0 && (!gid || !t))) return ARB_E_ARG;
     int64_t n = 0;
     arb_status st = arb_num_spikes(sim, &n);
     if (st != ARB_OK) return st;
-    std::vector<int32_t> g(n);
-    std::vector<double> tt(n);
-    if (n > 0) {
-        CU(cudaMemcpyAsync(g.data(), region(sim, "spk_gid"), 4 * n, cudaMemcpyDeviceToHost, sim->s));
-        CU(cudaMemcpyAsync(tt.data(), region(sim, "spk_t"), 8 * n, cudaMemcpyDeviceToHost, sim->s));
+    const int64_t k = std::max<int64_t>(0, n - first);
+    std::vector<int32_t> g(k);
+    std::vector<double> tt(k);
+    if (k > 0) {
+        CU(cudaMemcpyAsync(g.data(), (const int32_t*)region(sim, "spk_gid") + first, 4 * k, cudaMemcpyDeviceToHost, sim->s));
+        CU(cudaMemcpyAsync(tt.data(), (const double*)region(sim, "spk_t") + first, 8 * k, cudaMemcpyDeviceToHost, sim->s));
         CU(cudaStreamSynchronize(sim->s));
     }
-    std::vector<int64_t> o(n);
+    std::vector<int64_t> o(k);
     std::iota(o.begin(), o.end(), 0);
     std::sort(o.begin(), o.end(), [&](int64_t a, int64_t b) { return tt[a] != tt[b] ? tt[a] < tt[b] : g[a] < g[b]; });
-    const int64_t m = std::min(n, cap);
+    const int64_t m = std::min(k, cap);
     for (int64_t i = 0; i < m; ++i) { gid[i] = g[o[i]]; t[i] = tt[o[i]]; }
     *n_out = m;
     return ARB_OK;
+}
+
+arb_status arb_read_spikes(arb_sim* sim, int32_t* gid, double* t, int64_t cap, int64_t* n_out) {
+    return arb_read_spikes_from(sim, 0, gid, t, cap, n_out);
 }
 
 arb_status arb_set_probes(arb_sim* sim, int64_t n, const int64_t* cv, double* dev_trace, int64_t max_steps) {

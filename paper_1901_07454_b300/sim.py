@@ -171,13 +171,22 @@ class Simulation(Plan):
         L.check(L.load().arb_num_spikes(self.h, C.byref(n)), self.h)
         return n.value
 
-    def spikes(self):
-        n = self.num_spikes()
+    def spikes(self, first=0):
+        """Spikes recorded after the first `first` ones, sorted by (time, gid): (gid, t)."""
+        n = max(0, self.num_spikes() - int(first))
         gid = np.zeros(max(n, 1), np.int32)
         t = np.zeros(max(n, 1))
         got = C.c_int64()
-        L.check(L.load().arb_read_spikes(self.h, _p(gid), _p(t), n, C.byref(got)), self.h)
+        L.check(L.load().arb_read_spikes_from(self.h, int(first), _p(gid), _p(t), n, C.byref(got)), self.h)
         return gid[:got.value], t[:got.value]
+
+    def new_spikes(self):
+        """Spikes recorded since the previous new_spikes() call (all of them on the first
+        call), sorted by (time, gid); the per-epoch spike export."""
+        first = getattr(self, "_spike_cursor", 0)
+        gid, t = self.spikes(first)
+        self._spike_cursor = first + gid.size
+        return gid, t
 
     def set_probes(self, cvs, max_steps):
         cvs = np.ascontiguousarray(cvs, np.int64)

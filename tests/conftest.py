@@ -11,6 +11,10 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
+    # (re)build the CUDA library when it is missing or older than its sources, before any test
+    # module imports the package (a cross-compile: no GPU needed)
+    import __graft_entry__
+    __graft_entry__.build()
 
 
 @pytest.fixture(scope="session")

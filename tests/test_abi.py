@@ -129,6 +129,10 @@ def test_adjoint_workspace_query_and_unbound_handle(arb):
     loss = C.c_double()
     rc = lib.arb_adjoint(p.h, 10, 5, 0, None, None, 1.0, None, 0, None, 0, None, C.byref(loss))
     assert rc == -5 and b"bind" in lib.arb_last_error(p.h)
+    # spike reads: a negative start is an argument error, an unbound handle a state error
+    n = C.c_int64()
+    assert lib.arb_read_spikes_from(p.h, -1, None, None, 0, C.byref(n)) == -1
+    assert lib.arb_read_spikes_from(p.h, 0, None, None, 0, C.byref(n)) == -5
 
 
 def test_exact_event_times_validation_and_plan(arb):

@@ -90,6 +90,32 @@ def test_ring_closed_loop_spikes():
     assert rel_err(g["V"], o["V"]) <= TOL
 
 
+def test_ring_per_epoch_spike_export():
+    # new_spikes() after each advance returns that epoch's spikes only (arb_read_spikes_from);
+    # the pieces lie inside their epochs and concatenate to the oracle's sorted spike list
+    import paper_1901_07454_b300 as arb
+    m, spec = make_config(1, n_cells=48, t_end=150.0)
+    sim = arb.Simulation(m, dt=spec.dt, epoch_steps=spec.epoch_steps)
+    sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
+    E = spec.epoch_steps
+    gs, ts = [], []
+    k = 0
+    while k < spec.n_steps:
+        k0, k = k, min(spec.n_steps, k + E)
+        sim.advance(k * spec.dt)
+        g, t = sim.new_spikes()
+        assert np.all(t >= k0 * spec.dt - 1e-12) and np.all(t <= k * spec.dt + 1e-12)
+        gs.append(g)
+        ts.append(t)
+    assert sim.new_spikes()[0].size == 0
+    ga, ta = np.concatenate(gs), np.concatenate(ts)
+    gall, tall = sim.spikes()
+    assert np.array_equal(ga, gall) and np.array_equal(ta, tall)
+    o = run_oracle(m, spec)
+    compare_spikes((ga, ta), o["spikes"])
+    assert sim.spikes(first=10 ** 9)[0].size == 0
+
+
 def test_ring_divergence_of_the_explicit_scheme_is_reported():
     # With the membrane current on the right-hand side (explicit in V), the tiny soma CV of
     # cell 12 receives several simultaneous events and the step becomes unstable at 65 ms.
