@@ -330,6 +330,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="small-batch workloads: keep the static packing")
     ap.add_argument("--exact-events", action="store_true",
                     help="cut steps at event times (one cell per lane) instead of applying events at step starts")
+    ap.add_argument("--epoch-overlap", action="store_true",
+                    help="epochs of half the minimum delay with the spike exchange on a second stream; a step "
+                         "is still one minimum delay (two overlapped epochs)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps >= 1
 
@@ -364,19 +367,23 @@ def main():
     if args.exact_events:
         sim_kw["exact_events"] = True
         args.no_autotune = True
+    if args.epoch_overlap:
+        sim_kw["epoch_overlap"] = True
+    E_sim = 0 if args.epoch_overlap else E      # overlapped: the library halves the minimum delay
     tuned = None
     if args.cells_per_pack == 0 and args.workload != "batched" and not args.no_autotune:
         # small batches: time candidate packings on the GPU first (not part of the timed run)
-        best, times = arb.autotune_packing(model, dt=spec.dt, epoch_steps=E, precision=precision,
+        best, times = arb.autotune_packing(model, dt=spec.dt, epoch_steps=E_sim, precision=precision,
                                            scheme=args.scheme, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
                                            events=(spec.ev_syn, spec.ev_t, spec.ev_w), **sim_kw)
         args.cells_per_pack = best["cells_per_pack"]
         tuned = {"chosen": best, "epoch_kernel_ms": {str(dict(k)["cells_per_pack"]): round(v, 3) for k, v in times.items()}}
-    sim = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
+    sim = arb.Simulation(model, dt=spec.dt, epoch_steps=E_sim, precision=precision, scheme=args.scheme,
                          cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
                          **sim_kw)
     sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
     info = sim.plan_info()
+    assert info["epoch_steps"] * (2 if args.epoch_overlap else 1) == E, info
     stream = torch.cuda.current_stream()
     k = 0
     for _ in range(args.warmup):
@@ -419,12 +426,13 @@ def main():
     # roofline of the dominant kernel (the epoch kernel), timed with CUDA events around it on
     # the library's stream: FP64 issue (what binds it) and HBM (algorithmic bytes)
     bpc = algorithmic_bytes_per_cv_step(model, precision, SIM_KW.get(args.workload, {}).get("coalesce_synapses", False))
-    kern_mean_ms = sum(kern_ms) / len(kern_ms)
-    achieved = bpc * model.n_cv * E / (kern_mean_ms * 1e-3) / 1e9
+    lps = 2 if args.epoch_overlap else 1          # epoch-kernel launches per timed step
+    kern_mean_ms = sum(kern_ms) / len(kern_ms) / lps
+    achieved = bpc * model.n_cv * (E // lps) / (kern_mean_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     streamed = info["cells_per_pack"] == 32
     kname = "arb_stream_kernel" if streamed else "arb_epoch_kernel"
-    cv_steps_launch = model.n_cv * E
+    cv_steps_launch = model.n_cv * (E // lps)
     counted = streamed and precision == "fp64" and not args.exact_events   # the kernel the ncu counts are of
     fp64_per = STREAM_FP64_PER_CV_STEP.get(args.workload) if counted else None
     dram_per = STREAM_DRAM_BYTES_PER_CV_STEP.get(args.workload) if counted else None
@@ -448,7 +456,7 @@ def main():
     if rank == 0 and not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision=precision, scheme=args.scheme,
+        sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=E_sim, precision=precision, scheme=args.scheme,
                               cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
                               **sim_kw)
         h2d = model_bytes(model)
@@ -493,7 +501,11 @@ def main():
             "dtype": "f64" if precision == "fp64" else "f64 solve / f32 mechanisms", "data": "synthetic",
             "scheme": args.scheme, "event_timing": "exact" if args.exact_events else "step start",
             "config": {"workload": workload_name, "cells": model.n_cells, "cvs": model.n_cv, "epoch_steps": E,
-                       "dt_ms": spec.dt, "step": "one epoch (%d time steps) of all cells incl. spike exchange" % E,
+                       "dt_ms": spec.dt,
+                       "step": ("one minimum delay (%d time steps) of all cells: two overlapped epochs of %d steps, "
+                                "spike exchange on a second stream" % (E, E // 2)) if args.epoch_overlap else
+                               "one epoch (%d time steps) of all cells incl. spike exchange" % E,
+                       "epoch_overlap": bool(args.epoch_overlap),
                        "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],
                        "lane_efficiency": round(info["lane_efficiency"], 4), "smem_packs": info["smem_packs"],
                        "max_pack_rows": info["max_pack_rows"], "split_cvs": info["split_cvs"],

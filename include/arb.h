@@ -82,6 +82,15 @@ typedef struct {
                                     (each cell its own), every piece an implicit step of its own
                                     length; needs ARB_IMPLICIT and ARB_FP64 and runs one cell per
                                     lane (cells_per_pack 0 or 32, split_cvs 0 or -1). */
+    int32_t epoch_overlap;       /* 1: epochs of half the minimum delay, as in Sec.
+                                    "Implementation": while epoch i integrates, a second stream
+                                    walks the spikes of epoch i-1 against the connections and
+                                    builds the delivery lists of epoch i+1 (its events come from
+                                    spikes of epoch i-1 or earlier). Every delay must be at least
+                                    2 * epoch_steps * dt; epoch_steps = 0 then means
+                                    floor(min delay / (2 dt)). The results equal those of the
+                                    serial schedule with the same epoch length. 0 (default): each
+                                    epoch's exchange runs between two integrations. */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */

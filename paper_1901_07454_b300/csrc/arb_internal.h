@@ -83,19 +83,26 @@ struct PendEv {
 // Device control block: values that change from epoch to epoch live here, so one
 // captured CUDA graph serves every epoch.
 struct Ctl {
-    int64_t k0, k1, k_end;     // current epoch [k0, k1); run target k_end
-    int64_t ext_lo, ext_hi;    // external events of this epoch in the sorted external array
+    int64_t k0, k1, k_end;     // epoch being integrated [k0, k1); run target k_end
+    int64_t ext_lo, ext_hi;    // external events of the epoch being prepared, in the sorted
+                               // external array
     int64_t n_ext;             // external events resident
     int64_t n_spikes;          // spikes recorded so far
-    int64_t spk_lo;            // first spike of this epoch
+    int64_t spk_mark;          // spikes recorded before the epoch being integrated
     int64_t probe_k0;          // step at which probe row 0 is taken
     int64_t probe_max;         // probe rows available
     int64_t pool_n64[2];       // pending network events in pool 0 / 1 (may count past the capacity)
     int32_t parity;            // pool holding the events not yet delivered
-    int32_t n_due;             // events delivered in this epoch
+    int32_t n_due;             // events delivered in the last prepared epoch
     int32_t pack_next;         // work counter of the persistent epoch kernel
     int32_t status;            // ARBK_* flags
-    int32_t pad[2];
+    int64_t kp0, kp1;          // epoch whose delivery lists are being built [kp0, kp1); kp0 is
+                               // the first step whose lists are not built yet
+    int64_t xr_lo[2], xr_hi[2];// spike ranges of integrated epochs not yet walked (ring of two)
+    int32_t prep_slot;         // delivery-list buffer the preparation writes next (0 / 1); the
+                               // integration of the same epoch reads it through its own graph
+    int32_t xw, xr;            // spike-range ring: next entry written / next entry walked
+    int32_t pad_x;
 };
 
 enum : int32_t {
@@ -165,7 +172,7 @@ struct DevModel {
     int64_t n_probe;
     double* trace;
     // events
-    const int32_t* ev_off;    // [n_owner + 1]
+    const int32_t* ev_off;    // [n_owner + 1] of one delivery-list buffer
     const EvRec* ev;
     // spikes
     int32_t* spk_gid;
@@ -197,12 +204,15 @@ struct EvArgs {
     int32_t* off;
     EvRec* rec;
     EvRec* tmp;               // [bucket_cap] scratch of the long-list sort
-    int64_t bucket_cap;
+    int64_t bucket_cap;       // records per delivery-list buffer
     int32_t n_owner;
     int32_t epoch_steps;
     int32_t time_major;       // 1: order within a step by time first (exact event times)
-    int32_t pad_tm;
+    int32_t slot_mask;        // 1: two delivery-list buffers (overlapped exchange), 0: one
 };
+
+// Delivery lists of buffer `slot`: off[slot * (n_owner + 1) + o] .. [o + 1] index the records
+// of owner o in rec[], as absolute positions inside rec[slot * bucket_cap, (slot + 1) * bucket_cap).
 
 // Arguments of the spike-exchange kernel.
 struct SpkArgs {

@@ -1123,31 +1123,66 @@ template cudaError_t stream_occupancy<float>(bool, int, int, int*);
 
 
 
-__global__ void k_epoch_begin(EvArgs a) {
+// Preparation of one epoch's delivery lists: [kp0, kp1) with kp0 the first step whose lists
+// are not built yet. It reads only pending pools and external events, so with two list buffers
+// it can run while the previous epoch integrates.
+__global__ void k_prep_begin(EvArgs a) {
     Ctl* c = a.ctl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const int64_t k1 = min(c->k0 + (int64_t)a.epoch_steps, c->k_end);
-        c->k1 = k1;
+        const int64_t k1 = min(c->kp0 + (int64_t)a.epoch_steps, c->k_end);
+        c->kp1 = k1;
         int64_t lo = c->ext_lo, hi = c->n_ext;
         while (lo < hi) {                         // first external event at or after k1
             const int64_t mid = (lo + hi) / 2;
             if (a.ext_step[mid] < k1) lo = mid + 1; else hi = mid;
         }
         c->ext_hi = lo;
-        c->spk_lo = c->n_spikes;
         c->pool_n64[c->parity ^ 1] = 0;
-        c->pack_next = 0;
         c->n_due = 0;
     }
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_owner; o += gridDim.x * blockDim.x) a.counts[o] = 0;
+}
+
+__global__ void k_prep_end(Ctl* c, int64_t pool_cap, int32_t slot_mask) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c->kp0 = c->kp1;
+        c->ext_lo = c->ext_hi;
+        const int np = c->parity ^ 1;
+        if (c->pool_n64[np] > pool_cap) c->pool_n64[np] = pool_cap;
+        c->parity = np;
+        c->prep_slot ^= slot_mask;
+    }
+}
+
+// Integration epoch [k0, k1): bounds and the work counter before, the epoch's spike range
+// (for the spike walk) and the next epoch's start after.
+__global__ void k_int_begin(Ctl* c, int32_t epoch_steps) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c->k1 = min(c->k0 + (int64_t)epoch_steps, c->k_end);
+        c->pack_next = 0;
+    }
+}
+
+__global__ void k_int_end(Ctl* c, int64_t spike_cap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int64_t hi = min(c->n_spikes, spike_cap);
+        c->xr_lo[c->xw] = c->spk_mark;
+        c->xr_hi[c->xw] = hi;
+        c->xw ^= 1;
+        c->spk_mark = hi;
+        c->k0 = c->k1;
+    }
 }
 
 template <bool kScatter>
 __global__ void k_ev_walk(EvArgs a) {
     Ctl* c = a.ctl;
     const int par = c->parity;
-    const int64_t k0 = c->k0, k1 = c->k1;
+    const int64_t k0 = c->kp0, k1 = c->kp1;
     const int64_t n_pool = min((int64_t)c->pool_n64[par], a.pool_cap);
+    const int slot = c->prep_slot;
+    const int32_t* off = a.off + (size_t)slot * (a.n_owner + 1);
+    const int64_t rec_end = (int64_t)(slot + 1) * a.bucket_cap;
     if (!kScatter) {
         // pending events not due in this epoch move to the other pool: one atomic per warp
         const int lane = threadIdx.x & 31;
@@ -1193,8 +1228,8 @@ __global__ void k_ev_walk(EvArgs a) {
         if (!kScatter) {
             atomicAdd(&a.counts[owner], 1);
         } else {
-            const int64_t pos = (int64_t)a.off[owner] + atomicAdd(&a.counts[owner], 1);
-            if (pos < a.bucket_cap) {
+            const int64_t pos = (int64_t)off[owner] + atomicAdd(&a.counts[owner], 1);
+            if (pos < rec_end) {
                 EvRec r;
                 r.t = t; r.w = w; r.step_rel = (int32_t)(step - k0); r.js = a.syn_js[syn]; r.src = src; r.idx = idx;
                 a.rec[pos] = r;
@@ -1220,15 +1255,18 @@ __global__ void __launch_bounds__(1024) k_ev_scan(EvArgs a) {
         part[threadIdx.x] += v;
         __syncthreads();
     }
+    const int slot = a.ctl->prep_slot;
+    int32_t* off = a.off + (size_t)slot * (n + 1);
+    const int64_t base = (int64_t)slot * a.bucket_cap;
     int64_t run = part[threadIdx.x] - s;
     for (int o = lo; o < hi; ++o) {
         const int cnt = a.counts[o];
-        a.off[o] = (int32_t)min(run, a.bucket_cap);
+        off[o] = (int32_t)(base + min(run, a.bucket_cap));
         run += cnt;
         a.counts[o] = 0;
     }
     if (threadIdx.x == blockDim.x - 1) {
-        a.off[n] = (int32_t)min(part[blockDim.x - 1], a.bucket_cap);
+        off[n] = (int32_t)(base + min(part[blockDim.x - 1], a.bucket_cap));
         a.ctl->n_due = (int32_t)min(part[blockDim.x - 1], (int64_t)INT32_MAX);
         if (part[blockDim.x - 1] > a.bucket_cap) atomicOr(&a.ctl->status, kStBucketOverflow);
     }
@@ -1248,8 +1286,10 @@ __device__ __forceinline__ bool ev_less(const EvRec& x, const EvRec& y, bool tim
 // here by one thread each with an insertion sort; long ones are left to k_ev_sort_long.
 constexpr int kEvShort = 48;
 __global__ void k_ev_sort(EvArgs a) {
+    const int slot = a.ctl->prep_slot;
+    const int32_t* off = a.off + (size_t)slot * (a.n_owner + 1);
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_owner; o += gridDim.x * blockDim.x) {
-        const int lo = a.off[o], hi = min(a.off[o + 1], (int)min((int64_t)INT32_MAX, a.bucket_cap));
+        const int lo = off[o], hi = off[o + 1];
         const int n = hi - lo;
         if (n > kEvShort) continue;
         EvRec* r = a.rec + lo;
@@ -1276,12 +1316,15 @@ __global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
     int* cur = hist + kEvLongSteps + 1;                            // [kEvLongSteps]
     const int tid = threadIdx.x, nt = blockDim.x;
     const int E = a.epoch_steps;
+    const int slot = a.ctl->prep_slot;
+    const int32_t* off = a.off + (size_t)slot * (a.n_owner + 1);
+    const int64_t base = (int64_t)slot * a.bucket_cap;
     for (int o = blockIdx.x; o < a.n_owner; o += gridDim.x) {
-        const int lo = a.off[o], hi = min(a.off[o + 1], (int)min((int64_t)INT32_MAX, a.bucket_cap));
+        const int lo = off[o], hi = off[o + 1];
         const int n = hi - lo;
         if (n <= kEvShort) continue;                               // uniform across the block
         EvRec* r = a.rec + lo;
-        EvRec* t = a.tmp + lo;
+        EvRec* t = a.tmp + (lo - base);
         if (n > kEvLongMax || E > kEvLongSteps) {
             if (tid == 0) {
                 auto sift = [&](int root, int end) {               // max-heap on [0, end)
@@ -1352,27 +1395,30 @@ __global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
 
 
 
-// Spike exchange on one GPU: every spike of the epoch is walked against the connections of
-// its source (the connection table of Sec. "Implementation", grouped by source here), and each
-// resulting event waits in the pending pool for the epoch that contains its step.
+// Spike exchange on one GPU: every spike of an integrated epoch is walked against the
+// connections of its source (the connection table of Sec. "Implementation", grouped by source
+// here), and each resulting event waits in the pending pool for the epoch that contains its
+// step. Its spike range was recorded when that epoch ended, so the walk may run while the next
+// epoch integrates and records further spikes.
 __global__ void k_spike_expand(SpkArgs a) {
     // one warp per spike: lane 0 reserves the spike's whole fan-out in the pending pool with
     // one atomic, the lanes write its events
     Ctl* c = a.ctl;
     const int par = c->parity;
-    const int64_t k1 = c->k1;
-    const int64_t lo = c->spk_lo, hi = min(c->n_spikes, a.spike_cap);
+    const int64_t k_first = c->kp0;               // earliest step whose lists are not built yet
+    const int xr = c->xr;
+    const int64_t lo = c->xr_lo[xr], hi = c->xr_hi[xr];
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    PendEv* out = par ? a.pool[0] : a.pool[1];
+    PendEv* out = par ? a.pool[1] : a.pool[0];
     for (int64_t i = lo + warp; i < hi; i += nwarps) {
         const int32_t gid = a.spk_gid[i];
         const double ts = a.spk_t[i];
         const int64_t q0 = a.out_ptr[gid], deg = a.out_ptr[gid + 1] - q0;
         if (deg == 0) continue;
         int64_t base = 0;
-        if (lane == 0) base = atomicAdd((unsigned long long*)&c->pool_n64[par ^ 1], (unsigned long long)deg);
+        if (lane == 0) base = atomicAdd((unsigned long long*)&c->pool_n64[par], (unsigned long long)deg);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base + deg > a.pool_cap && lane == 0) atomicOr(&c->status, kStPoolOverflow);
         for (int64_t k = lane; k < deg; k += 32) {
@@ -1380,7 +1426,7 @@ __global__ void k_spike_expand(SpkArgs a) {
             PendEv e;
             e.t = __dadd_rn(ts, a.out_delay[q]);
             int64_t step = event_step(e.t, a.dt, a.exact != 0);
-            if (step < k1) step = k1;
+            if (step < k_first) step = k_first;
             e.step = step;
             e.w = a.out_w[q];
             e.syn = a.out_syn[q];
@@ -1392,14 +1438,8 @@ __global__ void k_spike_expand(SpkArgs a) {
     }
 }
 
-__global__ void k_epoch_end(Ctl* c, int64_t pool_cap) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        c->k0 = c->k1;
-        c->ext_lo = c->ext_hi;
-        const int np = c->parity ^ 1;
-        if (c->pool_n64[np] > pool_cap) c->pool_n64[np] = pool_cap;
-        c->parity = np;
-    }
+__global__ void k_expand_end(Ctl* c) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) c->xr ^= 1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1453,18 +1493,29 @@ cudaError_t events_prepare() {
 
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s) {
     const int owner_blocks = max(1, min(4 * n_sm, (a.n_owner + 255) / 256));
-    k_epoch_begin<<<owner_blocks, 256, 0, s>>>(a);
+    k_prep_begin<<<owner_blocks, 256, 0, s>>>(a);
     k_ev_walk<false><<<2 * n_sm, 256, 0, s>>>(a);
     k_ev_scan<<<1, 1024, 0, s>>>(a);
     k_ev_walk<true><<<2 * n_sm, 256, 0, s>>>(a);
     k_ev_sort<<<owner_blocks, 256, 0, s>>>(a);
     k_ev_sort_long<<<4 * n_sm, 256, ev_sort_long_smem(), s>>>(a);
+    k_prep_end<<<1, 32, 0, s>>>(a.ctl, a.pool_cap, a.slot_mask);
     return cudaGetLastError();
 }
 
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s) {
     k_spike_expand<<<4 * n_sm, 256, 0, s>>>(a);
-    k_epoch_end<<<1, 32, 0, s>>>(a.ctl, a.pool_cap);
+    k_expand_end<<<1, 32, 0, s>>>(a.ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_int_begin(Ctl* c, int32_t epoch_steps, cudaStream_t s) {
+    k_int_begin<<<1, 32, 0, s>>>(c, epoch_steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_int_end(Ctl* c, int64_t spike_cap, cudaStream_t s) {
+    k_int_end<<<1, 32, 0, s>>>(c, spike_cap);
     return cudaGetLastError();
 }
 

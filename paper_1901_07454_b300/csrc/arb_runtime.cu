@@ -38,6 +38,8 @@ cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_dou
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
 cudaError_t events_prepare();
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s);
+cudaError_t launch_int_begin(Ctl* c, int32_t epoch_steps, cudaStream_t s);
+cudaError_t launch_int_end(Ctl* c, int64_t spike_cap, cudaStream_t s);
 template <class T>
 cudaError_t launch_gather(double* out, const T* src, const int64_t* idx, int64_t n, cudaStream_t s);
 template <class T>
@@ -143,6 +145,7 @@ struct arb_sim {
     // synapse state units: one per synapse, or per (CV, tau, e) group when coalescing
     bool coalesce = false;
     bool exact = false;                     // steps cut at event times
+    bool overlap = false;                   // exchange overlapped with the next epoch
     std::vector<int32_t> syn_unit;          // model synapse -> unit
     std::vector<int64_t> u_cv;
     std::vector<double> u_tau, u_e;
@@ -171,8 +174,13 @@ struct arb_sim {
     int warps_per_cta = 2;
     int grid = 148;
     cudaStream_t s = nullptr;       // library stream (graphs are captured here)
+    cudaStream_t s2 = nullptr;      // exchange stream of the overlapped schedule
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraphExec_t graph[3] = {};   // event lists, epoch kernel, spike exchange
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr;   // hand-offs between the two streams
+    cudaGraphExec_t graph[6] = {};   // per epoch: delivery lists, epoch kernel, spike walk; the
+                                     // overlapped schedule adds the epoch kernel on list buffer 1
+                                     // and the integration's begin / end kernels
+    int64_t int_count = 0;           // epochs integrated: the overlapped schedule alternates buffers
     cudaEvent_t t0[kGraphRing] = {}, t1[kGraphRing] = {};
     bool pending_time[kGraphRing] = {};
     DevModel<double> dm64{};
@@ -494,6 +502,7 @@ static void layout_regions(arb_sim* sim) {
     const int64_t ne = pl.total_rows * kWarp;
     const int64_t npk = (int64_t)pl.packs.size();
     const int64_t nowner = npk * kWarp;
+    const int64_t nslot = sim->overlap ? 2 : 1;     // delivery-list buffers
     const bool mx = sim->mixed;
     const size_t mt = mx ? sizeof(float) : sizeof(double);
     const int64_t nsyn = (int64_t)sim->syn_cv.size(), nhh = (int64_t)sim->hh_cv.size();
@@ -515,8 +524,8 @@ static void layout_regions(arb_sim* sim) {
         {"st_off", 8 * pl.st_rows * kWarp}, {"st_amp", 8 * pl.st_rows * kWarp},
         {"det_slot", 4 * nowner}, {"det_gid", 4 * nowner},
         {"probe_slot", 4 * std::max<int64_t>(sim->n_cv, 1)}, {"probe_col", 4 * std::max<int64_t>(sim->n_cv, 1)},
-        {"ev_off", 4 * (nowner + 1)}, {"counts", 4 * std::max<int64_t>(nowner, 1)},
-        {"ev", sizeof(EvRec) * p.bucket_capacity}, {"ev_tmp", sizeof(EvRec) * p.bucket_capacity},
+        {"ev_off", 4 * (nowner + 1) * nslot}, {"counts", 4 * std::max<int64_t>(nowner, 1)},
+        {"ev", sizeof(EvRec) * p.bucket_capacity * nslot}, {"ev_tmp", sizeof(EvRec) * p.bucket_capacity},
         {"pool0", sizeof(PendEv) * p.event_capacity}, {"pool1", sizeof(PendEv) * p.event_capacity},
         {"ext_step", 8 * p.ext_event_capacity}, {"ext_t", 8 * p.ext_event_capacity}, {"ext_w", 8 * p.ext_event_capacity},
         {"ext_syn", 4 * p.ext_event_capacity}, {"ext_idx", 4 * p.ext_event_capacity},
@@ -657,6 +666,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     if (p.event_capacity < 1 || p.ext_event_capacity < 1 || p.spike_capacity < 1 || p.bucket_capacity < 1)
         return bad("capacities must be >= 1");
     if (p.event_capacity > INT32_MAX || p.bucket_capacity > INT32_MAX) return bad("event and bucket capacities must be < 2^31");
+    if (p.epoch_overlap != 0 && p.epoch_overlap != 1) return bad("epoch_overlap must be 0 or 1");
+    if (p.epoch_overlap && p.bucket_capacity > INT32_MAX / 2) return bad("with epoch_overlap the bucket capacity must be < 2^30");
     if (p.cells_per_pack < 0 || p.cells_per_pack > 32) return bad("cells_per_pack must be 0..32");
     if (p.split_cvs < -1) return bad("split_cvs must be >= -1");
     sim->mixed = p.precision == ARB_MIXED;
@@ -830,16 +841,21 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     }
     // epoch: no longer than the minimum delay (Sec. "Model": a positive minimum delay lets
     // cells advance independently over that interval)
+    // With the overlapped exchange an epoch is at most half the minimum delay (Sec.
+    // "Implementation"): spikes of epoch i then reach no epoch before i + 2.
+    const int lag = p.epoch_overlap ? 2 : 1;
     if (p.epoch_steps > 0) {
         sim->epoch_steps = p.epoch_steps;
     } else if (ncon > 0) {
-        const double e = std::floor(dmin / p.dt * (1.0 + 1e-12));
+        const double e = std::floor(dmin / (lag * p.dt) * (1.0 + 1e-12));
         sim->epoch_steps = (int32_t)std::max(1.0, std::min(e, 100000.0));
     } else {
         sim->epoch_steps = 400;
     }
-    if (ncon > 0 && dmin < sim->epoch_steps * p.dt * (1.0 - 1e-12))
-        return bad("epoch of " + std::to_string(sim->epoch_steps) + " steps is longer than the minimum delay");
+    if (ncon > 0 && dmin < lag * sim->epoch_steps * p.dt * (1.0 - 1e-12))
+        return bad("epoch of " + std::to_string(sim->epoch_steps) + " steps is longer than " +
+                   (p.epoch_overlap ? "half the minimum delay (overlapped exchange)" : "the minimum delay"));
+    sim->overlap = p.epoch_overlap != 0;
 
     // ------------------------------------------------------------------ discretisation
     hvec<double> area, cap, sigma, Glin, GElin;
@@ -1824,7 +1840,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
 void arb_destroy(arb_sim* sim) {
     if (!sim) return;
     if (sim->bound) {
-        for (int g = 0; g < 3; ++g)
+        for (int g = 0; g < 6; ++g)
             if (sim->graph[g]) cudaGraphExecDestroy(sim->graph[g]);
         for (int g = 0; g < kGraphRing; ++g) {
             if (sim->t0[g]) cudaEventDestroy(sim->t0[g]);
@@ -1832,6 +1848,12 @@ void arb_destroy(arb_sim* sim) {
         }
         if (sim->ev_in) cudaEventDestroy(sim->ev_in);
         if (sim->ev_out) cudaEventDestroy(sim->ev_out);
+        if (sim->ev_main) cudaEventDestroy(sim->ev_main);
+        if (sim->ev_side) cudaEventDestroy(sim->ev_side);
+        if (sim->s2) {
+            cudaStreamSynchronize(sim->s2);
+            cudaStreamDestroy(sim->s2);
+        }
         if (sim->s) {
             cudaStreamSynchronize(sim->s);
             cudaStreamDestroy(sim->s);
@@ -1877,19 +1899,42 @@ static arb_status upload_mech_state(arb_sim* sim, const std::vector<double>& m, 
 // One epoch = three captured graphs: the event-delivery kernels, the epoch kernel and the
 // spike exchange. Timing events are recorded between the graph launches, on the library's
 // stream, so the epoch kernel's own duration is measured with CUDA events.
+// The graphs of one epoch. The epoch kernel is always alone in its graph (with the one-thread
+// begin/end kernels as nodes of that graph it ran about 5% slower on the batched workload).
+//   0: delivery lists (serial schedule: then the integration's begin kernel)
+//   1: epoch kernel reading list buffer 0          3: the same reading list buffer 1
+//   2: (serial: the integration's end kernel) spike walk
+//   4 / 5: the integration's begin / end kernel (overlapped schedule)
 static arb_status capture_one(arb_sim* sim, int which, cudaGraphExec_t* out) {
     if (*out) { cudaGraphExecDestroy(*out); *out = nullptr; }
     cudaGraph_t g = nullptr;
+    Ctl* c = (Ctl*)region(sim, "ctl");
     CU(cudaStreamBeginCapture(sim->s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaSuccess;
-    if (which == 0) e1 = launch_events_pre(sim->ev_args, sim->n_sm, sim->s);
-    else if (which == 1 && sim->plan.stream)
-        e1 = sim->mixed ? launch_stream<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s)
-                        : launch_stream<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s);
-    else if (which == 1)
-        e1 = sim->mixed ? launch_epoch<float>(sim->dm32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
-                        : launch_epoch<double>(sim->dm64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
-    else e1 = launch_events_post(sim->spk_args, sim->n_sm, sim->s);
+    if (which == 0) {
+        e1 = launch_events_pre(sim->ev_args, sim->n_sm, sim->s);
+        if (e1 == cudaSuccess && !sim->overlap) e1 = launch_int_begin(c, sim->epoch_steps, sim->s);
+    } else if (which == 1 || which == 3) {
+        DevModel<double> d64 = sim->dm64;
+        DevModel<float> d32 = sim->dm32;
+        if (which == 3) {
+            d64.ev_off += d64.n_owner + 1;
+            d32.ev_off += d32.n_owner + 1;
+        }
+        if (sim->plan.stream)
+            e1 = sim->mixed ? launch_stream<float>(d32, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s)
+                            : launch_stream<double>(d64, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s);
+        else
+            e1 = sim->mixed ? launch_epoch<float>(d32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
+                            : launch_epoch<double>(d64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
+    } else if (which == 2) {
+        if (!sim->overlap) e1 = launch_int_end(c, sim->prm.spike_capacity, sim->s);
+        if (e1 == cudaSuccess) e1 = launch_events_post(sim->spk_args, sim->n_sm, sim->s);
+    } else if (which == 4) {
+        e1 = launch_int_begin(c, sim->epoch_steps, sim->s);
+    } else {
+        e1 = launch_int_end(c, sim->prm.spike_capacity, sim->s);
+    }
     cudaError_t e2 = cudaStreamEndCapture(sim->s, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -1902,7 +1947,7 @@ static arb_status capture_one(arb_sim* sim, int which, cudaGraphExec_t* out) {
 }
 
 static arb_status capture_graphs(arb_sim* sim) {
-    for (int w = 0; w < 3; ++w) {
+    for (int w = 0; w < (sim->overlap ? 6 : 3); ++w) {
         arb_status st = capture_one(sim, w, &sim->graph[w]);
         if (st != ARB_OK) return st;
     }
@@ -1925,6 +1970,14 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     CU(cudaStreamCreateWithFlags(&sim->s, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&sim->ev_in, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&sim->ev_out, cudaEventDisableTiming));
+    if (sim->overlap) {
+        // the exchange stream yields to the integration: lowest priority
+        int least = 0, greatest = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CU(cudaStreamCreateWithPriority(&sim->s2, cudaStreamNonBlocking, least));
+        CU(cudaEventCreateWithFlags(&sim->ev_main, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&sim->ev_side, cudaEventDisableTiming));
+    }
     for (int g = 0; g < kGraphRing; ++g) {
         CU(cudaEventCreate(&sim->t0[g]));
         CU(cudaEventCreate(&sim->t1[g]));
@@ -1984,6 +2037,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     a.n_owner = (int32_t)(pl.packs.size() * kWarp);
     a.epoch_steps = sim->epoch_steps;
     a.time_major = sim->exact ? 1 : 0;
+    a.slot_mask = sim->overlap ? 1 : 0;
     SpkArgs& b = sim->spk_args;
     b.ctl = a.ctl;
     b.spk_gid = (const int32_t*)region(sim, "spk_gid");
@@ -2118,7 +2172,8 @@ arb_status arb_advance(arb_sim* sim, double t_end) {
     const int64_t pieces = (k_end - sim->k + E - 1) / E;
     for (int g = 0; g < kGraphRing; ++g) sim->pending_time[g] = false;
     double ms_sum = 0.0;
-    for (int64_t i = 0; i < pieces; ++i) {
+    // one epoch's integration (graph 1) on the library stream, timed with a ring of events
+    auto integrate = [&]() -> arb_status {
         const int g = (int)(sim->graph_replays % kGraphRing);
         if (sim->pending_time[g]) {
             CU(cudaEventSynchronize(sim->t1[g]));
@@ -2127,13 +2182,41 @@ arb_status arb_advance(arb_sim* sim, double t_end) {
             ms_sum += ms;
             sim->pending_time[g] = false;
         }
-        CU(cudaGraphLaunch(sim->graph[0], sim->s));
         CU(cudaEventRecord(sim->t0[g], sim->s));
-        CU(cudaGraphLaunch(sim->graph[1], sim->s));
+        // the list buffer of this epoch: the preparation alternates them in the same order
+        CU(cudaGraphLaunch(sim->graph[sim->overlap && (sim->int_count & 1) ? 3 : 1], sim->s));
         CU(cudaEventRecord(sim->t1[g], sim->s));
-        CU(cudaGraphLaunch(sim->graph[2], sim->s));
+        sim->int_count++;
         sim->pending_time[g] = true;
         sim->graph_replays++;
+        return ARB_OK;
+    };
+    if (!sim->overlap) {
+        // serial: delivery lists, integration, spike walk
+        for (int64_t i = 0; i < pieces; ++i) {
+            CU(cudaGraphLaunch(sim->graph[0], sim->s));
+            if ((st = integrate()) != ARB_OK) return st;
+            CU(cudaGraphLaunch(sim->graph[2], sim->s));
+        }
+    } else {
+        // overlapped (epochs of half the minimum delay): while epoch i integrates, the
+        // exchange stream walks the spikes of epoch i-1 and builds the lists of epoch i+1
+        CU(cudaGraphLaunch(sim->graph[0], sim->s));
+        for (int64_t i = 0; i < pieces; ++i) {
+            if (i > 0) CU(cudaStreamWaitEvent(sim->s, sim->ev_side, 0));
+            CU(cudaEventRecord(sim->ev_main, sim->s));
+            CU(cudaGraphLaunch(sim->graph[4], sim->s));
+            if ((st = integrate()) != ARB_OK) return st;
+            CU(cudaGraphLaunch(sim->graph[5], sim->s));
+            if (i > 0 || i + 1 < pieces) {
+                CU(cudaStreamWaitEvent(sim->s2, sim->ev_main, 0));
+                if (i > 0) CU(cudaGraphLaunch(sim->graph[2], sim->s2));
+                if (i + 1 < pieces) CU(cudaGraphLaunch(sim->graph[0], sim->s2));
+                CU(cudaEventRecord(sim->ev_side, sim->s2));
+            }
+        }
+        if (pieces > 1) CU(cudaStreamWaitEvent(sim->s, sim->ev_side, 0));
+        CU(cudaGraphLaunch(sim->graph[2], sim->s));          // the last epoch's spikes
     }
     Ctl hc;
     CU(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sim->s));
@@ -2146,7 +2229,7 @@ arb_status arb_advance(arb_sim* sim, double t_end) {
             sim->pending_time[g] = false;
         }
     sim->last_epoch_ms = ms_sum;
-    sim->last_launches = pieces * 8;
+    sim->last_launches = pieces * 12;     // 7 list kernels, 3 integration, 2 spike walk
     sim->k = k_end;
     if ((st = sync_out(sim)) != ARB_OK) return st;
     if (hc.k0 != k_end) return fail(sim, ARB_E_STATE, "internal: device step count disagrees with the host");

@@ -142,3 +142,20 @@ def test_exact_event_times_validation_and_plan(arb):
     _expect_error(arb, m, "exact event times", exact_events=True, scheme="explicit")
     _expect_error(arb, m, "exact event times", exact_events=True, precision="mixed")
     _expect_error(arb, m, "one cell per lane", exact_events=True, cells_per_pack=8)
+
+
+def test_overlapped_exchange_epoch_rule_and_workspace(arb):
+    # ring of 16 cells, every delay 5 ms: serial epochs may be 200 steps of 0.025 ms, overlapped
+    # ones (half the minimum delay) at most 100
+    from inputs import make_config
+    m, _ = make_config(1, n_cells=16, t_end=10.0)
+    assert arb.Plan(m).plan_info()["epoch_steps"] == 200
+    assert arb.Plan(m, epoch_overlap=True).plan_info()["epoch_steps"] == 100
+    assert arb.Plan(m, epoch_overlap=True, epoch_steps=100).plan_info()["epoch_steps"] == 100
+    arb.Plan(m, epoch_steps=150)
+    _expect_error(arb, m, "half the minimum delay", epoch_overlap=True, epoch_steps=150)
+    _expect_error(arb, m, "bucket capacity", epoch_overlap=True, bucket_capacity=1 << 30)
+    # two delivery-list buffers
+    b_ser = arb.Plan(m, epoch_steps=100).workspace_bytes()
+    b_ovl = arb.Plan(m, epoch_overlap=True).workspace_bytes()
+    assert b_ovl > b_ser
