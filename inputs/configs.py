@@ -149,12 +149,15 @@ def _truncated_normal(rng, mean, sd, n):
 
 
 def make_config(config: int, n_cells: int | None = None, t_end: float | None = None,
-                variant: str = "", syn_per_cell: int | None = None) -> tuple[Model, SimSpec]:
+                variant: str = "", syn_per_cell: int | None = None,
+                virtual_ranks: int = 1) -> tuple[Model, SimSpec]:
     """Workload `config` (0..5); n_cells / t_end shrink it for tests; variant selects options.
 
     variant "ring_active" (config 1): the stimulus on cell 0 is raised so that the ring fires.
     variant "target" (config 4): the hidden parameter set that produces the target traces.
     syn_per_cell (config 5): synapses (and incoming connections) per cell, default 10,000.
+    virtual_ranks (configs 2, 3): the cells are rank 0 of that many ranks holding copies of them
+    (dry run); connection sources are drawn from all ranks' gids (virtual_ranks * n_cells).
     """
     if config == 0:
         n = 10 if n_cells is None else n_cells
@@ -229,8 +232,9 @@ def make_config(config: int, n_cells: int | None = None, t_end: float | None = N
         m = _assemble(cv_offset, parent, length, radius, bcv, hh_cv, pas_cv, syn_cv)
         nsyn_tot = n * nsyn
         cell_of_syn = np.repeat(np.arange(n), nsyn)
-        if n > 1:
-            src = rng.integers(0, n - 1, size=nsyn_tot)
+        n_glob = n * int(virtual_ranks)
+        if n_glob > 1:
+            src = rng.integers(0, n_glob - 1, size=nsyn_tot)
             src = np.where(src >= cell_of_syn, src + 1, src)   # no self connections
         else:
             src = np.zeros(nsyn_tot, np.int64)
@@ -241,7 +245,8 @@ def make_config(config: int, n_cells: int | None = None, t_end: float | None = N
         m.__post_init__()
         ev = _poisson_events(rng, np.arange(nsyn_tot, dtype=np.int64), 5.0, T, m.conn_weight)
         spec = SimSpec(dt=0.025, t_end=T, epoch_steps=40, ev_syn=ev[0], ev_t=ev[1], ev_w=ev[2],
-                       name=("batched" if config == 2 else "mixed") + "-%d" % n)
+                       name=("batched" if config == 2 else "mixed") + "-%d" % n +
+                       ("" if virtual_ranks == 1 else " (rank 0 of %d)" % virtual_ranks))
         return m, spec
 
     if config == 4:

@@ -104,6 +104,36 @@ class Model:
     def cell_sizes(self) -> np.ndarray:
         return np.diff(self.cv_offset)
 
+    def tiled(self, ranks: int):
+        """The network of `ranks` copies of this model: copy r holds cells r*n .. r*n+n-1 (CVs,
+        synapses and clamps shifted by r times the counts), and each connection (s -> synapse j)
+        of the model is repeated in copy r as ((s + r*n) mod (ranks*n) -> synapse j of copy r).
+        Connection sources of the model may be any of the ranks*n gids; copy 0's connections
+        come first, in the model's order. Index shifting only."""
+        R = int(ranks)
+        n, ncv, nsyn = self.n_cells, self.n_cv, self.n_syn
+        rr = np.arange(R, dtype=np.int64)
+
+        def shift(idx, step):
+            return (np.asarray(idx, np.int64)[None, :] + rr[:, None] * step).ravel()
+
+        def tile(a):
+            return np.tile(np.asarray(a), R)
+
+        off = np.concatenate([[0], shift(self.cv_offset[1:], ncv)])
+        m = Model(cv_offset=off, parent=tile(self.parent), length_um=tile(self.length_um),
+                  radius_um=tile(self.radius_um), cm=tile(self.cm), Ra=tile(self.Ra),
+                  branch_of_cv=tile(self.branch_of_cv),
+                  hh_cv=shift(self.hh_cv, ncv), gnabar=tile(self.gnabar), gkbar=tile(self.gkbar), gl=tile(self.gl),
+                  pas_cv=shift(self.pas_cv, ncv), g_pas=tile(self.g_pas), e_pas=tile(self.e_pas),
+                  syn_cv=shift(self.syn_cv, ncv), syn_tau=tile(self.syn_tau), syn_e=tile(self.syn_e),
+                  stim_cv=shift(self.stim_cv, ncv), stim_t_on=tile(self.stim_t_on), stim_dur=tile(self.stim_dur),
+                  stim_amp=tile(self.stim_amp), detector_cv=shift(self.detector_cv, ncv), threshold=self.threshold,
+                  conn_src=(shift(self.conn_src, n) % (R * n)).astype(np.int32),
+                  conn_dst_syn=shift(self.conn_dst_syn, nsyn),
+                  conn_delay=tile(self.conn_delay), conn_weight=tile(self.conn_weight))
+        return m
+
     # per-branch parameter groups: group = cell * (branches per cell) + branch
     PARAM_NAMES = ("gnabar", "gkbar", "gl", "cm")
 

@@ -58,6 +58,8 @@ def lib():
         vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
         L.orc_create.restype = vp
         L.orc_create.argtypes = [vp, dbl, i64, i32]
+        L.orc_create_dry.restype = vp
+        L.orc_create_dry.argtypes = [vp, dbl, i64, i32, i64]
         L.orc_destroy.argtypes = [vp]
         L.orc_enqueue.restype = i32
         L.orc_enqueue.argtypes = [vp, i64, vp, vp, vp]
@@ -164,15 +166,21 @@ class OracleSim:
     """FP64 CPU simulation of a Model; mirrors the library's create/enqueue/advance/read cycle."""
 
     def __init__(self, model, dt: float, epoch_steps: int, nthreads: int = 0, record_delivered=False,
-                 explicit=False, exact_events=False):
+                 explicit=False, exact_events=False, dry_run_ranks=1):
         """explicit=False: fully implicit voltage step (membrane conductance on the diagonal);
         explicit=True: the printed linear system with the membrane current at V(t).
-        exact_events=True: steps are cut at the times of the events inside them."""
+        exact_events=True: steps are cut at the times of the events inside them.
+        dry_run_ranks=R > 1: the model is rank 0 of R ranks holding copies of its cells;
+        connection sources are global gids < R * n_cells, and every local spike also stands
+        for the spikes of its copies on the other ranks (proxy spikes)."""
         self.model = model
         self.dt = float(dt)
         self.epoch_steps = int(epoch_steps)
+        R = int(dry_run_ranks)
+        if R < 1 or (model.conn_src.size and int(model.conn_src.max()) >= R * model.n_cells):
+            raise ValueError("oracle: connection source outside the R * n_cells global gids")
         self._b = _Bound(model)
-        self.h = lib().orc_create(C.byref(self._b.s), self.dt, self.epoch_steps, int(nthreads))
+        self.h = lib().orc_create_dry(C.byref(self._b.s), self.dt, self.epoch_steps, int(nthreads), R)
         if record_delivered:
             lib().orc_record_delivered(self.h, 1)
         if explicit:
@@ -265,10 +273,11 @@ class OracleSim:
 
 
 def simulate(model, spec, nthreads: int = 0, probes=None, record_delivered=False, n_steps=None, explicit=False,
-             exact_events=False):
+             exact_events=False, dry_run_ranks=1):
     """Run a whole SimSpec (or its first n_steps); returns (sim, probe trace or None)."""
     steps = spec.n_steps if n_steps is None else int(n_steps)
-    sim = OracleSim(model, spec.dt, spec.epoch_steps or 400, nthreads, record_delivered, explicit, exact_events)
+    sim = OracleSim(model, spec.dt, spec.epoch_steps or 400, nthreads, record_delivered, explicit, exact_events,
+                    dry_run_ranks)
     sim.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
     trace = sim.set_probes(probes, steps) if probes is not None else None
     sim.run_steps(steps)

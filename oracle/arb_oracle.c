@@ -37,6 +37,12 @@
  * Readings where the paper is silent: events at t_e are applied at the start of step
  * ceil(t_e/dt); the spike time is the linear interpolation of the upward crossing inside the
  * step; t_k = k*dt is formed as a product, never accumulated.
+ * Dry run (optional; Sec. "Scalability": one rank runs its cells and mimics a large cluster by
+ * generating proxy spikes for the cells of the other ranks): with R virtual ranks the model's
+ * n cells are those of rank 0 of a network of R*n cells in which rank r holds copies of them
+ * (gids r*n .. r*n+n-1); connection sources are global gids in [0, R*n). Every spike of local
+ * cell g at t stands for the R spikes of gids g + r*n at t, and each of them is walked against
+ * the connections of its gid.
  * Exact event times (optional): as Sec. "Model" describes, the time step is shortened so that
  * every synapse update falls at the start of an integration step: a step whose interval holds
  * events at t_e > t_k is cut at each distinct t_e, each piece is an integration step of its own
@@ -196,6 +202,7 @@ typedef struct {
     int exact_events;        /* 1: steps are cut at event times (events in step floor(t_e/dt)) */
     int64_t epoch_steps;
     int nthreads;
+    int64_t dry_ranks;       /* virtual ranks of the dry run (1: a plain run) */
     int64_t k;               /* steps taken */
     int64_t n_cv;
     double *area, *cap, *sigma;
@@ -300,12 +307,13 @@ static int64_t event_step(const orc_sim* s, double t) {
     return j;
 }
 
-orc_sim* orc_create(const orc_model* m, double dt, int64_t epoch_steps, int nthreads) {
+orc_sim* orc_create_dry(const orc_model* m, double dt, int64_t epoch_steps, int nthreads, int64_t dry_ranks) {
     orc_sim* s = (orc_sim*)xcalloc(1, sizeof(orc_sim));
     s->m = *m;
     s->dt = dt;
     s->epoch_steps = epoch_steps;
     s->nthreads = nthreads;
+    s->dry_ranks = dry_ranks < 1 ? 1 : dry_ranks;
     int64_t n_cv = m->cv_offset[m->n_cells];
     s->n_cv = n_cv;
     s->area = (double*)xmalloc(sizeof(double) * (size_t)n_cv);
@@ -342,14 +350,16 @@ orc_sim* orc_create(const orc_model* m, double dt, int64_t epoch_steps, int nthr
     s->syn_cell = (int64_t*)xmalloc(sizeof(int64_t) * (size_t)m->n_syn);
     for (int32_t c = 0; c < m->n_cells; ++c)
         for (int64_t j = s->syn_ptr[c]; j < s->syn_ptr[c + 1]; ++j) s->syn_cell[s->syn_list[j]] = c;
-    /* connections grouped by source gid, ascending connection index */
-    s->out_ptr = (int64_t*)xcalloc((size_t)m->n_cells + 1, sizeof(int64_t));
+    /* connections grouped by source gid (global: R*n sources in a dry run), ascending
+       connection index */
+    const int64_t n_src = (int64_t)m->n_cells * s->dry_ranks;
+    s->out_ptr = (int64_t*)xcalloc((size_t)n_src + 1, sizeof(int64_t));
     s->out_list = (int64_t*)xmalloc(sizeof(int64_t) * (size_t)m->n_conn);
     for (int64_t i = 0; i < m->n_conn; ++i) s->out_ptr[m->conn_src[i] + 1]++;
-    for (int32_t c = 0; c < m->n_cells; ++c) s->out_ptr[c + 1] += s->out_ptr[c];
+    for (int64_t c = 0; c < n_src; ++c) s->out_ptr[c + 1] += s->out_ptr[c];
     {
-        int64_t* fill = (int64_t*)xmalloc(sizeof(int64_t) * ((size_t)m->n_cells + 1));
-        memcpy(fill, s->out_ptr, sizeof(int64_t) * ((size_t)m->n_cells + 1));
+        int64_t* fill = (int64_t*)xmalloc(sizeof(int64_t) * ((size_t)n_src + 1));
+        memcpy(fill, s->out_ptr, sizeof(int64_t) * ((size_t)n_src + 1));
         for (int64_t i = 0; i < m->n_conn; ++i) s->out_list[fill[m->conn_src[i]]++] = i;
         free(fill);
     }
@@ -361,6 +371,10 @@ orc_sim* orc_create(const orc_model* m, double dt, int64_t epoch_steps, int nthr
     s->cell_ndeliv = (int64_t*)xcalloc((size_t)m->n_cells, sizeof(int64_t));
     s->cell_capdeliv = (int64_t*)xcalloc((size_t)m->n_cells, sizeof(int64_t));
     return s;
+}
+
+orc_sim* orc_create(const orc_model* m, double dt, int64_t epoch_steps, int nthreads) {
+    return orc_create_dry(m, dt, epoch_steps, nthreads, 1);
 }
 
 void orc_destroy(orc_sim* s) {
@@ -620,8 +634,10 @@ int orc_run(orc_sim* s, int64_t n_steps) {
         }
         qsort(ep, (size_t)nsp, sizeof(orc_spike), cmp_spike);
         s->n_spikes += nsp;
+        /* the global spike list: each local spike once per (virtual) rank */
+        for (int64_t r = 0; r < s->dry_ranks; ++r)
         for (int64_t j = 0; j < nsp; ++j) {
-            int32_t src = ep[j].gid;
+            int32_t src = (int32_t)(ep[j].gid + r * m->n_cells);
             for (int64_t o = s->out_ptr[src]; o < s->out_ptr[src + 1]; ++o) {
                 int64_t ci = s->out_list[o];
                 orc_event e;

@@ -429,6 +429,46 @@ def test_p10_epoch_length_and_threads_do_not_change_results(oracle_lib):
     assert np.all(d["step"] >= (spike_step // 200 + 1) * 200)
 
 
+def _tiled_run(oracle_lib, m, spec, R):
+    """The full network of R copies of m (inputs.Model.tiled), external events repeated on
+    every copy's synapses."""
+    import dataclasses
+    full = m.tiled(R)
+    fs = dataclasses.replace(spec, ev_syn=np.concatenate([spec.ev_syn + r * m.n_syn for r in range(R)]),
+                             ev_t=np.tile(spec.ev_t, R), ev_w=np.tile(spec.ev_w, R))
+    return oracle_lib.simulate(full, fs)[0]
+
+
+def test_dry_run_equals_rank_0_of_the_tiled_network(oracle_lib):
+    # Dry run (Sec. "Scalability": proxy spikes for the cells of other ranks): 64 cells as rank
+    # 0 of 4, connection sources drawn from all 256 gids. Its definition is the full network of
+    # 4 copies, in which every copy evolves like rank 0: the dry run must reproduce copy 0 bit
+    # for bit, and a walk that skipped the proxy spikes would miss 3/4 of the network input.
+    R = 4
+    m, spec = make_config(2, n_cells=64, t_end=30.0, virtual_ranks=R)
+    assert (m.conn_src >= m.n_cells).mean() > 0.7
+    dry = oracle_lib.simulate(m, spec, dry_run_ranks=R)[0]
+    full = _tiled_run(oracle_lib, m, spec, R)
+    ncv = m.n_cv
+    vf = full.voltage()
+    for r in range(R):      # the copies are identical ...
+        assert np.array_equal(vf[r * ncv:(r + 1) * ncv], vf[:ncv])
+    assert np.array_equal(dry.voltage(), vf[:ncv])    # ... and the dry run is copy 0
+    g, t = dry.spikes()
+    gf, tf = full.spikes()
+    sel = gf < m.n_cells
+    assert len(t) >= 40 and np.array_equal(g, gf[sel]) and np.array_equal(t, tf[sel])
+    assert len(tf) == R * len(t)
+    # without the proxies (sources beyond rank 0 silent) the network input is different
+    m1, spec1 = make_config(2, n_cells=64, t_end=30.0, virtual_ranks=R)
+    keep = m1.conn_src < m1.n_cells
+    m1.conn_src, m1.conn_dst_syn = m1.conn_src[keep], m1.conn_dst_syn[keep]
+    m1.conn_delay, m1.conn_weight = m1.conn_delay[keep], m1.conn_weight[keep]
+    assert not np.array_equal(oracle_lib.simulate(m1, spec1)[0].voltage(), dry.voltage())
+    with pytest.raises(ValueError):
+        oracle_lib.OracleSim(m, spec.dt, spec.epoch_steps, dry_run_ranks=2)   # sources beyond 2 ranks
+
+
 def test_explicit_reading_diverges_on_the_ring_and_implicit_does_not(oracle_lib):
     # tiny soma CVs receive several simultaneous events: dt*g/c > 2 in the explicit reading
     m, spec = make_config(1, n_cells=48, t_end=70.0)
