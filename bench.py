@@ -166,7 +166,7 @@ def run_reference(args, model, spec, precision, workload_name):
     oracle.build()
     sub, sspec, ncells = cell_sample(model, spec, args.ref_cells)
     E = spec.epoch_steps
-    sim = oracle.OracleSim(sub, spec.dt, E, nthreads=0)
+    sim = oracle.OracleSim(sub, spec.dt, E, nthreads=0, dry_run_ranks=args.dry_run_ranks)
     sim.enqueue(sspec.ev_syn, sspec.ev_t, sspec.ev_w)
     for _ in range(args.warmup):
         sim.run_steps(E)
@@ -290,7 +290,7 @@ def run_adjoint(args, model, spec):
         "cpu_baseline": cpu, "e2e": None, "gpu_launches": sim.last_timing()[1] * args.steps, "clocks": clk}), flush=True)
 
 
-def cpu_baseline(model, spec, budget_s):
+def cpu_baseline(model, spec, budget_s, dry_run_ranks=1):
     """Oracle on all host cores over a bounded sample: whole epochs of all cells until about
     budget_s seconds have passed (at least one epoch)."""
     import oracle
@@ -298,7 +298,7 @@ def cpu_baseline(model, spec, budget_s):
     oracle.build()
     sub, sspec, ncells = cell_sample(model, spec, 0)
     E = spec.epoch_steps
-    sim = oracle.OracleSim(sub, spec.dt, E, nthreads=0)
+    sim = oracle.OracleSim(sub, spec.dt, E, nthreads=0, dry_run_ranks=dry_run_ranks)
     sim.enqueue(sspec.ev_syn, sspec.ev_t, sspec.ev_w)
     t0 = time.perf_counter()
     ep = 0
@@ -330,6 +330,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="small-batch workloads: keep the static packing")
     ap.add_argument("--exact-events", action="store_true",
                     help="cut steps at event times (one cell per lane) instead of applying events at step starts")
+    ap.add_argument("--dry-run-ranks", type=int, default=1,
+                    help="batched/mixed: the cells are rank 0 of this many ranks; connection sources span "
+                         "all ranks and every spike is also walked as the proxies of the other ranks")
     ap.add_argument("--epoch-overlap", action="store_true",
                     help="epochs of half the minimum delay with the spike exchange on a second stream; a step "
                          "is still one minimum delay (two overlapped epochs)")
@@ -340,14 +343,17 @@ def main():
     cfg, precision = WORKLOADS[args.workload]
     E_ms = None
     ncells = args.cells if args.cells > 0 else None
-    model, spec = make_config(cfg, n_cells=ncells, t_end=None)
+    vr = dict(virtual_ranks=args.dry_run_ranks) if args.dry_run_ranks > 1 else {}
+    if vr and cfg not in (2, 3):
+        raise SystemExit("--dry-run-ranks applies to the batched and mixed workloads")
+    model, spec = make_config(cfg, n_cells=ncells, t_end=None, **vr)
     if args.workload == "adjoint":
         return run_adjoint(args, model, spec)
     E = spec.epoch_steps
     # the run must cover warm-up + timed epochs: extend external inputs if needed
     need_t = (args.warmup + args.steps) * E * spec.dt
     if need_t > spec.t_end + 1e-9:
-        model, spec = make_config(cfg, n_cells=ncells, t_end=need_t)
+        model, spec = make_config(cfg, n_cells=ncells, t_end=need_t, **vr)
     workload_name = "%s: %s, %d cells, %d CVs, dt %.3f ms, epoch %d steps" % (
         args.workload, spec.name, model.n_cells, model.n_cv, spec.dt, E)
 
@@ -369,6 +375,8 @@ def main():
         args.no_autotune = True
     if args.epoch_overlap:
         sim_kw["epoch_overlap"] = True
+    if args.dry_run_ranks > 1:
+        sim_kw["dry_run_ranks"] = args.dry_run_ranks
     E_sim = 0 if args.epoch_overlap else E      # overlapped: the library halves the minimum delay
     tuned = None
     if args.cells_per_pack == 0 and args.workload != "batched" and not args.no_autotune:
@@ -493,7 +501,7 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            cpu = cpu_baseline(model, spec, args.cpu_budget)
+            cpu = cpu_baseline(model, spec, args.cpu_budget, args.dry_run_ranks)
         line = {
             "metric": "compartment-steps/sec", "value": value, "unit": "CV-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
@@ -506,6 +514,8 @@ def main():
                                 "spike exchange on a second stream" % (E, E // 2)) if args.epoch_overlap else
                                "one epoch (%d time steps) of all cells incl. spike exchange" % E,
                        "epoch_overlap": bool(args.epoch_overlap),
+                       "dry_run_ranks": args.dry_run_ranks,
+                       "exchange_ms_per_step": (tot_ms / args.steps - lps * kern_mean_ms),
                        "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],
                        "lane_efficiency": round(info["lane_efficiency"], 4), "smem_packs": info["smem_packs"],
                        "max_pack_rows": info["max_pack_rows"], "split_cvs": info["split_cvs"],

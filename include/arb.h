@@ -91,6 +91,14 @@ typedef struct {
                                     floor(min delay / (2 dt)). The results equal those of the
                                     serial schedule with the same epoch length. 0 (default): each
                                     epoch's exchange runs between two integrations. */
+    int32_t dry_run_ranks;       /* dry run (Sec. "Scalability": one rank mimics a large cluster
+                                    by generating proxy spikes for the other ranks' cells): 0 or
+                                    1 = off; R > 1: the model's n cells are rank 0 of R ranks
+                                    holding copies of them (gids r*n .. r*n+n-1), connection
+                                    sources are global gids in [0, R*n), and every local spike
+                                    of gid g at t is walked against the connections of the R
+                                    gids g + r*n. Spike reads return the local spikes only.
+                                    R*n must be < 2^31. */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */
@@ -134,7 +142,8 @@ typedef struct {
     const int64_t* detector_cv;  /* [n_cells] a CV of that cell */
     double threshold;            /* mV, upward crossing */
     /* connections: a spike of cell conn_src[i] at t adds conn_weight[i] to synapse
-       conn_dst_syn[i] at t + conn_delay[i]; every delay must be >= epoch_steps*dt */
+       conn_dst_syn[i] at t + conn_delay[i]; every delay must be >= epoch_steps*dt (twice that
+       with epoch_overlap); conn_src < n_cells, or < dry_run_ranks * n_cells in a dry run */
     int64_t n_conn;
     const int32_t* conn_src;
     const int64_t* conn_dst_syn;

@@ -30,6 +30,7 @@ class arb_params(C.Structure):
                 ("cells_per_pack", C.c_int32), ("smem_budget", C.c_int32),
                 ("scheme", C.c_int32), ("split_cvs", C.c_int32),
                 ("coalesce_synapses", C.c_int32), ("event_timing", C.c_int32), ("epoch_overlap", C.c_int32),
+                ("dry_run_ranks", C.c_int32),
                 ("event_capacity", C.c_int64), ("ext_event_capacity", C.c_int64),
                 ("spike_capacity", C.c_int64), ("bucket_capacity", C.c_int64), ("stream", C.c_void_p)]
 

@@ -230,6 +230,8 @@ struct SpkArgs {
     PendEv* pool[2];
     int64_t pool_cap;
     double dt;
+    int64_t n_cells;          // local cells
+    int64_t dry_ranks;        // virtual ranks: each local spike is walked once per rank
 };
 
 // Step of an event at time t (ms). Fixed-step rule: the event is applied at the start of step

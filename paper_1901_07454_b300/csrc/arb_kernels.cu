@@ -1399,41 +1399,60 @@ __global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
 // connections of its source (the connection table of Sec. "Implementation", grouped by source
 // here), and each resulting event waits in the pending pool for the epoch that contains its
 // step. Its spike range was recorded when that epoch ended, so the walk may run while the next
-// epoch integrates and records further spikes.
+// epoch integrates and records further spikes. In a dry run (Sec. "Scalability") the global
+// spike list holds every local spike once per virtual rank r, as gid + r * n_cells.
 __global__ void k_spike_expand(SpkArgs a) {
-    // one warp per spike: lane 0 reserves the spike's whole fan-out in the pending pool with
-    // one atomic, the lanes write its events
+    // 32 spikes per warp iteration, one lookup of the out-list per lane; then the warp takes the
+    // spikes with connections one at a time: lane 0 reserves the whole fan-out in the pending
+    // pool with one atomic, the lanes write its events
     Ctl* c = a.ctl;
     const int par = c->parity;
     const int64_t k_first = c->kp0;               // earliest step whose lists are not built yet
     const int xr = c->xr;
-    const int64_t lo = c->xr_lo[xr], hi = c->xr_hi[xr];
+    const int64_t lo = c->xr_lo[xr], n_local = c->xr_hi[xr] - lo;
+    const int64_t n_glob = n_local * a.dry_ranks;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     PendEv* out = par ? a.pool[1] : a.pool[0];
-    for (int64_t i = lo + warp; i < hi; i += nwarps) {
-        const int32_t gid = a.spk_gid[i];
-        const double ts = a.spk_t[i];
-        const int64_t q0 = a.out_ptr[gid], deg = a.out_ptr[gid + 1] - q0;
-        if (deg == 0) continue;
-        int64_t base = 0;
-        if (lane == 0) base = atomicAdd((unsigned long long*)&c->pool_n64[par], (unsigned long long)deg);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base + deg > a.pool_cap && lane == 0) atomicOr(&c->status, kStPoolOverflow);
-        for (int64_t k = lane; k < deg; k += 32) {
-            const int64_t q = q0 + k;
-            PendEv e;
-            e.t = __dadd_rn(ts, a.out_delay[q]);
-            int64_t step = event_step(e.t, a.dt, a.exact != 0);
-            if (step < k_first) step = k_first;
-            e.step = step;
-            e.w = a.out_w[q];
-            e.syn = a.out_syn[q];
-            e.src = gid;
-            e.idx = a.out_idx[q];
-            e.pad = 0;
-            if (base + k < a.pool_cap) out[base + k] = e;
+    for (int64_t i0 = warp * 32; i0 < n_glob; i0 += nwarps * 32) {
+        const int64_t i = i0 + lane;
+        int32_t my_gid = 0;
+        double my_ts = 0.0;
+        int64_t my_q0 = 0, my_deg = 0;
+        if (i < n_glob) {
+            const int64_t r = i / n_local, j = lo + (i - r * n_local);
+            my_gid = (int32_t)(a.spk_gid[j] + r * a.n_cells);
+            my_ts = a.spk_t[j];
+            my_q0 = a.out_ptr[my_gid];
+            my_deg = a.out_ptr[my_gid + 1] - my_q0;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, my_deg > 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t gid = __shfl_sync(0xffffffffu, my_gid, src);
+            const double ts = __shfl_sync(0xffffffffu, my_ts, src);
+            const int64_t q0 = __shfl_sync(0xffffffffu, my_q0, src);
+            const int64_t deg = __shfl_sync(0xffffffffu, my_deg, src);
+            int64_t base = 0;
+            if (lane == 0) base = atomicAdd((unsigned long long*)&c->pool_n64[par], (unsigned long long)deg);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + deg > a.pool_cap && lane == 0) atomicOr(&c->status, kStPoolOverflow);
+            for (int64_t k = lane; k < deg; k += 32) {
+                const int64_t q = q0 + k;
+                PendEv e;
+                e.t = __dadd_rn(ts, a.out_delay[q]);
+                int64_t step = event_step(e.t, a.dt, a.exact != 0);
+                if (step < k_first) step = k_first;
+                e.step = step;
+                e.w = a.out_w[q];
+                e.syn = a.out_syn[q];
+                e.src = gid;
+                e.idx = a.out_idx[q];
+                e.pad = 0;
+                if (base + k < a.pool_cap) out[base + k] = e;
+            }
         }
     }
 }

@@ -146,6 +146,7 @@ struct arb_sim {
     bool coalesce = false;
     bool exact = false;                     // steps cut at event times
     bool overlap = false;                   // exchange overlapped with the next epoch
+    int64_t dry_ranks = 1;                  // virtual ranks of a dry run (1: a plain run)
     std::vector<int32_t> syn_unit;          // model synapse -> unit
     std::vector<int64_t> u_cv;
     std::vector<double> u_tau, u_e;
@@ -530,7 +531,7 @@ static void layout_regions(arb_sim* sim) {
         {"ext_step", 8 * p.ext_event_capacity}, {"ext_t", 8 * p.ext_event_capacity}, {"ext_w", 8 * p.ext_event_capacity},
         {"ext_syn", 4 * p.ext_event_capacity}, {"ext_idx", 4 * p.ext_event_capacity},
         {"syn_owner", 4 * std::max<int64_t>(nsyn, 1)}, {"syn_js", 4 * std::max<int64_t>(nsyn, 1)},
-        {"out_ptr", 8 * (sim->n_cells + 1)}, {"out_syn", 4 * std::max<size_t>(sim->out_syn.size(), 1)},
+        {"out_ptr", 8 * (sim->n_cells * sim->dry_ranks + 1)}, {"out_syn", 4 * std::max<size_t>(sim->out_syn.size(), 1)},
         {"out_idx", 4 * std::max<size_t>(sim->out_syn.size(), 1)}, {"out_delay", 8 * std::max<size_t>(sim->out_syn.size(), 1)},
         {"out_w", 8 * std::max<size_t>(sim->out_syn.size(), 1)},
         {"spk_gid", 4 * p.spike_capacity}, {"spk_t", 8 * p.spike_capacity},
@@ -667,6 +668,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         return bad("capacities must be >= 1");
     if (p.event_capacity > INT32_MAX || p.bucket_capacity > INT32_MAX) return bad("event and bucket capacities must be < 2^31");
     if (p.epoch_overlap != 0 && p.epoch_overlap != 1) return bad("epoch_overlap must be 0 or 1");
+    if (p.dry_run_ranks < 0) return bad("dry_run_ranks must be >= 0");
     if (p.epoch_overlap && p.bucket_capacity > INT32_MAX / 2) return bad("with epoch_overlap the bucket capacity must be < 2^30");
     if (p.cells_per_pack < 0 || p.cells_per_pack > 32) return bad("cells_per_pack must be 0..32");
     if (p.split_cvs < -1) return bad("split_cvs must be >= -1");
@@ -831,9 +833,15 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     sim->conn_dst.assign(m->conn_dst_syn, m->conn_dst_syn + ncon);
     sim->conn_delay.assign(m->conn_delay, m->conn_delay + ncon);
     sim->conn_w.assign(m->conn_weight, m->conn_weight + ncon);
+    // dry run: the sources are the gids of all virtual ranks
+    sim->dry_ranks = std::max<int64_t>(1, p.dry_run_ranks);
+    const int64_t n_src = (int64_t)nc * sim->dry_ranks;
+    if (n_src > INT32_MAX) return bad("dry_run_ranks * n_cells must be < 2^31");
     double dmin = INFINITY;
     for (int64_t i = 0; i < ncon; ++i) {
-        if (sim->conn_src[i] < 0 || sim->conn_src[i] >= nc) return bad("connection source gid out of range");
+        if (sim->conn_src[i] < 0 || sim->conn_src[i] >= n_src)
+            return bad(sim->dry_ranks > 1 ? "connection source gid out of range (dry run: < dry_run_ranks * n_cells)"
+                                          : "connection source gid out of range");
         if (sim->conn_dst[i] < 0 || sim->conn_dst[i] >= m->n_syn) return bad("connection target synapse out of range");
         if (!finite_pos(sim->conn_delay[i])) return bad("connection delays must be finite and > 0");
         if (!std::isfinite(sim->conn_w[i])) return bad("connection weights must be finite");
@@ -1815,10 +1823,12 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         sim->init_h.assign(sim->hh_cv.size(), hi);
         sim->init_n.assign(sim->hh_cv.size(), ni);
     }
-    // connections grouped by source, ascending connection index
-    sim->out_ptr.assign(nc + 1, 0);
+    // connections grouped by source (every virtual rank's gids in a dry run), ascending
+    // connection index
+    const int64_t n_out = (int64_t)nc * sim->dry_ranks;
+    sim->out_ptr.assign(n_out + 1, 0);
     for (int64_t i = 0; i < ncon; ++i) sim->out_ptr[sim->conn_src[i] + 1]++;
-    for (int32_t c = 0; c < nc; ++c) sim->out_ptr[c + 1] += sim->out_ptr[c];
+    for (int64_t c = 0; c < n_out; ++c) sim->out_ptr[c + 1] += sim->out_ptr[c];
     sim->out_syn.resize(ncon);
     sim->out_idx.resize(ncon);
     sim->out_delay.resize(ncon);
@@ -2053,6 +2063,8 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     b.pool_cap = sim->prm.event_capacity;
     b.dt = sim->prm.dt;
     b.exact = sim->exact ? 1 : 0;
+    b.n_cells = sim->n_cells;
+    b.dry_ranks = sim->dry_ranks;
     CU(events_prepare());
     // launch shape of the persistent epoch kernel
     if (pl.stream) {

@@ -61,7 +61,7 @@ class Plan:
     def __init__(self, model, dt=0.025, epoch_steps=0, precision="fp64", cells_per_pack=0, smem_budget=0,
                  event_capacity=None, ext_event_capacity=None, spike_capacity=None, bucket_capacity=None,
                  stream=None, scheme="implicit", split_cvs=0, coalesce_synapses=False, exact_events=False,
-                 epoch_overlap=False):
+                 epoch_overlap=False, dry_run_ranks=1):
         lib = L.load()
         self.model = model
         p = default_params()
@@ -74,6 +74,7 @@ class Plan:
         p.coalesce_synapses = 1 if coalesce_synapses else 0
         p.event_timing = L.ARB_EVENTS_EXACT if exact_events else L.ARB_EVENTS_STEP_START
         p.epoch_overlap = 1 if epoch_overlap else 0
+        p.dry_run_ranks = int(dry_run_ranks)
         if scheme not in ("implicit", "explicit"):
             raise ValueError("scheme must be 'implicit' or 'explicit'")
         p.scheme = L.ARB_EXPLICIT if scheme == "explicit" else L.ARB_IMPLICIT

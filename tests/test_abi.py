@@ -159,3 +159,17 @@ def test_overlapped_exchange_epoch_rule_and_workspace(arb):
     b_ser = arb.Plan(m, epoch_steps=100).workspace_bytes()
     b_ovl = arb.Plan(m, epoch_overlap=True).workspace_bytes()
     assert b_ovl > b_ser
+
+
+def test_dry_run_sources_and_validation(arb):
+    # 16 local cells as rank 0 of 8 ranks: sources may be any of the 128 global gids
+    from inputs import make_config
+    m, _ = make_config(2, n_cells=16, t_end=5.0, virtual_ranks=8)
+    assert m.conn_src.max() >= 16
+    _expect_error(arb, m, "source gid out of range")                        # not a dry run
+    _expect_error(arb, m, "dry_run_ranks", dry_run_ranks=4)                  # too few ranks
+    _expect_error(arb, m, "dry_run_ranks must be", dry_run_ranks=-1)
+    _expect_error(arb, m, "2\\^31", dry_run_ranks=1 << 28)
+    b8 = arb.Plan(m, dry_run_ranks=8).workspace_bytes()
+    b64 = arb.Plan(m, dry_run_ranks=64).workspace_bytes()
+    assert b64 - b8 >= 8 * 16 * 56        # one out-list offset per global gid
