@@ -62,8 +62,8 @@ FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
 # CV-step, and its DRAM bytes per CV-step, on the batched workload: from the ncu capture of
 # 40,000 cells (profiles/stream_kernel_batched_40000cells.md), which has the same cell-size
 # mix, synapse and HH densities per CV as the full 65,536-cell workload.
-STREAM_FP64_PER_CV_STEP = {"batched": 15.8}
-STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 123.5}
+STREAM_FP64_PER_CV_STEP = {"batched": 15.45}
+STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 122.0}
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
@@ -320,6 +320,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     ap.add_argument("--cells-per-pack", type=int, default=0)
+    ap.add_argument("--split-cvs", type=int, default=0,
+                    help="one cell per lane: spread cells above this many CVs over lanes (0: the library's choice)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-cells", type=int, default=4096, help="reference arm: cells sampled per step (0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -377,6 +379,8 @@ def main():
         sim_kw["epoch_overlap"] = True
     if args.dry_run_ranks > 1:
         sim_kw["dry_run_ranks"] = args.dry_run_ranks
+    if args.split_cvs:
+        sim_kw["split_cvs"] = args.split_cvs
     E_sim = 0 if args.epoch_overlap else E      # overlapped: the library halves the minimum delay
     tuned = None
     if args.cells_per_pack == 0 and args.workload != "batched" and not args.no_autotune:

@@ -32,7 +32,8 @@ struct PackDesc {
     int32_t stack;       // streamed packs: deepest per-lane hand-over stack (entries)
     int64_t c_off;       // streamed packs: offset of the pack's compact slots in Gm / Em
     int32_t nmb;         // streamed shared packs: mailbox slots (cross-lane hand-overs)
-    int32_t pad2;
+    int32_t nsc;         // streamed packs: compact slots [0, nsc) are the CVs with synapses,
+                         // whose terms the synapse pass writes whole (no read-modify-write)
 };
 
 // Pack modes: staged in shared memory (small batches, several cells share a warp), or

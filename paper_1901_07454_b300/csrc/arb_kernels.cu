@@ -443,12 +443,13 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
                                             const double* Vg, MT* gS, MT* mS, MT* hS, MT* nS, int lane, bool decay,
                                             bool update, int apply_step, bool terms, int& ev_i, int ev_end,
                                             int32_t& late, MT dt) {
+    const double* cE = d.cE + pk.c_off;
+    const double* cB = d.cB + pk.c_off;
     if (terms) {
         // implicit: the slots start from the constant diagonal and right-hand side of their
-        // entry, so the forward sweep adds nothing for them
-        const double* cE = d.cE + pk.c_off;
-        const double* cB = d.cB + pk.c_off;
-        for (int c = lane; c < pk.nvc; c += kWarp) {
+        // entry, so the forward sweep adds nothing for them. Slots [0, nsc) belong to CVs with
+        // synapses and are written whole by the synapse pass below.
+        for (int c = pk.nsc + lane; c < pk.nvc; c += kWarp) {
             if (kImp) {
                 Gm[c] = __ldg(cE + c);
                 Em[c] = __ldg(cB + c);
@@ -469,36 +470,50 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         n_w = r.w;
     }
     // synapses of one CV are consecutive on one lane: their terms are summed in registers and
-    // stored once per CV. Rows are fetched kSP ahead so that no load is waited for in the row
+    // the CV's slot is written once, starting from its constants (implicit scheme). Rows are
+    // fetched kSP ahead, their slot index 2 kSP ahead, so that no load is waited for in the row
     // that issued it.
-    constexpr int kSP = 4;
+    constexpr int kSP = 1;
     int cur = -1;
-    double gsum = 0.0, esum = 0.0;
-    int s_sl[kSP], s_c[kSP];
-    double s_dec[kSP], s_e[kSP], s_sc[kSP];
+    double gsum = 0.0, esum = 0.0, cur_e = 0.0, cur_b = 0.0;
+    int s_sl[kSP], s_c[kSP], s_cn[kSP];
+    double s_dec[kSP], s_e[kSP], s_sc[kSP], s_ce[kSP], s_cb[kSP];
     MT s_g[kSP];
-    auto sfetch = [&](int js, int u) {
+    auto sfetch_c = [&](int js) {
+        return js < pk.nsyn_row ? __ldg(d.syn_vs + (size_t)(pk.syn_row0 + js) * kWarp + lane) : -1;
+    };
+    auto sfetch = [&](int js, int u, int c) {
         const bool in = js < pk.nsyn_row;
         const size_t q = (size_t)(pk.syn_row0 + (in ? js : 0)) * kWarp + lane;
-        s_sl[u] = in ? __ldg(d.syn_slot + q) : -1;
-        s_c[u] = in ? __ldg(d.syn_vs + q) : -1;
+        s_c[u] = c;
+        s_sl[u] = (in && !kImp) ? __ldg(d.syn_slot + q) : -1;
         s_dec[u] = in ? __ldg(d.syn_decay + q) : 1.0;
         s_e[u] = in ? __ldg(d.syn_e + q) : 0.0;
         s_sc[u] = (in && !kImp) ? __ldg(d.syn_sc + q) : 0.0;
         s_g[u] = in ? gS[(in ? js : 0) * kWarp + lane] : (MT)0;
+        s_ce[u] = (kImp && terms && c >= 0) ? __ldg(cE + c) : 0.0;
+        s_cb[u] = (kImp && terms && c >= 0) ? __ldg(cB + c) : 0.0;
     };
+    {
+        int c0[kSP];
 #pragma unroll
-    for (int u = 0; u < kSP; ++u) sfetch(u, u);
+        for (int u = 0; u < kSP; ++u) c0[u] = sfetch_c(u);
+#pragma unroll
+        for (int u = 0; u < kSP; ++u) s_cn[u] = sfetch_c(kSP + u);
+#pragma unroll
+        for (int u = 0; u < kSP; ++u) sfetch(u, u, c0[u]);
+    }
     for (int jb = 0; jb < pk.nsyn_row; jb += kSP) {
 #pragma unroll
         for (int u = 0; u < kSP; ++u) {
             const int js = jb + u;
             if (js >= pk.nsyn_row) break;
             const int sl = s_sl[u], c = s_c[u];
-            const double dec = s_dec[u], esyn = s_e[u], sc = s_sc[u];
+            const double dec = s_dec[u], esyn = s_e[u], sc = s_sc[u], c_e = s_ce[u], c_b = s_cb[u];
             MT g = s_g[u];
-            sfetch(js + kSP, u);
-            if (sl < 0) continue;
+            sfetch(js + kSP, u, s_cn[u]);         // row js + kSP: its slot index is ready
+            s_cn[u] = sfetch_c(js + 2 * kSP);     // slot index of row js + 2 kSP
+            if (c < 0) continue;                  // padding
             if (decay) g = g * (MT)dec;
             while (n_step == apply_step && n_js == js) {
                 g = g + (MT)n_w;
@@ -517,13 +532,15 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
                 if (c != cur) {
                     if (cur >= 0) {
                         if (kImp) {
-                            Gm[cur] += gsum;
-                            Em[cur] += esum;
+                            Gm[cur] = cur_e + gsum;
+                            Em[cur] = cur_b + esum;
                         } else {
                             Em[cur] = esum;
                         }
                     }
                     cur = c;
+                    cur_e = c_e;
+                    cur_b = c_b;
                     gsum = 0.0;
                     esum = 0.0;
                 }
@@ -540,8 +557,8 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     }
     if (terms && cur >= 0) {
         if (kImp) {
-            Gm[cur] += gsum;
-            Em[cur] += esum;
+            Gm[cur] = cur_e + gsum;
+            Em[cur] = cur_b + esum;
         } else {
             Em[cur] = esum;
         }
@@ -582,7 +599,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
 }
 
 #ifndef ARB_STREAM_PF
-#define ARB_STREAM_PF 3
+#define ARB_STREAM_PF 1
 #endif
 #ifndef ARB_STREAM_PB
 #define ARB_STREAM_PB 6

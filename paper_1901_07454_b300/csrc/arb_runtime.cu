@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <functional>
 #include <cmath>
@@ -1377,9 +1378,9 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         // compact mechanism slots; stack depths (one cell per lane) and the round rule of the
         // mailbox (cells over several lanes)
         std::vector<char> mech(ncv, 0);
-        for (int64_t cv : sim->syn_cv) mech[cv] = 1;
         for (int64_t cv : sim->hh_cv) mech[cv] = 1;
         for (int64_t cv : sim->st_cv) mech[cv] = 1;
+        for (int64_t cv : sim->syn_cv) mech[cv] = 2;     // 2: the CV has synapses
         int64_t c_total = 0;
         int32_t max_depth = 1, max_mb = 0;
         pl.slot_lo.assign((size_t)npk * kWarp, 0);
@@ -1391,19 +1392,27 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             PackDesc& pd = pl.packs[pi];
             const int64_t base = (int64_t)pd.row0 * kWarp;
             int32_t nvc = 0;
+            // mechanism entries are marked -3 (with synapses) or -2 (without), then numbered
             for (int32_t c : sg[pi].cells)
                 for (int64_t cv = sim->cv_offset[c]; cv < sim->cv_offset[c + 1]; ++cv)
-                    if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = 0;
+                    if (mech[cv]) pl.vmap[pl.cv_tile[cv]] = mech[cv] == 2 ? -3 : -2;
+            pd.nsc = 0;
             if (!sim->exact) {
+                // CVs with synapses first: the synapse pass writes their slots' terms whole
                 for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
-                    if (pl.vmap[t] >= 0) pl.vmap[t] = nvc++;
+                    if (pl.vmap[t] == -3) pl.vmap[t] = nvc++;
+                pd.nsc = nvc;
+                for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
+                    if (pl.vmap[t] == -2) pl.vmap[t] = nvc++;
             } else {
+                for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
+                    if (pl.vmap[t] < -1) pl.vmap[t] = -2;
                 // lane by lane, so that each lane's slots are one range of its own
                 for (int l = 0; l < kWarp; ++l) {
                     pl.slot_lo[(size_t)pi * kWarp + l] = nvc;
                     for (int32_t j = 0; j < pd.nrow; ++j) {
                         const int64_t t = base + (int64_t)j * kWarp + l;
-                        if (pl.vmap[t] >= 0) pl.vmap[t] = nvc++;
+                        if (pl.vmap[t] == -2) pl.vmap[t] = nvc++;
                     }
                     pl.slot_hi[(size_t)pi * kWarp + l] = nvc;
                 }
@@ -1523,6 +1532,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         pl.st_slot.assign(st_rows * kWarp, -1); pl.st_sc.assign(st_rows * kWarp, 0.0);
         pl.st_on.assign(st_rows * kWarp, 0.0); pl.st_off.assign(st_rows * kWarp, 0.0); pl.st_amp.assign(st_rows * kWarp, 0.0);
         pl.det_slot.assign((size_t)npk * kWarp, -1); pl.det_gid.assign((size_t)npk * kWarp, -1);
+        std::atomic<int> slot_err{0};
         parallel_for(npk, [&](int64_t pi) {          // packs own their rows and instances
             const PackDesc& pd = pl.packs[pi];
             const int64_t base = (int64_t)pd.row0 * kWarp;
@@ -1534,6 +1544,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     const int64_t cv = sim->u_cv[i];
                     pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
                     pl.syn_vs[q] = pl.vmap[pl.cv_tile[cv]];
+                    if (!sim->exact && (pl.syn_vs[q] < 0 || pl.syn_vs[q] >= pd.nsc)) slot_err = 1;
                     pl.syn_e[q] = sim->u_e[i];
                     pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
                     pl.syn_ntau[q] = -1.0 / sim->u_tau[i];
@@ -1580,6 +1591,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 pl.det_gid[(size_t)pi * kWarp + dd] = sg[pi].cells[dd];
             }
         });
+        if (slot_err) return bad("internal error: a synapse slot outside the pack's synapse slots");
     } else {
     if (groups.empty() && nc > 0) build_k(kpp, groups);
     {   // per-warp tile: the largest shared-memory pack's need, so that more warps fit an SM
