@@ -269,6 +269,18 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
 enum { ARB_FN_EXP = 0, ARB_FN_EXPM1 = 1, ARB_FN_HH_RATES = 2 };
 arb_status arb_math_eval(int32_t fn, int64_t n, const double* x, double* y, void* stream);
 
+/* The tabulated HH gate update that the streamed FP64 kernel uses for steps of fixed length dt
+ * (ms): host-only, for validation. The exact update of a gate at frozen V (Sec. "Model":
+ * channel states advanced with the new voltage) is x' = x_inf + (x - x_inf) e with
+ * x_inf = alpha/(alpha + beta) and e = exp(-dt (alpha + beta)); these six functions of V (for m,
+ * h and n: m_inf, e_m, h_inf, e_h, n_inf, e_n) are cubic on each interval
+ * [v_lo + i/per_mv, v_lo + (i+1)/per_mv), i < n_intervals: coef[24 i + 4 q + k] is the
+ * coefficient of s^k of function q, s = (V - v_lo) per_mv - i. Outside the range the kernel
+ * evaluates the rates directly. With coef = NULL (or cap too small) only the three sizes are
+ * returned; cap counts doubles. dt must be finite and > 0 (else ARB_E_ARG). */
+arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_intervals, double* v_lo,
+                             double* per_mv);
+
 /* Message of the last failing call on this handle; with NULL, of the last failing call on
  * this thread that has no handle (arb_create, arb_solve_trees_noalloc, arb_math_eval). */
 const char* arb_last_error(const arb_sim* sim);

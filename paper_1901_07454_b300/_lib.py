@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "ARB_OK", -1: "ARB_E_ARG", -2: "ARB_E_CUDA", -3: "ARB_E_OVERF
 # Every symbol declared in include/arb.h.
 EXPORTED = ["arb_default_params", "arb_create", "arb_destroy", "arb_workspace_bytes", "arb_bind_workspace",
             "arb_enqueue_events", "arb_advance", "arb_time", "arb_read_voltage", "arb_num_spikes",
-            "arb_read_spikes", "arb_read_spikes_from", "arb_set_probes", "arb_get_state", "arb_set_state", "arb_plan_info",
+            "arb_read_spikes", "arb_read_spikes_from", "arb_hh_gate_table", "arb_set_probes", "arb_get_state", "arb_set_state", "arb_plan_info",
             "arb_last_timing", "arb_last_error", "arb_solve_trees_noalloc", "arb_adjoint_workspace_bytes",
             "arb_adjoint", "arb_math_eval"]
 
@@ -77,6 +77,7 @@ def load():
         "arb_num_spikes": (i32, [vp, C.POINTER(i64)]),
         "arb_read_spikes": (i32, [vp, vp, vp, i64, C.POINTER(i64)]),
         "arb_read_spikes_from": (i32, [vp, i64, vp, vp, i64, C.POINTER(i64)]),
+        "arb_hh_gate_table": (i32, [dbl, vp, i64, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
         "arb_set_probes": (i32, [vp, i64, vp, vp, i64]),
         "arb_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
         "arb_set_state": (i32, [vp, vp, vp, vp, vp, vp]),

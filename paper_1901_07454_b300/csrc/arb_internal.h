@@ -106,6 +106,17 @@ struct Ctl {
     int32_t pad_x;
 };
 
+// Tabulated HH gate update (streamed packs, FP64, steps of fixed dt): for V in
+// [kHHTabVlo, kHHTabVlo + kHHTabN / kHHTabPerMV) mV the six functions of V that the exact gate
+// update x' = x_inf + (x - x_inf) e needs, x_inf = alpha / (alpha + beta) and
+// e = exp(-dt (alpha + beta)) for the gates m, h and n, are cubic polynomials in
+// s = (V - V_i) kHHTabPerMV on each interval [V_i, V_i + 1 / kHHTabPerMV): 24 coefficients per
+// interval, function-major (m_inf, e_m, h_inf, e_h, n_inf, e_n), each c0 + c1 s + c2 s^2 + c3 s^3.
+constexpr double kHHTabVlo = -128.0;
+constexpr double kHHTabPerMV = 256.0;
+constexpr int32_t kHHTabN = 192 * 256;
+constexpr int32_t kHHTabStride = 24;
+
 enum : int32_t {
     kStSpikeOverflow = 1,
     kStPoolOverflow = 2,
@@ -153,6 +164,7 @@ struct DevModel {
     const int32_t* hh_slot;
     const int32_t* hh_vs;
     const double* hh_sc;
+    const double* hh_tab;     // tabulated gate update ([kHHTabN][24]), or null: rates evaluated
     const double* hh_gna;     // uS
     const double* hh_gk;      // uS
     MT* hh_m;

@@ -573,10 +573,32 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         const MT v = (MT)vd;
         MT m = mS[idx], h = hS[idx], n = nS[idx];
         if (update) {
-            const auto r = hh_rates(v);
-            m = gate(m, r.am, r.bm, dt);
-            h = gate(h, r.ah, r.bh, dt);
-            n = gate(n, r.an, r.bn, dt);
+            bool done = false;
+            if constexpr (std::is_same<MT, double>::value) {
+                // x_inf and exp(-dt (alpha + beta)) of the three gates from the table
+                const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
+                if (d.hh_tab != nullptr && tv >= 0.0 && tv < (double)kHHTabN) {
+                    const int it = (int)tv;
+                    const double s = tv - (double)it;
+                    const double2* c = reinterpret_cast<const double2*>(d.hh_tab + (size_t)it * kHHTabStride);
+                    double f[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
+                        f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
+                    }
+                    m = fma(m - f[0], f[1], f[0]);
+                    h = fma(h - f[2], f[3], f[2]);
+                    n = fma(n - f[4], f[5], f[4]);
+                    done = true;
+                }
+            }
+            if (!done) {
+                const auto r = hh_rates(v);
+                m = gate(m, r.am, r.bm, dt);
+                h = gate(h, r.ah, r.bh, dt);
+                n = gate(n, r.an, r.bn, dt);
+            }
             mS[idx] = m;
             hS[idx] = h;
             nS[idx] = n;

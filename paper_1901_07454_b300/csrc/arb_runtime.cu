@@ -163,6 +163,7 @@ struct arb_sim {
     // ---- prepared data
     Plan plan;
     std::vector<double> init_m, init_h, init_n;   // HH initial gates, model order
+    hvec<double> hh_tab;                          // tabulated gate update (streamed FP64 plans)
     // connections grouped by source
     std::vector<int64_t> out_ptr;
     std::vector<int32_t> out_syn, out_idx;
@@ -264,6 +265,60 @@ void hh_steady(double v, double& m, double& h, double& n) {
     m = am / (am + bm);
     h = ah / (ah + bh);
     n = an / (an + bn);
+}
+
+// The tabulated gate update (see kHHTabVlo): at every node V_i the six functions and their
+// derivatives in V, from the rate formulas and their derivatives in long double; on each
+// interval the cubic with those values and slopes at both ends (Hermite), whose error is
+// h^4/384 max|f^(4)| (h = 1/256 mV: below 1e-17 for these functions), written as
+// c0 + c1 s + c2 s^2 + c3 s^3 with s = (V - V_i)/h.
+void build_hh_table(double dt, double* tab) {
+    typedef long double LD;
+    const int64_t nn = (int64_t)kHHTabN + 1;
+    std::vector<LD> f((size_t)nn * 6), g((size_t)nn * 6);       // values, h * slopes
+    const LD h = 1.0L / (LD)kHHTabPerMV;
+    parallel_for(nn, [&](int64_t i) {
+        const LD v = (LD)kHHTabVlo + (LD)i * h;
+        // x / (e^x - 1) and its derivative; the Bernoulli series where |x| < 1e-3
+        auto exr = [](LD x, LD& dx) {
+            if (fabsl(x) < 1e-3L) {
+                const LD x2 = x * x;
+                dx = -0.5L + x / 6.0L - x * x2 / 180.0L;
+                return 1.0L - x / 2.0L + x2 / 12.0L - x2 * x2 / 720.0L;
+            }
+            const LD em = expm1l(x);
+            dx = (em - x * (em + 1.0L)) / (em * em);
+            return x / em;
+        };
+        LD d1, d2;
+        const LD am = exr(-(v + 40.0L) / 10.0L, d1), dam = -0.1L * d1;
+        const LD bm = 4.0L * expl(-(v + 65.0L) / 18.0L), dbm = -bm / 18.0L;
+        const LD ah = 0.07L * expl(-(v + 65.0L) / 20.0L), dah = -ah / 20.0L;
+        const LD eh = expl(-(v + 35.0L) / 10.0L);
+        const LD bh = 1.0L / (1.0L + eh), dbh = 0.1L * eh * bh * bh;
+        const LD an = 0.1L * exr(-(v + 55.0L) / 10.0L, d2), dan = -0.01L * d2;
+        const LD bn = 0.125L * expl(-(v + 65.0L) / 80.0L), dbn = -bn / 80.0L;
+        const LD a[3] = {am, ah, an}, b[3] = {bm, bh, bn}, da[3] = {dam, dah, dan}, db[3] = {dbm, dbh, dbn};
+        for (int q = 0; q < 3; ++q) {
+            const LD s = a[q] + b[q], ds = da[q] + db[q];
+            const LD e = expl(-(LD)dt * s);
+            f[(size_t)i * 6 + 2 * q] = a[q] / s;
+            g[(size_t)i * 6 + 2 * q] = h * (da[q] * s - a[q] * ds) / (s * s);
+            f[(size_t)i * 6 + 2 * q + 1] = e;
+            g[(size_t)i * 6 + 2 * q + 1] = h * (-(LD)dt * ds * e);
+        }
+    });
+    parallel_for(kHHTabN, [&](int64_t i) {
+        for (int q = 0; q < 6; ++q) {
+            const LD f0 = f[(size_t)i * 6 + q], f1 = f[(size_t)(i + 1) * 6 + q];
+            const LD g0 = g[(size_t)i * 6 + q], g1 = g[(size_t)(i + 1) * 6 + q];
+            double* c = tab + (size_t)i * kHHTabStride + 4 * q;
+            c[0] = (double)f0;
+            c[1] = (double)g0;
+            c[2] = (double)(3.0L * (f1 - f0) - 2.0L * g0 - g1);
+            c[3] = (double)(2.0L * (f0 - f1) + g0 + g1);
+        }
+    });
 }
 
 // Per-CV membrane area (um^2), capacitance (nF) and axial conductance to the parent (uS):
@@ -519,6 +574,7 @@ static void layout_regions(arb_sim* sim) {
         {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
         {"syn_e", 8 * pl.syn_rows * kWarp}, {"syn_decay", 8 * pl.syn_rows * kWarp}, {"syn_sc", 8 * pl.syn_rows * kWarp},
         {"syn_ntau", 8 * pl.syn_rows * kWarp}, {"slot_lo", 4 * std::max<int64_t>(nowner, 1)}, {"slot_hi", 4 * std::max<int64_t>(nowner, 1)},
+        {"hh_tab", 8 * std::max<int64_t>((int64_t)sim->hh_tab.size(), 1)},
         {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_vs", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
         {"hh_gk", 8 * pl.hh_rows * kWarp}, {"hh_m", mt * pl.hh_rows * kWarp}, {"hh_h", mt * pl.hh_rows * kWarp},
         {"hh_n", mt * pl.hh_rows * kWarp},
@@ -580,6 +636,7 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.pslot = (const int32_t*)region(sim, "pslot");
     d.vmap = (const int32_t*)region(sim, "vmap");
     d.V = (double*)region(sim, "V");
+    d.hh_tab = sim->hh_tab.empty() ? nullptr : (const double*)region(sim, "hh_tab");
     d.Sg = (double*)region(sim, "Sg");
     d.Rg = (double*)region(sim, "Rg");
     d.Gm = (double*)region(sim, "Gm");
@@ -629,6 +686,16 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
 // C ABI
 
 extern "C" {
+
+arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_intervals, double* v_lo,
+                             double* per_mv) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return ARB_E_ARG;
+    if (n_intervals) *n_intervals = kHHTabN;
+    if (v_lo) *v_lo = kHHTabVlo;
+    if (per_mv) *per_mv = kHHTabPerMV;
+    if (coef && cap >= (int64_t)kHHTabN * kHHTabStride) build_hh_table(dt, coef);
+    return ARB_OK;
+}
 
 arb_status arb_default_params(arb_params* p) {
     if (!p) return ARB_E_ARG;
@@ -1832,6 +1899,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         double mi, hi, ni;
         hh_steady(-65.0, mi, hi, ni);
         sim->init_m.assign(sim->hh_cv.size(), mi);
+        // streamed FP64 packs with steps of fixed length take the gate update from a table
+        if (pl.stream && !sim->mixed && !sim->exact && !sim->hh_cv.empty()) {
+            sim->hh_tab.resize((size_t)kHHTabN * kHHTabStride);
+            build_hh_table(p.dt, sim->hh_tab.data());
+        }
         sim->init_h.assign(sim->hh_cv.size(), hi);
         sim->init_n.assign(sim->hh_cv.size(), ni);
     }
@@ -2016,6 +2088,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("cE", pl.cE); UP("cB", pl.cB);
     UP("syn_ntau", pl.syn_ntau); UP("slot_lo", pl.slot_lo); UP("slot_hi", pl.slot_hi);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
+    if (!sim->hh_tab.empty()) UP("hh_tab", sim->hh_tab);
     UP("hh_slot", pl.hh_slot); UP("hh_vs", pl.hh_vs); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
     UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
     UP("det_slot", pl.det_slot); UP("det_gid", pl.det_gid);
