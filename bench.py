@@ -62,8 +62,8 @@ FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
 # CV-step, and its DRAM bytes per CV-step, on the batched workload: from the ncu capture of
 # 40,000 cells (profiles/stream_kernel_batched_40000cells.md), which has the same cell-size
 # mix, synapse and HH densities per CV as the full 65,536-cell workload.
-STREAM_FP64_PER_CV_STEP = {"batched": 15.45}
-STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 122.0}
+STREAM_FP64_PER_CV_STEP = {"batched": 12.55}
+STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 121.8}
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
