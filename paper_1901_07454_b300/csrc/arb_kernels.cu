@@ -87,6 +87,26 @@ __device__ __forceinline__ void syn_pass(const DevModel<MT>& d, const PackDesc& 
 
 // Hodgkin-Huxley: gate update with the new voltage, then the Na and K terms of the next
 // step (the leak is constant and sits in the constants of the entry).
+// Gate update of one HH instance from the tabulated x_inf and exp(-dt (alpha + beta)) (see
+// kHHTabVlo); false when there is no table or V lies outside it.
+__device__ __forceinline__ bool hh_gates_tab(const double* tab, double vd, double& m, double& h, double& n) {
+    const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
+    if (tab == nullptr || !(tv >= 0.0 && tv < (double)kHHTabN)) return false;
+    const int it = (int)tv;
+    const double s = tv - (double)it;
+    const double2* c = reinterpret_cast<const double2*>(tab + (size_t)it * kHHTabStride);
+    double f[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
+        f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
+    }
+    m = fma(m - f[0], f[1], f[0]);
+    h = fma(h - f[2], f[3], f[2]);
+    n = fma(n - f[4], f[5], f[4]);
+    return true;
+}
+
 template <class MT, bool kSmem, bool kImp>
 __device__ __forceinline__ void hh_pass(const DevModel<MT>& d, const PackDesc& pk, const Work<MT>& w, int lane,
                                         bool update, bool current, MT dt) {
@@ -100,10 +120,14 @@ __device__ __forceinline__ void hh_pass(const DevModel<MT>& d, const PackDesc& p
         const MT v = (MT)vd;
         MT m = w.m[idx], h = w.h[idx], n = w.n[idx];
         if (update) {
-            const auto r = hh_rates(v);
-            m = gate(m, r.am, r.bm, dt);
-            h = gate(h, r.ah, r.bh, dt);
-            n = gate(n, r.an, r.bn, dt);
+            bool done = false;
+            if constexpr (std::is_same<MT, double>::value) done = hh_gates_tab(d.hh_tab, vd, m, h, n);
+            if (!done) {
+                const auto r = hh_rates(v);
+                m = gate(m, r.am, r.bm, dt);
+                h = gate(h, r.ah, r.bh, dt);
+                n = gate(n, r.an, r.bn, dt);
+            }
             w.m[idx] = m;
             w.h[idx] = h;
             w.n[idx] = n;
@@ -574,25 +598,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         MT m = mS[idx], h = hS[idx], n = nS[idx];
         if (update) {
             bool done = false;
-            if constexpr (std::is_same<MT, double>::value) {
-                // x_inf and exp(-dt (alpha + beta)) of the three gates from the table
-                const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
-                if (d.hh_tab != nullptr && tv >= 0.0 && tv < (double)kHHTabN) {
-                    const int it = (int)tv;
-                    const double s = tv - (double)it;
-                    const double2* c = reinterpret_cast<const double2*>(d.hh_tab + (size_t)it * kHHTabStride);
-                    double f[6];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
-                        f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
-                    }
-                    m = fma(m - f[0], f[1], f[0]);
-                    h = fma(h - f[2], f[3], f[2]);
-                    n = fma(n - f[4], f[5], f[4]);
-                    done = true;
-                }
-            }
+            if constexpr (std::is_same<MT, double>::value) done = hh_gates_tab(d.hh_tab, vd, m, h, n);
             if (!done) {
                 const auto r = hh_rates(v);
                 m = gate(m, r.am, r.bm, dt);

@@ -1899,8 +1899,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         double mi, hi, ni;
         hh_steady(-65.0, mi, hi, ni);
         sim->init_m.assign(sim->hh_cv.size(), mi);
-        // streamed FP64 packs with steps of fixed length take the gate update from a table
-        if (pl.stream && !sim->mixed && !sim->exact && !sim->hh_cv.empty()) {
+        // FP64 mechanisms with steps of fixed length take the gate update from a table
+        if (!sim->mixed && !sim->exact && !sim->hh_cv.empty()) {
             sim->hh_tab.resize((size_t)kHHTabN * kHHTabStride);
             build_hh_table(p.dt, sim->hh_tab.data());
         }
