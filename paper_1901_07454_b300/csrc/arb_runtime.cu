@@ -243,6 +243,22 @@ void parallel_for(int64_t n, F fn) {
     for (auto& x : th) x.join();
 }
 
+// Runs fn(t, nt) for t in [0, nt) on nt host threads, nt = min(hardware threads, max_tasks):
+// for work split into a few large, balanced parts.
+template <class F>
+void run_tasks(int64_t max_tasks, F fn) {
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int64_t nt = std::max<int64_t>(1, std::min(hw, max_tasks));
+    if (nt == 1) {
+        fn((int64_t)0, (int64_t)1);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (int64_t t = 0; t < nt; ++t) th.emplace_back([&, t] { fn(t, nt); });
+    for (auto& x : th) x.join();
+}
+
 // v = n copies of val, written in parallel.
 template <class T, class A>
 void par_assign(std::vector<T, A>& v, int64_t n, T val) {
@@ -905,15 +921,43 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     sim->dry_ranks = std::max<int64_t>(1, p.dry_run_ranks);
     const int64_t n_src = (int64_t)nc * sim->dry_ranks;
     if (n_src > INT32_MAX) return bad("dry_run_ranks * n_cells must be < 2^31");
+    // checked in parallel parts; the first failing connection (lowest index) is reported
     double dmin = INFINITY;
-    for (int64_t i = 0; i < ncon; ++i) {
-        if (sim->conn_src[i] < 0 || sim->conn_src[i] >= n_src)
+    {
+        const int64_t max_t = ncon >= (1 << 20) ? 16 : 1;
+        std::vector<int64_t> bad_at(max_t, ncon);
+        std::vector<int> bad_kind(max_t, 0);
+        std::vector<double> part_min(max_t, INFINITY);
+        run_tasks(max_t, [&](int64_t t, int64_t nt) {
+            const int64_t lo = ncon * t / nt, hi = ncon * (t + 1) / nt;
+            double mn = INFINITY;
+            for (int64_t i = lo; i < hi; ++i) {
+                int k = 0;
+                if (sim->conn_src[i] < 0 || sim->conn_src[i] >= n_src) k = 1;
+                else if (sim->conn_dst[i] < 0 || sim->conn_dst[i] >= m->n_syn) k = 2;
+                else if (!finite_pos(sim->conn_delay[i])) k = 3;
+                else if (!std::isfinite(sim->conn_w[i])) k = 4;
+                if (k) {
+                    bad_at[t] = i;
+                    bad_kind[t] = k;
+                    break;
+                }
+                mn = std::min(mn, sim->conn_delay[i]);
+            }
+            part_min[t] = mn;
+        });
+        int64_t first = ncon;
+        int kind = 0;
+        for (int64_t t = 0; t < max_t; ++t) {
+            if (bad_at[t] < first) { first = bad_at[t]; kind = bad_kind[t]; }
+            dmin = std::min(dmin, part_min[t]);
+        }
+        if (kind == 1)
             return bad(sim->dry_ranks > 1 ? "connection source gid out of range (dry run: < dry_run_ranks * n_cells)"
                                           : "connection source gid out of range");
-        if (sim->conn_dst[i] < 0 || sim->conn_dst[i] >= m->n_syn) return bad("connection target synapse out of range");
-        if (!finite_pos(sim->conn_delay[i])) return bad("connection delays must be finite and > 0");
-        if (!std::isfinite(sim->conn_w[i])) return bad("connection weights must be finite");
-        dmin = std::min(dmin, sim->conn_delay[i]);
+        if (kind == 2) return bad("connection target synapse out of range");
+        if (kind == 3) return bad("connection delays must be finite and > 0");
+        if (kind == 4) return bad("connection weights must be finite");
     }
     // epoch: no longer than the minimum delay (Sec. "Model": a positive minimum delay lets
     // cells advance independently over that interval)
@@ -1911,21 +1955,44 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     // connection index
     const int64_t n_out = (int64_t)nc * sim->dry_ranks;
     sim->out_ptr.assign(n_out + 1, 0);
-    for (int64_t i = 0; i < ncon; ++i) sim->out_ptr[sim->conn_src[i] + 1]++;
-    for (int64_t c = 0; c < n_out; ++c) sim->out_ptr[c + 1] += sim->out_ptr[c];
     sim->out_syn.resize(ncon);
     sim->out_idx.resize(ncon);
     sim->out_delay.resize(ncon);
     sim->out_w.resize(ncon);
-    {
-        std::vector<int64_t> fill(sim->out_ptr.begin(), sim->out_ptr.end() - 1);
-        for (int64_t i = 0; i < ncon; ++i) {
-            const int64_t q = fill[sim->conn_src[i]]++;
-            sim->out_syn[q] = (int32_t)sim->conn_dst[i];
-            sim->out_idx[q] = (int32_t)i;
-            sim->out_delay[q] = sim->conn_delay[i];
-            sim->out_w[q] = sim->conn_w[i];
+    auto put = [&](int64_t q, int64_t i) {
+        sim->out_syn[q] = (int32_t)sim->conn_dst[i];
+        sim->out_idx[q] = (int32_t)i;
+        sim->out_delay[q] = sim->conn_delay[i];
+        sim->out_w[q] = sim->conn_w[i];
+    };
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>(16, hw);
+    if (ncon >= (1 << 20) && nt > 1 && n_out * nt <= ((int64_t)1 << 26)) {
+        // counting sort in nt contiguous parts: part t's connections of a source follow those
+        // of parts < t, so each source's list stays in ascending connection index
+        std::vector<int64_t> cnt((size_t)(nt * n_out), 0);
+        run_tasks(nt, [&](int64_t t, int64_t k) {
+            int64_t* c = cnt.data() + t * n_out;
+            for (int64_t i = ncon * t / k; i < ncon * (t + 1) / k; ++i) c[sim->conn_src[i]]++;
+        });
+        for (int64_t s = 0; s < n_out; ++s) {
+            int64_t run = sim->out_ptr[s];
+            for (int64_t t = 0; t < nt; ++t) {
+                const int64_t x = cnt[t * n_out + s];
+                cnt[t * n_out + s] = run;
+                run += x;
+            }
+            sim->out_ptr[s + 1] = run;
         }
+        run_tasks(nt, [&](int64_t t, int64_t k) {
+            int64_t* c = cnt.data() + t * n_out;
+            for (int64_t i = ncon * t / k; i < ncon * (t + 1) / k; ++i) put(c[sim->conn_src[i]]++, i);
+        });
+    } else {
+        for (int64_t i = 0; i < ncon; ++i) sim->out_ptr[sim->conn_src[i] + 1]++;
+        for (int64_t c = 0; c < n_out; ++c) sim->out_ptr[c + 1] += sim->out_ptr[c];
+        std::vector<int64_t> fill(sim->out_ptr.begin(), sim->out_ptr.end() - 1);
+        for (int64_t i = 0; i < ncon; ++i) put(fill[sim->conn_src[i]]++, i);
     }
     *out = sim;
     return ARB_OK;
