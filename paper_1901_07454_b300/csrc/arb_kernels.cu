@@ -1447,9 +1447,11 @@ __global__ void __launch_bounds__(256) k_ev_sort_long(EvArgs a) {
 // epoch integrates and records further spikes. In a dry run (Sec. "Scalability") the global
 // spike list holds every local spike once per virtual rank r, as gid + r * n_cells.
 __global__ void k_spike_expand(SpkArgs a) {
-    // 32 spikes per warp iteration, one lookup of the out-list per lane; then the warp takes the
-    // spikes with connections one at a time: lane 0 reserves the whole fan-out in the pending
-    // pool with one atomic, the lanes write its events
+    // per warp iteration, one spike (few spikes: every warp gets one, and a spike's fan-out is
+    // written by all 32 lanes) or 32 spikes with one out-list lookup per lane (many spikes, as
+    // in a dry run, where most have no local connection); then the warp takes the spikes with
+    // connections one at a time: lane 0 reserves the whole fan-out in the pending pool with one
+    // atomic, the lanes write its events
     Ctl* c = a.ctl;
     const int par = c->parity;
     const int64_t k_first = c->kp0;               // earliest step whose lists are not built yet
@@ -1460,12 +1462,13 @@ __global__ void k_spike_expand(SpkArgs a) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     PendEv* out = par ? a.pool[1] : a.pool[0];
-    for (int64_t i0 = warp * 32; i0 < n_glob; i0 += nwarps * 32) {
+    const int per = n_glob >= nwarps * 32 ? 32 : 1;     // spikes per warp iteration
+    for (int64_t i0 = warp * per; i0 < n_glob; i0 += nwarps * per) {
         const int64_t i = i0 + lane;
         int32_t my_gid = 0;
         double my_ts = 0.0;
         int64_t my_q0 = 0, my_deg = 0;
-        if (i < n_glob) {
+        if (lane < per && i < n_glob) {
             const int64_t r = i / n_local, j = lo + (i - r * n_local);
             my_gid = (int32_t)(a.spk_gid[j] + r * a.n_cells);
             my_ts = a.spk_t[j];
