@@ -173,3 +173,25 @@ def test_dry_run_sources_and_validation(arb):
     b8 = arb.Plan(m, dry_run_ranks=8).workspace_bytes()
     b64 = arb.Plan(m, dry_run_ranks=64).workspace_bytes()
     assert b64 - b8 >= 8 * 16 * 56        # one out-list offset per global gid
+
+
+def test_connection_checks_report_the_first_failing_connection(arb):
+    # more than 2^20 connections: checked in parallel parts, and the lowest failing index
+    # decides the message, as a serial check would
+    m = small_tree_model(3, n_cells=2, n_branches=4, cv_range=(2, 4), n_syn=2)
+    n = (1 << 20) + 7
+    m.conn_src = np.zeros(n, np.int32)
+    m.conn_dst_syn = np.zeros(n, np.int64)
+    m.conn_delay = np.full(n, 1.0)
+    m.conn_weight = np.full(n, 0.01)
+    m.__post_init__()
+    assert arb.Plan(m).plan_info()["epoch_steps"] == 40
+    m.conn_delay[700001] = -1.0
+    m.conn_src[900000] = 5
+    _expect_error(arb, m, "delays must be finite and > 0")
+    m.conn_src[600000] = 5
+    _expect_error(arb, m, "source gid out of range")
+    m.conn_src[:] = 0
+    m.conn_delay[:] = 1.0
+    m.conn_weight[n - 1] = np.nan
+    _expect_error(arb, m, "weights must be finite")
