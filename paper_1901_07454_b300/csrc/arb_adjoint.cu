@@ -196,11 +196,28 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             Vd[i] = v;
             const int32_t j = a.hidx[i];
             if (j >= 0) {
-                if (mode == 0) {
+                Gates3 xg{Ys[j], Ys[nhh + j], Ys[2 * nhh + j]}, dvg, eg;
+                if (mode == 0 && hh_gates_tab(a.hh_tab, v, xg.m, xg.h, xg.n)) {
+                    Yd[j] = xg.m;
+                    Yd[nhh + j] = xg.h;
+                    Yd[2 * nhh + j] = xg.n;
+                } else if (mode == 0) {
                     const Rates r = hh_rates(v);
                     Yd[j] = gate(Ys[j], r.am, r.bm, a.dt);
                     Yd[nhh + j] = gate(Ys[nhh + j], r.ah, r.bh, a.dt);
                     Yd[2 * nhh + j] = gate(Ys[2 * nhh + j], r.an, r.bn, a.dt);
+                } else if (hh_gates_tab_dv(a.hh_tab, v, xg, dvg, eg)) {
+                    // from the table: the gate update, dPhi/dV and exp(-dt (alpha + beta))
+                    Yd[j] = xg.m;
+                    Yd[nhh + j] = xg.h;
+                    Yd[2 * nhh + j] = xg.n;
+                    double* G6 = segG + (s - s0) * 6 * nhh;
+                    G6[j] = dvg.m;
+                    G6[nhh + j] = dvg.h;
+                    G6[2 * nhh + j] = dvg.n;
+                    G6[3 * nhh + j] = eg.m;
+                    G6[4 * nhh + j] = eg.h;
+                    G6[5 * nhh + j] = eg.n;
                 } else {
                     // the gate update, and what the reverse sweep of this step needs from it:
                     // dPhi/dV and exp(-dt (alpha + beta)) of each gate

@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "arb_exp_table.h"
+#include "arb_internal.h"
 
 namespace arbk {
 
@@ -113,6 +114,56 @@ __device__ __forceinline__ float gate(float x, float a, float b, float dt) {
     const float s = a + b;
     const float xinf = a / s;
     return xinf + (x - xinf) * expf(-dt * s);
+}
+
+// Gate update of one HH instance from the tabulated x_inf and exp(-dt (alpha + beta)) (see
+// kHHTabVlo); false when there is no table or V lies outside it.
+__device__ __forceinline__ bool hh_gates_tab(const double* tab, double vd, double& m, double& h, double& n) {
+    const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
+    if (tab == nullptr || !(tv >= 0.0 && tv < (double)kHHTabN)) return false;
+    const int it = (int)tv;
+    const double s = tv - (double)it;
+    const double2* c = reinterpret_cast<const double2*>(tab + (size_t)it * kHHTabStride);
+    double f[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
+        f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
+    }
+    m = fma(m - f[0], f[1], f[0]);
+    h = fma(h - f[2], f[3], f[2]);
+    n = fma(n - f[4], f[5], f[4]);
+    return true;
+}
+
+// The same from the table, with what the reverse sweep of the adjoint needs: each gate x of
+// (m, h, n) becomes x_inf + (x - x_inf) e, with dx'/dV = x_inf' (1 - e) + (x - x_inf) e' (slopes
+// of the cubics) in dv and e in ef, in that order. False when there is no table or V lies
+// outside it.
+struct Gates3 { double m, h, n; };
+__device__ __forceinline__ bool hh_gates_tab_dv(const double* tab, double vd, Gates3& x, Gates3& dv, Gates3& ef) {
+    const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
+    if (tab == nullptr || !(tv >= 0.0 && tv < (double)kHHTabN)) return false;
+    const int it = (int)tv;
+    const double s = tv - (double)it;
+    const double2* c = reinterpret_cast<const double2*>(tab + (size_t)it * kHHTabStride);
+    double f[6], g[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
+        f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
+        g[q] = fma(fma(3.0 * hi.y, s, 2.0 * hi.x), s, lo.y) * kHHTabPerMV;
+    }
+    auto one = [&](double& xx, double& dd, double& ee, int q) {
+        const double xinf = f[2 * q], e = f[2 * q + 1], d = xx - xinf;
+        dd = fma(d, g[2 * q + 1], g[2 * q] * (1.0 - e));
+        ee = e;
+        xx = fma(d, e, xinf);
+    };
+    one(x.m, dv.m, ef.m, 0);
+    one(x.h, dv.h, ef.h, 1);
+    one(x.n, dv.n, ef.n, 2);
+    return true;
 }
 
 // ------------------------------------------------------------------------------------------

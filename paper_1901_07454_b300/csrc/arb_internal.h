@@ -272,6 +272,7 @@ struct AdjArgs {
     const double* gelin;       // [n_cv] passive conductance x reversal (nA)
     const double* area;        // [n_cv] um^2
     const int32_t* hidx;       // [n_cv] HH instance on the CV, -1 none
+    const double* hh_tab;      // tabulated gate update of the simulation's dt, or null
     const double* gna;         // [n_hh] uS
     const double* gk;
     const double* gl;

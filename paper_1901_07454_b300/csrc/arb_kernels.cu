@@ -87,26 +87,6 @@ __device__ __forceinline__ void syn_pass(const DevModel<MT>& d, const PackDesc& 
 
 // Hodgkin-Huxley: gate update with the new voltage, then the Na and K terms of the next
 // step (the leak is constant and sits in the constants of the entry).
-// Gate update of one HH instance from the tabulated x_inf and exp(-dt (alpha + beta)) (see
-// kHHTabVlo); false when there is no table or V lies outside it.
-__device__ __forceinline__ bool hh_gates_tab(const double* tab, double vd, double& m, double& h, double& n) {
-    const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
-    if (tab == nullptr || !(tv >= 0.0 && tv < (double)kHHTabN)) return false;
-    const int it = (int)tv;
-    const double s = tv - (double)it;
-    const double2* c = reinterpret_cast<const double2*>(tab + (size_t)it * kHHTabStride);
-    double f[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
-        f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
-    }
-    m = fma(m - f[0], f[1], f[0]);
-    h = fma(h - f[2], f[3], f[2]);
-    n = fma(n - f[4], f[5], f[4]);
-    return true;
-}
-
 template <class MT, bool kSmem, bool kImp>
 __device__ __forceinline__ void hh_pass(const DevModel<MT>& d, const PackDesc& pk, const Work<MT>& w, int lane,
                                         bool update, bool current, MT dt) {

@@ -2867,6 +2867,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.target = target;
     a.loss_scale = loss_scale;
     a.dt = dt;
+    a.hh_tab = sim->hh_tab.empty() ? nullptr : (const double*)region(sim, "hh_tab");
     a.k0 = sim->k;
     a.n_steps = n_steps;
     a.ckpt = checkpoint_every;
