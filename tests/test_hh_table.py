@@ -57,3 +57,28 @@ def test_table_pieces_join(table):
     end = coef.sum(axis=2)[:-1]
     start = coef[1:, :, 0]
     assert np.max(np.abs(end - start)) <= 1e-15
+
+
+def test_table_slopes_match_the_derivatives_of_the_gate_update(table, oracle_lib):
+    # the discrete adjoint takes dPhi/dV from the slopes of the cubics: x_inf' and e' against
+    # the same formed from the oracle's rate derivatives
+    coef, vlo, pm = table
+    dt = 0.025
+    rng = np.random.default_rng(7)
+    V = rng.uniform(vlo + 1e-6, vlo + coef.shape[0] / pm - 1e-6, 4000)
+    t = (V - vlo) * pm
+    i = np.floor(t).astype(np.int64)
+    s = (t - i)[:, None]
+    c = coef[i]
+    slope = (3.0 * c[..., 3] * s + 2.0 * c[..., 2]) * s + c[..., 1]
+    slope *= pm
+    ref = np.zeros_like(slope)
+    for k, v in enumerate(V):
+        r = oracle_lib.hh_rates(v)
+        dr = oracle_lib.hh_rate_derivs(v)
+        for q in range(3):
+            a, b, da, db = r[2 * q], r[2 * q + 1], dr[2 * q], dr[2 * q + 1]
+            ref[k, 2 * q] = (da * b - a * db) / (a + b) ** 2
+            ref[k, 2 * q + 1] = -dt * (da + db) * np.exp(-dt * (a + b))
+    err = np.abs(slope - ref)
+    assert err.max() <= 1e-11 * max(1.0, np.abs(ref).max()), err.max()
