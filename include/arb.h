@@ -276,8 +276,9 @@ arb_status arb_math_eval(int32_t fn, int64_t n, const double* x, double* y, void
  * h and n: m_inf, e_m, h_inf, e_h, n_inf, e_n) are cubic on each interval
  * [v_lo + i/per_mv, v_lo + (i+1)/per_mv), i < n_intervals: coef[24 i + 4 q + k] is the
  * coefficient of s^k of function q, s = (V - v_lo) per_mv - i. Outside the range the kernel
- * evaluates the rates directly. With coef = NULL (or cap too small) only the three sizes are
- * returned; cap counts doubles. dt must be finite and > 0 (else ARB_E_ARG). */
+ * evaluates the rates directly. With coef = NULL only the three sizes are returned; cap counts
+ * doubles, and a non-NULL coef with cap < 24 n_intervals returns ARB_E_ARG and writes nothing.
+ * dt must be finite and > 0 (else ARB_E_ARG). Messages via arb_last_error(NULL). */
 arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_intervals, double* v_lo,
                              double* per_mv);
 
@@ -287,25 +288,33 @@ const char* arb_last_error(const arb_sim* sim);
 
 /* Tree solve that allocates no memory. The paper has no counterpart to this entry point; it
  * serves callers that cannot call cudaMalloc where they need a solve: code that runs while a
- * stream is being captured into a CUDA graph, host callbacks, or runtimes whose device memory
- * pool is fixed up front.
+ * stream is being captured into a CUDA graph (an allocation would break the capture), host
+ * callbacks, or runtimes whose device memory pool is fixed up front.
  *
- * For each of n_cells cells it solves the symmetric tree system of the implicit Euler step
- * (Sec. "Model"): diagonal d[i], off-diagonal a[i] at (i, parent(i)) and (parent(i), i),
- * right-hand side b[i], solution x[i], by elimination from the leaves and back substitution
- * (Hines' extension of the Thomas algorithm). All arrays are caller-owned DEVICE memory, in the
- * layout of arb_model: cv_offset [n_cells+1] (cv_offset[0] = 0, n_cv = cv_offset[n_cells]),
- * parent [n_cv] cell-local with parent of a cell's first CV = -1 and 0 <= parent[i] < i
- * otherwise (a cell that breaks this gets NaN in x), d, a, b, x [n_cv] (a of a first CV unused).
- * The launch goes on `stream` (cudaStream_t, 0 = legacy default) and is asynchronous.
+ * For each of n_cells cells it solves a symmetric linear system whose graph is the cell's tree
+ * (the kind of system one implicit Euler step of a cable produces): diagonal d[i],
+ * off-diagonal a[i] at (i, parent(i)) and (parent(i), i), right-hand side b[i], solution x[i],
+ * by elimination from the leaves and back substitution. All arrays are caller-owned DEVICE
+ * memory, in the layout of arb_model: cv_offset [n_cells+1], parent [n_cv] cell-local, and
+ * d, a, b, x [n_cv] (a of a cell's first CV unused).
+ *  - cv_offset must be a CSR over the CVs: cv_offset[0] = 0, never decreasing,
+ *    cv_offset[n_cells] = n_cv. If it is not, every x[i] is set to NaN (the check runs on the
+ *    device, so the call still returns ARB_OK).
+ *  - parent of a cell's first CV is -1, otherwise 0 <= parent[i] < i; a cell that breaks this
+ *    gets NaN over its own x, and the other cells are solved normally.
+ * The launches go on `stream` (cudaStream_t, 0 = legacy default) and are asynchronous.
  *
- * Scratch: a fixed array of 262,144 CVs x 16 bytes (4 MiB) in the library's device memory,
- * which every GPU that loads the library holds until the process exits. Larger n_cv returns
- * ARB_E_ARG (message via arb_last_error(NULL)). The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) for that device; make that first call before
- * any stream capture. Every call reuses the same array: calls whose kernels overlap on the GPU
- * (different streams, or several devices sharing a context) race and must be serialised by
- * the caller. Nothing from an earlier call is read; nothing needs clearing. */
+ * Scratch: a fixed array of 262,144 CVs x 16 bytes (4 MiB) plus a status word in the library's
+ * device memory, which every GPU that loads the library holds until the process exits. Larger
+ * n_cv returns ARB_E_ARG (message via arb_last_error(NULL)). The first call on a device looks up
+ * the arrays' device addresses (cudaGetSymbolAddress) for that device and keeps them; make that
+ * first call before any stream capture, and do not call cudaDeviceReset on that device
+ * afterwards (the kept addresses would belong to the destroyed context). Every call on a device
+ * reuses the same arrays: calls on one device whose kernels may overlap (different streams, or
+ * different host threads) race on them and must be serialised by the caller; calls on
+ * different devices use different copies and do not interfere. Nothing from an earlier call
+ * is read: the status word is cleared by each call and the scratch rows are written before
+ * they are read. */
 arb_status arb_solve_trees_noalloc(int32_t n_cells, int64_t n_cv, const int64_t* cv_offset,
                                    const int32_t* parent, const double* d, const double* a,
                                    const double* b, double* x, void* stream);

@@ -705,11 +705,20 @@ extern "C" {
 
 arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_intervals, double* v_lo,
                              double* per_mv) {
-    if (!(dt > 0.0) || !std::isfinite(dt)) return ARB_E_ARG;
+    g_create_error.clear();
+    if (!(dt > 0.0) || !std::isfinite(dt)) {
+        g_create_error = "arb_hh_gate_table: dt must be finite and > 0";
+        return ARB_E_ARG;
+    }
+    if (coef && cap < (int64_t)kHHTabN * kHHTabStride) {
+        g_create_error = "arb_hh_gate_table: coef holds " + std::to_string(cap) + " doubles, the table needs " +
+                         std::to_string((int64_t)kHHTabN * kHHTabStride);
+        return ARB_E_ARG;
+    }
     if (n_intervals) *n_intervals = kHHTabN;
     if (v_lo) *v_lo = kHHTabVlo;
     if (per_mv) *per_mv = kHHTabPerMV;
-    if (coef && cap >= (int64_t)kHHTabN * kHHTabStride) build_hh_table(dt, coef);
+    if (coef) build_hh_table(dt, coef);
     return ARB_OK;
 }
 

@@ -17,6 +17,11 @@ def table():
     assert lib.arb_hh_gate_table(0.025, C.c_void_p(tab.ctypes.data), tab.size, C.byref(n), C.byref(vlo),
                                  C.byref(pm)) == 0
     assert lib.arb_hh_gate_table(0.0, None, 0, C.byref(n), C.byref(vlo), C.byref(pm)) == -1
+    assert b"dt" in lib.arb_last_error(None)
+    # a buffer too small for the table is refused and left untouched
+    small = np.full(24, 7.0)
+    assert lib.arb_hh_gate_table(0.025, C.c_void_p(small.ctypes.data), small.size, None, None, None) == -1
+    assert b"needs" in lib.arb_last_error(None) and np.all(small == 7.0)
     return tab.reshape(n.value, 6, 4), vlo.value, pm.value
 
 

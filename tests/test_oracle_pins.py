@@ -224,6 +224,92 @@ def test_hh_rest_gate_values_match_literature(oracle_lib):
     assert abs(r[4] / (r[4] + r[5]) - g["n_inf"]) < g["abs_tol"]
 
 
+def _hh_published():
+    return json.load(open(os.path.join(HERE, "golden", "hh_published.json")))
+
+
+def _rate_1952(spec, v):
+    """One rate of the 1952 equations in their original convention (v: displacement from rest,
+    depolarisation negative), evaluated from the published constants."""
+    A, K = spec.get("A", 1.0), spec["K"]
+    if spec["form"] == "exp":
+        return A * math.exp(v / K)
+    x = (v + spec["S"]) / K
+    if spec["form"] == "logistic":
+        return 1.0 / (math.exp(x) + 1.0)
+    # ratio: A (v + S) / (exp((v + S)/K) - 1), whose removable point v = -S has the limit A K
+    return A * K if x == 0.0 else A * (v + spec["S"]) / math.expm1(x)
+
+
+def test_hh_rates_match_the_1952_equations_in_their_original_convention(oracle_lib):
+    # The oracle writes the rates in the -65 mV rest convention; the published equations use the
+    # displacement from rest with the opposite sign, so every offset and factor of the oracle is
+    # checked against constants of another form (a shifted or sign-flipped offset, or a factor that
+    # barely moves the rest values, fails here). Voltages span hyperpolarised to the spike peak and
+    # include the removable points of alpha_m (-40 mV) and alpha_n (-55 mV) and beta_h's midpoint.
+    g = _hh_published()["rate_equations_1952"]
+    names = ["alpha_m", "beta_m", "alpha_h", "beta_h", "alpha_n", "beta_n"]
+    worst = 0.0
+    for V in (-100.0, -90.0, -65.0, -55.0, -40.0, -35.0, -20.0, -10.0, 0.0, 20.0, 45.0):
+        r = oracle_lib.hh_rates(V)
+        for q, nm in enumerate(names):
+            want = _rate_1952(g[nm], -(V + 65.0))
+            err = abs(r[q] - want) / abs(want)
+            worst = max(worst, err)
+            assert err <= g["rel_tol"], (V, nm, r[q], want)
+    print("HH rates vs the 1952 equations: max rel err %.1e" % worst)
+
+
+def _hh_membrane_current(rates, mem, V, m, h, n):
+    return (mem["gNa"] * m ** 3 * h * (V - mem["ENa"]) + mem["gK"] * n ** 4 * (V - mem["EK"])
+            + mem["gL"] * (V - mem["EL"]))
+
+
+def _hh_steady(rates, V):
+    am, bm, ah, bh, an, bn = rates(V)
+    return am / (am + bm), ah / (ah + bh), an / (an + bn)
+
+
+def _hh_max_growth_rate(rates, mem, I):
+    """Largest real part of the eigenvalues of the 4-variable HH system linearised at its
+    steady state under the constant current I (uA/cm^2); the rate derivatives are central
+    differences of the oracle's rates."""
+    from scipy.optimize import brentq
+    V0 = brentq(lambda V: _hh_membrane_current(rates, mem, V, *_hh_steady(rates, V)) - I, -90.0, 30.0)
+    y0 = np.array([V0, *_hh_steady(rates, V0)])
+
+    def f(y):
+        V, m, h, n = y
+        am, bm, ah, bh, an, bn = rates(V)
+        return np.array([(I - _hh_membrane_current(rates, mem, V, m, h, n)) / mem["C"],
+                         am - (am + bm) * m, ah - (ah + bh) * h, an - (an + bn) * n])
+    J = np.zeros((4, 4))
+    for k in range(4):
+        d = np.zeros(4)
+        d[k] = 1e-6 * max(1.0, abs(y0[k]))
+        J[:, k] = (f(y0 + d) - f(y0 - d)) / (2 * d[k])
+    return float(np.max(np.linalg.eigvals(J).real))
+
+
+def test_hh_rest_potential_and_hopf_currents_match_the_published_values(oracle_lib):
+    # Whole-model properties of the published HH model, computed from the oracle's rate
+    # functions alone: the resting potential with the published leak reversal, and the two
+    # steady currents at which the rest state loses and regains stability. A 1-mV offset or a
+    # 5% factor error in any one rate moves I1 by 0.3 uA/cm^2 or more.
+    from scipy.optimize import brentq
+    pub = _hh_published()
+    mem, hopf = pub["membrane"], pub["hopf"]
+    rates = oracle_lib.hh_rates
+    rest = brentq(lambda V: _hh_membrane_current(rates, mem, V, *_hh_steady(rates, V)), -90.0, -40.0)
+    assert abs(rest - mem["rest_mV"]) <= mem["rest_tol_mV"], rest
+    assert _hh_max_growth_rate(rates, mem, 0.0) < 0.0                 # rest is stable
+    I1 = brentq(lambda I: _hh_max_growth_rate(rates, mem, I), 5.0, 15.0)
+    I2 = brentq(lambda I: _hh_max_growth_rate(rates, mem, I), 100.0, 200.0)
+    print("HH rest %.4f mV, Hopf currents %.4f and %.3f uA/cm^2" % (rest, I1, I2))
+    assert abs(I1 - hopf["I1"]) <= hopf["I1_tol"], I1
+    assert abs(I2 - hopf["I2"]) <= hopf["I2_tol"], I2
+
+
 def test_exprelr_limits(oracle_lib):
     assert oracle_lib.exprelr(0.0) == 1.0
     for x in (1e-12, -1e-9, 1e-4, 0.3, -2.0, 5.0):
