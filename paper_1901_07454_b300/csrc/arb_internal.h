@@ -199,6 +199,14 @@ struct DevModel {
     const double* syn_ntau;   // per synapse row entry: -1/tau (exact event times)
     const int32_t* slot_lo;   // exact event times: per lane (owner), its range of compact slots
     const int32_t* slot_hi;
+    // streamed packs, implicit scheme, step-start events (the row-ring path): per entry the
+    // diagonal Ee and right-hand side Be of the step (constants, rewritten every step for
+    // mechanism CVs), the forward result (u, e) UE, and per compact slot its pack-relative entry
+    // c_ent; syn_vs, hh_vs and st_slot then hold pack-relative entries instead of compact slots
+    double* Ee;
+    double* Be;
+    double2* UE;
+    const int32_t* c_ent;
 };
 
 // Arguments of the event-delivery kernels.

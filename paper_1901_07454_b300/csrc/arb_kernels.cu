@@ -1095,12 +1095,405 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
     __syncwarp();
 }
 
+// ------------------------------------------------------------------------------------------
+// Streamed packs, implicit scheme: the rows of the forward elimination and of the back
+// substitution stream through a per-warp ring of rows in shared memory, filled by asynchronous
+// copies (cp.async) kRF rows (forward) or kRB rows (back substitution) ahead, so that the
+// global-memory latency of a row is hidden behind the FP64 work of the rows before it without
+// holding the prefetched rows in registers. Each lane copies, and later reads, only its own
+// elements of a row, so no barrier is needed between the copy and the read.
+//
+// The diagonal and right-hand side of every entry come from the per-entry arrays Ee / Be: entries
+// without mechanisms hold their constant parts (written once at bind), and the mechanism pass
+// writes the entries of mechanism CVs every step (constant part + membrane conductance, and
+// constant part + conductance x reversal + clamp current). The forward sweep writes (u, e) of
+// each entry as one 16-byte pair, which the back substitution streams back in reverse order.
+
+#ifndef ARB_STREAM_RF
+#define ARB_STREAM_RF 4
+#endif
+#ifndef ARB_STREAM_RB
+#define ARB_STREAM_RB 8
+#endif
+constexpr int kRF = ARB_STREAM_RF;   // rows in flight in the forward ring (power of two)
+constexpr int kRB = ARB_STREAM_RB;   // rows in flight in the back-substitution ring (power of two)
+static_assert((kRF & (kRF - 1)) == 0 && (kRB & (kRB - 1)) == 0 && kRF >= 2 && kRB >= 2, "ring sizes");
+
+struct FwdRow {            // one row of the forward sweep, 32 lanes
+    double v[kWarp], a[kWarp], k[kWarp], e[kWarp], b[kWarp];
+    int32_t f[kWarp];
+};
+struct BwdRow {            // one row of the back substitution, 32 lanes
+    double2 ue[kWarp];
+    int32_t f[kWarp];
+};
+constexpr int kRingBytes = (int)(sizeof(FwdRow) * kRF > sizeof(BwdRow) * kRB ? sizeof(FwdRow) * kRF : sizeof(BwdRow) * kRB);
+constexpr int kRingDouble2 = (kRingBytes + 15) / 16;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// Asynchronous global -> shared copies of one element; with valid = false nothing is read and
+// the destination is zero-filled (src must still be a valid address).
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Mechanism pass of the implicit streamed path: events, synapse decay, HH gate update and the
+// terms of the next step, written to the entries of the mechanism CVs in Ee / Be (pack-relative
+// entry indices in syn_vs, hh_vs, st_slot and c_ent).
+template <class MT>
+__device__ __forceinline__ void stream_mech_imp(const DevModel<MT>& d, const PackDesc& pk, double* Ee, double* Be,
+                                                const double* ce_p, const double* cb_p, const double* Vg, MT* gS,
+                                                MT* mS, MT* hS, MT* nS, int lane, bool decay, bool update,
+                                                int apply_step, bool terms, int& ev_i, int ev_end, int32_t& late,
+                                                MT dt) {
+    if (terms) {
+        // mechanism CVs without synapses start from their constants; those with synapses are
+        // written whole by the synapse pass
+        for (int c = pk.nsc + lane; c < pk.nvc; c += kWarp) {
+            const int e = __ldg(d.c_ent + pk.c_off + c);
+            Ee[e] = __ldg(ce_p + e);
+            Be[e] = __ldg(cb_p + e);
+        }
+    }
+    __syncwarp();
+    while (apply_step >= 0 && ev_i < ev_end && d.ev[ev_i].step_rel < apply_step) { ++ev_i; late = 1; }
+    int n_step = 0x7fffffff, n_js = -1;
+    double n_w = 0.0;
+    if (apply_step >= 0 && ev_i < ev_end) {
+        const EvRec r = d.ev[ev_i];
+        n_step = r.step_rel;
+        n_js = r.js;
+        n_w = r.w;
+    }
+    // synapses of one CV are consecutive on one lane: their terms are summed in registers and the
+    // CV's entry written once. Rows are fetched one ahead, their entry index two ahead.
+    int cur = -1;
+    double gsum = 0.0, esum = 0.0, cur_e = 0.0, cur_b = 0.0;
+    auto sfetch_c = [&](int js) {
+        return js < pk.nsyn_row ? __ldg(d.syn_vs + (size_t)(pk.syn_row0 + js) * kWarp + lane) : -1;
+    };
+    int s_c, s_cn;
+    double s_dec, s_e, s_ce, s_cb;
+    MT s_g;
+    auto sfetch = [&](int js, int c) {
+        const bool in = js < pk.nsyn_row;
+        const size_t q = (size_t)(pk.syn_row0 + (in ? js : 0)) * kWarp + lane;
+        s_c = c;
+        s_dec = in ? __ldg(d.syn_decay + q) : 1.0;
+        s_e = in ? __ldg(d.syn_e + q) : 0.0;
+        s_g = in ? gS[(in ? js : 0) * kWarp + lane] : (MT)0;
+        s_ce = (terms && c >= 0) ? __ldg(ce_p + c) : 0.0;
+        s_cb = (terms && c >= 0) ? __ldg(cb_p + c) : 0.0;
+    };
+    {
+        const int c0 = sfetch_c(0);
+        s_cn = sfetch_c(1);
+        sfetch(0, c0);
+    }
+    for (int js = 0; js < pk.nsyn_row; ++js) {
+        const int c = s_c;
+        const double dec = s_dec, esyn = s_e, c_e = s_ce, c_b = s_cb;
+        MT g = s_g;
+        sfetch(js + 1, s_cn);
+        s_cn = sfetch_c(js + 2);
+        if (c < 0) continue;                  // padding
+        if (decay) g = g * (MT)dec;
+        while (n_step == apply_step && n_js == js) {
+            g = g + (MT)n_w;
+            ++ev_i;
+            if (ev_i < ev_end) {
+                const EvRec r = d.ev[ev_i];
+                n_step = r.step_rel;
+                n_js = r.js;
+                n_w = r.w;
+            } else {
+                n_step = 0x7fffffff;
+            }
+        }
+        gS[js * kWarp + lane] = g;
+        if (terms) {
+            if (c != cur) {
+                if (cur >= 0) {
+                    Ee[cur] = cur_e + gsum;
+                    Be[cur] = cur_b + esum;
+                }
+                cur = c;
+                cur_e = c_e;
+                cur_b = c_b;
+                gsum = 0.0;
+                esum = 0.0;
+            }
+            const double gd = (double)g;
+            gsum += gd;
+            esum = fma(gd, esyn, esum);
+        }
+    }
+    if (terms && cur >= 0) {
+        Ee[cur] = cur_e + gsum;
+        Be[cur] = cur_b + esum;
+    }
+    __syncwarp();
+    for (int jh = 0; jh < pk.nhh_row; ++jh) {
+        const size_t q = (size_t)(pk.hh_row0 + jh) * kWarp + lane;
+        const int sl = __ldg(d.hh_slot + q);
+        if (sl < 0) continue;
+        const int idx = jh * kWarp + lane;
+        const double vd = Vg[sl];
+        const MT v = (MT)vd;
+        MT m = mS[idx], h = hS[idx], n = nS[idx];
+        if (update) {
+            bool done = false;
+            if constexpr (std::is_same<MT, double>::value) done = hh_gates_tab(d.hh_tab, vd, m, h, n);
+            if (!done) {
+                const auto r = hh_rates(v);
+                m = gate(m, r.am, r.bm, dt);
+                h = gate(h, r.ah, r.bh, dt);
+                n = gate(n, r.an, r.bn, dt);
+            }
+            mS[idx] = m;
+            hS[idx] = h;
+            nS[idx] = n;
+        }
+        if (terms) {
+            const int c = __ldg(d.hh_vs + q);
+            const MT n2 = n * n;
+            const MT gna = (MT)__ldg(d.hh_gna + q) * (m * m * m * h);
+            const MT gk = (MT)__ldg(d.hh_gk + q) * (n2 * n2);
+            Ee[c] += (double)(gna + gk);
+            Be[c] += (double)(gna * (MT)kENa + gk * (MT)kEK);
+        }
+    }
+    __syncwarp();
+}
+
+template <class MT, bool kShared>
+__device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, double2* stack, int64_t k0, int nsteps,
+                                    int lane) {
+    const PackDesc pk = d.packs[p];
+    const int J = pk.nrow;
+    const size_t base = (size_t)pk.row0 * kWarp;
+    double* Vg = d.V + base;
+    double* Ee = d.Ee + base;
+    double* Be = d.Be + base;
+    double2* UE = d.UE + base;                 // forward result (u, e) per entry
+    const double* ce_p = d.ce + base;
+    const double* cb_p = d.cb + base;
+    const double* ca_p = d.ca + base;
+    const double* ck_p = d.ck + base;
+    const int32_t* fl_p = d.pslot + base;
+    MT* gS = d.syn_g + (size_t)pk.syn_row0 * kWarp;
+    MT* mS = d.hh_m + (size_t)pk.hh_row0 * kWarp;
+    MT* hS = d.hh_h + (size_t)pk.hh_row0 * kWarp;
+    MT* nS = d.hh_n + (size_t)pk.hh_row0 * kWarp;
+    FwdRow* fr = reinterpret_cast<FwdRow*>(ring);
+    BwdRow* br = reinterpret_cast<BwdRow*>(ring);
+    double2* stk = stack;                      // [depth][32] (one cell per lane)
+    double* mbd = (double*)stack;              // mailbox (cells spread over lanes): [nmb] x (d, b),
+    double* mbb = mbd + pk.nmb;                // and the published voltages over d in the back
+    double* mbv = mbd;                         // substitution
+    const int R = kShared ? pk.round_rows : 0;
+
+    const int owner = p * kWarp + lane;
+    int ev_i = d.ev_off[owner];
+    const int ev_end = d.ev_off[owner + 1];
+    int32_t late = 0;
+    const double dt = d.dt;
+    const MT dt_m = (MT)dt;
+    stream_mech_imp<MT>(d, pk, Ee, Be, ce_p, cb_p, Vg, gS, mS, hS, nS, lane, false, false, 0, true, ev_i, ev_end, late,
+                        dt_m);
+
+    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const double thr = d.threshold;
+    const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
+    const bool probing = pk.npr > 0 && probe_max > 0;
+    bool bad = false;
+
+    // row j of the forward sweep into ring slot j mod kRF (rows past the end: zero fill)
+    auto issue_f = [&](int j) {
+        FwdRow& r = fr[j & (kRF - 1)];
+        const bool in = j < J;
+        const size_t o = (size_t)(in ? j : 0) * kWarp + lane;
+        cp_async_8(&r.v[lane], Vg + o, in);
+        cp_async_8(&r.a[lane], ca_p + o, in);
+        cp_async_8(&r.k[lane], ck_p + o, in);
+        cp_async_8(&r.e[lane], Ee + o, in);
+        cp_async_8(&r.b[lane], Be + o, in);
+        cp_async_4(&r.f[lane], fl_p + o, in);
+        cp_async_commit();
+    };
+    // the i-th row of the back substitution (row J-1-i) into slot i mod kRB
+    auto issue_b = [&](int i) {
+        BwdRow& r = br[i & (kRB - 1)];
+        const int j = J - 1 - i;
+        const bool in = j >= 0;
+        const size_t o = (size_t)(in ? j : 0) * kWarp + lane;
+        cp_async_16(&r.ue[lane], UE + o, in);
+        cp_async_4(&r.f[lane], fl_p + o, in);
+        cp_async_commit();
+    };
+
+    for (int s = 0; s < nsteps; ++s) {
+        const int64_t k = k0 + s;
+        const double t = __dmul_rn((double)k, dt);
+        const bool last = (s + 1) == nsteps;
+        for (int js = 0; js < pk.nst_row; ++js) {
+            const size_t q = (size_t)(pk.st_row0 + js) * kWarp + lane;
+            const int c = __ldg(d.st_slot + q);
+            if (c >= 0 && __ldg(d.st_on + q) <= t && t < __ldg(d.st_off + q)) Be[c] += __ldg(d.st_amp + q);
+        }
+        __syncwarp();
+        const double v0 = det >= 0 ? Vg[det] : 0.0;
+
+        // forward elimination, leaves to root
+        {
+            if (kShared) {
+                for (int i = lane; i < pk.nmb; i += kWarp) { mbd[i] = 0.0; mbb[i] = 0.0; }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int u = 0; u < kRF - 1; ++u) issue_f(u);
+            int sp = 0, left = R;
+            double yprev = 0.0, kprev = 0.0, eprev = 0.0;
+            for (int j = 0; j < J; ++j) {
+                issue_f(j + kRF - 1);
+                cp_async_wait<kRF - 1>();                // row j has landed
+                const FwdRow& r = fr[j & (kRF - 1)];
+                const double V = r.v[lane], A = r.a[lane], K = r.k[lane], E = r.e[lane], Bc = r.b[lane];
+                const int f = r.f[lane];
+                if (kShared && R > 0) {
+                    if (left == 0) { __syncwarp(); left = R; }
+                    --left;
+                }
+                const int mb_in = kShared ? (int)((unsigned)f >> kMbInShift) : kMbNone;
+                const int mb_out = kShared ? ((f >> kMbOutShift) & kMbNone) : kMbNone;
+                double dd = fma(-kprev, eprev, E);
+                double bb = fma(kprev, yprev, fma(A, V, Bc));
+                if (kShared) {
+                    if (mb_in != kMbNone) { dd -= mbd[mb_in]; bb += mbb[mb_in]; }
+                } else {
+                    for (int q = f & kFlagPopMask; q > 0; --q) {
+                        const double2 c2 = stk[(--sp) * kWarp + lane];
+                        dd -= c2.x;
+                        bb += c2.y;
+                    }
+                }
+                const double rr = rcp_nr(dd);
+                const double uu = rr * bb;
+                const double ee = K * rr;
+                UE[(size_t)j * kWarp + lane] = make_double2(uu, ee);
+                const bool remote = (f & kFlagRemote) != 0;
+                if (remote && !(f & kFlagRoot)) {
+                    if (kShared) { mbd[mb_out] += K * ee; mbb[mb_out] += K * uu; }
+                    else stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                }
+                kprev = remote ? 0.0 : K;
+                eprev = ee;
+                yprev = uu;
+            }
+            cp_async_wait<0>();                          // the zero-filled tail copies too
+        }
+        __syncwarp();
+        // back substitution, root to leaves (preorder)
+        {
+#pragma unroll
+            for (int u = 0; u < kRB - 1; ++u) issue_b(u);
+            int sp = 0;
+            double vnext = 0.0;
+            int left = kShared ? ((R > 0) ? ((J - 1) % R) + 1 : 0) : 0;
+            for (int i = 0; i < J; ++i) {
+                const int j = J - 1 - i;
+                issue_b(i + kRB - 1);
+                cp_async_wait<kRB - 1>();
+                const BwdRow& r = br[i & (kRB - 1)];
+                const double2 ue = r.ue[lane];
+                const int f = r.f[lane];
+                if (kShared && R > 0) {
+                    if (left == 0) { __syncwarp(); left = R; }
+                    --left;
+                }
+                double vp;
+                if (f & kFlagRoot) vp = 0.0;
+                else if (f & kFlagRemote) vp = kShared ? mbv[(f >> kMbOutShift) & kMbNone] : stk[(--sp) * kWarp + lane].x;
+                else vp = vnext;
+                const double v = fma(ue.y, vp, ue.x);
+                if (kShared) {
+                    const int mb_in = (int)((unsigned)f >> kMbInShift);
+                    if (mb_in != kMbNone) mbv[mb_in] = v;
+                } else {
+                    for (int q = f & kFlagPopMask; q > 0; --q) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                }
+                Vg[(size_t)j * kWarp + lane] = v;
+                if (last) bad |= !isfinite(v);
+                vnext = v;
+            }
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+
+        // state updates with V(t_{k+1}); terms of the next step
+        stream_mech_imp<MT>(d, pk, Ee, Be, ce_p, cb_p, Vg, gS, mS, hS, nS, lane, true, true, last ? -1 : s + 1, !last,
+                            ev_i, ev_end, late, dt_m);
+
+        bool spk = false;
+        double ts = 0.0;
+        if (det >= 0) {
+            const double v1 = Vg[det];
+            if (v0 < thr && v1 >= thr) {
+                spk = true;
+                ts = __dadd_rn(t, __dmul_rn(dt, __ddiv_rn(__dsub_rn(thr, v0), __dsub_rn(v1, v0))));
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, spk);
+        if (ball) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd((unsigned long long*)&d.ctl->n_spikes, (unsigned long long)__popc(ball));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            if (spk) {
+                const int64_t pos = (int64_t)b0 + __popc(ball & ((1u << lane) - 1u));
+                if (pos < d.spike_cap) {
+                    d.spk_gid[pos] = d.det_gid[owner];
+                    d.spk_t[pos] = ts;
+                } else {
+                    atomicOr(&d.ctl->status, kStSpikeOverflow);
+                }
+            }
+        }
+        if (probing) {
+            const int64_t prow = k - probe_k0;
+            if (prow >= 0 && prow < probe_max)
+                for (int q = lane; q < pk.npr; q += kWarp)
+                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+        }
+        __syncwarp();
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    const bool any_late = __any_sync(0xffffffffu, late != 0);
+    if (lane == 0 && (any_bad || any_late))
+        atomicOr(&d.ctl->status, (any_bad ? kStNonFinite : 0) | (any_late ? kStLateEvent : 0));
+    __syncwarp();
+}
+
 template <class MT, bool kImp>
 __global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(DevModel<MT> d, int warp_smem_double2) {
     extern __shared__ double2 stk_smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    double2* stack = stk_smem + (size_t)wid * warp_smem_double2;
+    // implicit scheme: each warp's row ring, then its hand-over stack or mailbox
+    constexpr int ring = kImp ? kRingDouble2 : 0;
+    double2* wbase = stk_smem + (size_t)wid * (size_t)(warp_smem_double2 + ring);
+    double2* stack = wbase + ring;
     const int64_t k0 = d.ctl->k0;
     const int nsteps = (int)(d.ctl->k1 - k0);
     for (;;) {
@@ -1114,14 +1507,25 @@ __global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(Dev
                 continue;
             }
         }
-        if (d.packs[p].round_rows > 0) run_pack_stream<MT, kImp, true>(d, p, stack, k0, nsteps, lane);
-        else run_pack_stream<MT, kImp, false>(d, p, stack, k0, nsteps, lane);
+        if constexpr (kImp) {
+            if (d.packs[p].round_rows > 0) run_pack_stream_imp<MT, true>(d, p, (char*)wbase, stack, k0, nsteps, lane);
+            else run_pack_stream_imp<MT, false>(d, p, (char*)wbase, stack, k0, nsteps, lane);
+        } else {
+            if (d.packs[p].round_rows > 0) run_pack_stream<MT, kImp, true>(d, p, stack, k0, nsteps, lane);
+            else run_pack_stream<MT, kImp, false>(d, p, stack, k0, nsteps, lane);
+        }
     }
+}
+
+// Shared memory of one warp of the streamed kernel (double2 units): its row ring (implicit scheme)
+// and its hand-over stack or mailbox.
+int stream_warp_double2(bool implicit, int warp_smem_double2) {
+    return warp_smem_double2 + (implicit ? kRingDouble2 : 0);
 }
 
 template <class MT>
 cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int warp_smem_double2, cudaStream_t s) {
-    const size_t smem = (size_t)warps_per_cta * (size_t)warp_smem_double2 * sizeof(double2);
+    const size_t smem = (size_t)warps_per_cta * (size_t)stream_warp_double2(implicit, warp_smem_double2) * sizeof(double2);
     if (implicit) arb_stream_kernel<MT, true><<<grid, warps_per_cta * kWarp, smem, s>>>(d, warp_smem_double2);
     else arb_stream_kernel<MT, false><<<grid, warps_per_cta * kWarp, smem, s>>>(d, warp_smem_double2);
     return cudaGetLastError();
@@ -1129,7 +1533,7 @@ cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int wa
 
 template <class MT>
 cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm) {
-    const size_t smem = (size_t)warps_per_cta * (size_t)warp_smem_double2 * sizeof(double2);
+    const size_t smem = (size_t)warps_per_cta * (size_t)stream_warp_double2(implicit, warp_smem_double2) * sizeof(double2);
     auto fn = implicit ? arb_stream_kernel<MT, true> : arb_stream_kernel<MT, false>;
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

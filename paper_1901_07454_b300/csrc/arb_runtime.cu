@@ -34,6 +34,7 @@ template <class MT>
 cudaError_t epoch_occupancy(bool implicit, int warps_per_cta, int tile_doubles, int* blocks_per_sm);
 template <class MT>
 cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int warp_smem_double2, cudaStream_t s);
+int stream_warp_double2(bool implicit, int warp_smem_double2);
 template <class MT>
 cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm);
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
@@ -125,6 +126,8 @@ struct Plan {
     int32_t stack_depth = 1;                // streamed packs: deepest hand-over stack
     int64_t warp_smem = 32;                 // streamed packs: shared memory per warp (double2)
     int64_t split_cvs = -1;                 // streamed packs: cells above this size are spread
+    bool stream_imp = false;                // streamed packs on the row-ring path (implicit, step-start events)
+    std::vector<int32_t> c_ent;             // row-ring path: pack-relative entry of each compact slot
 };
 
 struct Region {
@@ -584,7 +587,10 @@ static void layout_regions(arb_sim* sim) {
         {"ctl", sizeof(Ctl)},
         {"packs", sizeof(PackDesc) * std::max<int64_t>(npk, 1)},
         {"ca", 8 * ne}, {"cb", 8 * ne}, {"ck", 8 * ne}, {"ce", 8 * ne}, {"pslot", 4 * ne}, {"vmap", 4 * ne},
-        {"V", 8 * ne}, {"Sg", 8 * std::max<int64_t>(pl.sg_total, 1)}, {"Rg", 8 * std::max<int64_t>(pl.sg_total, 1)},
+        {"V", 8 * ne},
+        {"Sg", 8 * std::max<int64_t>(pl.stream_imp ? 1 : pl.sg_total, 1)}, {"Rg", 8 * std::max<int64_t>(pl.stream_imp ? 1 : pl.sg_total, 1)},
+        {"Ee", 8 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)}, {"Be", 8 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)},
+        {"UE", 16 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)}, {"c_ent", 4 * std::max<int64_t>((int64_t)pl.c_ent.size(), 1)},
         {"Gm", 8 * std::max<int64_t>(pl.c_total, 1)}, {"Em", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"cE", 8 * std::max<int64_t>(pl.c_total, 1)}, {"cB", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
@@ -659,6 +665,10 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.cE = (const double*)region(sim, "cE");
     d.cB = (const double*)region(sim, "cB");
     d.Em = (double*)region(sim, "Em");
+    d.Ee = (double*)region(sim, "Ee");
+    d.Be = (double*)region(sim, "Be");
+    d.UE = (double2*)region(sim, "UE");
+    d.c_ent = (const int32_t*)region(sim, "c_ent");
     d.syn_slot = (const int32_t*)region(sim, "syn_slot");
     d.syn_vs = (const int32_t*)region(sim, "syn_vs");
     d.syn_g = (MT*)region(sim, "syn_g");
@@ -1245,7 +1255,12 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             bool shared = false;
         };
         const int64_t n_slots = (int64_t)n_sm * kStreamWarps;
-        const int64_t mb_max = std::min<int64_t>(kMbNone - 1, (227 * 1024 / kStreamWarps - 64) / 24);
+        // the row-ring path keeps two doubles per mailbox slot (the voltages reuse the diagonal
+        // slot) next to its row ring; the other paths three
+        const bool ring_path = sim->implicit && !sim->exact;
+        const int64_t mb_max = ring_path
+            ? std::min<int64_t>(kMbNone - 1, (227 * 1024 / kStreamWarps - 16 * (int64_t)stream_warp_double2(true, 0) - 64) / 16)
+            : std::min<int64_t>(kMbNone - 1, (227 * 1024 / kStreamWarps - 64) / 24);
         std::vector<int64_t> ncv_of(nc), depth_of(nc);
         for (int32_t c = 0; c < nc; ++c) {
             ncv_of[c] = sim->cv_offset[c + 1] - sim->cv_offset[c];
@@ -1620,8 +1635,18 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 }
         });
         pl.c_total = c_total;
+        if (ring_path) {   // pack-relative entry of every compact slot
+            pl.c_ent.assign(std::max<int64_t>(c_total, 1), -1);
+            parallel_for(npk, [&](int64_t pi) {
+                const PackDesc& pd = pl.packs[pi];
+                const int64_t base = (int64_t)pd.row0 * kWarp;
+                for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
+                    if (pl.vmap[t] >= 0) pl.c_ent[pd.c_off + pl.vmap[t]] = (int32_t)(t - base);
+            });
+        }
         pl.stack_depth = max_depth;
-        pl.warp_smem = std::max<int64_t>((int64_t)max_depth * kWarp, ((int64_t)3 * max_mb + 1) / 2);
+        pl.stream_imp = ring_path;
+        pl.warp_smem = std::max<int64_t>((int64_t)max_depth * kWarp, ((int64_t)(ring_path ? 2 : 3) * max_mb + 1) / 2);
         pl.split_cvs = split;
         pl.smem_packs = 0;
         for (const SGroup& G : sg) pl.smem_packs += G.shared;
@@ -1665,6 +1690,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
                     pl.syn_vs[q] = pl.vmap[pl.cv_tile[cv]];
                     if (!sim->exact && (pl.syn_vs[q] < 0 || pl.syn_vs[q] >= pd.nsc)) slot_err = 1;
+                    if (pl.stream_imp) pl.syn_vs[q] = pl.syn_slot[q];      // the CV's entry
                     pl.syn_e[q] = sim->u_e[i];
                     pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
                     pl.syn_ntau[q] = -1.0 / sim->u_tau[i];
@@ -1678,7 +1704,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     const int32_t i = w[rr];
                     const int64_t q = ((int64_t)pd.st_row0 + (int64_t)rr) * kWarp + l;
                     const int64_t cv = sim->st_cv[i];
-                    pl.st_slot[q] = pl.vmap[pl.cv_tile[cv]];
+                    pl.st_slot[q] = pl.stream_imp ? (int32_t)(pl.cv_tile[cv] - base) : pl.vmap[pl.cv_tile[cv]];
                     pl.st_sc[q] = invd[cv];
                     pl.st_on[q] = sim->st_on[i];
                     pl.st_off[q] = sim->st_on[i] + sim->st_dur[i];
@@ -1700,7 +1726,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 const int64_t q = hq.second;
                 const int64_t cv = sim->hh_cv[i];
                 pl.hh_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
-                pl.hh_vs[q] = pl.vmap[pl.cv_tile[cv]];
+                pl.hh_vs[q] = pl.stream_imp ? pl.hh_slot[q] : pl.vmap[pl.cv_tile[cv]];
                 pl.hh_sc[q] = invd[cv];
                 pl.hh_gna[q] = hh_gna[i];
                 pl.hh_gk[q] = hh_gk[i];
@@ -2162,6 +2188,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot); UP("vmap", pl.vmap);
     UP("V", pl.V0);
     UP("cE", pl.cE); UP("cB", pl.cB);
+    if (pl.stream_imp) { UP("Ee", pl.ce); UP("Be", pl.cb); UP("c_ent", pl.c_ent); }
     UP("syn_ntau", pl.syn_ntau); UP("slot_lo", pl.slot_lo); UP("slot_hi", pl.slot_hi);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     if (!sim->hh_tab.empty()) UP("hh_tab", sim->hh_tab);
@@ -2230,7 +2257,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     // launch shape of the persistent epoch kernel
     if (pl.stream) {
         // fewer warps per CTA when one warp's stack or mailbox is large
-        const int64_t per_warp = pl.warp_smem * (int64_t)sizeof(double2);
+        const int64_t per_warp = (int64_t)stream_warp_double2(sim->implicit, (int)pl.warp_smem) * (int64_t)sizeof(double2);
         sim->warps_per_cta = (int)std::min<int64_t>(kStreamWarps, (int64_t)(227 * 1024) / std::max<int64_t>(per_warp, 1));
         if (sim->warps_per_cta < 1) return fail(sim, ARB_E_ARG, "hand-over stack of one warp exceeds shared memory");
         int bps = 0;
