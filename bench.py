@@ -322,6 +322,10 @@ def main():
     ap.add_argument("--cells-per-pack", type=int, default=0)
     ap.add_argument("--split-cvs", type=int, default=0,
                     help="one cell per lane: spread cells above this many CVs over lanes (0: the library's choice)")
+    ap.add_argument("--kernel-variant", type=int, default=-1,
+                    help="streamed implicit plans: compiled variant of the epoch kernel (-1: the library's default)")
+    ap.add_argument("--spread-rows", type=int, default=0,
+                    help="streamed plans: target rows of a pack of spread cells (0: the library's choice)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-cells", type=int, default=4096, help="reference arm: cells sampled per step (0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -381,6 +385,10 @@ def main():
         sim_kw["dry_run_ranks"] = args.dry_run_ranks
     if args.split_cvs:
         sim_kw["split_cvs"] = args.split_cvs
+    if args.kernel_variant >= 0:
+        sim_kw["kernel_variant"] = args.kernel_variant
+    if args.spread_rows > 0:
+        sim_kw["spread_rows"] = args.spread_rows
     E_sim = 0 if args.epoch_overlap else E      # overlapped: the library halves the minimum delay
     tuned = None
     if args.cells_per_pack == 0 and args.workload != "batched" and not args.no_autotune:

@@ -99,6 +99,15 @@ typedef struct {
                                     of gid g at t is walked against the connections of the R
                                     gids g + r*n. Spike reads return the local spikes only.
                                     R*n must be < 2^31. */
+    int32_t spread_rows;         /* cells_per_pack 32: target solve rows of a pack of spread cells
+                                    (large cells are grouped until their schedule would run about
+                                    this long); 0 = the split threshold, or with split_cvs = 0 both
+                                    chosen together by the library's cost model */
+    int32_t kernel_variant;      /* streamed packs, ARB_IMPLICIT with step-start events: which
+                                    compiled variant of the epoch kernel runs (warps per SM and
+                                    rows prefetched, see arb_kernel_variants); -1 (default) = 0.
+                                    The choice changes the plan's schedule (and so the rounding
+                                    order of spread cells), not the method. */
     int64_t event_capacity;      /* pending network events held on the device at once */
     int64_t ext_event_capacity;  /* external events (arb_enqueue_events) held on the device */
     int64_t spike_capacity;      /* spikes recorded over the whole run */
@@ -222,6 +231,13 @@ arb_status arb_get_state(arb_sim* sim, double* V, double* m, double* h, double* 
 arb_status arb_set_state(arb_sim* sim, const double* V, const double* m, const double* h,
                          const double* n, const double* g);
 
+/* Per pack, in the order the persistent epoch kernel takes them (for i < cap; arrays may be
+ * NULL): solve rows; kind (0 streamed, one cell per lane; 1 streamed, cells spread over lanes in
+ * rounds; 2 tile in shared memory; 3 tile in global memory); synapse + HH + clamp rows. *n_packs
+ * gets the number of packs. Valid after arb_create; host-only. */
+arb_status arb_plan_packs(const arb_sim* sim, int64_t cap, int32_t* rows, int32_t* kind, int32_t* mech_rows,
+                          int64_t* n_packs);
+
 /* Packing summary, valid after arb_create (any pointer may be NULL): number of packs (warp
  * programs); solve rows over all packs and in the longest pack; packs that use shared memory
  * (state tiles, or in streamed plans the mailbox of cells spread over lanes); the fraction of
@@ -281,6 +297,11 @@ arb_status arb_math_eval(int32_t fn, int64_t n, const double* x, double* y, void
  * dt must be finite and > 0 (else ARB_E_ARG). Messages via arb_last_error(NULL). */
 arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_intervals, double* v_lo,
                              double* per_mv);
+
+/* The compiled variants of the streamed epoch kernel (arb_params.kernel_variant): returns their
+ * number; for v < cap, warps[v] = warps per SM, fwd_rows[v] and back_rows[v] = rows each warp
+ * keeps in flight in the forward elimination and the back substitution. Arrays may be NULL. */
+int32_t arb_kernel_variants(int32_t cap, int32_t* warps, int32_t* fwd_rows, int32_t* back_rows);
 
 /* Message of the last failing call on this handle; with NULL, of the last failing call on
  * this thread that has no handle (arb_create, arb_solve_trees_noalloc, arb_math_eval). */

@@ -4,7 +4,7 @@ The CUDA library libarb_b300.so (sm_103a) does all the work; this package is its
 Importing it fails when the library has not been built: there is no CPU fallback.
 """
 from . import _lib
-from ._lib import ArbError, load, EXPORTED
+from ._lib import ArbError, load, EXPORTED, kernel_variants
 from .sim import Plan, Simulation, default_params
 
 load()
@@ -13,4 +13,4 @@ from .adjoint import AdjointLoss, adjoint_loss, spread_params  # noqa: E402  (ne
 from .autotune import autotune_packing  # noqa: E402
 
 __all__ = ["ArbError", "Plan", "Simulation", "default_params", "load", "EXPORTED", "AdjointLoss", "adjoint_loss",
-           "spread_params", "autotune_packing"]
+           "spread_params", "autotune_packing", "kernel_variants"]

@@ -22,7 +22,7 @@ EXPORTED = ["arb_default_params", "arb_create", "arb_destroy", "arb_workspace_by
             "arb_enqueue_events", "arb_advance", "arb_time", "arb_read_voltage", "arb_num_spikes",
             "arb_read_spikes", "arb_read_spikes_from", "arb_hh_gate_table", "arb_set_probes", "arb_get_state", "arb_set_state", "arb_plan_info",
             "arb_last_timing", "arb_last_error", "arb_solve_trees_noalloc", "arb_adjoint_workspace_bytes",
-            "arb_adjoint", "arb_math_eval"]
+            "arb_adjoint", "arb_math_eval", "arb_kernel_variants", "arb_plan_packs"]
 
 
 class arb_params(C.Structure):
@@ -30,7 +30,7 @@ class arb_params(C.Structure):
                 ("cells_per_pack", C.c_int32), ("smem_budget", C.c_int32),
                 ("scheme", C.c_int32), ("split_cvs", C.c_int32),
                 ("coalesce_synapses", C.c_int32), ("event_timing", C.c_int32), ("epoch_overlap", C.c_int32),
-                ("dry_run_ranks", C.c_int32),
+                ("dry_run_ranks", C.c_int32), ("spread_rows", C.c_int32), ("kernel_variant", C.c_int32),
                 ("event_capacity", C.c_int64), ("ext_event_capacity", C.c_int64),
                 ("spike_capacity", C.c_int64), ("bucket_capacity", C.c_int64), ("stream", C.c_void_p)]
 
@@ -89,6 +89,8 @@ def load():
         "arb_adjoint_workspace_bytes": (i32, [vp, i64, i32, i64, i32, C.POINTER(i64)]),
         "arb_adjoint": (i32, [vp, i64, i32, i64, vp, vp, dbl, vp, i32, vp, i64, vp, C.POINTER(dbl)]),
         "arb_math_eval": (i32, [i32, i64, vp, vp, vp]),
+        "arb_kernel_variants": (i32, [i32, vp, vp, vp]),
+        "arb_plan_packs": (i32, [vp, i64, vp, vp, vp, C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -108,3 +110,15 @@ def check(status, handle=None):
     if status != ARB_OK:
         msg = load().arb_last_error(handle)
         raise ArbError(status, msg.decode() if msg else "")
+
+
+def kernel_variants():
+    """The compiled variants of the streamed epoch kernel: [(warps per SM, forward rows in
+    flight, back-substitution rows in flight)], indexed by arb_params.kernel_variant."""
+    import numpy as np
+    lib = load()
+    n = lib.arb_kernel_variants(0, None, None, None)
+    w, f, b = (np.zeros(n, np.int32) for _ in range(3))
+    lib.arb_kernel_variants(n, w.ctypes.data_as(C.c_void_p), f.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p))
+    return [(int(w[i]), int(f[i]), int(b[i])) for i in range(n)]
+

@@ -199,14 +199,14 @@ struct DevModel {
     const double* syn_ntau;   // per synapse row entry: -1/tau (exact event times)
     const int32_t* slot_lo;   // exact event times: per lane (owner), its range of compact slots
     const int32_t* slot_hi;
-    // streamed packs, implicit scheme, step-start events (the row-ring path): per entry the
-    // diagonal Ee and right-hand side Be of the step (constants, rewritten every step for
-    // mechanism CVs), the forward result (u, e) UE, and per compact slot its pack-relative entry
-    // c_ent; syn_vs, hh_vs and st_slot then hold pack-relative entries instead of compact slots
-    double* Ee;
-    double* Be;
+    // streamed packs, implicit scheme, step-start events (the row-ring path): the forward result
+    // (u, e) per entry; per entry its position among its row's compact slots (cpos, -1 none); per
+    // global row the range of its compact slots with synapses (row_cs: first slot | count << 24)
+    // and of its other compact slots (row_cn: first slot counted from nsc | count << 24)
     double2* UE;
-    const int32_t* c_ent;
+    const int32_t* cpos;
+    const int32_t* row_cs;
+    const int32_t* row_cn;
 };
 
 // Arguments of the event-delivery kernels.

@@ -1103,32 +1103,32 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
 // holding the prefetched rows in registers. Each lane copies, and later reads, only its own
 // elements of a row, so no barrier is needed between the copy and the read.
 //
-// The diagonal and right-hand side of every entry come from the per-entry arrays Ee / Be: entries
-// without mechanisms hold their constant parts (written once at bind), and the mechanism pass
-// writes the entries of mechanism CVs every step (constant part + membrane conductance, and
-// constant part + conductance x reversal + clamp current). The forward sweep writes (u, e) of
-// each entry as one 16-byte pair, which the back substitution streams back in reverse order.
+// The diagonal and right-hand side of an entry without mechanisms are its constants (ce, cb);
+// those of mechanism CVs sit in the compact slots Gm / Em, which the mechanism pass writes densely
+// (slots numbered row by row within a pack, CVs with synapses first). The row's slots are two
+// contiguous ranges (row_cs, row_cn: start and count), which the ring copies together with the
+// row, and each entry's position in them (cpos) selects its terms. The forward sweep writes (u, e)
+// of each entry as one 16-byte pair, which the back substitution streams back in reverse order.
 
-#ifndef ARB_STREAM_RF
-#define ARB_STREAM_RF 4
-#endif
-#ifndef ARB_STREAM_RB
-#define ARB_STREAM_RB 8
-#endif
-constexpr int kRF = ARB_STREAM_RF;   // rows in flight in the forward ring (power of two)
-constexpr int kRB = ARB_STREAM_RB;   // rows in flight in the back-substitution ring (power of two)
-static_assert((kRF & (kRF - 1)) == 0 && (kRB & (kRB - 1)) == 0 && kRF >= 2 && kRB >= 2, "ring sizes");
-
+// Ring depths and warps per CTA of the compiled variants of the ring kernel (see kStreamVariants).
+template <int kRF, int kRB>
+__host__ __device__ constexpr int ring_double2();
 struct FwdRow {            // one row of the forward sweep, 32 lanes
     double v[kWarp], a[kWarp], k[kWarp], e[kWarp], b[kWarp];
+    double gm[kWarp], em[kWarp];   // the row's compact mechanism slots (synapse CVs, then others)
     int32_t f[kWarp];
+    int32_t cpos[kWarp];           // the entry's position in gm / em, -1 none
 };
 struct BwdRow {            // one row of the back substitution, 32 lanes
     double2 ue[kWarp];
     int32_t f[kWarp];
 };
-constexpr int kRingBytes = (int)(sizeof(FwdRow) * kRF > sizeof(BwdRow) * kRB ? sizeof(FwdRow) * kRF : sizeof(BwdRow) * kRB);
-constexpr int kRingDouble2 = (kRingBytes + 15) / 16;
+// shared memory of one warp's row ring, in double2 units: kRF forward rows or kRB back rows
+template <int kRF, int kRB>
+__host__ __device__ constexpr int ring_double2() {
+    static_assert((kRF & (kRF - 1)) == 0 && (kRB & (kRB - 1)) == 0 && kRF >= 2 && kRB >= 2, "ring sizes");
+    return (int)(((sizeof(FwdRow) * kRF > sizeof(BwdRow) * kRB ? sizeof(FwdRow) * kRF : sizeof(BwdRow) * kRB) + 15) / 16);
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 // Asynchronous global -> shared copies of one element; with valid = false nothing is read and
@@ -1149,150 +1149,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Mechanism pass of the implicit streamed path: events, synapse decay, HH gate update and the
-// terms of the next step, written to the entries of the mechanism CVs in Ee / Be (pack-relative
-// entry indices in syn_vs, hh_vs, st_slot and c_ent).
-template <class MT>
-__device__ __forceinline__ void stream_mech_imp(const DevModel<MT>& d, const PackDesc& pk, double* Ee, double* Be,
-                                                const double* ce_p, const double* cb_p, const double* Vg, MT* gS,
-                                                MT* mS, MT* hS, MT* nS, int lane, bool decay, bool update,
-                                                int apply_step, bool terms, int& ev_i, int ev_end, int32_t& late,
-                                                MT dt) {
-    if (terms) {
-        // mechanism CVs without synapses start from their constants; those with synapses are
-        // written whole by the synapse pass
-        for (int c = pk.nsc + lane; c < pk.nvc; c += kWarp) {
-            const int e = __ldg(d.c_ent + pk.c_off + c);
-            Ee[e] = __ldg(ce_p + e);
-            Be[e] = __ldg(cb_p + e);
-        }
-    }
-    __syncwarp();
-    while (apply_step >= 0 && ev_i < ev_end && d.ev[ev_i].step_rel < apply_step) { ++ev_i; late = 1; }
-    int n_step = 0x7fffffff, n_js = -1;
-    double n_w = 0.0;
-    if (apply_step >= 0 && ev_i < ev_end) {
-        const EvRec r = d.ev[ev_i];
-        n_step = r.step_rel;
-        n_js = r.js;
-        n_w = r.w;
-    }
-    // synapses of one CV are consecutive on one lane: their terms are summed in registers and the
-    // CV's entry written once. Rows are fetched one ahead, their entry index two ahead.
-    int cur = -1;
-    double gsum = 0.0, esum = 0.0, cur_e = 0.0, cur_b = 0.0;
-    auto sfetch_c = [&](int js) {
-        return js < pk.nsyn_row ? __ldg(d.syn_vs + (size_t)(pk.syn_row0 + js) * kWarp + lane) : -1;
-    };
-    int s_c, s_cn;
-    double s_dec, s_e, s_ce, s_cb;
-    MT s_g;
-    auto sfetch = [&](int js, int c) {
-        const bool in = js < pk.nsyn_row;
-        const size_t q = (size_t)(pk.syn_row0 + (in ? js : 0)) * kWarp + lane;
-        s_c = c;
-        s_dec = in ? __ldg(d.syn_decay + q) : 1.0;
-        s_e = in ? __ldg(d.syn_e + q) : 0.0;
-        s_g = in ? gS[(in ? js : 0) * kWarp + lane] : (MT)0;
-        s_ce = (terms && c >= 0) ? __ldg(ce_p + c) : 0.0;
-        s_cb = (terms && c >= 0) ? __ldg(cb_p + c) : 0.0;
-    };
-    {
-        const int c0 = sfetch_c(0);
-        s_cn = sfetch_c(1);
-        sfetch(0, c0);
-    }
-    for (int js = 0; js < pk.nsyn_row; ++js) {
-        const int c = s_c;
-        const double dec = s_dec, esyn = s_e, c_e = s_ce, c_b = s_cb;
-        MT g = s_g;
-        sfetch(js + 1, s_cn);
-        s_cn = sfetch_c(js + 2);
-        if (c < 0) continue;                  // padding
-        if (decay) g = g * (MT)dec;
-        while (n_step == apply_step && n_js == js) {
-            g = g + (MT)n_w;
-            ++ev_i;
-            if (ev_i < ev_end) {
-                const EvRec r = d.ev[ev_i];
-                n_step = r.step_rel;
-                n_js = r.js;
-                n_w = r.w;
-            } else {
-                n_step = 0x7fffffff;
-            }
-        }
-        gS[js * kWarp + lane] = g;
-        if (terms) {
-            if (c != cur) {
-                if (cur >= 0) {
-                    Ee[cur] = cur_e + gsum;
-                    Be[cur] = cur_b + esum;
-                }
-                cur = c;
-                cur_e = c_e;
-                cur_b = c_b;
-                gsum = 0.0;
-                esum = 0.0;
-            }
-            const double gd = (double)g;
-            gsum += gd;
-            esum = fma(gd, esyn, esum);
-        }
-    }
-    if (terms && cur >= 0) {
-        Ee[cur] = cur_e + gsum;
-        Be[cur] = cur_b + esum;
-    }
-    __syncwarp();
-    for (int jh = 0; jh < pk.nhh_row; ++jh) {
-        const size_t q = (size_t)(pk.hh_row0 + jh) * kWarp + lane;
-        const int sl = __ldg(d.hh_slot + q);
-        if (sl < 0) continue;
-        const int idx = jh * kWarp + lane;
-        const double vd = Vg[sl];
-        const MT v = (MT)vd;
-        MT m = mS[idx], h = hS[idx], n = nS[idx];
-        if (update) {
-            bool done = false;
-            if constexpr (std::is_same<MT, double>::value) done = hh_gates_tab(d.hh_tab, vd, m, h, n);
-            if (!done) {
-                const auto r = hh_rates(v);
-                m = gate(m, r.am, r.bm, dt);
-                h = gate(h, r.ah, r.bh, dt);
-                n = gate(n, r.an, r.bn, dt);
-            }
-            mS[idx] = m;
-            hS[idx] = h;
-            nS[idx] = n;
-        }
-        if (terms) {
-            const int c = __ldg(d.hh_vs + q);
-            const MT n2 = n * n;
-            const MT gna = (MT)__ldg(d.hh_gna + q) * (m * m * m * h);
-            const MT gk = (MT)__ldg(d.hh_gk + q) * (n2 * n2);
-            Ee[c] += (double)(gna + gk);
-            Be[c] += (double)(gna * (MT)kENa + gk * (MT)kEK);
-        }
-    }
-    __syncwarp();
-}
-
-template <class MT, bool kShared>
+template <class MT, bool kShared, int kRF, int kRB>
 __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, double2* stack, int64_t k0, int nsteps,
                                     int lane) {
     const PackDesc pk = d.packs[p];
     const int J = pk.nrow;
     const size_t base = (size_t)pk.row0 * kWarp;
     double* Vg = d.V + base;
-    double* Ee = d.Ee + base;
-    double* Be = d.Be + base;
+    double* Gm = d.Gm + pk.c_off;
+    double* Em = d.Em + pk.c_off;
     double2* UE = d.UE + base;                 // forward result (u, e) per entry
     const double* ce_p = d.ce + base;
     const double* cb_p = d.cb + base;
     const double* ca_p = d.ca + base;
     const double* ck_p = d.ck + base;
     const int32_t* fl_p = d.pslot + base;
+    const int32_t* cp_p = d.cpos + base;
+    const int32_t* rcs = d.row_cs + pk.row0;   // per row: first synapse-CV slot | count << 24
+    const int32_t* rcn = d.row_cn + pk.row0;   // per row: first other slot (from nsc) | count << 24
     MT* gS = d.syn_g + (size_t)pk.syn_row0 * kWarp;
     MT* mS = d.hh_m + (size_t)pk.hh_row0 * kWarp;
     MT* hS = d.hh_h + (size_t)pk.hh_row0 * kWarp;
@@ -1311,8 +1185,7 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
     int32_t late = 0;
     const double dt = d.dt;
     const MT dt_m = (MT)dt;
-    stream_mech_imp<MT>(d, pk, Ee, Be, ce_p, cb_p, Vg, gS, mS, hS, nS, lane, false, false, 0, true, ev_i, ev_end, late,
-                        dt_m);
+    stream_mech<MT, true>(d, pk, Gm, Em, Vg, gS, mS, hS, nS, lane, false, false, 0, true, ev_i, ev_end, late, dt_m);
 
     const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
     const double thr = d.threshold;
@@ -1320,17 +1193,44 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
     const bool probing = pk.npr > 0 && probe_max > 0;
     bool bad = false;
 
-    // row j of the forward sweep into ring slot j mod kRF (rows past the end: zero fill)
+    // The slot ranges of 32 rows at a time are held one per lane (rows 32q .. 32q+31), the next
+    // 32 fetched one chunk ahead.
+    int q_cur = -1;
+    int32_t cs_cur = 0, cn_cur = 0, cs_nxt = 0, cn_nxt = 0;
+    auto chunk = [&](int q, int32_t& cs, int32_t& cn) {
+        const int r = q * kWarp + lane;
+        cs = r < J ? __ldg(rcs + r) : 0;
+        cn = r < J ? __ldg(rcn + r) : 0;
+    };
+    // row j of the forward sweep into ring slot j mod kRF (rows past the end: zero fill), with
+    // the compact slots of its mechanism CVs: lane l copies the l-th of them
     auto issue_f = [&](int j) {
         FwdRow& r = fr[j & (kRF - 1)];
         const bool in = j < J;
         const size_t o = (size_t)(in ? j : 0) * kWarp + lane;
+        const int q = j >> 5;
+        if (q != q_cur) {
+            if (q == q_cur + 1 && q_cur >= 0) { cs_cur = cs_nxt; cn_cur = cn_nxt; }
+            else chunk(q, cs_cur, cn_cur);
+            chunk(q + 1, cs_nxt, cn_nxt);
+            q_cur = q;
+        }
+        const uint32_t ws = (uint32_t)__shfl_sync(0xffffffffu, cs_cur, j & 31);
+        const uint32_t wn = (uint32_t)__shfl_sync(0xffffffffu, cn_cur, j & 31);
+        const int ns = (int)(ws >> 24), nn = (int)(wn >> 24);
+        int slot = -1;
+        if (lane < ns) slot = (int)(ws & 0xFFFFFF) + lane;
+        else if (lane < ns + nn) slot = pk.nsc + (int)(wn & 0xFFFFFF) + (lane - ns);
+        const bool mc = in && slot >= 0;
         cp_async_8(&r.v[lane], Vg + o, in);
         cp_async_8(&r.a[lane], ca_p + o, in);
         cp_async_8(&r.k[lane], ck_p + o, in);
-        cp_async_8(&r.e[lane], Ee + o, in);
-        cp_async_8(&r.b[lane], Be + o, in);
+        cp_async_8(&r.e[lane], ce_p + o, in);
+        cp_async_8(&r.b[lane], cb_p + o, in);
+        cp_async_8(&r.gm[lane], mc ? Gm + slot : d.Gm, mc);
+        cp_async_8(&r.em[lane], mc ? Em + slot : d.Em, mc);
         cp_async_4(&r.f[lane], fl_p + o, in);
+        cp_async_4(&r.cpos[lane], cp_p + o, in);
         cp_async_commit();
     };
     // the i-th row of the back substitution (row J-1-i) into slot i mod kRB
@@ -1351,7 +1251,7 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
         for (int js = 0; js < pk.nst_row; ++js) {
             const size_t q = (size_t)(pk.st_row0 + js) * kWarp + lane;
             const int c = __ldg(d.st_slot + q);
-            if (c >= 0 && __ldg(d.st_on + q) <= t && t < __ldg(d.st_off + q)) Be[c] += __ldg(d.st_amp + q);
+            if (c >= 0 && __ldg(d.st_on + q) <= t && t < __ldg(d.st_off + q)) Em[c] += __ldg(d.st_amp + q);
         }
         __syncwarp();
         const double v0 = det >= 0 ? Vg[det] : 0.0;
@@ -1362,16 +1262,22 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 for (int i = lane; i < pk.nmb; i += kWarp) { mbd[i] = 0.0; mbb[i] = 0.0; }
                 __syncwarp();
             }
+            q_cur = -1;
 #pragma unroll
-            for (int u = 0; u < kRF - 1; ++u) issue_f(u);
+            for (int u = 0; u < kRF; ++u) issue_f(u);
             int sp = 0, left = R;
             double yprev = 0.0, kprev = 0.0, eprev = 0.0;
             for (int j = 0; j < J; ++j) {
-                issue_f(j + kRF - 1);
-                cp_async_wait<kRF - 1>();                // row j has landed
+                cp_async_wait<kRF - 1>();                // row j has landed (this lane's copies)
+                __syncwarp();                            // ... and every lane's (compact slots)
                 const FwdRow& r = fr[j & (kRF - 1)];
-                const double V = r.v[lane], A = r.a[lane], K = r.k[lane], E = r.e[lane], Bc = r.b[lane];
+                const int cp = r.cpos[lane];
+                const double V = r.v[lane], A = r.a[lane], K = r.k[lane];
+                const double E = cp >= 0 ? r.gm[cp] : r.e[lane];
+                const double Bc = cp >= 0 ? r.em[cp] : r.b[lane];
                 const int f = r.f[lane];
+                __syncwarp();                            // slot read by every lane before refilling it
+                issue_f(j + kRF);
                 if (kShared && R > 0) {
                     if (left == 0) { __syncwarp(); left = R; }
                     --left;
@@ -1443,8 +1349,8 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
         __syncwarp();
 
         // state updates with V(t_{k+1}); terms of the next step
-        stream_mech_imp<MT>(d, pk, Ee, Be, ce_p, cb_p, Vg, gS, mS, hS, nS, lane, true, true, last ? -1 : s + 1, !last,
-                            ev_i, ev_end, late, dt_m);
+        stream_mech<MT, true>(d, pk, Gm, Em, Vg, gS, mS, hS, nS, lane, true, true, last ? -1 : s + 1, !last, ev_i,
+                              ev_end, late, dt_m);
 
         bool spk = false;
         double ts = 0.0;
@@ -1485,15 +1391,18 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
     __syncwarp();
 }
 
-template <class MT, bool kImp>
-__global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(DevModel<MT> d, int warp_smem_double2) {
+// The streamed epoch kernels: a persistent grid of one CTA per SM whose warps take packs from
+// the work counter. The implicit scheme with step-start events runs the row-ring path, compiled
+// for several warp counts and ring depths (kStreamVariants, chosen at arb_create); the explicit
+// scheme and exact event times run their own kernels (16 warps, no ring).
+template <class MT, int kW, int kRF, int kRB>
+__global__ void __launch_bounds__(kW * kWarp, 1) arb_stream_ring_kernel(DevModel<MT> d, int warp_smem_double2) {
     extern __shared__ double2 stk_smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    // implicit scheme: each warp's row ring, then its hand-over stack or mailbox
-    constexpr int ring = kImp ? kRingDouble2 : 0;
-    double2* wbase = stk_smem + (size_t)wid * (size_t)(warp_smem_double2 + ring);
-    double2* stack = wbase + ring;
+    constexpr int ring = ring_double2<kRF, kRB>();
+    double2* wbase = stk_smem + (size_t)wid * (size_t)(warp_smem_double2 + ring);   // row ring, then
+    double2* stack = wbase + ring;                                                   // stack / mailbox
     const int64_t k0 = d.ctl->k0;
     const int nsteps = (int)(d.ctl->k1 - k0);
     for (;;) {
@@ -1501,49 +1410,119 @@ __global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(Dev
         if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= d.n_packs) break;
-        if constexpr (std::is_same<MT, double>::value && kImp) {
-            if (d.exact) {
-                run_pack_exact(d, p, stack, k0, nsteps, lane);
-                continue;
-            }
-        }
-        if constexpr (kImp) {
-            if (d.packs[p].round_rows > 0) run_pack_stream_imp<MT, true>(d, p, (char*)wbase, stack, k0, nsteps, lane);
-            else run_pack_stream_imp<MT, false>(d, p, (char*)wbase, stack, k0, nsteps, lane);
-        } else {
-            if (d.packs[p].round_rows > 0) run_pack_stream<MT, kImp, true>(d, p, stack, k0, nsteps, lane);
-            else run_pack_stream<MT, kImp, false>(d, p, stack, k0, nsteps, lane);
-        }
+        if (d.packs[p].round_rows > 0) run_pack_stream_imp<MT, true, kRF, kRB>(d, p, (char*)wbase, stack, k0, nsteps, lane);
+        else run_pack_stream_imp<MT, false, kRF, kRB>(d, p, (char*)wbase, stack, k0, nsteps, lane);
     }
 }
 
-// Shared memory of one warp of the streamed kernel (double2 units): its row ring (implicit scheme)
-// and its hand-over stack or mailbox.
-int stream_warp_double2(bool implicit, int warp_smem_double2) {
-    return warp_smem_double2 + (implicit ? kRingDouble2 : 0);
+template <class MT>
+__global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_kernel(DevModel<MT> d, int warp_smem_double2) {
+    extern __shared__ double2 stk_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    double2* stack = stk_smem + (size_t)wid * warp_smem_double2;
+    const int64_t k0 = d.ctl->k0;
+    const int nsteps = (int)(d.ctl->k1 - k0);
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= d.n_packs) break;
+        if (d.packs[p].round_rows > 0) run_pack_stream<MT, false, true>(d, p, stack, k0, nsteps, lane);
+        else run_pack_stream<MT, false, false>(d, p, stack, k0, nsteps, lane);
+    }
+}
+
+__global__ void __launch_bounds__(kStreamWarps * kWarp, 1) arb_stream_exact_kernel(DevModel<double> d, int warp_smem_double2) {
+    extern __shared__ double2 stk_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    double2* stack = stk_smem + (size_t)wid * warp_smem_double2;
+    const int64_t k0 = d.ctl->k0;
+    const int nsteps = (int)(d.ctl->k1 - k0);
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(&d.ctl->pack_next, 1);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= d.n_packs) break;
+        run_pack_exact(d, p, stack, k0, nsteps, lane);
+    }
+}
+
+// Compiled variants of the row-ring kernel: warps per CTA, forward ring rows, back ring rows.
+struct StreamVariant { int warps, rf, rb; };
+constexpr StreamVariant kStreamVariants[] = {{16, 2, 4}, {12, 4, 8}, {20, 2, 4}, {12, 2, 4}, {24, 2, 4}};
+constexpr int kNumStreamVariants = (int)(sizeof(kStreamVariants) / sizeof(kStreamVariants[0]));
+
+int stream_variant_count() { return kNumStreamVariants; }
+void stream_variant_info(int v, int* warps, int* rf, int* rb) {
+    *warps = kStreamVariants[v].warps;
+    *rf = kStreamVariants[v].rf;
+    *rb = kStreamVariants[v].rb;
+}
+
+// Warps per CTA and shared memory per warp (double2 units: row ring plus stack or mailbox) of the
+// kernel that runs a streamed plan: the ring variant v for the implicit scheme with step-start
+// events, else 16 warps without a ring.
+void stream_variant_shape(bool ring_path, int v, int warp_smem_double2, int* warps, int* per_warp_double2) {
+    int w = kStreamWarps, ring = 0;
+    if (ring_path && v >= 0 && v < kNumStreamVariants) {
+        const StreamVariant sv = kStreamVariants[v];
+        w = sv.warps;
+        switch (v) {
+            case 1: ring = ring_double2<4, 8>(); break;
+            default: ring = ring_double2<2, 4>(); break;
+        }
+    }
+    if (warps) *warps = w;
+    if (per_warp_double2) *per_warp_double2 = warp_smem_double2 + ring;
 }
 
 template <class MT>
-cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int warp_smem_double2, cudaStream_t s) {
-    const size_t smem = (size_t)warps_per_cta * (size_t)stream_warp_double2(implicit, warp_smem_double2) * sizeof(double2);
-    if (implicit) arb_stream_kernel<MT, true><<<grid, warps_per_cta * kWarp, smem, s>>>(d, warp_smem_double2);
-    else arb_stream_kernel<MT, false><<<grid, warps_per_cta * kWarp, smem, s>>>(d, warp_smem_double2);
-    return cudaGetLastError();
+static const void* stream_fn(int mode, int v) {
+    if (mode == 1) {
+        switch (v) {
+            case 0: return (const void*)arb_stream_ring_kernel<MT, 16, 2, 4>;
+            case 1: return (const void*)arb_stream_ring_kernel<MT, 12, 4, 8>;
+            case 2: return (const void*)arb_stream_ring_kernel<MT, 20, 2, 4>;
+            case 3: return (const void*)arb_stream_ring_kernel<MT, 12, 2, 4>;
+            default: return (const void*)arb_stream_ring_kernel<MT, 24, 2, 4>;
+        }
+    }
+    if constexpr (std::is_same<MT, double>::value)
+        if (mode == 2) return (const void*)arb_stream_exact_kernel;
+    return (const void*)arb_stream_kernel<MT>;
+}
+
+// mode: 0 explicit scheme, 1 implicit row-ring path (variant v), 2 exact event times (FP64).
+// warp_smem_double2: each warp's stack or mailbox; the ring kernel adds its row ring.
+template <class MT>
+cudaError_t launch_stream(const DevModel<MT>& d, int mode, int v, int grid, int warps_per_cta, int warp_smem_double2,
+                          cudaStream_t s) {
+    int w = 0, pw = 0;
+    stream_variant_shape(mode == 1, v, warp_smem_double2, &w, &pw);
+    const size_t smem = (size_t)warps_per_cta * (size_t)pw * sizeof(double2);
+    DevModel<MT> dd = d;
+    int ws = warp_smem_double2;
+    void* args[] = {(void*)&dd, (void*)&ws};
+    return cudaLaunchKernel(stream_fn<MT>(mode, v), dim3(grid), dim3(warps_per_cta * kWarp), args, smem, s);
 }
 
 template <class MT>
-cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm) {
-    const size_t smem = (size_t)warps_per_cta * (size_t)stream_warp_double2(implicit, warp_smem_double2) * sizeof(double2);
-    auto fn = implicit ? arb_stream_kernel<MT, true> : arb_stream_kernel<MT, false>;
+cudaError_t stream_occupancy(int mode, int v, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm) {
+    int w = 0, pw = 0;
+    stream_variant_shape(mode == 1, v, warp_smem_double2, &w, &pw);
+    const size_t smem = (size_t)warps_per_cta * (size_t)pw * sizeof(double2);
+    const void* fn = stream_fn<MT>(mode, v);
     cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, warps_per_cta * kWarp, smem);
 }
 
-template cudaError_t launch_stream<double>(const DevModel<double>&, bool, int, int, int, cudaStream_t);
-template cudaError_t launch_stream<float>(const DevModel<float>&, bool, int, int, int, cudaStream_t);
-template cudaError_t stream_occupancy<double>(bool, int, int, int*);
-template cudaError_t stream_occupancy<float>(bool, int, int, int*);
+template cudaError_t launch_stream<double>(const DevModel<double>&, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_stream<float>(const DevModel<float>&, int, int, int, int, int, cudaStream_t);
+template cudaError_t stream_occupancy<double>(int, int, int, int, int*);
+template cudaError_t stream_occupancy<float>(int, int, int, int, int*);
 
 // ------------------------------------------------------------------------------------------
 // Event delivery lists (the "enqueue" and "merge" of Sec. "Implementation": each spike's

@@ -33,10 +33,13 @@ cudaError_t launch_epoch(const DevModel<MT>& d, bool implicit, int grid, int war
 template <class MT>
 cudaError_t epoch_occupancy(bool implicit, int warps_per_cta, int tile_doubles, int* blocks_per_sm);
 template <class MT>
-cudaError_t launch_stream(const DevModel<MT>& d, bool implicit, int grid, int warps_per_cta, int warp_smem_double2, cudaStream_t s);
-int stream_warp_double2(bool implicit, int warp_smem_double2);
+cudaError_t launch_stream(const DevModel<MT>& d, int mode, int v, int grid, int warps_per_cta, int warp_smem_double2,
+                          cudaStream_t s);
+int stream_variant_count();
+void stream_variant_info(int v, int* warps, int* rf, int* rb);
+void stream_variant_shape(bool ring_path, int v, int warp_smem_double2, int* warps, int* per_warp_double2);
 template <class MT>
-cudaError_t stream_occupancy(bool implicit, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm);
+cudaError_t stream_occupancy(int mode, int v, int warps_per_cta, int warp_smem_double2, int* blocks_per_sm);
 cudaError_t launch_events_pre(const EvArgs& a, int n_sm, cudaStream_t s);
 cudaError_t events_prepare();
 cudaError_t launch_events_post(const SpkArgs& a, int n_sm, cudaStream_t s);
@@ -126,8 +129,10 @@ struct Plan {
     int32_t stack_depth = 1;                // streamed packs: deepest hand-over stack
     int64_t warp_smem = 32;                 // streamed packs: shared memory per warp (double2)
     int64_t split_cvs = -1;                 // streamed packs: cells above this size are spread
+    int64_t spread_rows = -1;               // streamed packs: target rows of a pack of spread cells
     bool stream_imp = false;                // streamed packs on the row-ring path (implicit, step-start events)
-    std::vector<int32_t> c_ent;             // row-ring path: pack-relative entry of each compact slot
+    hvec<int32_t> cpos;                     // row-ring path: per entry, its position among its row's slots
+    hvec<int32_t> row_cs, row_cn;           // row-ring path: per row, its compact slot ranges
 };
 
 struct Region {
@@ -177,6 +182,7 @@ struct arb_sim {
     int64_t ws_bytes = 0;
     std::vector<std::pair<std::string, Region>> regions;
     int n_sm = 148;
+    int variant = 0;                // compiled variant of the streamed kernel (row-ring path)
     int warps_per_cta = 2;
     int grid = 148;
     cudaStream_t s = nullptr;       // library stream (graphs are captured here)
@@ -211,6 +217,10 @@ struct arb_sim {
 namespace {
 
 thread_local std::string g_create_error;   // errors of calls without a handle
+
+// Which streamed kernel runs a streamed plan: 0 explicit scheme, 1 implicit row-ring path,
+// 2 exact event times.
+int stream_mode(const arb_sim* sim) { return sim->exact ? 2 : (sim->implicit ? 1 : 0); }
 
 arb_status fail(arb_sim* s, arb_status st, const std::string& msg) {
     if (s) s->err = msg;
@@ -589,8 +599,8 @@ static void layout_regions(arb_sim* sim) {
         {"ca", 8 * ne}, {"cb", 8 * ne}, {"ck", 8 * ne}, {"ce", 8 * ne}, {"pslot", 4 * ne}, {"vmap", 4 * ne},
         {"V", 8 * ne},
         {"Sg", 8 * std::max<int64_t>(pl.stream_imp ? 1 : pl.sg_total, 1)}, {"Rg", 8 * std::max<int64_t>(pl.stream_imp ? 1 : pl.sg_total, 1)},
-        {"Ee", 8 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)}, {"Be", 8 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)},
-        {"UE", 16 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)}, {"c_ent", 4 * std::max<int64_t>((int64_t)pl.c_ent.size(), 1)},
+        {"UE", 16 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)}, {"cpos", 4 * std::max<int64_t>((int64_t)pl.cpos.size(), 1)},
+        {"row_cs", 4 * std::max<int64_t>((int64_t)pl.row_cs.size(), 1)}, {"row_cn", 4 * std::max<int64_t>((int64_t)pl.row_cn.size(), 1)},
         {"Gm", 8 * std::max<int64_t>(pl.c_total, 1)}, {"Em", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"cE", 8 * std::max<int64_t>(pl.c_total, 1)}, {"cB", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
@@ -665,10 +675,10 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.cE = (const double*)region(sim, "cE");
     d.cB = (const double*)region(sim, "cB");
     d.Em = (double*)region(sim, "Em");
-    d.Ee = (double*)region(sim, "Ee");
-    d.Be = (double*)region(sim, "Be");
     d.UE = (double2*)region(sim, "UE");
-    d.c_ent = (const int32_t*)region(sim, "c_ent");
+    d.cpos = (const int32_t*)region(sim, "cpos");
+    d.row_cs = (const int32_t*)region(sim, "row_cs");
+    d.row_cn = (const int32_t*)region(sim, "row_cn");
     d.syn_slot = (const int32_t*)region(sim, "syn_slot");
     d.syn_vs = (const int32_t*)region(sim, "syn_vs");
     d.syn_g = (MT*)region(sim, "syn_g");
@@ -732,9 +742,22 @@ arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_in
     return ARB_OK;
 }
 
+int32_t arb_kernel_variants(int32_t cap, int32_t* warps, int32_t* fwd_rows, int32_t* back_rows) {
+    const int n = stream_variant_count();
+    for (int v = 0; v < n && v < cap; ++v) {
+        int w = 0, rf = 0, rb = 0;
+        stream_variant_info(v, &w, &rf, &rb);
+        if (warps) warps[v] = w;
+        if (fwd_rows) fwd_rows[v] = rf;
+        if (back_rows) back_rows[v] = rb;
+    }
+    return n;
+}
+
 arb_status arb_default_params(arb_params* p) {
     if (!p) return ARB_E_ARG;
     std::memset(p, 0, sizeof(*p));
+    p->kernel_variant = -1;
     p->dt = 0.025;
     p->epoch_steps = 0;
     p->precision = ARB_FP64;
@@ -775,6 +798,9 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     if (p.epoch_overlap && p.bucket_capacity > INT32_MAX / 2) return bad("with epoch_overlap the bucket capacity must be < 2^30");
     if (p.cells_per_pack < 0 || p.cells_per_pack > 32) return bad("cells_per_pack must be 0..32");
     if (p.split_cvs < -1) return bad("split_cvs must be >= -1");
+    if (p.spread_rows < 0) return bad("spread_rows must be >= 0");
+    if (p.kernel_variant < -1 || p.kernel_variant >= stream_variant_count())
+        return bad("kernel_variant must be -1 or in [0, " + std::to_string(stream_variant_count()) + ")");
     sim->mixed = p.precision == ARB_MIXED;
     if (p.scheme != ARB_IMPLICIT && p.scheme != ARB_EXPLICIT) return bad("scheme must be ARB_IMPLICIT or ARB_EXPLICIT");
     sim->implicit = p.scheme == ARB_IMPLICIT;
@@ -938,6 +964,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     sim->conn_w.assign(m->conn_weight, m->conn_weight + ncon);
     // dry run: the sources are the gids of all virtual ranks
     sim->dry_ranks = std::max<int64_t>(1, p.dry_run_ranks);
+    sim->variant = std::max<int32_t>(0, p.kernel_variant);
     const int64_t n_src = (int64_t)nc * sim->dry_ranks;
     if (n_src > INT32_MAX) return bad("dry_run_ranks * n_cells must be < 2^31");
     // checked in parallel parts; the first failing connection (lowest index) is reported
@@ -1254,13 +1281,16 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             PackRows rows;
             bool shared = false;
         };
-        const int64_t n_slots = (int64_t)n_sm * kStreamWarps;
+        // the kernel variant that will run this plan: its warps per SM and row ring
+        const bool ring_path = sim->implicit && !sim->exact;
+        int kv_warps = kStreamWarps, kv_ring = 0;
+        stream_variant_shape(ring_path, sim->variant, 0, &kv_warps, &kv_ring);
+        const int64_t n_slots = (int64_t)n_sm * kv_warps;
         // the row-ring path keeps two doubles per mailbox slot (the voltages reuse the diagonal
         // slot) next to its row ring; the other paths three
-        const bool ring_path = sim->implicit && !sim->exact;
         const int64_t mb_max = ring_path
-            ? std::min<int64_t>(kMbNone - 1, (227 * 1024 / kStreamWarps - 16 * (int64_t)stream_warp_double2(true, 0) - 64) / 16)
-            : std::min<int64_t>(kMbNone - 1, (227 * 1024 / kStreamWarps - 64) / 24);
+            ? std::min<int64_t>(kMbNone - 1, (227 * 1024 / kv_warps - 16 * (int64_t)kv_ring - 64) / 16)
+            : std::min<int64_t>(kMbNone - 1, (227 * 1024 / kv_warps - 64) / 24);
         std::vector<int64_t> ncv_of(nc), depth_of(nc);
         for (int32_t c = 0; c < nc; ++c) {
             ncv_of[c] = sim->cv_offset[c + 1] - sim->cv_offset[c];
@@ -1304,20 +1334,47 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 }
                 out.push_back(std::move(G));
             };
-        // rows of a pack of large cells, estimated without scheduling
+        constexpr double kSpreadFill = 0.93;   // lane-rows holding a CV in a round schedule
+        // Cost model of a pack's run time (measured on the batched workload: the epoch kernel's
+        // time follows the makespan of the warp slots under this cost): a solve row costs 1, a row
+        // of a pack whose cells are spread over lanes 1.05, and each synapse, HH and clamp row 1.
+        std::vector<int64_t> nsyn_of(nc), nhh_of(nc), nst_of(nc);
+        for (int32_t c = 0; c < nc; ++c) {
+            nsyn_of[c] = (int64_t)cell_syn[c].size();
+            nhh_of[c] = (int64_t)cell_hh[c].size();
+            nst_of[c] = (int64_t)cell_st[c].size();
+        }
+        // estimated cost of a pack of cells one per lane (cells[i .. i+32) of a size-sorted list)
+        auto est_lane = [&](const std::vector<int32_t>& cs, size_t i) {
+            int64_t rows = 0, sy = 0, st = 0, hh = 0;
+            for (size_t k = i; k < std::min(cs.size(), i + 32); ++k) {
+                const int32_t c = cs[k];
+                rows = std::max(rows, ncv_of[c]);
+                sy = std::max(sy, nsyn_of[c]);
+                st = std::max(st, nst_of[c]);
+                hh += nhh_of[c];
+            }
+            return (double)rows + (double)sy + (double)st + (double)((hh + 31) / 32);
+        };
+        // estimated costs of greedy packs of large cells with about kSpreadFill x 32 x target CVs
+        // each (the round schedule fills about that fraction of the lane-rows)
         auto est_shared = [&](const std::vector<int32_t>& big, int64_t target, std::vector<double>& cost) {
             size_t i = 0;
             while (i < big.size()) {
-                int64_t sum = 0, dep = 0;
+                int64_t sum = 0, dep = 0, sy = 0, hh = 0, st = 0;
                 size_t k = 0;
                 while (i + k < big.size() && k < 32) {
                     const int64_t n = ncv_of[big[i + k]];
-                    if (k > 0 && (double)(sum + n) > 0.8 * 32.0 * (double)target) break;
+                    if (k > 0 && (double)(sum + n) > kSpreadFill * 32.0 * (double)target) break;
                     sum += n;
                     dep = std::max(dep, depth_of[big[i + k]]);
+                    sy += nsyn_of[big[i + k]];
+                    hh += nhh_of[big[i + k]];
+                    st += nst_of[big[i + k]];
                     ++k;
                 }
-                cost.push_back(std::max((double)sum / (0.8 * 32.0), (double)(dep + kStreamRound)) * 1.1);
+                const double rows = std::max((double)sum / (kSpreadFill * 32.0), (double)(dep + kStreamRound));
+                cost.push_back(1.05 * rows + 1.1 * (double)(sy + st) / 32.0 + (double)((hh + 31) / 32));
                 i += k;
             }
         };
@@ -1334,28 +1391,37 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             }
             return ms;
         };
-        std::vector<double> ucost;
-        for (int32_t i = 0; i < nc; i += 32) ucost.push_back((double)ncv_of[by_size[i]]);
+        // estimated makespan with cells above thr spread into packs of about `target` rows
+        auto plan_cost = [&](int64_t thr, int64_t target) {
+            std::vector<int32_t> big, rest;
+            for (int32_t c : by_size) ((thr > 0 && ncv_of[c] > thr) ? big : rest).push_back(c);
+            std::vector<double> cost;
+            for (size_t i = 0; i < rest.size(); i += 32) cost.push_back(est_lane(rest, i));
+            if (!big.empty()) est_shared(big, target, cost);
+            return makespan(cost);
+        };
         int64_t split = sim->exact ? -1 : p.split_cvs;
+        int64_t target = p.spread_rows > 0 ? p.spread_rows : split;
         if (split == 0) {
-            // choose the threshold with the smallest estimated makespan over the warp slots
-            double sumJ = 0;
-            for (double x : ucost) sumJ += x;
-            const double avg = std::max(1.0, sumJ / (double)n_slots);
-            double best = makespan(ucost);
+            // choose the threshold and the spread packs' rows with the smallest estimated makespan
+            // over the warp slots
+            double sumc = 0;
+            for (size_t i = 0; i < by_size.size(); i += 32) sumc += est_lane(by_size, i);
+            const double avg = std::max(1.0, sumc / (double)n_slots);
+            double best = plan_cost(-1, 0);
             split = -1;
-            for (double f : {2.0, 1.5, 1.25, 1.0, 0.8}) {
+            target = 0;
+            for (double f : {2.0, 1.5, 1.25, 1.0, 0.8, 0.65, 0.5}) {
                 const int64_t thr = std::max<int64_t>(1, (int64_t)(f * avg));
-                std::vector<int32_t> big, rest;
-                for (int32_t c : by_size) (ncv_of[c] > thr ? big : rest).push_back(c);
-                if (big.empty()) continue;
-                std::vector<double> cost;
-                for (size_t i = 0; i < rest.size(); i += 32) cost.push_back((double)ncv_of[rest[i]]);
-                est_shared(big, thr, cost);
-                const double ms = makespan(cost);
-                if (ms < best * 0.97) { best = ms; split = thr; }
+                for (double g : {0.0, 0.7, 0.85, 1.0}) {
+                    const int64_t tg = p.spread_rows > 0 ? p.spread_rows : (g == 0.0 ? thr : std::max<int64_t>(1, (int64_t)(g * avg)));
+                    if (g != 0.0 && p.spread_rows > 0) continue;
+                    const double ms = plan_cost(thr, tg);
+                    if (ms < best * 0.99) { best = ms; split = thr; target = tg; }
+                }
             }
         }
+        if (target <= 0) target = split;
         std::vector<SGroup> sg;
         {
             std::vector<int32_t> big, rest;
@@ -1367,7 +1433,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 int64_t sum = 0;
                 while (i < big.size() && g.size() < 32) {
                     const int64_t n = ncv_of[big[i]];
-                    if (!g.empty() && (double)(sum + n) > 0.8 * 32.0 * (double)split) break;
+                    if (!g.empty() && (double)(sum + n) > kSpreadFill * 32.0 * (double)target) break;
                     g.push_back(big[i]);
                     sum += n;
                     ++i;
@@ -1376,7 +1442,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             }
             // schedule the groups on host threads; the results keep the groups' order
             std::vector<std::vector<SGroup>> placed(cand.size());
-            parallel_for((int64_t)cand.size(), [&](int64_t k) { place_shared(cand[k], split, placed[k]); });
+            parallel_for((int64_t)cand.size(), [&](int64_t k) { place_shared(cand[k], target, placed[k]); });
             for (auto& v : placed)
                 for (auto& G : v) sg.push_back(std::move(G));
             for (size_t r = 0; r < rest.size(); r += 32) {
@@ -1386,10 +1452,38 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 sg.push_back(std::move(G));
             }
         }
-        // the persistent kernel takes packs in order: longest first
-        std::stable_sort(sg.begin(), sg.end(), [](const SGroup& x, const SGroup& y) {
-            return x.rows.rows.size() > y.rows.rows.size();
-        });
+        pl.spread_rows = split > 0 ? target : -1;
+        // the persistent kernel takes packs in order: most expensive first (the cost model above,
+        // with the pack's scheduled rows)
+        {
+            std::vector<double> pc(sg.size());
+            parallel_for((int64_t)sg.size(), [&](int64_t k) {
+                const SGroup& G = sg[k];
+                std::array<int64_t, 32> sy{}, st{};
+                int64_t hh = 0;
+                if (G.shared) {
+                    int64_t s_all = 0, t_all = 0;
+                    for (int32_t c : G.cells) { s_all += nsyn_of[c]; t_all += nst_of[c]; hh += nhh_of[c]; }
+                    pc[k] = 1.05 * (double)G.rows.rows.size() + 1.1 * (double)(s_all + t_all) / 32.0 + (double)((hh + 31) / 32);
+                } else {
+                    int64_t ms = 0, mt = 0;
+                    for (size_t l = 0; l < G.cells.size() && l < 32; ++l) {
+                        ms = std::max(ms, nsyn_of[G.cells[l]]);
+                        mt = std::max(mt, nst_of[G.cells[l]]);
+                        hh += nhh_of[G.cells[l]];
+                    }
+                    (void)sy; (void)st;
+                    pc[k] = (double)G.rows.rows.size() + (double)(ms + mt) + (double)((hh + 31) / 32);
+                }
+            });
+            std::vector<int64_t> ordp(sg.size());
+            std::iota(ordp.begin(), ordp.end(), 0);
+            std::stable_sort(ordp.begin(), ordp.end(), [&](int64_t x, int64_t y) { return pc[x] > pc[y]; });
+            std::vector<SGroup> sorted;
+            sorted.reserve(sg.size());
+            for (int64_t k : ordp) sorted.push_back(std::move(sg[k]));
+            sg = std::move(sorted);
+        }
         const int32_t npk = (int32_t)sg.size();
         pl.packs.resize(npk);
         par_assign(pl.cv_tile, ncv, (int64_t)-1);
@@ -1635,14 +1729,43 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 }
         });
         pl.c_total = c_total;
-        if (ring_path) {   // pack-relative entry of every compact slot
-            pl.c_ent.assign(std::max<int64_t>(c_total, 1), -1);
+        if (ring_path) {
+            // slots are numbered row by row (synapse CVs first, then the others), so a row's slots
+            // are two contiguous ranges; each entry's position in the row's list of them
+            par_assign(pl.cpos, pl.total_rows * kWarp, (int32_t)-1);
+            par_assign(pl.row_cs, pl.total_rows, (int32_t)0);
+            par_assign(pl.row_cn, pl.total_rows, (int32_t)0);
+            std::vector<char> r_err(npk, 0);
             parallel_for(npk, [&](int64_t pi) {
                 const PackDesc& pd = pl.packs[pi];
-                const int64_t base = (int64_t)pd.row0 * kWarp;
-                for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t)
-                    if (pl.vmap[t] >= 0) pl.c_ent[pd.c_off + pl.vmap[t]] = (int32_t)(t - base);
+                int32_t next_s = 0, next_n = pd.nsc;
+                for (int32_t j = 0; j < pd.nrow; ++j) {
+                    const int64_t r = (int64_t)pd.row0 + j;
+                    int32_t ns = 0, nn = 0;
+                    const int32_t s0 = next_s, n0 = next_n;
+                    for (int l = 0; l < kWarp; ++l) {
+                        const int32_t c = pl.vmap[r * kWarp + l];
+                        if (c >= 0 && c < pd.nsc) {
+                            if (c != next_s) r_err[pi] = 1;
+                            pl.cpos[r * kWarp + l] = ns++;
+                            ++next_s;
+                        }
+                    }
+                    for (int l = 0; l < kWarp; ++l) {
+                        const int32_t c = pl.vmap[r * kWarp + l];
+                        if (c >= pd.nsc) {
+                            if (c != next_n) r_err[pi] = 1;
+                            pl.cpos[r * kWarp + l] = ns + nn++;
+                            ++next_n;
+                        }
+                    }
+                    if (s0 >= (1 << 24) || n0 - pd.nsc >= (1 << 24)) r_err[pi] = 1;
+                    pl.row_cs[r] = s0 | (ns << 24);
+                    pl.row_cn[r] = (n0 - pd.nsc) | (nn << 24);
+                }
             });
+            for (char e : r_err)
+                if (e) return bad("internal error: compact slots are not numbered row by row");
         }
         pl.stack_depth = max_depth;
         pl.stream_imp = ring_path;
@@ -1690,7 +1813,6 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     pl.syn_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
                     pl.syn_vs[q] = pl.vmap[pl.cv_tile[cv]];
                     if (!sim->exact && (pl.syn_vs[q] < 0 || pl.syn_vs[q] >= pd.nsc)) slot_err = 1;
-                    if (pl.stream_imp) pl.syn_vs[q] = pl.syn_slot[q];      // the CV's entry
                     pl.syn_e[q] = sim->u_e[i];
                     pl.syn_decay[q] = std::exp(-p.dt / sim->u_tau[i]);
                     pl.syn_ntau[q] = -1.0 / sim->u_tau[i];
@@ -1704,7 +1826,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     const int32_t i = w[rr];
                     const int64_t q = ((int64_t)pd.st_row0 + (int64_t)rr) * kWarp + l;
                     const int64_t cv = sim->st_cv[i];
-                    pl.st_slot[q] = pl.stream_imp ? (int32_t)(pl.cv_tile[cv] - base) : pl.vmap[pl.cv_tile[cv]];
+                    pl.st_slot[q] = pl.vmap[pl.cv_tile[cv]];
                     pl.st_sc[q] = invd[cv];
                     pl.st_on[q] = sim->st_on[i];
                     pl.st_off[q] = sim->st_on[i] + sim->st_dur[i];
@@ -1726,7 +1848,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 const int64_t q = hq.second;
                 const int64_t cv = sim->hh_cv[i];
                 pl.hh_slot[q] = (int32_t)(pl.cv_tile[cv] - base);
-                pl.hh_vs[q] = pl.stream_imp ? pl.hh_slot[q] : pl.vmap[pl.cv_tile[cv]];
+                pl.hh_vs[q] = pl.vmap[pl.cv_tile[cv]];
                 pl.hh_sc[q] = invd[cv];
                 pl.hh_gna[q] = hh_gna[i];
                 pl.hh_gk[q] = hh_gk[i];
@@ -2089,6 +2211,20 @@ arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_ro
 
 
 
+arb_status arb_plan_packs(const arb_sim* sim, int64_t cap, int32_t* rows, int32_t* kind, int32_t* mech_rows,
+                          int64_t* n_packs) {
+    if (!sim) return ARB_E_ARG;
+    const auto& P = sim->plan.packs;
+    if (n_packs) *n_packs = (int64_t)P.size();
+    for (int64_t i = 0; i < (int64_t)P.size() && i < cap; ++i) {
+        const PackDesc& pd = P[i];
+        if (rows) rows[i] = pd.nrow;
+        if (kind) kind[i] = pd.smem == kPackStream ? (pd.round_rows > 0 ? 1 : 0) : (pd.smem == kPackSmem ? 2 : 3);
+        if (mech_rows) mech_rows[i] = pd.nsyn_row + pd.nhh_row + pd.nst_row;
+    }
+    return ARB_OK;
+}
+
 static arb_status upload_mech_state(arb_sim* sim, const std::vector<double>& m, const std::vector<double>& h,
                                     const std::vector<double>& n, const std::vector<double>& g);
 
@@ -2118,8 +2254,8 @@ static arb_status capture_one(arb_sim* sim, int which, cudaGraphExec_t* out) {
             d32.ev_off += d32.n_owner + 1;
         }
         if (sim->plan.stream)
-            e1 = sim->mixed ? launch_stream<float>(d32, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s)
-                            : launch_stream<double>(d64, sim->implicit, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s);
+            e1 = sim->mixed ? launch_stream<float>(d32, stream_mode(sim), sim->variant, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s)
+                            : launch_stream<double>(d64, stream_mode(sim), sim->variant, sim->grid, sim->warps_per_cta, (int)sim->plan.warp_smem, sim->s);
         else
             e1 = sim->mixed ? launch_epoch<float>(d32, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s)
                             : launch_epoch<double>(d64, sim->implicit, sim->grid, sim->warps_per_cta, sim->plan.tile_doubles, sim->s);
@@ -2188,7 +2324,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot); UP("vmap", pl.vmap);
     UP("V", pl.V0);
     UP("cE", pl.cE); UP("cB", pl.cB);
-    if (pl.stream_imp) { UP("Ee", pl.ce); UP("Be", pl.cb); UP("c_ent", pl.c_ent); }
+    if (pl.stream_imp) { UP("cpos", pl.cpos); UP("row_cs", pl.row_cs); UP("row_cn", pl.row_cn); }
     UP("syn_ntau", pl.syn_ntau); UP("slot_lo", pl.slot_lo); UP("slot_hi", pl.slot_hi);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     if (!sim->hh_tab.empty()) UP("hh_tab", sim->hh_tab);
@@ -2257,12 +2393,14 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     // launch shape of the persistent epoch kernel
     if (pl.stream) {
         // fewer warps per CTA when one warp's stack or mailbox is large
-        const int64_t per_warp = (int64_t)stream_warp_double2(sim->implicit, (int)pl.warp_smem) * (int64_t)sizeof(double2);
-        sim->warps_per_cta = (int)std::min<int64_t>(kStreamWarps, (int64_t)(227 * 1024) / std::max<int64_t>(per_warp, 1));
+        int kw = 0, pw = 0;
+        stream_variant_shape(stream_mode(sim) == 1, sim->variant, (int)pl.warp_smem, &kw, &pw);
+        const int64_t per_warp = (int64_t)pw * (int64_t)sizeof(double2);
+        sim->warps_per_cta = (int)std::min<int64_t>(kw, (int64_t)(227 * 1024) / std::max<int64_t>(per_warp, 1));
         if (sim->warps_per_cta < 1) return fail(sim, ARB_E_ARG, "hand-over stack of one warp exceeds shared memory");
         int bps = 0;
-        cudaError_t eo = sim->mixed ? stream_occupancy<float>(sim->implicit, sim->warps_per_cta, (int)pl.warp_smem, &bps)
-                                    : stream_occupancy<double>(sim->implicit, sim->warps_per_cta, (int)pl.warp_smem, &bps);
+        cudaError_t eo = sim->mixed ? stream_occupancy<float>(stream_mode(sim), sim->variant, sim->warps_per_cta, (int)pl.warp_smem, &bps)
+                                    : stream_occupancy<double>(stream_mode(sim), sim->variant, sim->warps_per_cta, (int)pl.warp_smem, &bps);
         if (eo != cudaSuccess) return fail(sim, ARB_E_CUDA, std::string("stream kernel occupancy: ") + cudaGetErrorString(eo));
         if (bps < 1) return fail(sim, ARB_E_CUDA, "stream kernel does not fit on an SM");
         sim->grid = sim->n_sm * bps;

@@ -61,7 +61,7 @@ class Plan:
     def __init__(self, model, dt=0.025, epoch_steps=0, precision="fp64", cells_per_pack=0, smem_budget=0,
                  event_capacity=None, ext_event_capacity=None, spike_capacity=None, bucket_capacity=None,
                  stream=None, scheme="implicit", split_cvs=0, coalesce_synapses=False, exact_events=False,
-                 epoch_overlap=False, dry_run_ranks=1):
+                 epoch_overlap=False, dry_run_ranks=1, kernel_variant=-1, spread_rows=0):
         lib = L.load()
         self.model = model
         p = default_params()
@@ -75,6 +75,8 @@ class Plan:
         p.event_timing = L.ARB_EVENTS_EXACT if exact_events else L.ARB_EVENTS_STEP_START
         p.epoch_overlap = 1 if epoch_overlap else 0
         p.dry_run_ranks = int(dry_run_ranks)
+        p.kernel_variant = int(kernel_variant)
+        p.spread_rows = int(spread_rows)
         if scheme not in ("implicit", "explicit"):
             raise ValueError("scheme must be 'implicit' or 'explicit'")
         p.scheme = L.ARB_EXPLICIT if scheme == "explicit" else L.ARB_IMPLICIT
@@ -109,6 +111,16 @@ class Plan:
         n = C.c_int64()
         L.check(L.load().arb_workspace_bytes(self.h, C.byref(n)), self.h)
         return n.value
+
+    def plan_packs(self):
+        """Per pack, in the persistent kernel's order: (solve rows, kind, mechanism rows) arrays;
+        kind 0 streamed one cell per lane, 1 streamed spread over lanes, 2/3 tile packs."""
+        lib = L.load()
+        n = C.c_int64()
+        L.check(lib.arb_plan_packs(self.h, 0, None, None, None, C.byref(n)), self.h)
+        rows, kind, mech = (np.zeros(n.value, np.int32) for _ in range(3))
+        L.check(lib.arb_plan_packs(self.h, n.value, _p(rows), _p(kind), _p(mech), C.byref(n)), self.h)
+        return rows, kind, mech
 
     def plan_info(self):
         npk, rows, smem, mxr, split = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()

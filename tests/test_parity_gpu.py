@@ -69,6 +69,31 @@ def test_random_trees_every_cv_every_step(kpp, scheme, split):
     assert len(o["spikes"][1]) > 0
 
 
+def test_every_kernel_variant_keeps_parity():
+    # each compiled variant of the streamed implicit kernel (warps per SM, rows in flight) on
+    # ragged trees, with cells one per lane and spread over lanes
+    import paper_1901_07454_b300 as arb
+    m = small_tree_model(11, n_cells=37, n_branches=9, cv_range=(1, 12), n_syn=4)
+    m.stim_cv = m.cv_offset[:-1:3].copy()
+    k = m.stim_cv.size
+    m.stim_t_on, m.stim_dur, m.stim_amp = np.full(k, 2.0), np.full(k, 10.0), np.linspace(0.05, 1.0, k)
+    m.__post_init__()
+    syn, t, w = _with_events(m, 3, 40.0, 30.0)
+    spec = SimSpec(dt=0.025, t_end=30.0, epoch_steps=40, ev_syn=syn, ev_t=t, ev_w=w)
+    probes = np.arange(m.n_cv)
+    o = run_oracle(m, spec, probes=probes)
+    bar = trace_bar(TOL, oracle_spread(m, spec, probes))
+    variants = arb.kernel_variants()
+    assert len(variants) >= 4
+    for v in range(len(variants)):
+        for split in (-1, 40):
+            g = run_gpu(m, spec, probes=probes, cells_per_pack=32, split_cvs=split, kernel_variant=v)
+            e_end, e_tr = rel_err(g["V"], o["V"]), rel_err(g["trace"], o["trace"])
+            print("variant %d %s split %d: end %.2e trace %.2e (bar %.2e)" % (v, variants[v], split, e_end, e_tr, bar))
+            assert e_end <= TOL and e_tr <= bar, (v, split, e_end, e_tr)
+            compare_spikes(g["spikes"], o["spikes"])
+
+
 @pytest.mark.parametrize("scheme", ["implicit", "explicit"])
 def test_config0_plain_small_full_run(scheme):
     m, spec = make_config(0)
