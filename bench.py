@@ -333,7 +333,8 @@ def main():
     ap.add_argument("--cells", type=int, default=0, help="use only this many cells of the workload (0 = all)")
     ap.add_argument("--scheme", default="implicit", choices=["implicit", "explicit"])
     ap.add_argument("--checkpoint-every", type=int, default=500, help="adjoint workload: steps between checkpoints")
-    ap.add_argument("--no-autotune", action="store_true", help="small-batch workloads: keep the static packing")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's packing (no GPU timing of candidate packings and kernel variants)")
     ap.add_argument("--exact-events", action="store_true",
                     help="cut steps at event times (one cell per lane) instead of applying events at step starts")
     ap.add_argument("--dry-run-ranks", type=int, default=1,
@@ -391,7 +392,28 @@ def main():
         sim_kw["spread_rows"] = args.spread_rows
     E_sim = 0 if args.epoch_overlap else E      # overlapped: the library halves the minimum delay
     tuned = None
-    if args.cells_per_pack == 0 and args.workload != "batched" and not args.no_autotune:
+    streamed_workload = args.workload in ("batched", "mixed")
+    if (streamed_workload and args.cells_per_pack in (0, 32) and not args.no_autotune and args.kernel_variant < 0
+            and not args.split_cvs and not args.spread_rows and not args.exact_events and args.scheme == "implicit"):
+        # large batches: time the compiled kernel variants and plan settings on the GPU first (not
+        # part of the timed run); the fastest runs the benchmark
+        t_tune = time.perf_counter()
+        best, trials = arb.autotune_streamed(model, dt=spec.dt, epoch_steps=E_sim, precision=precision,
+                                             scheme=args.scheme,
+                                             ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
+                                             events=(spec.ev_syn, spec.ev_t, spec.ev_w), **sim_kw)
+        variants = arb.kernel_variants()
+        tuned = {"chosen": best, "seconds": round(time.perf_counter() - t_tune, 1),
+                 "trials": [{"kernel_variant": c["kernel_variant"],
+                             "warps_per_sm": variants[c["kernel_variant"]][0],
+                             "rows_in_flight": list(variants[c["kernel_variant"]][1:]),
+                             "split_cvs": pinfo["split_cvs"], "spread_rows": pinfo["spread_rows"],
+                             "packs": pinfo["n_packs"], "epoch_kernel_ms": round(ms, 3)} for c, pinfo, ms in trials]}
+        args.cells_per_pack = 32
+        for key in ("kernel_variant", "split_cvs", "spread_rows"):
+            if key in best:
+                sim_kw[key] = best[key]
+    if args.cells_per_pack == 0 and not streamed_workload and not args.no_autotune:
         # small batches: time candidate packings on the GPU first (not part of the timed run)
         best, times = arb.autotune_packing(model, dt=spec.dt, epoch_steps=E_sim, precision=precision,
                                            scheme=args.scheme, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
@@ -531,6 +553,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)", "packs": info["n_packs"],
                        "lane_efficiency": round(info["lane_efficiency"], 4), "smem_packs": info["smem_packs"],
                        "max_pack_rows": info["max_pack_rows"], "split_cvs": info["split_cvs"],
+                       "spread_rows": info["spread_rows"], "kernel_variant": info["kernel_variant"],
                        "cells_per_pack": info["cells_per_pack"], "autotune": tuned,
                        "spikes": nspk, "wall_s": wall, "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline,

@@ -241,11 +241,13 @@ arb_status arb_plan_packs(const arb_sim* sim, int64_t cap, int32_t* rows, int32_
 /* Packing summary, valid after arb_create (any pointer may be NULL): number of packs (warp
  * programs); solve rows over all packs and in the longest pack; packs that use shared memory
  * (state tiles, or in streamed plans the mailbox of cells spread over lanes); the fraction of
- * lane-rows that carry a CV; steps per epoch; cells per pack (32 = streamed plan); and the
- * CV count above which a cell is spread over several lanes (-1 = none). */
+ * lane-rows that carry a CV; steps per epoch; cells per pack (32 = streamed plan); the CV
+ * count above which a cell is spread over several lanes (-1 = none); the target rows of a pack
+ * of spread cells (-1 = none); and the kernel variant that runs the plan. */
 arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_rows,
                          int64_t* smem_packs, double* lane_efficiency, int32_t* epoch_steps,
-                         int64_t* max_pack_rows, int32_t* cells_per_pack, int64_t* split_cvs);
+                         int64_t* max_pack_rows, int32_t* cells_per_pack, int64_t* split_cvs,
+                         int64_t* spread_rows, int32_t* kernel_variant);
 
 /* Device time of the epoch kernel summed over the last arb_advance call, in ms, and the
  * number of kernel launches it issued; after arb_adjoint, the device time of its forward,

@@ -10,7 +10,7 @@ from .sim import Plan, Simulation, default_params
 load()
 
 from .adjoint import AdjointLoss, adjoint_loss, spread_params  # noqa: E402  (needs the library)
-from .autotune import autotune_packing  # noqa: E402
+from .autotune import autotune_packing, autotune_streamed  # noqa: E402
 
 __all__ = ["ArbError", "Plan", "Simulation", "default_params", "load", "EXPORTED", "AdjointLoss", "adjoint_loss",
-           "spread_params", "autotune_packing", "kernel_variants"]
+           "spread_params", "autotune_packing", "autotune_streamed", "kernel_variants"]

@@ -82,7 +82,7 @@ def load():
         "arb_get_state": (i32, [vp, vp, vp, vp, vp, vp]),
         "arb_set_state": (i32, [vp, vp, vp, vp, vp, vp]),
         "arb_plan_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i32),
-                               C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]),
+                               C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "arb_last_timing": (i32, [vp, C.POINTER(dbl), C.POINTER(i64)]),
         "arb_last_error": (C.c_char_p, [vp]),
         "arb_solve_trees_noalloc": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, vp]),

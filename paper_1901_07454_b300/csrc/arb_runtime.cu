@@ -2192,8 +2192,11 @@ arb_status arb_workspace_bytes(const arb_sim* csim, int64_t* bytes) {
 
 arb_status arb_plan_info(const arb_sim* sim, int64_t* n_packs, int64_t* total_rows, int64_t* smem_packs,
                          double* lane_efficiency, int32_t* epoch_steps, int64_t* max_pack_rows,
-                         int32_t* cells_per_pack, int64_t* split_cvs) {
+                         int32_t* cells_per_pack, int64_t* split_cvs, int64_t* spread_rows,
+                         int32_t* kernel_variant) {
     if (!sim) return ARB_E_ARG;
+    if (spread_rows) *spread_rows = sim->plan.stream ? sim->plan.spread_rows : -1;
+    if (kernel_variant) *kernel_variant = sim->variant;
     if (max_pack_rows) {
         int64_t mx = 0;
         for (const PackDesc& pd : sim->plan.packs) mx = std::max<int64_t>(mx, pd.nrow);

@@ -123,12 +123,13 @@ class Plan:
         return rows, kind, mech
 
     def plan_info(self):
-        npk, rows, smem, mxr, split = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
-        eff, ep, kpp = C.c_double(), C.c_int32(), C.c_int32()
+        npk, rows, smem, mxr, split, srows = (C.c_int64() for _ in range(6))
+        eff, ep, kpp, kv = C.c_double(), C.c_int32(), C.c_int32(), C.c_int32()
         L.check(L.load().arb_plan_info(self.h, C.byref(npk), C.byref(rows), C.byref(smem), C.byref(eff), C.byref(ep),
-                                       C.byref(mxr), C.byref(kpp), C.byref(split)), self.h)
+                                       C.byref(mxr), C.byref(kpp), C.byref(split), C.byref(srows), C.byref(kv)), self.h)
         return dict(n_packs=npk.value, total_rows=rows.value, smem_packs=smem.value, lane_efficiency=eff.value,
-                    epoch_steps=ep.value, max_pack_rows=mxr.value, cells_per_pack=kpp.value, split_cvs=split.value)
+                    epoch_steps=ep.value, max_pack_rows=mxr.value, cells_per_pack=kpp.value, split_cvs=split.value,
+                    spread_rows=srows.value, kernel_variant=kv.value)
 
 
 class Simulation(Plan):

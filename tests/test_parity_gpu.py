@@ -372,3 +372,25 @@ def test_autotuned_packing_is_timed_and_keeps_parity():
     g = run_gpu(m, spec, **best)
     o = run_oracle(m, spec)
     assert rel_err(g["V"], o["V"]) <= TOL
+
+
+def test_streamed_autotuner_times_every_variant_and_keeps_parity():
+    # the large-batch tuner on a 2,048-cell slice of the batched workload: every kernel variant is
+    # timed, the refinements too, and the chosen settings give the oracle's voltages on sampled
+    # cells (open loop over the first millisecond, before any network event can arrive)
+    import paper_1901_07454_b300 as arb
+    m, spec = make_config(2, n_cells=2048, t_end=1.0)
+    best, trials = arb.autotune_streamed(m, dt=spec.dt, epoch_steps=spec.epoch_steps, warmup=1, epochs=1,
+                                         events=(spec.ev_syn, spec.ev_t, spec.ev_w))
+    nv = len(arb.kernel_variants())
+    assert {c["kernel_variant"] for c, _, _ in trials} == set(range(nv))
+    assert len(trials) > nv and all(ms > 0 for _, _, ms in trials)
+    assert best == min(trials, key=lambda x: x[2])[0]
+    g = run_gpu(m, spec, **best)
+    cells = np.unique(np.concatenate([np.arange(0, m.n_cells, 97), np.argsort(np.diff(m.cv_offset))[-3:]]))
+    sm, ss, cv_old = submodel(m, spec, cells)
+    o = run_oracle(sm, ss)
+    err = rel_err(g["V"][cv_old], o["V"])
+    print("tuned %s: max rel err %.2e on %d sampled cells" % (best, err, cells.size))
+    assert err <= TOL
+
