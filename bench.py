@@ -330,6 +330,7 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=4096, help="reference arm: cells sampled per step (0 = all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-forms", action="store_true", help="batched workload: skip the mixed-precision comparison")
     ap.add_argument("--cells", type=int, default=0, help="use only this many cells of the workload (0 = all)")
     ap.add_argument("--scheme", default="implicit", choices=["implicit", "explicit"])
     ap.add_argument("--checkpoint-every", type=int, default=500, help="adjoint workload: steps between checkpoints")
@@ -532,6 +533,10 @@ def main():
                            "external events from host, advance one epoch, that epoch's spikes to host; all voltages to host at the end"}
         del sim2
 
+    forms = None
+    if rank == 0 and args.workload == "batched" and not args.no_forms and not args.exact_events and not args.epoch_overlap:
+        forms = measure_forms(arb, model, spec, sim, E, args, sim_kw, kern_mean_ms, tot_ms / args.steps, tuned)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -557,6 +562,7 @@ def main():
                        "cells_per_pack": info["cells_per_pack"], "autotune": tuned,
                        "spikes": nspk, "wall_s": wall, "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline,
+            "forms": forms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -565,6 +571,58 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_forms(arb, model, spec, sim64, E, args, sim_kw, fp64_kernel_ms, fp64_step_ms, tuned):
+    """The chosen forms next to the plain FP64 path on the same workload and box:
+    - mixed precision (FP32 mechanism states and currents, FP64 solve and voltages): epoch time
+      with the same plan, speed-up over FP64, and its voltages against the FP64 run after the same
+      epochs of the closed-loop network (the per-cell accuracy of this form, open loop against the
+      FP64 oracle, is what tests/test_mixed_config3_gpu.py measures);
+    - autotuned packing and kernel variant against the library's default plan (the trials of the
+      autotuner, same box)."""
+    import torch
+    out = {}
+    k_end = sim64.time()[1]
+    mx = arb.Simulation(model, dt=spec.dt, epoch_steps=E, precision="mixed", scheme=args.scheme,
+                        cells_per_pack=args.cells_per_pack, ext_event_capacity=max(1 << 20, spec.ev_t.size + 16),
+                        **sim_kw)
+    mx.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
+    k = 0
+    kern, step = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    while k < k_end:
+        k = min(k_end, k + E)
+        timed = k > args.warmup * E
+        if timed:
+            flush.zero_()
+            ev0.record(stream)
+        mx.advance(k * spec.dt)
+        if timed:
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            step.append(ev0.elapsed_time(ev1))
+            kern.append(mx.last_timing()[0])
+    v64, vmx = sim64.voltage(), mx.voltage()
+    n64, nmx = sim64.num_spikes(), mx.num_spikes()
+    mk, ms_ = sum(kern) / len(kern), sum(step) / len(step)
+    out["mixed"] = {"epoch_kernel_ms": mk, "ms_per_step": ms_, "speedup_kernel": fp64_kernel_ms / mk,
+                    "speedup_step": fp64_step_ms / ms_, "epochs_timed": len(kern),
+                    "closed_loop_after_ms": k_end * spec.dt, "max_abs_dv_vs_fp64_mV": float(np.max(np.abs(vmx - v64))),
+                    "median_abs_dv_vs_fp64_mV": float(np.median(np.abs(vmx - v64))),
+                    "spikes_fp64": int(n64), "spikes_mixed": int(nmx),
+                    "accuracy_note": "closed-loop network: spike-time differences propagate; the open-loop per-cell "
+                                     "error against the FP64 oracle is in tests/test_mixed_config3_gpu.py"}
+    del mx
+    if tuned and tuned.get("trials"):
+        d0 = [t for t in tuned["trials"] if t["kernel_variant"] == 0 and t["split_cvs"] == tuned["trials"][0]["split_cvs"]]
+        if d0:
+            out["autotuned"] = {"default_plan_epoch_kernel_ms": d0[0]["epoch_kernel_ms"],
+                                "tuned_epoch_kernel_ms": min(t["epoch_kernel_ms"] for t in tuned["trials"]),
+                                "speedup": d0[0]["epoch_kernel_ms"] / min(t["epoch_kernel_ms"] for t in tuned["trials"])}
+    return out
 
 
 def model_bytes(m):

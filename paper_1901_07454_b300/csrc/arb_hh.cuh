@@ -136,6 +136,27 @@ __device__ __forceinline__ bool hh_gates_tab(const double* tab, double vd, doubl
     return true;
 }
 
+// FP32 mechanisms (mixed precision): the same update from the table's coefficients rounded to
+// float, evaluated in float at the interval offset of the FP64 voltage; false when there is no
+// table or V lies outside it.
+__device__ __forceinline__ bool hh_gates_tab_f(const float* tab, double vd, float& m, float& h, float& n) {
+    const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
+    if (tab == nullptr || !(tv >= 0.0 && tv < (double)kHHTabN)) return false;
+    const int it = (int)tv;
+    const float s = (float)(tv - (double)it);
+    const float4* c = reinterpret_cast<const float4*>(tab + (size_t)it * kHHTabStride);
+    float f[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const float4 cc = __ldg(c + q);
+        f[q] = fmaf(fmaf(fmaf(cc.w, s, cc.z), s, cc.y), s, cc.x);
+    }
+    m = fmaf(m - f[0], f[1], f[0]);
+    h = fmaf(h - f[2], f[3], f[2]);
+    n = fmaf(n - f[4], f[5], f[4]);
+    return true;
+}
+
 // The same from the table, with what the reverse sweep of the adjoint needs: each gate x of
 // (m, h, n) becomes x_inf + (x - x_inf) e, with dx'/dV = x_inf' (1 - e) + (x - x_inf) e' (slopes
 // of the cubics) in dv and e in ef, in that order. False when there is no table or V lies

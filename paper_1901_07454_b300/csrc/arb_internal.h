@@ -165,6 +165,7 @@ struct DevModel {
     const int32_t* hh_vs;
     const double* hh_sc;
     const double* hh_tab;     // tabulated gate update ([kHHTabN][24]), or null: rates evaluated
+    const float* hh_tab_f;    // the same rounded to float (FP32 mechanisms), or null
     const double* hh_gna;     // uS
     const double* hh_gk;      // uS
     MT* hh_m;

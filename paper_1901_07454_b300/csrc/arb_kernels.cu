@@ -102,6 +102,7 @@ __device__ __forceinline__ void hh_pass(const DevModel<MT>& d, const PackDesc& p
         if (update) {
             bool done = false;
             if constexpr (std::is_same<MT, double>::value) done = hh_gates_tab(d.hh_tab, vd, m, h, n);
+            else done = hh_gates_tab_f(d.hh_tab_f, vd, m, h, n);
             if (!done) {
                 const auto r = hh_rates(v);
                 m = gate(m, r.am, r.bm, dt);
@@ -478,8 +479,11 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     // fetched kSP ahead, their slot index 2 kSP ahead, so that no load is waited for in the row
     // that issued it.
     constexpr int kSP = 1;
+    // sums of the synapse terms of one CV in the mechanism precision (FP32 currents in the mixed form)
+    using ST = typename std::conditional<kImp, MT, double>::type;
     int cur = -1;
-    double gsum = 0.0, esum = 0.0, cur_e = 0.0, cur_b = 0.0;
+    ST gsum = 0, esum = 0;
+    double cur_e = 0.0, cur_b = 0.0;
     int s_sl[kSP], s_c[kSP], s_cn[kSP];
     double s_dec[kSP], s_e[kSP], s_sc[kSP], s_ce[kSP], s_cb[kSP];
     MT s_g[kSP];
@@ -536,22 +540,21 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
                 if (c != cur) {
                     if (cur >= 0) {
                         if (kImp) {
-                            Gm[cur] = cur_e + gsum;
-                            Em[cur] = cur_b + esum;
+                            Gm[cur] = cur_e + (double)gsum;
+                            Em[cur] = cur_b + (double)esum;
                         } else {
-                            Em[cur] = esum;
+                            Em[cur] = (double)esum;
                         }
                     }
                     cur = c;
                     cur_e = c_e;
                     cur_b = c_b;
-                    gsum = 0.0;
-                    esum = 0.0;
+                    gsum = 0;
+                    esum = 0;
                 }
                 if constexpr (kImp) {
-                    const double gd = (double)g;
-                    gsum += gd;
-                    esum = fma(gd, esyn, esum);
+                    gsum += (ST)g;
+                    esum = fma((ST)g, (ST)esyn, esum);
                 } else {
                     const MT i_syn = g * (MT)(Vg[sl] - esyn);
                     esum = fma(-sc, (double)i_syn, esum);
@@ -561,10 +564,10 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     }
     if (terms && cur >= 0) {
         if (kImp) {
-            Gm[cur] = cur_e + gsum;
-            Em[cur] = cur_b + esum;
+            Gm[cur] = cur_e + (double)gsum;
+            Em[cur] = cur_b + (double)esum;
         } else {
-            Em[cur] = esum;
+            Em[cur] = (double)esum;
         }
     }
     __syncwarp();
@@ -579,6 +582,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         if (update) {
             bool done = false;
             if constexpr (std::is_same<MT, double>::value) done = hh_gates_tab(d.hh_tab, vd, m, h, n);
+            else done = hh_gates_tab_f(d.hh_tab_f, vd, m, h, n);
             if (!done) {
                 const auto r = hh_rates(v);
                 m = gate(m, r.am, r.bm, dt);

@@ -171,7 +171,8 @@ struct arb_sim {
     // ---- prepared data
     Plan plan;
     std::vector<double> init_m, init_h, init_n;   // HH initial gates, model order
-    hvec<double> hh_tab;                          // tabulated gate update (streamed FP64 plans)
+    hvec<double> hh_tab;                          // tabulated gate update (FP64 mechanisms)
+    hvec<float> hh_tab_f;                         // the same in float (FP32 mechanisms)
     // connections grouped by source
     std::vector<int64_t> out_ptr;
     std::vector<int32_t> out_syn, out_idx;
@@ -607,6 +608,7 @@ static void layout_regions(arb_sim* sim) {
         {"syn_e", 8 * pl.syn_rows * kWarp}, {"syn_decay", 8 * pl.syn_rows * kWarp}, {"syn_sc", 8 * pl.syn_rows * kWarp},
         {"syn_ntau", 8 * pl.syn_rows * kWarp}, {"slot_lo", 4 * std::max<int64_t>(nowner, 1)}, {"slot_hi", 4 * std::max<int64_t>(nowner, 1)},
         {"hh_tab", 8 * std::max<int64_t>((int64_t)sim->hh_tab.size(), 1)},
+        {"hh_tab_f", 4 * std::max<int64_t>((int64_t)sim->hh_tab_f.size(), 1)},
         {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_vs", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
         {"hh_gk", 8 * pl.hh_rows * kWarp}, {"hh_m", mt * pl.hh_rows * kWarp}, {"hh_h", mt * pl.hh_rows * kWarp},
         {"hh_n", mt * pl.hh_rows * kWarp},
@@ -669,6 +671,7 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.vmap = (const int32_t*)region(sim, "vmap");
     d.V = (double*)region(sim, "V");
     d.hh_tab = sim->hh_tab.empty() ? nullptr : (const double*)region(sim, "hh_tab");
+    d.hh_tab_f = sim->hh_tab_f.empty() ? nullptr : (const float*)region(sim, "hh_tab_f");
     d.Sg = (double*)region(sim, "Sg");
     d.Rg = (double*)region(sim, "Rg");
     d.Gm = (double*)region(sim, "Gm");
@@ -1459,7 +1462,6 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             std::vector<double> pc(sg.size());
             parallel_for((int64_t)sg.size(), [&](int64_t k) {
                 const SGroup& G = sg[k];
-                std::array<int64_t, 32> sy{}, st{};
                 int64_t hh = 0;
                 if (G.shared) {
                     int64_t s_all = 0, t_all = 0;
@@ -1472,7 +1474,6 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                         mt = std::max(mt, nst_of[G.cells[l]]);
                         hh += nhh_of[G.cells[l]];
                     }
-                    (void)sy; (void)st;
                     pc[k] = (double)G.rows.rows.size() + (double)(ms + mt) + (double)((hh + 31) / 32);
                 }
             });
@@ -2105,6 +2106,14 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             sim->hh_tab.resize((size_t)kHHTabN * kHHTabStride);
             build_hh_table(p.dt, sim->hh_tab.data());
         }
+        // FP32 mechanisms: the same table rounded to float
+        if (sim->mixed && !sim->exact && !sim->hh_cv.empty()) {
+            hvec<double> tab;
+            tab.resize((size_t)kHHTabN * kHHTabStride);
+            build_hh_table(p.dt, tab.data());
+            sim->hh_tab_f.resize(tab.size());
+            parallel_for((int64_t)tab.size(), [&](int64_t i) { sim->hh_tab_f[i] = (float)tab[i]; });
+        }
         sim->init_h.assign(sim->hh_cv.size(), hi);
         sim->init_n.assign(sim->hh_cv.size(), ni);
     }
@@ -2331,6 +2340,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("syn_ntau", pl.syn_ntau); UP("slot_lo", pl.slot_lo); UP("slot_hi", pl.slot_hi);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     if (!sim->hh_tab.empty()) UP("hh_tab", sim->hh_tab);
+    if (!sim->hh_tab_f.empty()) UP("hh_tab_f", sim->hh_tab_f);
     UP("hh_slot", pl.hh_slot); UP("hh_vs", pl.hh_vs); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
     UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
     UP("det_slot", pl.det_slot); UP("det_gid", pl.det_gid);

@@ -72,11 +72,45 @@ def oracle_sensitivity(model, spec, probes, scheme="implicit", n_steps=None, rel
     return float(np.max(np.abs(tb - ta))) if absolute else rel_err(tb, ta)
 
 
-def trace_bar(tol, spread, factor=20.0):
+TRACE_FACTOR = 20.0
+
+
+def trace_bar(tol, spread, factor=TRACE_FACTOR):
     """Comparison bar for step-by-step traces through spikes: the tolerance, or a small multiple
     of how far two equally valid FP64 oracle runs drift apart (oracle_spread) when that is
     larger -- the trajectory's own conditioning."""
     return max(tol, factor * spread)
+
+
+def record(kind, **vals):
+    """Prints the error a parity check reached (and appends it to the file named by
+    ARB_PARITY_LOG, one JSON object per line), tagged with the running test."""
+    import json
+    import os
+    line = {"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "kind": kind}
+    line.update({k: (float(v) if isinstance(v, (int, float, np.floating, np.integer)) else v) for k, v in vals.items()})
+    print("PARITY " + json.dumps(line))
+    path = os.environ.get("ARB_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(line) + "\n")
+
+
+def check_end(v_gpu, v_orc, tol=1e-9, **tags):
+    """End-of-run voltages: max relative error (as rel_err) within tol."""
+    e = rel_err(v_gpu, v_orc)
+    record("end", err=e, bar=tol, **tags)
+    assert e <= tol, (e, tol)
+    return e
+
+
+def check_trace(tr_gpu, tr_orc, spread, tol=1e-9, **tags):
+    """Step-by-step traces: within trace_bar(tol, spread)."""
+    e = rel_err(tr_gpu, tr_orc)
+    bar = trace_bar(tol, spread)
+    record("trace", err=e, bar=bar, spread=spread, ratio=(e / spread if spread > 0 else 0.0), **tags)
+    assert e <= bar, (e, bar, spread)
+    return e
 
 
 def renumbered(model):
