@@ -60,10 +60,22 @@ FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
 
 # FP64 thread instructions (DFMA + DMUL + DADD) the streamed epoch kernel executes per
 # CV-step, and its DRAM bytes per CV-step, on the batched workload: from the ncu capture of
-# 40,000 cells (profiles/stream_kernel_batched_40000cells.md), which has the same cell-size
-# mix, synapse and HH densities per CV as the full 65,536-cell workload.
-STREAM_FP64_PER_CV_STEP = {"batched": 12.55}
-STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 121.8}
+# 40,000 cells with the row-ring kernel at 12 warps per SM (profiles/stream_kernel_batched_40000cells.md,
+# capture of the kernel as of commit a4df58d), which has the same cell-size mix, synapse and HH
+# densities per CV as the full 65,536-cell workload. Re-measure when the kernel changes.
+STREAM_FP64_PER_CV_STEP = {"batched": 11.87}
+STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 119.0}
+
+
+# Discrete adjoint (every CV with HH, checkpoint every 500 steps): FP64 thread instructions per
+# gradient CV-step of the forward, recompute and reverse kernels together (ncu on the 256-cell
+# fitting workload, profiles/adjoint_config4_256cells.md: 51.1 in k_adj_forward, 162 in
+# k_adj_stage), and the algorithmic state bytes per gradient CV-step: forward V and gates
+# read+write (64), recompute V and gates read and V, gates, dPhi/dV and decay factors written
+# (112), reverse segment states and factors read, lambda, gate adjoints and gradient sums
+# read+write (216).
+ADJ_FP64_PER_CV_STEP = 213.0
+ADJ_BYTES_PER_CV_STEP = 392.0
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
@@ -156,8 +168,8 @@ def dist_env():
 
 
 def run_reference(args, model, spec, precision, workload_name):
-    """The oracle (FP64 CPU) as it stands, timed on the host cores; each step is one epoch of
-    the workload over a bounded sample of its cells."""
+    """The oracle (FP64 CPU) as it stands, timed on the host cores; each step is one epoch of the
+    workload (by default every cell, closed loop, the same epochs as the timed arm)."""
     import oracle
     from inputs.sample import cell_sample
     rank, world, _ = dist_env()
@@ -184,7 +196,9 @@ def run_reference(args, model, spec, precision, workload_name):
         "config": {"workload": workload_name, "cells": model.n_cells, "cvs": model.n_cv, "epoch_steps": E,
                    "dt_ms": spec.dt, "sampled_cells": ncells},
         "cpu_baseline": {"value": value, "unit": "CV-steps/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d of %d cells, %d epochs of %d steps" % (ncells, model.n_cells, args.steps, E)},
+                         "sample": "%d of %d cells%s, %d timed epochs of %d steps after %d warm-up epochs" % (
+                             ncells, model.n_cells, " (closed loop)" if ncells == model.n_cells else " (open loop)",
+                             args.steps, E, args.warmup)},
         "e2e": {"value": value, "unit": "CV-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -280,14 +294,45 @@ def run_adjoint(args, model, spec):
         el = time.perf_counter() - t0
         cpu = {"value": sm.n_cv * K / el, "unit": "CV-steps/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d of %d cells, whole run (%d steps), %.1f s" % (cells.size, model.n_cells, K, el)}
+    # roofline of the gradient: the kernels' FP64 thread instructions per gradient CV-step (ncu)
+    # against the FP64 issue ceiling, and the algorithmic state bytes against HBM
+    kern_mean = sum(kern) / len(kern)
+    ach = ADJ_FP64_PER_CV_STEP * units / args.steps / (kern_mean * 1e-3)
+    hbm_ach = ADJ_BYTES_PER_CV_STEP * units / args.steps / (kern_mean * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_INST_PER_S, "unit": "FP64 inst/s",
+                "frac": ach / FP64_PEAK_INST_PER_S, "traffic": None,
+                "peak_kind": "derived: 148 SMs x 2 FP64 FMA/clk x 2032 MHz",
+                "fp64_inst_per_cv_step": ADJ_FP64_PER_CV_STEP, "kernel": "k_adj_forward + k_adj_stage",
+                "kernel_ms_mean": kern_mean,
+                "hbm": {"achieved": hbm_ach, "peak": peak, "unit": "GB/s", "frac": hbm_ach / peak, "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_cv_step": ADJ_BYTES_PER_CV_STEP}}
+    # end to end through the public API with host buffers: handle creation and model upload from
+    # host arrays, the target traces from host memory, the gradient back to host memory
+    e2e = None
+    if not args.no_e2e:
+        tgt_host = target.cpu().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = arb.Simulation(model, dt=spec.dt, epoch_steps=spec.epoch_steps)
+        for _ in range(args.steps):
+            l2, g2 = sim2.adjoint(K, obs, tgt_host, scale, group, ng, checkpoint_every=args.checkpoint_every)
+            g2h = g2.cpu().numpy()
+        el = time.perf_counter() - t0
+        assert abs(l2 - loss) <= 1e-12 * abs(loss) and g2h.shape == (ng, 4)
+        e2e = {"value": units / el, "unit": "CV-steps/s", "h2d_bytes_per_step": int(tgt_host.nbytes + model_bytes(model) / args.steps),
+               "d2h_bytes_per_step": int(g2h.nbytes + 8),
+               "includes": "handle creation and model upload from host arrays; per step: target traces from host, "
+                           "loss and gradient, gradient to host"}
+        del sim2
     print(json.dumps({
         "metric": "compartment-steps/sec (gradient)", "value": value, "unit": "CV-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "cells": model.n_cells, "cvs": model.n_cv, "loss": loss,
                    "l2": "working set (checkpoints and a 500-step segment, ~1.3 GB) larger than L2"},
-        "adjoint_kernels_ms_mean": sum(kern) / len(kern),
-        "cpu_baseline": cpu, "e2e": None, "gpu_launches": sim.last_timing()[1] * args.steps, "clocks": clk}), flush=True)
+        "adjoint_kernels_ms_mean": kern_mean, "roofline": roofline,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": sim.last_timing()[1] * args.steps, "clocks": clk}), flush=True)
 
 
 def cpu_baseline(model, spec, budget_s, dry_run_ranks=1):
@@ -327,7 +372,9 @@ def main():
     ap.add_argument("--spread-rows", type=int, default=0,
                     help="streamed plans: target rows of a pack of spread cells (0: the library's choice)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-cells", type=int, default=4096, help="reference arm: cells sampled per step (0 = all)")
+    ap.add_argument("--ref-cells", type=int, default=0,
+                    help="reference arm: time the oracle on the first this many cells, open loop (0 = every cell of "
+                         "the workload, closed loop, as the timed arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-forms", action="store_true", help="batched workload: skip the mixed-precision comparison")

@@ -300,6 +300,23 @@ arb_status arb_math_eval(int32_t fn, int64_t n, const double* x, double* y, void
 arb_status arb_hh_gate_table(double dt, double* coef, int64_t cap, int64_t* n_intervals, double* v_lo,
                              double* per_mv);
 
+/* Debug builds (libarb_b300_debug.so, compiled with ARB_DEBUG): every index read from an index
+ * array on the device (parent hand-over stacks and mailbox slots, compact mechanism slots,
+ * detector and probe slots, synapse owners, spike positions) is checked against its range; a
+ * value outside it is replaced by 0 and reported by arb_advance as ARB_E_STATE ("debug check").
+ * Every workspace region is followed by 256 guard bytes, written at arb_bind_workspace and
+ * compared after every arb_advance and by arb_check_canaries, which returns ARB_E_STATE naming
+ * the region whose guard was overwritten (ARB_OK if all are intact; in release builds ARB_OK with
+ * the message that there are no guard words). arb_debug_build returns 1 in a debug build. */
+arb_status arb_check_canaries(arb_sim* sim);
+int32_t arb_debug_build(void);
+
+/* Where a named array of the plan lies in the workspace (byte offset from the bound base, and
+ * its size), valid after arb_create: e.g. "V" (voltages, tile order), "det_slot", "pslot". Host
+ * only; ARB_E_ARG for an unknown name. In debug builds the region's 256 guard bytes start at the
+ * next multiple of 256 after offset + bytes. */
+arb_status arb_workspace_region(const arb_sim* sim, const char* name, int64_t* offset, int64_t* bytes);
+
 /* The compiled variants of the streamed epoch kernel (arb_params.kernel_variant): returns their
  * number; for v < cap, warps[v] = warps per SM, fwd_rows[v] and back_rows[v] = rows each warp
  * keeps in flight in the forward elimination and the back substitution. Arrays may be NULL. */

@@ -1,43 +1,63 @@
-"""Builds the CUDA library in-tree: csrc/*.cu -> libarb_b300.so (sm_103a only)."""
+"""Builds the CUDA library in-tree: csrc/*.cu -> libarb_b300.so (sm_103a only), and the same
+sources with ARB_DEBUG (device index checks and workspace guard words) -> libarb_b300_debug.so.
+Sources compile in parallel to objects under _build/, then link into the shared library."""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libarb_b300.so")
+LIB_DEBUG = os.path.join(HERE, "libarb_b300_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+OBJ = os.path.join(HERE, "_build")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-shared"]
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + NVCC_FLAGS + ["-I", INCLUDE] + sources() + ["-o", tmp]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.makedirs(OBJ, exist_ok=True)
+    extra = ["-DARB_DEBUG"] if debug else []
+    tag = "%s.%d" % ("dbg" if debug else "rel", os.getpid())
+
+    def compile_one(src):
+        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + "." + tag + ".o")
+        cmd = [nvcc] + NVCC_FLAGS + extra + ["-I", INCLUDE, "-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(sources()), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, sources()))
+    tmp = lib + ".%d.tmp" % os.getpid()
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared"] + objs + ["-o", tmp], check=True)
+    os.replace(tmp, lib)
+    for o in objs:
+        os.remove(o)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build(force=True, verbose=True, debug=True))

@@ -22,7 +22,8 @@ EXPORTED = ["arb_default_params", "arb_create", "arb_destroy", "arb_workspace_by
             "arb_enqueue_events", "arb_advance", "arb_time", "arb_read_voltage", "arb_num_spikes",
             "arb_read_spikes", "arb_read_spikes_from", "arb_hh_gate_table", "arb_set_probes", "arb_get_state", "arb_set_state", "arb_plan_info",
             "arb_last_timing", "arb_last_error", "arb_solve_trees_noalloc", "arb_adjoint_workspace_bytes",
-            "arb_adjoint", "arb_math_eval", "arb_kernel_variants", "arb_plan_packs"]
+            "arb_adjoint", "arb_math_eval", "arb_kernel_variants", "arb_plan_packs", "arb_check_canaries",
+            "arb_debug_build", "arb_workspace_region"]
 
 
 class arb_params(C.Structure):
@@ -51,18 +52,21 @@ class arb_model(C.Structure):
     ]
 
 
-_lib = None
+LIB_DEBUG_PATH = os.path.join(HERE, "libarb_b300_debug.so")
+_libs = {}
 
 
-def load():
-    """Loads libarb_b300.so; raises if it has not been built (no CPU fallback exists)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError("libarb_b300.so is missing: build it with __graft_entry__.build() or "
-                          "python paper_1901_07454_b300/_build.py (there is no CPU fallback)")
-    L = C.CDLL(LIB_PATH)
+def load(debug=False):
+    """Loads libarb_b300.so (or, with debug, libarb_b300_debug.so: device index checks and
+    workspace guard words); raises if it has not been built (no CPU fallback exists)."""
+    key = bool(debug)
+    if key in _libs:
+        return _libs[key]
+    path = LIB_DEBUG_PATH if debug else LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("%s is missing: build it with __graft_entry__.build() or "
+                          "python paper_1901_07454_b300/_build.py (there is no CPU fallback)" % os.path.basename(path))
+    L = C.CDLL(path)
     vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
     sig = {
         "arb_default_params": (i32, [vp]),
@@ -91,12 +95,15 @@ def load():
         "arb_math_eval": (i32, [i32, i64, vp, vp, vp]),
         "arb_kernel_variants": (i32, [i32, vp, vp, vp]),
         "arb_plan_packs": (i32, [vp, i64, vp, vp, vp, C.POINTER(i64)]),
+        "arb_check_canaries": (i32, [vp]),
+        "arb_debug_build": (i32, []),
+        "arb_workspace_region": (i32, [vp, C.c_char_p, C.POINTER(i64), C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    _lib = L
+    _libs[key] = L
     return L
 
 
@@ -106,9 +113,9 @@ class ArbError(RuntimeError):
         self.status = status
 
 
-def check(status, handle=None):
+def check(status, handle=None, lib=None):
     if status != ARB_OK:
-        msg = load().arb_last_error(handle)
+        msg = (lib or load()).arb_last_error(handle)
         raise ArbError(status, msg.decode() if msg else "")
 
 

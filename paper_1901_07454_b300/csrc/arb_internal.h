@@ -123,7 +123,22 @@ enum : int32_t {
     kStBucketOverflow = 4,
     kStNonFinite = 8,
     kStLateEvent = 16,
+    kStBounds = 32,           // debug builds: an index array held a value outside its range
 };
+
+// Debug builds (ARB_DEBUG): ARB_IDX(i, n, ctl) checks an index read from an index array against
+// [0, n). Outside it, the kernel records kStBounds in the control block and uses index 0 instead
+// (an address that exists), so that nothing faults and no lane leaves a warp-synchronous region
+// early; the host reports the flag after the epoch. Release builds use the index unchecked.
+struct Ctl;
+#ifdef ARB_DEBUG
+__device__ __forceinline__ int64_t dbg_idx(int64_t i, int64_t n, Ctl* ctl);
+#define ARB_IDX(i, n, ctl) ((int)::arbk::dbg_idx((int64_t)(i), (int64_t)(n), (ctl)))
+#define ARB_IDX64(i, n, ctl) (::arbk::dbg_idx((int64_t)(i), (int64_t)(n), (ctl)))
+#else
+#define ARB_IDX(i, n, ctl) (i)
+#define ARB_IDX64(i, n, ctl) (i)
+#endif
 
 // Everything the device kernels read; pointers into the caller's workspace.
 template <class MT>
@@ -231,6 +246,7 @@ struct EvArgs {
     int32_t epoch_steps;
     int32_t time_major;       // 1: order within a step by time first (exact event times)
     int32_t slot_mask;        // 1: two delivery-list buffers (overlapped exchange), 0: one
+    int64_t n_syn;            // synapse state units (debug index checks)
 };
 
 // Delivery lists of buffer `slot`: off[slot * (n_owner + 1) + o] .. [o + 1] index the records
@@ -327,5 +343,15 @@ struct AdjArgs {
     int32_t n_groups;
     double* grad;              // [n_groups][4] output
 };
+
+#ifdef ARB_DEBUG
+__device__ __forceinline__ int64_t dbg_idx(int64_t i, int64_t n, Ctl* ctl) {
+    if (i < 0 || i >= n) {
+        atomicOr(&ctl->status, (int)kStBounds);
+        return 0;
+    }
+    return i;
+}
+#endif
 
 }  // namespace arbk

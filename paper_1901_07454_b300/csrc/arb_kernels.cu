@@ -211,7 +211,7 @@ __device__ void run_pack(const DevModel<MT>& d, int p, double* tile, int64_t k0,
     hh_pass<MT, kSmem, kImp>(d, pk, w, lane, false, true, dt_m);
     __syncwarp();
 
-    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const int det = (lane < pk.ncell) ? ARB_IDX(d.det_slot[owner], pk.nrow * kWarp, d.ctl) : -1;
     const double thr = d.threshold;
     const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
     const bool probing = pk.npr > 0 && probe_max > 0;
@@ -392,7 +392,8 @@ __device__ void run_pack(const DevModel<MT>& d, int p, double* tile, int64_t k0,
             const int64_t prow = k - probe_k0;
             if (prow >= 0 && prow < probe_max)
                 for (int q = lane; q < pk.npr; q += kWarp)
-                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+                    d.trace[prow * d.n_probe + ARB_IDX(d.probe_col[pk.pr0 + q], d.n_probe, d.ctl)] =
+                        Vg[ARB_IDX(d.probe_slot[pk.pr0 + q], pk.nrow * kWarp, d.ctl)];
         }
         __syncwarp();
     }
@@ -516,7 +517,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         for (int u = 0; u < kSP; ++u) {
             const int js = jb + u;
             if (js >= pk.nsyn_row) break;
-            const int sl = s_sl[u], c = s_c[u];
+            const int sl = s_sl[u], c = s_c[u] < 0 ? s_c[u] : ARB_IDX(s_c[u], pk.nvc, d.ctl);
             const double dec = s_dec[u], esyn = s_e[u], sc = s_sc[u], c_e = s_ce[u], c_b = s_cb[u];
             MT g = s_g[u];
             sfetch(js + kSP, u, s_cn[u]);         // row js + kSP: its slot index is ready
@@ -573,8 +574,9 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     __syncwarp();
     for (int jh = 0; jh < pk.nhh_row; ++jh) {
         const size_t q = (size_t)(pk.hh_row0 + jh) * kWarp + lane;
-        const int sl = __ldg(d.hh_slot + q);
+        int sl = __ldg(d.hh_slot + q);
         if (sl < 0) continue;
+        sl = ARB_IDX(sl, pk.nrow * kWarp, d.ctl);
         const int idx = jh * kWarp + lane;
         const double vd = Vg[sl];
         const MT v = (MT)vd;
@@ -594,7 +596,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
             nS[idx] = n;
         }
         if (terms) {
-            const int c = __ldg(d.hh_vs + q);
+            const int c = ARB_IDX(__ldg(d.hh_vs + q), pk.nvc, d.ctl);
             const MT n2 = n * n;
             const MT gna = (MT)__ldg(d.hh_gna + q) * (m * m * m * h);
             const MT gk = (MT)__ldg(d.hh_gk + q) * (n2 * n2);
@@ -653,7 +655,7 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
     const MT dt_m = (MT)dt;
     stream_mech<MT, kImp>(d, pk, Gm, Em, Vg, gS, mS, hS, nS, lane, false, false, 0, true, ev_i, ev_end, late, dt_m);
 
-    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const int det = (lane < pk.ncell) ? ARB_IDX(d.det_slot[owner], pk.nrow * kWarp, d.ctl) : -1;
     const double thr = d.threshold;
     const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
     const bool probing = pk.npr > 0 && probe_max > 0;
@@ -734,10 +736,10 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                             double dd = fma(-kprev, eprev, E);
                             double bb = fma(kprev, yprev, fma(A, V, Bc));
                             if (kShared) {
-                                if (mb_in != kMbNone) { dd -= mbd[mb_in]; bb += mbb[mb_in]; }
+                                if (mb_in != kMbNone) { dd -= mbd[ARB_IDX(mb_in, pk.nmb, d.ctl)]; bb += mbb[ARB_IDX(mb_in, pk.nmb, d.ctl)]; }
                             } else {
                                 for (int q = f & kFlagPopMask; q > 0; --q) {
-                                    const double2 c2 = stk[(--sp) * kWarp + lane];
+                                    const double2 c2 = stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane];
                                     dd -= c2.x;
                                     bb += c2.y;
                                 }
@@ -749,8 +751,8 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                             Rs[sl] = ee;
                             const bool remote = (f & kFlagRemote) != 0;
                             if (remote && !(f & kFlagRoot)) {
-                                if (kShared) { mbd[mb_out] += K * ee; mbb[mb_out] += K * uu; }
-                                else stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                                if (kShared) { mbd[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * ee; mbb[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * uu; }
+                                else stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(K * ee, K * uu);
                             }
                             kprev = remote ? 0.0 : K;
                             eprev = ee;
@@ -758,15 +760,15 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                         } else {
                             double y = fma(-kprev, yprev, fma(A, V, Bc) + M);
                             if (kShared) {
-                                if (mb_in != kMbNone) y -= mbd[mb_in];
+                                if (mb_in != kMbNone) y -= mbd[ARB_IDX(mb_in, pk.nmb, d.ctl)];
                             } else {
-                                for (int q = f & kFlagPopMask; q > 0; --q) y -= stk[(--sp) * kWarp + lane].x;
+                                for (int q = f & kFlagPopMask; q > 0; --q) y -= stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane].x;
                             }
                             Bs[sl] = y;
                             const bool remote = (f & kFlagRemote) != 0;
                             if (remote && !(f & kFlagRoot)) {
-                                if (kShared) mbd[mb_out] += K * y;
-                                else stk[(sp++) * kWarp + lane] = make_double2(K * y, 0.0);
+                                if (kShared) mbd[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * y;
+                                else stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(K * y, 0.0);
                             }
                             kprev = remote ? 0.0 : K;
                             yprev = y;
@@ -806,14 +808,14 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
                         fetch(j - kPB, u);
                         double vp;
                         if (f & kFlagRoot) vp = 0.0;
-                        else if (f & kFlagRemote) vp = kShared ? mbv[(f >> kMbOutShift) & kMbNone] : stk[(--sp) * kWarp + lane].x;
+                        else if (f & kFlagRemote) vp = kShared ? mbv[ARB_IDX((f >> kMbOutShift) & kMbNone, pk.nmb, d.ctl)] : stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane].x;
                         else vp = vnext;
                         const double v = fma(X, vp, U);
                         if (kShared) {
                             const int mb_in = (int)((unsigned)f >> kMbInShift);
-                            if (mb_in != kMbNone) mbv[mb_in] = v;
+                            if (mb_in != kMbNone) mbv[ARB_IDX(mb_in, pk.nmb, d.ctl)] = v;
                         } else {
-                            for (int q = f & kFlagPopMask; q > 0; --q) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                            for (int q = f & kFlagPopMask; q > 0; --q) stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(v, 0.0);
                         }
                         Vg[j * kWarp + lane] = v;
                         if (last) bad |= !isfinite(v);
@@ -856,7 +858,8 @@ __device__ void run_pack_stream(const DevModel<MT>& d, int p, double2* stack, in
             const int64_t prow = k - probe_k0;
             if (prow >= 0 && prow < probe_max)
                 for (int q = lane; q < pk.npr; q += kWarp)
-                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+                    d.trace[prow * d.n_probe + ARB_IDX(d.probe_col[pk.pr0 + q], d.n_probe, d.ctl)] =
+                        Vg[ARB_IDX(d.probe_slot[pk.pr0 + q], pk.nrow * kWarp, d.ctl)];
         }
         __syncwarp();
     }
@@ -961,7 +964,7 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
 
     mech(dt, 0, (double)k0 * dt, false, true);   // terms of the first piece; events at its start
 
-    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const int det = (lane < pk.ncell) ? ARB_IDX(d.det_slot[owner], pk.nrow * kWarp, d.ctl) : -1;
     const double thr = d.threshold;
     const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
     const bool probing = pk.npr > 0 && probe_max > 0;
@@ -1010,7 +1013,7 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
                     double dd = fma(-kprev, eprev, E);
                     double bb = fma(kprev, yprev, fma(A, V, B));
                     for (int qq = f & kFlagPopMask; qq > 0; --qq) {
-                        const double2 c2 = stk[(--sp) * kWarp + lane];
+                        const double2 c2 = stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane];
                         dd -= c2.x;
                         bb += c2.y;
                     }
@@ -1022,7 +1025,7 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
                         Rs[j * kWarp + lane] = ee;
                     }
                     const bool remote = (f & kFlagRemote) != 0;
-                    if (remote && !(f & kFlagRoot)) stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                    if (remote && !(f & kFlagRoot)) stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(K * ee, K * uu);
                     kprev = remote ? 0.0 : K;
                     eprev = ee;
                     yprev = uu;
@@ -1037,10 +1040,10 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
                     const double U = Bs[j * kWarp + lane], X = Rs[j * kWarp + lane];
                     double vp;
                     if (f & kFlagRoot) vp = 0.0;
-                    else if (f & kFlagRemote) vp = stk[(--sp) * kWarp + lane].x;
+                    else if (f & kFlagRemote) vp = stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane].x;
                     else vp = vnext;
                     const double v = fma(X, vp, U);
-                    for (int qq = f & kFlagPopMask; qq > 0; --qq) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                    for (int qq = f & kFlagPopMask; qq > 0; --qq) stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(v, 0.0);
                     if (act) {
                         Vg[j * kWarp + lane] = v;
                         if (last) bad |= !isfinite(v);
@@ -1088,7 +1091,8 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
             const int64_t prow = k - probe_k0;
             if (prow >= 0 && prow < probe_max)
                 for (int q = lane; q < pk.npr; q += kWarp)
-                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+                    d.trace[prow * d.n_probe + ARB_IDX(d.probe_col[pk.pr0 + q], d.n_probe, d.ctl)] =
+                        Vg[ARB_IDX(d.probe_slot[pk.pr0 + q], pk.nrow * kWarp, d.ctl)];
         }
         __syncwarp();
     }
@@ -1191,7 +1195,7 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
     const MT dt_m = (MT)dt;
     stream_mech<MT, true>(d, pk, Gm, Em, Vg, gS, mS, hS, nS, lane, false, false, 0, true, ev_i, ev_end, late, dt_m);
 
-    const int det = (lane < pk.ncell) ? d.det_slot[owner] : -1;
+    const int det = (lane < pk.ncell) ? ARB_IDX(d.det_slot[owner], pk.nrow * kWarp, d.ctl) : -1;
     const double thr = d.threshold;
     const int64_t probe_k0 = d.ctl->probe_k0, probe_max = d.ctl->probe_max;
     const bool probing = pk.npr > 0 && probe_max > 0;
@@ -1225,6 +1229,7 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
         int slot = -1;
         if (lane < ns) slot = (int)(ws & 0xFFFFFF) + lane;
         else if (lane < ns + nn) slot = pk.nsc + (int)(wn & 0xFFFFFF) + (lane - ns);
+        if (slot >= 0) slot = ARB_IDX(slot, pk.nvc, d.ctl);
         const bool mc = in && slot >= 0;
         cp_async_8(&r.v[lane], Vg + o, in);
         cp_async_8(&r.a[lane], ca_p + o, in);
@@ -1275,7 +1280,7 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 cp_async_wait<kRF - 1>();                // row j has landed (this lane's copies)
                 __syncwarp();                            // ... and every lane's (compact slots)
                 const FwdRow& r = fr[j & (kRF - 1)];
-                const int cp = r.cpos[lane];
+                const int cp = r.cpos[lane] < 0 ? -1 : ARB_IDX(r.cpos[lane], kWarp, d.ctl);
                 const double V = r.v[lane], A = r.a[lane], K = r.k[lane];
                 const double E = cp >= 0 ? r.gm[cp] : r.e[lane];
                 const double Bc = cp >= 0 ? r.em[cp] : r.b[lane];
@@ -1291,10 +1296,10 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 double dd = fma(-kprev, eprev, E);
                 double bb = fma(kprev, yprev, fma(A, V, Bc));
                 if (kShared) {
-                    if (mb_in != kMbNone) { dd -= mbd[mb_in]; bb += mbb[mb_in]; }
+                    if (mb_in != kMbNone) { dd -= mbd[ARB_IDX(mb_in, pk.nmb, d.ctl)]; bb += mbb[ARB_IDX(mb_in, pk.nmb, d.ctl)]; }
                 } else {
                     for (int q = f & kFlagPopMask; q > 0; --q) {
-                        const double2 c2 = stk[(--sp) * kWarp + lane];
+                        const double2 c2 = stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane];
                         dd -= c2.x;
                         bb += c2.y;
                     }
@@ -1305,8 +1310,8 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 UE[(size_t)j * kWarp + lane] = make_double2(uu, ee);
                 const bool remote = (f & kFlagRemote) != 0;
                 if (remote && !(f & kFlagRoot)) {
-                    if (kShared) { mbd[mb_out] += K * ee; mbb[mb_out] += K * uu; }
-                    else stk[(sp++) * kWarp + lane] = make_double2(K * ee, K * uu);
+                    if (kShared) { mbd[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * ee; mbb[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * uu; }
+                    else stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(K * ee, K * uu);
                 }
                 kprev = remote ? 0.0 : K;
                 eprev = ee;
@@ -1335,14 +1340,14 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 }
                 double vp;
                 if (f & kFlagRoot) vp = 0.0;
-                else if (f & kFlagRemote) vp = kShared ? mbv[(f >> kMbOutShift) & kMbNone] : stk[(--sp) * kWarp + lane].x;
+                else if (f & kFlagRemote) vp = kShared ? mbv[ARB_IDX((f >> kMbOutShift) & kMbNone, pk.nmb, d.ctl)] : stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane].x;
                 else vp = vnext;
                 const double v = fma(ue.y, vp, ue.x);
                 if (kShared) {
                     const int mb_in = (int)((unsigned)f >> kMbInShift);
-                    if (mb_in != kMbNone) mbv[mb_in] = v;
+                    if (mb_in != kMbNone) mbv[ARB_IDX(mb_in, pk.nmb, d.ctl)] = v;
                 } else {
-                    for (int q = f & kFlagPopMask; q > 0; --q) stk[(sp++) * kWarp + lane] = make_double2(v, 0.0);
+                    for (int q = f & kFlagPopMask; q > 0; --q) stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(v, 0.0);
                 }
                 Vg[(size_t)j * kWarp + lane] = v;
                 if (last) bad |= !isfinite(v);
@@ -1384,7 +1389,8 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
             const int64_t prow = k - probe_k0;
             if (prow >= 0 && prow < probe_max)
                 for (int q = lane; q < pk.npr; q += kWarp)
-                    d.trace[prow * d.n_probe + d.probe_col[pk.pr0 + q]] = Vg[d.probe_slot[pk.pr0 + q]];
+                    d.trace[prow * d.n_probe + ARB_IDX(d.probe_col[pk.pr0 + q], d.n_probe, d.ctl)] =
+                        Vg[ARB_IDX(d.probe_slot[pk.pr0 + q], pk.nrow * kWarp, d.ctl)];
         }
         __syncwarp();
     }
@@ -1636,7 +1642,8 @@ __global__ void k_ev_walk(EvArgs a) {
             t = a.ext_t[x]; w = a.ext_w[x]; step = a.ext_step[x]; syn = a.ext_syn[x]; src = -1; idx = a.ext_idx[x];
         }
         if (step < k0) { atomicOr(&c->status, kStLateEvent); step = k0; }
-        const int owner = a.syn_owner[syn];
+        syn = ARB_IDX(syn, a.n_syn, c);
+        const int owner = ARB_IDX(a.syn_owner[syn], a.n_owner, c);
         if (!kScatter) {
             atomicAdd(&a.counts[owner], 1);
         } else {
@@ -1837,7 +1844,7 @@ __global__ void k_spike_expand(SpkArgs a) {
         int64_t my_q0 = 0, my_deg = 0;
         if (lane < per && i < n_glob) {
             const int64_t r = i / n_local, j = lo + (i - r * n_local);
-            my_gid = (int32_t)(a.spk_gid[j] + r * a.n_cells);
+            my_gid = (int32_t)ARB_IDX64(a.spk_gid[ARB_IDX64(j, a.spike_cap, c)] + r * a.n_cells, a.n_cells * a.dry_ranks, c);
             my_ts = a.spk_t[j];
             my_q0 = a.out_ptr[my_gid];
             my_deg = a.out_ptr[my_gid + 1] - my_q0;

@@ -63,6 +63,10 @@ using namespace arbk;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+#ifdef ARB_DEBUG
+constexpr int kCanaryBytes = 256;
+constexpr unsigned char kCanaryByte = 0xA5;
+#endif
 constexpr int kGraphRing = 4;
 
 struct ExtEvent {
@@ -638,8 +642,43 @@ static void layout_regions(arb_sim* sim) {
         r.bytes = w.second;
         sim->regions.push_back({w.first, r});
         off += w.second;
+#ifdef ARB_DEBUG
+        off = (off + 255) & ~(size_t)255;
+        off += kCanaryBytes;                 // guard words after the region
+#endif
     }
     sim->ws_bytes = (int64_t)((off + 255) & ~(size_t)255);
+}
+
+#ifdef ARB_DEBUG
+// Debug builds: kCanaryBytes of kCanaryByte after every workspace region, written at bind and
+// compared after every arb_advance (arb_check_canaries); a kernel writing past the end of a
+// region changes them.
+static size_t canary_off(const Region& r) { return ((r.off + r.bytes + 255) & ~(size_t)255); }
+
+static arb_status write_canaries(arb_sim* sim) {
+    for (auto& r : sim->regions)
+        CU(cudaMemsetAsync(sim->ws + canary_off(r.second), kCanaryByte, kCanaryBytes, sim->s));
+    return ARB_OK;
+}
+#endif
+
+static arb_status check_canaries(arb_sim* sim) {
+#ifdef ARB_DEBUG
+    std::vector<unsigned char> h(kCanaryBytes * sim->regions.size());
+    for (size_t i = 0; i < sim->regions.size(); ++i)
+        CU(cudaMemcpyAsync(h.data() + i * kCanaryBytes, sim->ws + canary_off(sim->regions[i].second), kCanaryBytes,
+                           cudaMemcpyDeviceToHost, sim->s));
+    CU(cudaStreamSynchronize(sim->s));
+    for (size_t i = 0; i < sim->regions.size(); ++i)
+        for (int b = 0; b < kCanaryBytes; ++b)
+            if (h[i * kCanaryBytes + b] != kCanaryByte)
+                return fail(sim, ARB_E_STATE, "debug check: the guard words after workspace region '" +
+                                                  sim->regions[i].first + "' were overwritten");
+    return ARB_OK;
+#else
+    return fail(sim, ARB_OK, "this build keeps no guard words (build with ARB_DEBUG)");
+#endif
 }
 
 static char* region(arb_sim* sim, const char* name) {
@@ -2361,6 +2400,9 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     CU(cudaMemcpyAsync(region(sim, "ctl"), &c0, sizeof(Ctl), cudaMemcpyHostToDevice, sim->s));
     fill_devmodel(sim, sim->dm64);
     fill_devmodel(sim, sim->dm32);
+#ifdef ARB_DEBUG
+    if ((st = write_canaries(sim)) != ARB_OK) return st;
+#endif
     sim->bound = true;
     st = upload_mech_state(sim, sim->init_m, sim->init_h, sim->init_n, std::vector<double>(sim->syn_cv.size(), 0.0));
     if (st != ARB_OK) return st;
@@ -2382,6 +2424,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     a.tmp = (EvRec*)region(sim, "ev_tmp");
     a.bucket_cap = sim->prm.bucket_capacity;
     a.n_owner = (int32_t)(pl.packs.size() * kWarp);
+    a.n_syn = (int64_t)sim->u_cv.size();
     a.epoch_steps = sim->epoch_steps;
     a.time_major = sim->exact ? 1 : 0;
     a.slot_mask = sim->overlap ? 1 : 0;
@@ -2591,9 +2634,38 @@ arb_status arb_advance(arb_sim* sim, double t_end) {
         if (hc.status & kStBucketOverflow) what += " bucket_capacity";
         return fail(sim, ARB_E_OVERFLOW, "capacity exceeded:" + what);
     }
+    if (hc.status & kStBounds) return fail(sim, ARB_E_STATE, "debug check: an index array held a value outside its range");
     if (hc.status & kStNonFinite) return fail(sim, ARB_E_NONFINITE, "a voltage became NaN or infinite");
     if (hc.status & kStLateEvent) return fail(sim, ARB_E_STATE, "internal: an event arrived after its step");
+#ifdef ARB_DEBUG
+    if ((st = check_canaries(sim)) != ARB_OK) return st;
+#endif
     return ARB_OK;
+}
+
+arb_status arb_workspace_region(const arb_sim* sim, const char* name, int64_t* offset, int64_t* bytes) {
+    if (!sim || !name) return ARB_E_ARG;
+    for (const auto& r : sim->regions)
+        if (r.first == name) {
+            if (offset) *offset = (int64_t)r.second.off;
+            if (bytes) *bytes = (int64_t)r.second.bytes;
+            return ARB_OK;
+        }
+    return ARB_E_ARG;
+}
+
+arb_status arb_check_canaries(arb_sim* sim) {
+    if (!sim) return ARB_E_ARG;
+    if (!sim->bound) return fail(sim, ARB_E_STATE, "no workspace bound");
+    return check_canaries(sim);
+}
+
+int32_t arb_debug_build(void) {
+#ifdef ARB_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 arb_status arb_time(const arb_sim* sim, double* t, int64_t* steps) {

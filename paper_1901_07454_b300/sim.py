@@ -61,8 +61,10 @@ class Plan:
     def __init__(self, model, dt=0.025, epoch_steps=0, precision="fp64", cells_per_pack=0, smem_budget=0,
                  event_capacity=None, ext_event_capacity=None, spike_capacity=None, bucket_capacity=None,
                  stream=None, scheme="implicit", split_cvs=0, coalesce_synapses=False, exact_events=False,
-                 epoch_overlap=False, dry_run_ranks=1, kernel_variant=-1, spread_rows=0):
-        lib = L.load()
+                 epoch_overlap=False, dry_run_ranks=1, kernel_variant=-1, spread_rows=0, debug=False):
+        """debug=True runs on the debug build (device index checks, workspace guard words)."""
+        lib = L.load(debug)
+        self.lib = lib
         self.model = model
         p = default_params()
         p.dt = float(dt)
@@ -93,12 +95,12 @@ class Plan:
         self._ms, self._keep = _model_struct(model)
         h = C.c_void_p()
         st = lib.arb_create(C.byref(self._ms), C.byref(p), C.byref(h))
-        L.check(st, None)
+        L.check(st, None, lib)
         self.h = h
 
     def close(self):
         if getattr(self, "h", None):
-            L.load().arb_destroy(self.h)
+            self.lib.arb_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -109,24 +111,35 @@ class Plan:
 
     def workspace_bytes(self) -> int:
         n = C.c_int64()
-        L.check(L.load().arb_workspace_bytes(self.h, C.byref(n)), self.h)
+        L.check(self.lib.arb_workspace_bytes(self.h, C.byref(n)), self.h, self.lib)
         return n.value
+
+    def workspace_region(self, name):
+        """(byte offset, bytes) of a named plan array in the workspace (arb_workspace_region)."""
+        off, nb = C.c_int64(), C.c_int64()
+        L.check(self.lib.arb_workspace_region(self.h, name.encode(), C.byref(off), C.byref(nb)), self.h, self.lib)
+        return off.value, nb.value
+
+    def check_canaries(self):
+        """Debug builds: raises ArbError when a guard word after a workspace region was overwritten."""
+        L.check(self.lib.arb_check_canaries(self.h), self.h, self.lib)
 
     def plan_packs(self):
         """Per pack, in the persistent kernel's order: (solve rows, kind, mechanism rows) arrays;
         kind 0 streamed one cell per lane, 1 streamed spread over lanes, 2/3 tile packs."""
-        lib = L.load()
+        lib = self.lib
         n = C.c_int64()
-        L.check(lib.arb_plan_packs(self.h, 0, None, None, None, C.byref(n)), self.h)
+        L.check(lib.arb_plan_packs(self.h, 0, None, None, None, C.byref(n)), self.h, self.lib)
         rows, kind, mech = (np.zeros(n.value, np.int32) for _ in range(3))
-        L.check(lib.arb_plan_packs(self.h, n.value, _p(rows), _p(kind), _p(mech), C.byref(n)), self.h)
+        L.check(lib.arb_plan_packs(self.h, n.value, _p(rows), _p(kind), _p(mech), C.byref(n)), self.h, self.lib)
         return rows, kind, mech
 
     def plan_info(self):
         npk, rows, smem, mxr, split, srows = (C.c_int64() for _ in range(6))
         eff, ep, kpp, kv = C.c_double(), C.c_int32(), C.c_int32(), C.c_int32()
-        L.check(L.load().arb_plan_info(self.h, C.byref(npk), C.byref(rows), C.byref(smem), C.byref(eff), C.byref(ep),
-                                       C.byref(mxr), C.byref(kpp), C.byref(split), C.byref(srows), C.byref(kv)), self.h)
+        L.check(self.lib.arb_plan_info(self.h, C.byref(npk), C.byref(rows), C.byref(smem), C.byref(eff), C.byref(ep),
+                                       C.byref(mxr), C.byref(kpp), C.byref(split), C.byref(srows), C.byref(kv)), self.h,
+                self.lib)
         return dict(n_packs=npk.value, total_rows=rows.value, smem_packs=smem.value, lane_efficiency=eff.value,
                     epoch_steps=ep.value, max_pack_rows=mxr.value, cells_per_pack=kpp.value, split_cvs=split.value,
                     spread_rows=srows.value, kernel_variant=kv.value)
@@ -150,7 +163,8 @@ class Simulation(Plan):
         self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
         aligned = (base + 255) & ~255
-        L.check(L.load().arb_bind_workspace(self.h, C.c_void_p(aligned), nbytes), self.h)
+        self._ws_shift = aligned - base          # the bound workspace starts here in self._ws
+        L.check(self.lib.arb_bind_workspace(self.h, C.c_void_p(aligned), nbytes), self.h, self.lib)
         self.dt = float(dt)
         self._trace = None
 
@@ -160,14 +174,14 @@ class Simulation(Plan):
         t = np.ascontiguousarray(t, np.float64)
         w = np.ascontiguousarray(w, np.float64)
         if syn.size:
-            L.check(L.load().arb_enqueue_events(self.h, syn.size, _p(syn), _p(t), _p(w)), self.h)
+            L.check(self.lib.arb_enqueue_events(self.h, syn.size, _p(syn), _p(t), _p(w)), self.h, self.lib)
 
     def advance(self, t_end: float):
-        L.check(L.load().arb_advance(self.h, float(t_end)), self.h)
+        L.check(self.lib.arb_advance(self.h, float(t_end)), self.h, self.lib)
 
     def time(self):
         t, k = C.c_double(), C.c_int64()
-        L.check(L.load().arb_time(self.h, C.byref(t), C.byref(k)), self.h)
+        L.check(self.lib.arb_time(self.h, C.byref(t), C.byref(k)), self.h, self.lib)
         return t.value, k.value
 
     # --- outputs
@@ -176,15 +190,15 @@ class Simulation(Plan):
         n = int(self.model.n_cv)
         if out is not None:
             assert out.is_cuda and out.dtype == self.torch.float64 and out.numel() == n
-            L.check(L.load().arb_read_voltage(self.h, C.c_void_p(out.data_ptr()), n, 1), self.h)
+            L.check(self.lib.arb_read_voltage(self.h, C.c_void_p(out.data_ptr()), n, 1), self.h, self.lib)
             return out
         v = np.zeros(n)
-        L.check(L.load().arb_read_voltage(self.h, _p(v), n, 0), self.h)
+        L.check(self.lib.arb_read_voltage(self.h, _p(v), n, 0), self.h, self.lib)
         return v
 
     def num_spikes(self) -> int:
         n = C.c_int64()
-        L.check(L.load().arb_num_spikes(self.h, C.byref(n)), self.h)
+        L.check(self.lib.arb_num_spikes(self.h, C.byref(n)), self.h, self.lib)
         return n.value
 
     def spikes(self, first=0):
@@ -193,7 +207,7 @@ class Simulation(Plan):
         gid = np.zeros(max(n, 1), np.int32)
         t = np.zeros(max(n, 1))
         got = C.c_int64()
-        L.check(L.load().arb_read_spikes_from(self.h, int(first), _p(gid), _p(t), n, C.byref(got)), self.h)
+        L.check(self.lib.arb_read_spikes_from(self.h, int(first), _p(gid), _p(t), n, C.byref(got)), self.h, self.lib)
         return gid[:got.value], t[:got.value]
 
     def new_spikes(self):
@@ -207,23 +221,23 @@ class Simulation(Plan):
     def set_probes(self, cvs, max_steps):
         cvs = np.ascontiguousarray(cvs, np.int64)
         self._trace = self.torch.full((int(max_steps), cvs.size), float("nan"), dtype=self.torch.float64, device=self.device)
-        L.check(L.load().arb_set_probes(self.h, cvs.size, _p(cvs), C.c_void_p(self._trace.data_ptr()), int(max_steps)), self.h)
+        L.check(self.lib.arb_set_probes(self.h, cvs.size, _p(cvs), C.c_void_p(self._trace.data_ptr()), int(max_steps)), self.h, self.lib)
         return self._trace
 
     def get_state(self):
         m = self.model
         nh = np.asarray(m.hh_cv).size
         V, mm, hh, nn, g = np.zeros(m.n_cv), np.zeros(nh), np.zeros(nh), np.zeros(nh), np.zeros(m.n_syn)
-        L.check(L.load().arb_get_state(self.h, _p(V), _p(mm), _p(hh), _p(nn), _p(g)), self.h)
+        L.check(self.lib.arb_get_state(self.h, _p(V), _p(mm), _p(hh), _p(nn), _p(g)), self.h, self.lib)
         return dict(V=V, m=mm, h=hh, n=nn, g=g)
 
     def set_state(self, st):
         arrs = [np.ascontiguousarray(st[k], np.float64) for k in ("V", "m", "h", "n", "g")]
-        L.check(L.load().arb_set_state(self.h, *[_p(a) for a in arrs]), self.h)
+        L.check(self.lib.arb_set_state(self.h, *[_p(a) for a in arrs]), self.h, self.lib)
 
     def last_timing(self):
         ms, n = C.c_double(), C.c_int64()
-        L.check(L.load().arb_last_timing(self.h, C.byref(ms), C.byref(n)), self.h)
+        L.check(self.lib.arb_last_timing(self.h, C.byref(ms), C.byref(n)), self.h, self.lib)
         return ms.value, n.value
 
     # --- discrete adjoint
@@ -232,20 +246,21 @@ class Simulation(Plan):
         state is left unchanged. target: [n_steps, n_obs] (host or device); returns
         (loss float, grad float64 tensor [n_groups, 4] on the device)."""
         torch = self.torch
-        lib = L.load()
+        lib = self.lib
         n_steps, n_groups = int(n_steps), int(n_groups)
         obs_cv = np.ascontiguousarray(obs_cv, np.int64)
         group = np.ascontiguousarray(group_of_cv, np.int32)
         tgt = torch.as_tensor(target, dtype=torch.float64).to(self.device).reshape(n_steps, obs_cv.size).contiguous()
         nbytes = C.c_int64()
         L.check(lib.arb_adjoint_workspace_bytes(self.h, n_steps, int(checkpoint_every), obs_cv.size, n_groups,
-                                                C.byref(nbytes)), self.h)
+                                                C.byref(nbytes)), self.h, self.lib)
         ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
         aligned = (ws.data_ptr() + 255) & ~255
         grad = torch.zeros((n_groups, 4), dtype=torch.float64, device=self.device)
         loss = C.c_double()
         L.check(lib.arb_adjoint(self.h, n_steps, int(checkpoint_every), obs_cv.size, _p(obs_cv),
                                 C.c_void_p(tgt.data_ptr()), float(loss_scale), _p(group), n_groups,
-                                C.c_void_p(aligned), nbytes.value, C.c_void_p(grad.data_ptr()), C.byref(loss)), self.h)
+                                C.c_void_p(aligned), nbytes.value, C.c_void_p(grad.data_ptr()), C.byref(loss)), self.h,
+                self.lib)
         self._adj_keep = (ws, tgt)     # freed with the next call or the handle
         return loss.value, grad
