@@ -223,6 +223,12 @@ struct DevModel {
     const int32_t* cpos;
     const int32_t* row_cs;
     const int32_t* row_cn;
+    // FP32 mechanisms: float copies of the per-synapse decay factor and reversal and of the HH
+    // conductances (null otherwise)
+    const float* syn_decay_f;
+    const float* syn_e_f;
+    const float* hh_gna_f;
+    const float* hh_gk_f;
 };
 
 // Arguments of the event-delivery kernels.

@@ -486,8 +486,20 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
     ST gsum = 0, esum = 0;
     double cur_e = 0.0, cur_b = 0.0;
     int s_sl[kSP], s_c[kSP], s_cn[kSP];
-    double s_dec[kSP], s_e[kSP], s_sc[kSP], s_ce[kSP], s_cb[kSP];
+    ST s_dec[kSP], s_e[kSP];
+    double s_sc[kSP], s_ce[kSP], s_cb[kSP];
     MT s_g[kSP];
+    // per-synapse decay factor and reversal in the precision of the sums (float copies for FP32
+    // mechanisms, so that no conversion is needed per synapse row)
+    const ST* syn_dec_p;
+    const ST* syn_e_p;
+    if constexpr (std::is_same<ST, float>::value) {
+        syn_dec_p = d.syn_decay_f;
+        syn_e_p = d.syn_e_f;
+    } else {
+        syn_dec_p = d.syn_decay;
+        syn_e_p = d.syn_e;
+    }
     auto sfetch_c = [&](int js) {
         return js < pk.nsyn_row ? __ldg(d.syn_vs + (size_t)(pk.syn_row0 + js) * kWarp + lane) : -1;
     };
@@ -496,8 +508,8 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         const size_t q = (size_t)(pk.syn_row0 + (in ? js : 0)) * kWarp + lane;
         s_c[u] = c;
         s_sl[u] = (in && !kImp) ? __ldg(d.syn_slot + q) : -1;
-        s_dec[u] = in ? __ldg(d.syn_decay + q) : 1.0;
-        s_e[u] = in ? __ldg(d.syn_e + q) : 0.0;
+        s_dec[u] = in ? __ldg(syn_dec_p + q) : (ST)1;
+        s_e[u] = in ? __ldg(syn_e_p + q) : (ST)0;
         s_sc[u] = (in && !kImp) ? __ldg(d.syn_sc + q) : 0.0;
         s_g[u] = in ? gS[(in ? js : 0) * kWarp + lane] : (MT)0;
         s_ce[u] = (kImp && terms && c >= 0) ? __ldg(cE + c) : 0.0;
@@ -518,7 +530,8 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
             const int js = jb + u;
             if (js >= pk.nsyn_row) break;
             const int sl = s_sl[u], c = s_c[u] < 0 ? s_c[u] : ARB_IDX(s_c[u], pk.nvc, d.ctl);
-            const double dec = s_dec[u], esyn = s_e[u], sc = s_sc[u], c_e = s_ce[u], c_b = s_cb[u];
+            const ST dec = s_dec[u], esyn = s_e[u];
+            const double sc = s_sc[u], c_e = s_ce[u], c_b = s_cb[u];
             MT g = s_g[u];
             sfetch(js + kSP, u, s_cn[u]);         // row js + kSP: its slot index is ready
             s_cn[u] = sfetch_c(js + 2 * kSP);     // slot index of row js + 2 kSP
@@ -598,8 +611,16 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         if (terms) {
             const int c = ARB_IDX(__ldg(d.hh_vs + q), pk.nvc, d.ctl);
             const MT n2 = n * n;
-            const MT gna = (MT)__ldg(d.hh_gna + q) * (m * m * m * h);
-            const MT gk = (MT)__ldg(d.hh_gk + q) * (n2 * n2);
+            MT gbna, gbk;
+            if constexpr (std::is_same<MT, float>::value) {
+                gbna = __ldg(d.hh_gna_f + q);
+                gbk = __ldg(d.hh_gk_f + q);
+            } else {
+                gbna = __ldg(d.hh_gna + q);
+                gbk = __ldg(d.hh_gk + q);
+            }
+            const MT gna = gbna * (m * m * m * h);
+            const MT gk = gbk * (n2 * n2);
             if constexpr (kImp) {
                 Gm[c] += (double)(gna + gk);
                 Em[c] += (double)(gna * (MT)kENa + gk * (MT)kEK);

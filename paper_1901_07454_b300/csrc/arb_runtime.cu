@@ -613,6 +613,8 @@ static void layout_regions(arb_sim* sim) {
         {"syn_ntau", 8 * pl.syn_rows * kWarp}, {"slot_lo", 4 * std::max<int64_t>(nowner, 1)}, {"slot_hi", 4 * std::max<int64_t>(nowner, 1)},
         {"hh_tab", 8 * std::max<int64_t>((int64_t)sim->hh_tab.size(), 1)},
         {"hh_tab_f", 4 * std::max<int64_t>((int64_t)sim->hh_tab_f.size(), 1)},
+        {"syn_decay_f", 4 * (mx ? pl.syn_rows * kWarp : 1)}, {"syn_e_f", 4 * (mx ? pl.syn_rows * kWarp : 1)},
+        {"hh_gna_f", 4 * (mx ? pl.hh_rows * kWarp : 1)}, {"hh_gk_f", 4 * (mx ? pl.hh_rows * kWarp : 1)},
         {"hh_slot", 4 * pl.hh_rows * kWarp}, {"hh_vs", 4 * pl.hh_rows * kWarp}, {"hh_sc", 8 * pl.hh_rows * kWarp}, {"hh_gna", 8 * pl.hh_rows * kWarp},
         {"hh_gk", 8 * pl.hh_rows * kWarp}, {"hh_m", mt * pl.hh_rows * kWarp}, {"hh_h", mt * pl.hh_rows * kWarp},
         {"hh_n", mt * pl.hh_rows * kWarp},
@@ -711,6 +713,10 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.V = (double*)region(sim, "V");
     d.hh_tab = sim->hh_tab.empty() ? nullptr : (const double*)region(sim, "hh_tab");
     d.hh_tab_f = sim->hh_tab_f.empty() ? nullptr : (const float*)region(sim, "hh_tab_f");
+    d.syn_decay_f = (const float*)region(sim, "syn_decay_f");
+    d.syn_e_f = (const float*)region(sim, "syn_e_f");
+    d.hh_gna_f = (const float*)region(sim, "hh_gna_f");
+    d.hh_gk_f = (const float*)region(sim, "hh_gk_f");
     d.Sg = (double*)region(sim, "Sg");
     d.Rg = (double*)region(sim, "Rg");
     d.Gm = (double*)region(sim, "Gm");
@@ -2380,6 +2386,15 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     if (!sim->hh_tab.empty()) UP("hh_tab", sim->hh_tab);
     if (!sim->hh_tab_f.empty()) UP("hh_tab_f", sim->hh_tab_f);
+    if (sim->mixed) {   // float copies of the mechanism constants the FP32 mechanisms use
+        auto to_f = [](const std::vector<double>& v) {
+            std::vector<float> f(v.size());
+            for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+            return f;
+        };
+        UP("syn_decay_f", to_f(pl.syn_decay)); UP("syn_e_f", to_f(pl.syn_e));
+        UP("hh_gna_f", to_f(pl.hh_gna)); UP("hh_gk_f", to_f(pl.hh_gk));
+    }
     UP("hh_slot", pl.hh_slot); UP("hh_vs", pl.hh_vs); UP("hh_sc", pl.hh_sc); UP("hh_gna", pl.hh_gna); UP("hh_gk", pl.hh_gk);
     UP("st_slot", pl.st_slot); UP("st_sc", pl.st_sc); UP("st_on", pl.st_on); UP("st_off", pl.st_off); UP("st_amp", pl.st_amp);
     UP("det_slot", pl.det_slot); UP("det_gid", pl.det_gid);
