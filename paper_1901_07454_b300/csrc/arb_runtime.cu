@@ -1361,8 +1361,9 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             }
             return nb;
         };
-        // greedy packs of large cells, about 0.8 x 32 x target CVs each; a pack whose schedule
-        // runs much past the target, or whose mailbox would not fit, is halved
+        // greedy packs of large cells; a pack whose schedule runs past the target by more than
+        // kSpreadOver, or whose mailbox would not fit, is halved
+        constexpr double kSpreadOver = 1.25;
         std::function<void(const std::vector<int32_t>&, int64_t, std::vector<SGroup>&)> place_shared =
             [&](const std::vector<int32_t>& cs, int64_t target, std::vector<SGroup>& out) {
                 SGroup G;
@@ -1370,7 +1371,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 G.shared = true;
                 const bool fits = branch_points(cs) <= mb_max;
                 if (fits) G.rows = schedule_shared(cs, ord, sim->cv_offset, kStreamRound);
-                if (cs.size() > 1 && (!fits || (double)G.rows.rows.size() > 1.25 * (double)target)) {
+                if (cs.size() > 1 && (!fits || (double)G.rows.rows.size() > kSpreadOver * (double)target)) {
                     const size_t h = cs.size() / 2;
                     place_shared(std::vector<int32_t>(cs.begin(), cs.begin() + h), target, out);
                     place_shared(std::vector<int32_t>(cs.begin() + h, cs.end()), target, out);
@@ -1404,16 +1405,36 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             }
             return (double)rows + (double)sy + (double)st + (double)((hh + 31) / 32);
         };
-        // estimated costs of greedy packs of large cells with about kSpreadFill x 32 x target CVs
-        // each (the round schedule fills about that fraction of the lane-rows)
+        // Packs of large cells are grouped by estimated cost, not by CVs alone: a cell weighs its
+        // solve rows in a round schedule (its CVs over kSpreadFill x 32 lane-rows, x 1.05) plus its
+        // mechanism rows spread over the 32 lanes; a group is closed when its weight would pass
+        // the target, which is `target` solve rows of a pack of average composition (so a pack
+        // of cells with many synapses gets fewer CVs and every pack costs about the same).
+        auto spread_weight = [&](int32_t c) {
+            return 1.05 * (double)ncv_of[c] / (kSpreadFill * 32.0) + 1.1 * (double)(nsyn_of[c] + nst_of[c]) / 32.0 +
+                   (double)nhh_of[c] / 32.0;
+        };
+        auto target_weight = [&](const std::vector<int32_t>& big, int64_t target) {
+            double rows = 0.0, mech = 0.0;
+            for (int32_t c : big) {
+                rows += (double)ncv_of[c] / (kSpreadFill * 32.0);
+                mech += 1.1 * (double)(nsyn_of[c] + nst_of[c]) / 32.0 + (double)nhh_of[c] / 32.0;
+            }
+            return (double)target * (1.05 + (rows > 0.0 ? mech / rows : 0.0));
+        };
+        // estimated costs of the greedy packs of large cells
         auto est_shared = [&](const std::vector<int32_t>& big, int64_t target, std::vector<double>& cost) {
+            const double wt = target_weight(big, target);
             size_t i = 0;
             while (i < big.size()) {
                 int64_t sum = 0, dep = 0, sy = 0, hh = 0, st = 0;
+                double w = 0.0;
                 size_t k = 0;
                 while (i + k < big.size() && k < 32) {
                     const int64_t n = ncv_of[big[i + k]];
-                    if (k > 0 && (double)(sum + n) > kSpreadFill * 32.0 * (double)target) break;
+                    const double wc = spread_weight(big[i + k]);
+                    if (k > 0 && w + wc > wt) break;
+                    w += wc;
                     sum += n;
                     dep = std::max(dep, depth_of[big[i + k]]);
                     sy += nsyn_of[big[i + k]];
@@ -1459,13 +1480,21 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             double best = plan_cost(-1, 0);
             split = -1;
             target = 0;
-            for (double f : {2.0, 1.5, 1.25, 1.0, 0.8, 0.65, 0.5}) {
+            // spread-pack rows: the threshold itself, or rows whose estimated cost (with the
+            // mechanism rows of an average pack of the spread cells) is about the average cost of
+            // a warp slot, a little below it, or above it
+            for (double f : {2.0, 1.5, 1.25, 1.0, 0.8, 0.65, 0.5, 0.4}) {
                 const int64_t thr = std::max<int64_t>(1, (int64_t)(f * avg));
-                for (double g : {0.0, 0.7, 0.85, 1.0}) {
-                    const int64_t tg = p.spread_rows > 0 ? p.spread_rows : (g == 0.0 ? thr : std::max<int64_t>(1, (int64_t)(g * avg)));
+                std::vector<int32_t> big;
+                for (int32_t c : by_size) if (ncv_of[c] > thr) big.push_back(c);
+                if (big.empty()) continue;
+                const double per_row = target_weight(big, 1);      // cost of one target row
+                for (double g : {0.0, 0.85, 0.92, 1.0, 1.08}) {
                     if (g != 0.0 && p.spread_rows > 0) continue;
+                    const int64_t tg = p.spread_rows > 0 ? p.spread_rows
+                                                         : (g == 0.0 ? thr : std::max<int64_t>(1, (int64_t)(g * avg / per_row)));
                     const double ms = plan_cost(thr, tg);
-                    if (ms < best * 0.99) { best = ms; split = thr; target = tg; }
+                    if (ms < best * 0.995) { best = ms; split = thr; target = tg; }
                 }
             }
         }
@@ -1475,15 +1504,16 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             std::vector<int32_t> big, rest;
             for (int32_t c : by_size) ((split > 0 && ncv_of[c] > split) ? big : rest).push_back(c);
             std::vector<std::vector<int32_t>> cand;   // greedy groups of large cells
+            const double wt = target_weight(big, target);
             size_t i = 0;
             while (i < big.size()) {
                 std::vector<int32_t> g;
-                int64_t sum = 0;
+                double w = 0.0;
                 while (i < big.size() && g.size() < 32) {
-                    const int64_t n = ncv_of[big[i]];
-                    if (!g.empty() && (double)(sum + n) > kSpreadFill * 32.0 * (double)target) break;
+                    const double wc = spread_weight(big[i]);
+                    if (!g.empty() && w + wc > wt) break;
                     g.push_back(big[i]);
-                    sum += n;
+                    w += wc;
                     ++i;
                 }
                 cand.push_back(std::move(g));
