@@ -627,7 +627,9 @@ def measure_forms(arb, model, spec, sim64, E, args, sim_kw, fp64_kernel_ms, fp64
       epochs of the closed-loop network (the per-cell accuracy of this form, open loop against the
       FP64 oracle, is what tests/test_mixed_config3_gpu.py measures);
     - autotuned packing and kernel variant against the library's default plan (the trials of the
-      autotuner, same box)."""
+      autotuner, same box);
+    - the plain GPU path (one launch sequence per time step, default plan) against the batched
+      persistent epochs."""
     import torch
     out = {}
     k_end = sim64.time()[1]
@@ -663,6 +665,24 @@ def measure_forms(arb, model, spec, sim64, E, args, sim_kw, fp64_kernel_ms, fp64
                     "accuracy_note": "closed-loop network: spike-time differences propagate; the open-loop per-cell "
                                      "error against the FP64 oracle is in tests/test_mixed_config3_gpu.py"}
     del mx
+    # the plain GPU path: the same FP64 method with one launch sequence per time step (epochs of
+    # one step: no persistence across steps) and the library's default plan; its results equal
+    # the batched run's (the epoch length does not change them)
+    pl = arb.Simulation(model, dt=spec.dt, epoch_steps=1, scheme=args.scheme,
+                        ext_event_capacity=max(1 << 20, spec.ev_t.size + 16))
+    pl.enqueue(spec.ev_syn, spec.ev_t, spec.ev_w)
+    pl.advance(E * spec.dt)                                  # warm-up: one minimum delay
+    torch.cuda.synchronize()
+    flush.zero_()
+    ev0.record(stream)
+    pl.advance(2 * E * spec.dt)                              # timed: one minimum delay (E steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)
+    out["plain_per_step_launch"] = {"ms_per_min_delay": plain_ms, "steps": E,
+                                    "speedup_of_batched": plain_ms / fp64_step_ms,
+                                    "plan": "library default packing, epochs of one step (a launch sequence per step)"}
+    del pl
     if tuned and tuned.get("trials"):
         d0 = [t for t in tuned["trials"] if t["kernel_variant"] == 0 and t["split_cvs"] == tuned["trials"][0]["split_cvs"]]
         if d0:

@@ -1142,11 +1142,14 @@ __device__ void run_pack_exact(const DevModel<double>& d, int p, double2* stack,
 // Ring depths and warps per CTA of the compiled variants of the ring kernel (see kStreamVariants).
 template <int kRF, int kRB>
 __host__ __device__ constexpr int ring_double2();
-struct FwdRow {            // one row of the forward sweep, 32 lanes
-    double v[kWarp], a[kWarp], k[kWarp], e[kWarp], b[kWarp];
+struct __align__(16) FwdRec {   // one lane's entry of a forward row: read back with three 16-byte loads
+    double v, a, k, e, b;
+    int32_t f;                     // flags
+    int32_t cpos;                  // the entry's position in the row's gm / em, -1 none
+};
+struct FwdRow {                    // one row of the forward sweep, 32 lanes
+    FwdRec rec[kWarp];
     double gm[kWarp], em[kWarp];   // the row's compact mechanism slots (synapse CVs, then others)
-    int32_t f[kWarp];
-    int32_t cpos[kWarp];           // the entry's position in gm / em, -1 none
 };
 struct BwdRow {            // one row of the back substitution, 32 lanes
     double2 ue[kWarp];
@@ -1252,15 +1255,16 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
         else if (lane < ns + nn) slot = pk.nsc + (int)(wn & 0xFFFFFF) + (lane - ns);
         if (slot >= 0) slot = ARB_IDX(slot, pk.nvc, d.ctl);
         const bool mc = in && slot >= 0;
-        cp_async_8(&r.v[lane], Vg + o, in);
-        cp_async_8(&r.a[lane], ca_p + o, in);
-        cp_async_8(&r.k[lane], ck_p + o, in);
-        cp_async_8(&r.e[lane], ce_p + o, in);
-        cp_async_8(&r.b[lane], cb_p + o, in);
+        FwdRec& e = r.rec[lane];
+        cp_async_8(&e.v, Vg + o, in);
+        cp_async_8(&e.a, ca_p + o, in);
+        cp_async_8(&e.k, ck_p + o, in);
+        cp_async_8(&e.e, ce_p + o, in);
+        cp_async_8(&e.b, cb_p + o, in);
+        cp_async_4(&e.f, fl_p + o, in);
+        cp_async_4(&e.cpos, cp_p + o, in);
         cp_async_8(&r.gm[lane], mc ? Gm + slot : d.Gm, mc);
         cp_async_8(&r.em[lane], mc ? Em + slot : d.Em, mc);
-        cp_async_4(&r.f[lane], fl_p + o, in);
-        cp_async_4(&r.cpos[lane], cp_p + o, in);
         cp_async_commit();
     };
     // the i-th row of the back substitution (row J-1-i) into slot i mod kRB
@@ -1301,11 +1305,12 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 cp_async_wait<kRF - 1>();                // row j has landed (this lane's copies)
                 __syncwarp();                            // ... and every lane's (compact slots)
                 const FwdRow& r = fr[j & (kRF - 1)];
-                const int cp = r.cpos[lane] < 0 ? -1 : ARB_IDX(r.cpos[lane], kWarp, d.ctl);
-                const double V = r.v[lane], A = r.a[lane], K = r.k[lane];
-                const double E = cp >= 0 ? r.gm[cp] : r.e[lane];
-                const double Bc = cp >= 0 ? r.em[cp] : r.b[lane];
-                const int f = r.f[lane];
+                const FwdRec x = r.rec[lane];
+                const int cp = x.cpos < 0 ? -1 : ARB_IDX(x.cpos, kWarp, d.ctl);
+                const double V = x.v, A = x.a, K = x.k;
+                const double E = cp >= 0 ? r.gm[cp] : x.e;
+                const double Bc = cp >= 0 ? r.em[cp] : x.b;
+                const int f = x.f;
                 __syncwarp();                            // slot read by every lane before refilling it
                 issue_f(j + kRF);
                 if (kShared && R > 0) {
