@@ -30,11 +30,13 @@ namespace {
 
 constexpr int kAdjThreads = 128;   // threads per cell (block)
 
-// Conductance (uS) and conductance x reversal (nA) of CV i with the gates of one step.
-__device__ __forceinline__ void membrane(const AdjArgs& a, int64_t i, const double* Y, double& G, double& GE) {
-    G = a.glin[i];
-    GE = a.gelin[i];
-    const int32_t j = a.hidx[i];
+// Conductance (uS) and conductance x reversal (nA) of CV i with the gates of one step; gl, gel and
+// hj are the CV's passive conductance, its product with the reversal and its HH instance.
+__device__ __forceinline__ void membrane(const AdjArgs& a, double gl, double gel, int32_t hj, const double* Y, double& G,
+                                         double& GE) {
+    G = gl;
+    GE = gel;
+    const int32_t j = hj;
     if (j >= 0) {
         const double m = Y[j], h = Y[a.n_hh + j], n = Y[2 * a.n_hh + j];
         const double n2 = n * n;
@@ -45,23 +47,77 @@ __device__ __forceinline__ void membrane(const AdjArgs& a, int64_t i, const doub
     }
 }
 
+// Shared memory of one block (one cell): the solve's working arrays, and the cell's constants
+// and solve schedule, copied once per launch so that no step waits on a global load for them
+// (a chain's next CV index, its axial conductance, the membrane constants).
 struct Smem {
-    double* d;    // [smem_cv] diagonal, then eliminated pivots
-    double* b;    // [smem_cv] right-hand side, then the solution
-    double* r;    // [smem_cv] 1 / eliminated pivot
-    double* cd;   // [smem_ch] a chain's elimination into its parent's diagonal
-    double* cb;   //           ... and right-hand side
+    double* d;     // [smem_cv] diagonal, then eliminated pivots
+    double* b;     // [smem_cv] right-hand side, then the solution
+    double* r;     // [smem_cv] 1 / eliminated pivot
+    double* cd;    // [smem_ch] a chain's elimination into its parent's diagonal
+    double* cb;    //           ... and right-hand side
+    double* sig;   // [smem_cv] axial conductance to the parent (cell-local CV order)
+    double* cdt;   // [smem_cv] C / dt
+    double* dsig;  // [smem_cv] sum of the CV's axial conductances (own + children)
+    double* glin;  // [smem_cv] passive conductance
+    double* gelin; // [smem_cv] passive conductance x reversal
+    int32_t* par;  // [smem_cv] cell-local parent, -1 at the root
+    int32_t* hidx; // [smem_cv] HH instance of the CV, -1 none
+    int32_t* cvs;  // [smem_cv] CVs of the cell's chains, chain after chain (as ch_cvs)
+    int32_t* chp;  // [smem_ch + 1] cell-local chain -> range in cvs
+    int32_t* kidp; // [smem_ch + 1] cell-local chain -> range in kids
+    int32_t* kids; // [smem_ch] cell-local child chains
+    int32_t* levb; // [smem_ch + 2] first cell-local chain of each level, then the end
 };
 
 __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
     extern __shared__ double adj_smem[];
     Smem m;
+    const int ncv = a.smem_cv, nch = a.smem_ch;
     m.d = adj_smem;
-    m.b = m.d + a.smem_cv;
-    m.r = m.b + a.smem_cv;
-    m.cd = m.r + a.smem_cv;
-    m.cb = m.cd + a.smem_ch;
+    m.b = m.d + ncv;
+    m.r = m.b + ncv;
+    m.cd = m.r + ncv;
+    m.cb = m.cd + nch;
+    m.sig = m.cb + nch;
+    m.cdt = m.sig + ncv;
+    m.dsig = m.cdt + ncv;
+    m.glin = m.dsig + ncv;
+    m.gelin = m.glin + ncv;
+    m.par = reinterpret_cast<int32_t*>(m.gelin + ncv);
+    m.hidx = m.par + ncv;
+    m.cvs = m.hidx + ncv;
+    m.chp = m.cvs + ncv;
+    m.kidp = m.chp + nch + 1;
+    m.kids = m.kidp + nch + 1;
+    m.levb = m.kids + nch;
     return m;
+}
+
+// Copies cell c's constants and solve schedule into shared memory (all threads of the block).
+__device__ void load_cell(const AdjArgs& a, int c, const Smem& sm) {
+    const int tid = threadIdx.x;
+    const int64_t off = a.off[c], n = a.off[c + 1] - off;
+    const int64_t q0 = a.ch_ptr[c], nq = a.ch_ptr[c + 1] - q0;
+    const int64_t l0 = a.lev_off[c], nlb = a.lev_off[c + 1] - l0;
+    const int64_t cv0 = a.ch_cv_ptr[q0], k0 = a.ch_kid_ptr[q0];
+    for (int64_t i = tid; i < n; i += kAdjThreads) {
+        sm.sig[i] = a.sig[off + i];
+        sm.cdt[i] = a.cdt[off + i];
+        sm.dsig[i] = a.dsig[off + i];
+        sm.glin[i] = a.glin[off + i];
+        sm.gelin[i] = a.gelin[off + i];
+        sm.par[i] = a.parent[off + i];
+        sm.hidx[i] = a.hidx[off + i];
+        sm.cvs[i] = a.ch_cvs[cv0 + i];          // a cell's chains hold each of its CVs once
+    }
+    for (int64_t q = tid; q <= nq; q += kAdjThreads) {
+        sm.chp[q] = (int32_t)(a.ch_cv_ptr[q0 + q] - cv0);
+        sm.kidp[q] = (int32_t)(a.ch_kid_ptr[q0 + q] - k0);
+    }
+    for (int64_t k = tid; k < a.ch_kid_ptr[q0 + nq] - k0; k += kAdjThreads) sm.kids[k] = (int32_t)(a.ch_kids[k0 + k] - q0);
+    for (int64_t L = tid; L < nlb; L += kAdjThreads) sm.levb[L] = (int32_t)(a.lev_bound[l0 + L] - q0);
+    __syncthreads();
 }
 
 // Tree solve of cell c in shared memory (first warp): symmetric matrix with diagonal sm.d and
@@ -70,24 +126,21 @@ __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
 // farthest from the root, which first takes its child chains' eliminations) to its head,
 // whose elimination goes to the chain's slot. Back substitution: levels in reverse order, each
 // chain from its head (using its parent's solution) to its tail.
-__device__ void chain_solve(const AdjArgs& a, int c, int64_t off, int lane, const Smem& sm) {
-    const int64_t q0 = a.ch_ptr[c];
-    const int64_t l0 = a.lev_off[c];
-    const int nl = (int)(a.lev_off[c + 1] - l0) - 1;
-    const double* sig = a.sig + off;
+__device__ void chain_solve(const AdjArgs& a, int c, int lane, const Smem& sm) {
+    const int nl = (int)(a.lev_off[c + 1] - a.lev_off[c]) - 1;
     for (int L = 0; L < nl; ++L) {
-        for (int64_t q = a.lev_bound[l0 + L] + lane; q < a.lev_bound[l0 + L + 1]; q += 32) {
-            const int64_t cs = a.ch_cv_ptr[q], ce = a.ch_cv_ptr[q + 1];
-            int x = a.ch_cvs[ce - 1];
+        for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
+            const int cs = sm.chp[q], ce = sm.chp[q + 1];
+            int x = sm.cvs[ce - 1];
             double dx = sm.d[x], bx = sm.b[x];
-            for (int64_t k = a.ch_kid_ptr[q]; k < a.ch_kid_ptr[q + 1]; ++k) {
-                const int64_t j = a.ch_kids[k] - q0;
+            for (int k = sm.kidp[q]; k < sm.kidp[q + 1]; ++k) {
+                const int j = sm.kids[k];
                 dx += sm.cd[j];
                 bx += sm.cb[j];
             }
-            for (int64_t u = ce - 1; u > cs; --u) {
-                const int y = a.ch_cvs[u - 1];
-                const double sg = sig[x];
+            for (int u = ce - 1; u > cs; --u) {
+                const int y = sm.cvs[u - 1];
+                const double sg = sm.sig[x];
                 const double r = rcp_nr(dx);
                 sm.r[x] = r;
                 sm.b[x] = bx;
@@ -99,25 +152,25 @@ __device__ void chain_solve(const AdjArgs& a, int c, int64_t off, int lane, cons
             const double r = rcp_nr(dx);
             sm.r[x] = r;
             sm.b[x] = bx;
-            if (a.parent[off + x] >= 0) {
-                const double sg = sig[x];
+            if (sm.par[x] >= 0) {
+                const double sg = sm.sig[x];
                 const double f = sg * r;
-                sm.cd[q - q0] = -f * sg;
-                sm.cb[q - q0] = f * bx;
+                sm.cd[q] = -f * sg;
+                sm.cb[q] = f * bx;
             }
         }
         __syncwarp();
     }
     for (int L = nl - 1; L >= 0; --L) {
-        for (int64_t q = a.lev_bound[l0 + L] + lane; q < a.lev_bound[l0 + L + 1]; q += 32) {
-            const int64_t cs = a.ch_cv_ptr[q], ce = a.ch_cv_ptr[q + 1];
-            int x = a.ch_cvs[cs];
-            const int32_t p = a.parent[off + x];
-            double v = (p >= 0) ? (sm.b[x] + sig[x] * sm.b[p]) * sm.r[x] : sm.b[x] * sm.r[x];
+        for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
+            const int cs = sm.chp[q], ce = sm.chp[q + 1];
+            int x = sm.cvs[cs];
+            const int32_t p = sm.par[x];
+            double v = (p >= 0) ? (sm.b[x] + sm.sig[x] * sm.b[p]) * sm.r[x] : sm.b[x] * sm.r[x];
             sm.b[x] = v;
-            for (int64_t u = cs + 1; u < ce; ++u) {
-                x = a.ch_cvs[u];
-                v = (sm.b[x] + sig[x] * v) * sm.r[x];
+            for (int u = cs + 1; u < ce; ++u) {
+                x = sm.cvs[u];
+                v = (sm.b[x] + sm.sig[x] * v) * sm.r[x];
                 sm.b[x] = v;
             }
         }
@@ -136,12 +189,13 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
     double* const segG = a.segG[buf];
     const int64_t nhh = a.n_hh;
     const Smem sm = smem_of(a);
+    load_cell(a, c, sm);
     if (mode == 1) {
         const double* cV = a.ckV + (s0 / a.ckpt) * a.n_cv;
         const double* cY = a.ckY + (s0 / a.ckpt) * 3 * nhh;
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
             segV[i] = cV[i];
-            const int32_t j = a.hidx[i];
+            const int32_t j = sm.hidx[i - off];
             if (j >= 0)
                 for (int g = 0; g < 3; ++g) segY[g * nhh + j] = cY[g * nhh + j];
         }
@@ -161,7 +215,7 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                 double* cY = a.ckY + (s / a.ckpt) * 3 * nhh;
                 for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
                     cV[i] = a.V[i];
-                    const int32_t j = a.hidx[i];
+                    const int32_t j = sm.hidx[i - off];
                     if (j >= 0)
                         for (int g = 0; g < 3; ++g) cY[g * nhh + j] = a.Y[g * nhh + j];
                 }
@@ -174,10 +228,11 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         }
         // assemble A(y^s) and the right-hand side
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
+            const int64_t li = i - off;
             double G, GE;
-            membrane(a, i, Ys, G, GE);
-            sm.d[i - off] = a.cdt[i] + G + a.dsig[i];
-            sm.b[i - off] = a.cdt[i] * Vs[i] + GE;
+            membrane(a, sm.glin[li], sm.gelin[li], sm.hidx[li], Ys, G, GE);
+            sm.d[li] = sm.cdt[li] + G + sm.dsig[li];
+            sm.b[li] = sm.cdt[li] * Vs[i] + GE;
         }
         __syncthreads();
         if (tid < 32) {
@@ -187,14 +242,14 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                     if (a.st_on[q] <= t && t < a.st_on[q] + a.st_dur[q]) sm.b[a.st_cv[q] - off] += a.st_amp[q];
             }
             __syncwarp();
-            chain_solve(a, c, off, lane, sm);
+            chain_solve(a, c, lane, sm);
         }
         __syncthreads();
         // new voltage, gates with it, loss
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
             const double v = sm.b[i - off];
             Vd[i] = v;
-            const int32_t j = a.hidx[i];
+            const int32_t j = sm.hidx[i - off];
             if (j >= 0) {
                 Gates3 xg{Ys[j], Ys[nhh + j], Ys[2 * nhh + j]}, dvg, eg;
                 if (mode == 0 && hh_gates_tab(a.hh_tab, v, xg.m, xg.h, xg.n)) {
@@ -274,19 +329,21 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
     const int64_t nhh = a.n_hh, ncv = a.n_cv;
     const double dt = a.dt;
     const Smem sm = smem_of(a);
+    load_cell(a, c, sm);
     for (int64_t s = s1 - 1; s >= s0; --s) {
         const double* V0 = segV + (s - s0) * ncv;
         const double* V1 = V0 + ncv;
         const double* Y0 = segY + (s - s0) * 3 * nhh;
         // Vbar = (C/dt) lam + dL/dV^{s+1} + dPhi/dV^T ybar; A(y^s); ybar <- dPhi/dy ybar
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
+            const int64_t li = i - off;
             double G, GE;
-            membrane(a, i, Y0, G, GE);
-            sm.d[i - off] = a.cdt[i] + G + a.dsig[i];
-            double vb = a.cdt[i] * a.lam[i];
+            membrane(a, sm.glin[li], sm.gelin[li], sm.hidx[li], Y0, G, GE);
+            sm.d[li] = sm.cdt[li] + G + sm.dsig[li];
+            double vb = sm.cdt[li] * a.lam[i];
             const int32_t o = a.obs[i];
             if (o >= 0) vb += 2.0 * a.loss_scale * (V1[i] - a.target[s * a.n_obs + o]);
-            const int32_t j = a.hidx[i];
+            const int32_t j = sm.hidx[i - off];
             if (j >= 0) {
                 const double* G6 = segG + (s - s0) * 6 * nhh;
                 double* yb = a.ybar;
@@ -298,7 +355,7 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             sm.b[i - off] = vb;
         }
         __syncthreads();
-        if (tid < 32) chain_solve(a, c, off, lane, sm);
+        if (tid < 32) chain_solve(a, c, lane, sm);
         __syncthreads();
         // lam_s; gradient terms; gate adjoint of y^s
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
@@ -306,7 +363,7 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             a.lam[i] = lam;
             const double v1 = V1[i];
             a.gacc[3 * ncv + i] += lam * (V0[i] - v1) / dt * (a.area[i] * 1e-5);
-            const int32_t j = a.hidx[i];
+            const int32_t j = sm.hidx[i - off];
             if (j >= 0) {
                 const double m = Y0[j], h = Y0[nhh + j], nn = Y0[2 * nhh + j];
                 const double lna = lam * (kENa - v1), lk = lam * (kEK - v1), ll = lam * (kEL - v1);
@@ -361,7 +418,10 @@ __global__ void k_adj_reduce(AdjArgs a) {
 
 }  // namespace
 
-size_t adj_smem_bytes(const AdjArgs& a) { return sizeof(double) * (3 * (size_t)a.smem_cv + 2 * (size_t)a.smem_ch); }
+size_t adj_smem_bytes(const AdjArgs& a) {
+    return sizeof(double) * (8 * (size_t)a.smem_cv + 2 * (size_t)a.smem_ch) +
+           sizeof(int32_t) * (3 * (size_t)a.smem_cv + 4 * (size_t)a.smem_ch + 4);
+}
 
 cudaError_t adj_prepare(const AdjArgs& a) {
     const int bytes = (int)adj_smem_bytes(a);

@@ -3116,8 +3116,9 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         }
     }
     const ChainPlan CP = chain_plan(sim);
-    if (3 * (size_t)CP.max_cv + 2 * (size_t)CP.max_ch > (size_t)200 * 1024 / 8)
-        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve in shared memory (cells up to ~8,000 CVs)");
+    if (8 * (8 * (size_t)CP.max_cv + 2 * (size_t)CP.max_ch) + 4 * (3 * (size_t)CP.max_cv + 4 * (size_t)CP.max_ch + 4) >
+        (size_t)200 * 1024)
+        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to ~2,900 CVs)");
     arb_status st = sync_in(sim);
     if (st != ARB_OK) return st;
     char* base = (char*)workspace;
