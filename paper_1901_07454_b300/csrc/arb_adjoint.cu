@@ -11,13 +11,31 @@
 //
 // Work is per cell and cells never interact, so every kernel runs one block per cell over a
 // whole range of steps: the element-wise parts (membrane terms, gates and their derivatives,
-// gradient terms) are spread over the block's threads; the tree solve runs in shared memory
-// on the first warp, which takes the cell's unbranched chains level by level (leaf chains
-// first), one chain per lane, and hands each chain's elimination to its parent chain through
-// a per-chain slot. The forward pass keeps a checkpoint of the state every `ckpt` steps. The
-// backward pass goes segment by segment: each stage sweeps one segment backwards while other
-// blocks of the same launch recompute the previous segment from its checkpoint into the second
-// segment buffer, keeping every state and the gate-update derivatives the sweep will need.
+// gradient terms) are spread over the block's threads; the tree solve runs in shared memory.
+// The forward pass keeps a checkpoint of the state every `ckpt` steps. The backward pass goes
+// segment by segment: each stage sweeps one segment backwards while other blocks of the same
+// launch recompute the previous segment from its checkpoint into the second segment buffer,
+// keeping every state and the gate-update derivatives the sweep will need.
+//
+// Tree solve. On this GPU a warp issues at most one FP64 instruction every 64 cycles, however
+// many of its lanes are active, so the solve's time is the number of FP64 instructions on its
+// longest dependent path, not the number of lanes doing work. The cell's unbranched chains are
+// taken level by level (leaf chains first), and along a chain, from its tail (farthest from the
+// root) to its head, the elimination is written in projective form: with D_k the eliminated
+// pivots, B_k the eliminated right-hand sides and s_k the axial conductance from CV k to the
+// next one of the chain,
+//   P_k = d_k P_{k-1} - s_{k-1}^2 P_{k-2},   W_k = b_k P_{k-1} + s_{k-1} W_{k-1},
+//   D_k = P_k / P_{k-1},  B_k = W_k / P_{k-1}   (P_{-1} = 1, P_0 = D_0, W_0 = B_0).
+// Scaled by per-CV constants (P^_k = P_k / c_k, W^_k = W_k / g_k with c_k = s_{k-1}^2 c_{k-2},
+// g_k = s_{k-1} g_{k-1}) each step is one fused multiply-add:
+//   P^_k = (d_k rho_k) P^_{k-1} - P^_{k-2},   W^_k = (b_k beta_k) P^_{k-1} + W^_{k-1},
+// rho_k = c_{k-1} / c_k, beta_k = c_{k-1} / g_k. Two lanes take one chain: the even lane carries
+// P^, the odd lane W^ one CV behind, in the same instruction. No division is on that path. The
+// chain's elimination into its parent (-s_h^2 / D_h and s_h B_h / D_h at its head h) takes one
+// reciprocal per chain. Then every thread forms, per CV, u_k = B_k / D_k and e_k = s_k / D_k
+// (one reciprocal each, in parallel), and the back substitution, V_k = u_k + e_k V_parent, is
+// one fused multiply-add per CV. The host computes the constants and cuts a chain wherever
+// their range, or the range P^ can reach, would leave about 2^{+-300}.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -51,19 +69,24 @@ __device__ __forceinline__ void membrane(const AdjArgs& a, double gl, double gel
 // and solve schedule, copied once per launch so that no step waits on a global load for them
 // (a chain's next CV index, its axial conductance, the membrane constants).
 struct Smem {
-    double* d;     // [smem_cv] diagonal, then eliminated pivots
-    double* b;     // [smem_cv] right-hand side, then the solution
-    double* r;     // [smem_cv] 1 / eliminated pivot
-    double* cd;    // [smem_ch] a chain's elimination into its parent's diagonal
-    double* cb;    //           ... and right-hand side
+    double* A2;    // [2 smem_cv] per CV: d rho (even), b beta (odd); then (u, e) of the back substitution
+    double* PW;    // [2 smem_cv] per CV: P^ (even), W^ (odd)
+    double* X;     // [smem_cv] solution
     double* sig;   // [smem_cv] axial conductance to the parent (cell-local CV order)
     double* cdt;   // [smem_cv] C / dt
     double* dsig;  // [smem_cv] sum of the CV's axial conductances (own + children)
     double* glin;  // [smem_cv] passive conductance
     double* gelin; // [smem_cv] passive conductance x reversal
+    double* rho;   // [smem_cv] scaling of the diagonal in the chain recurrence
+    double* beta;  // [smem_cv] scaling of the right-hand side in the chain recurrence
+    double* gcf;   // [smem_cv] g_k / c_k: u_k = gcf W^_k / P^_k
+    double* srf;   // [smem_cv] s_k rho_k: e_k = srf P^_{k-1} / P^_k
+    double* CDB;   // [2 smem_ch] a chain's elimination into its parent's diagonal (even) and rhs (odd)
+    double* KPW;   // [2 smem_ch] per chain: s_h^2 rho_h (even), s_h g_h / c_h (odd)
     int32_t* par;  // [smem_cv] cell-local parent, -1 at the root
     int32_t* hidx; // [smem_cv] HH instance of the CV, -1 none
     int32_t* cvs;  // [smem_cv] CVs of the cell's chains, chain after chain (as ch_cvs)
+    int32_t* prev; // [smem_cv] the CV before this one in its chain, -1 at a chain's tail
     int32_t* chp;  // [smem_ch + 1] cell-local chain -> range in cvs
     int32_t* kidp; // [smem_ch + 1] cell-local chain -> range in kids
     int32_t* kids; // [smem_ch] cell-local child chains
@@ -74,20 +97,25 @@ __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
     extern __shared__ double adj_smem[];
     Smem m;
     const int ncv = a.smem_cv, nch = a.smem_ch;
-    m.d = adj_smem;
-    m.b = m.d + ncv;
-    m.r = m.b + ncv;
-    m.cd = m.r + ncv;
-    m.cb = m.cd + nch;
-    m.sig = m.cb + nch;
+    m.A2 = adj_smem;
+    m.PW = m.A2 + 2 * ncv;
+    m.X = m.PW + 2 * ncv;
+    m.sig = m.X + ncv;
     m.cdt = m.sig + ncv;
     m.dsig = m.cdt + ncv;
     m.glin = m.dsig + ncv;
     m.gelin = m.glin + ncv;
-    m.par = reinterpret_cast<int32_t*>(m.gelin + ncv);
+    m.rho = m.gelin + ncv;
+    m.beta = m.rho + ncv;
+    m.gcf = m.beta + ncv;
+    m.srf = m.gcf + ncv;
+    m.CDB = m.srf + ncv;
+    m.KPW = m.CDB + 2 * nch;
+    m.par = reinterpret_cast<int32_t*>(m.KPW + 2 * nch);
     m.hidx = m.par + ncv;
     m.cvs = m.hidx + ncv;
-    m.chp = m.cvs + ncv;
+    m.prev = m.cvs + ncv;
+    m.chp = m.prev + ncv;
     m.kidp = m.chp + nch + 1;
     m.kids = m.kidp + nch + 1;
     m.levb = m.kids + nch;
@@ -107,72 +135,171 @@ __device__ void load_cell(const AdjArgs& a, int c, const Smem& sm) {
         sm.dsig[i] = a.dsig[off + i];
         sm.glin[i] = a.glin[off + i];
         sm.gelin[i] = a.gelin[off + i];
+        sm.rho[i] = a.rho[off + i];
+        sm.beta[i] = a.beta[off + i];
+        sm.gcf[i] = a.gcf[off + i];
+        sm.srf[i] = a.srf[off + i];
         sm.par[i] = a.parent[off + i];
         sm.hidx[i] = a.hidx[off + i];
+        sm.prev[i] = a.prev[off + i];
         sm.cvs[i] = a.ch_cvs[cv0 + i];          // a cell's chains hold each of its CVs once
     }
     for (int64_t q = tid; q <= nq; q += kAdjThreads) {
         sm.chp[q] = (int32_t)(a.ch_cv_ptr[q0 + q] - cv0);
         sm.kidp[q] = (int32_t)(a.ch_kid_ptr[q0 + q] - k0);
     }
+    for (int64_t q = tid; q < nq; q += kAdjThreads) {
+        sm.KPW[2 * q] = a.kpw[2 * (q0 + q)];
+        sm.KPW[2 * q + 1] = a.kpw[2 * (q0 + q) + 1];
+    }
     for (int64_t k = tid; k < a.ch_kid_ptr[q0 + nq] - k0; k += kAdjThreads) sm.kids[k] = (int32_t)(a.ch_kids[k0 + k] - q0);
     for (int64_t L = tid; L < nlb; L += kAdjThreads) sm.levb[L] = (int32_t)(a.lev_bound[l0 + L] - q0);
     __syncthreads();
 }
 
-// Tree solve of cell c in shared memory (first warp): symmetric matrix with diagonal sm.d and
-// off-diagonal -sigma between a CV and its parent; the solution replaces sm.b.
-// Elimination: chains level by level from the leaves; within a chain from its tail (the CV
-// farthest from the root, which first takes its child chains' eliminations) to its head,
-// whose elimination goes to the chain's slot. Back substitution: levels in reverse order, each
-// chain from its head (using its parent's solution) to its tail.
-__device__ void chain_solve(const AdjArgs& a, int c, int lane, const Smem& sm) {
+// Double-precision helpers on 32-bit halves (integer pipe): a select, a sign flip and a shuffle.
+// Selecting or moving a double as one 64-bit value measured slower here.
+__device__ __forceinline__ double sel_d(bool c, double a, double b) {
+    return __hiloint2double(c ? __double2hiint(a) : __double2hiint(b), c ? __double2loint(a) : __double2loint(b));
+}
+__device__ __forceinline__ double neg_d(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double shfl_d(double x, int src) {
+    return __hiloint2double(__shfl_sync(0xffffffffu, __double2hiint(x), src),
+                            __shfl_sync(0xffffffffu, __double2loint(x), src));
+}
+
+// Elimination of cell c (first warp), leaf chains first. Input: sm.A2 = (d rho, b beta) per CV.
+// Output: P^ and W^ of every CV in sm.PW, and each chain's elimination into its parent in sm.CDB.
+// Lanes 2j and 2j+1 take the j-th chain of a group of 16; every lane runs the group's longest
+// chain so that the pair exchange stays converged. Step k is one multiply-add fma(A, X, Y) on
+// each lane; with p = k on the P lane and p = k - 2 on the W lane (the CV it works on):
+//   P lane: A = d_p rho_p,    X = P^_{p-1}, Y = -P^_{p-2}  ->  P^_p    (1 <= p <= len-1)
+//   W lane: A = b_p beta_p,   X = P^_{p-1}, Y = W^_{p-1}   ->  W^_p    (1 <= p <= len-1; A = 0 for p <= 0)
+// The W lane gets P^ from its partner by a shuffle issued one step before it is needed, so
+// neither the shuffle's latency nor a move waiting on it is on the dependent path. Operands are
+// loaded two steps ahead and the loop is unrolled by two with one register set per parity, so
+// no instruction waits on a shared-memory load; everything except the final select is formed
+// before the multiply-add, and the store of its result comes last.
+__device__ void tree_eliminate(const AdjArgs& a, int c, int lane, const Smem& sm) {
     const int nl = (int)(a.lev_off[c + 1] - a.lev_off[c]) - 1;
+    const int role = lane & 1;                   // 0: P^, 1: W^
+    const int lag = 2 * role;
+    const unsigned full = 0xffffffffu;
     for (int L = 0; L < nl; ++L) {
-        for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
-            const int cs = sm.chp[q], ce = sm.chp[q + 1];
-            int x = sm.cvs[ce - 1];
-            double dx = sm.d[x], bx = sm.b[x];
-            for (int k = sm.kidp[q]; k < sm.kidp[q + 1]; ++k) {
-                const int j = sm.kids[k];
-                dx += sm.cd[j];
-                bx += sm.cb[j];
+        const int q1 = sm.levb[L + 1];
+        for (int qb = sm.levb[L]; qb < q1; qb += 16) {
+            const int q = qb + (lane >> 1);
+            const bool on = q < q1;
+            int cs = 0, len = 0;
+            if (on) {
+                cs = sm.chp[q];
+                len = sm.chp[q + 1] - cs;
             }
-            for (int u = ce - 1; u > cs; --u) {
-                const int y = sm.cvs[u - 1];
-                const double sg = sm.sig[x];
-                const double r = rcp_nr(dx);
-                sm.r[x] = r;
-                sm.b[x] = bx;
-                const double f = sg * r;
-                dx = sm.d[y] - f * sg;
-                bx = sm.b[y] + f * bx;
-                x = y;
+            const int e0 = cs + len - 1;         // the tail's position in cvs; CV p of the chain is cvs[e0 - p]
+            auto cv_at = [&](int k) -> int {
+                const int p = k - lag;
+                return (on && p >= 0 && p <= len - 1) ? sm.cvs[e0 - p] : 0;
+            };
+            auto opnd = [&](int k, int x) -> double {
+                const int p = k - lag;
+                return (on && p >= 1 && p <= len - 1) ? sm.A2[2 * x + role] : 0.0;
+            };
+            // the tail: its own diagonal / right-hand side and the eliminations of its child chains
+            double X = 1.0, Y = -1.0;            // P lane: P^_0, -P^_{-1}; W lane: P^_{-1}, W^_0
+            if (on) {
+                const int x0 = sm.cvs[e0];
+                double acc = sm.A2[2 * x0 + role];
+                for (int k = sm.kidp[q]; k < sm.kidp[q + 1]; ++k) acc += sm.CDB[2 * sm.kids[k] + role];
+                sm.PW[2 * x0 + role] = acc;
+                if (role) Y = acc;
+                else X = acc;
             }
-            const double r = rcp_nr(dx);
-            sm.r[x] = r;
-            sm.b[x] = bx;
-            if (sm.par[x] >= 0) {
-                const double sg = sm.sig[x];
-                const double f = sg * r;
-                sm.cd[q] = -f * sg;
-                sm.cb[q] = f * bx;
+            int m = len;
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(full, m, o));
+            m += 1;                              // the W lane's last step
+            int sxa = cv_at(1), sxb = cv_at(2), cva = cv_at(3), cvb = cv_at(4);
+            double Aa = opnd(1, sxa), Ab = opnd(2, sxb);
+            double sha = 1.0, shb = 1.0;
+#define ARB_ELIM_STEP(K, A, SX, CV, SH_NEW, SH_USE)                                            \
+    {                                                                                            \
+        const int k_ = (K);                                                                      \
+        const int p_ = k_ - lag;                                                                 \
+        const bool act_ = on && p_ <= len - 1;                                                   \
+        const bool st_ = act_ && p_ >= 0;                                                        \
+        SH_NEW = shfl_d(X, lane & ~1);                                                           \
+        const double xalt_ = sel_d(act_ && role, SH_USE, X);                                     \
+        const double yalt_ = sel_d(act_ && !role, neg_d(X), Y);                                  \
+        const double out_ = fma(A, X, Y);                                                        \
+        const int sx_k_ = SX;                                                                    \
+        A = opnd(k_ + 2, CV);                                                                    \
+        SX = CV;                                                                                 \
+        CV = cv_at(k_ + 4);                                                                      \
+        X = sel_d(act_ && !role, out_, xalt_);                                                   \
+        Y = sel_d(act_ && role, out_, yalt_);                                                    \
+        if (st_) sm.PW[2 * sx_k_ + role] = out_;                                                 \
+    }
+            for (int k = 1; k <= m; k += 2) {
+                ARB_ELIM_STEP(k, Aa, sxa, cva, sha, shb)
+                ARB_ELIM_STEP(k + 1, Ab, sxb, cvb, shb, sha)
             }
+#undef ARB_ELIM_STEP
+            // the head's elimination into its parent: P lane -s_h^2 / D_h, W lane s_h B_h / D_h
+            // (X = P^_h on both lanes; Y = -P^_{h-1} on the P lane, W^_h on the W lane)
+            if (on && sm.par[sm.cvs[cs]] >= 0) sm.CDB[2 * q + role] = (sm.KPW[2 * q + role] * Y) * rcp_nr(X);
         }
         __syncwarp();
     }
+}
+
+// Coefficients of the back substitution (all threads): u_k = B_k / D_k, e_k = s_k / D_k per CV,
+// into sm.A2 (whose elimination operands are used up).
+__device__ void tree_coefficients(int n, const Smem& sm) {
+    for (int li = threadIdx.x; li < n; li += kAdjThreads) {
+        const int pv = sm.prev[li];
+        const double Pp = pv >= 0 ? sm.PW[2 * pv] : 1.0;
+        const double r = rcp_nr(sm.PW[2 * li]);
+        const double u = (sm.gcf[li] * sm.PW[2 * li + 1]) * r;
+        const double e = (sm.srf[li] * Pp) * r;
+        sm.A2[2 * li] = u;
+        sm.A2[2 * li + 1] = e;
+    }
+}
+
+// Back substitution (first warp): levels in reverse order, each chain from its head (using its
+// parent's solution; e = 0 at the root) to its tail, one lane per chain, one multiply-add per CV.
+// As in the elimination, operands come two CVs ahead, unrolled by two with a register set per
+// parity, and the store of each value comes after the next multiply-add. Result in sm.X.
+__device__ void tree_substitute(const AdjArgs& a, int c, int lane, const Smem& sm) {
+    const int nl = (int)(a.lev_off[c + 1] - a.lev_off[c]) - 1;
     for (int L = nl - 1; L >= 0; --L) {
         for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
             const int cs = sm.chp[q], ce = sm.chp[q + 1];
-            int x = sm.cvs[cs];
-            const int32_t p = sm.par[x];
-            double v = (p >= 0) ? (sm.b[x] + sm.sig[x] * sm.b[p]) * sm.r[x] : sm.b[x] * sm.r[x];
-            sm.b[x] = v;
-            for (int u = cs + 1; u < ce; ++u) {
-                x = sm.cvs[u];
-                v = (sm.b[x] + sm.sig[x] * v) * sm.r[x];
-                sm.b[x] = v;
+            auto cv_at = [&](int i) -> int { return i < ce ? sm.cvs[i] : 0; };
+            const int x0 = sm.cvs[cs];
+            const int32_t p = sm.par[x0];
+            double vp = p >= 0 ? sm.X[p] : 0.0;
+            int xa = x0, xb = cv_at(cs + 1), ya = cv_at(cs + 2), yb = cv_at(cs + 3);
+            double ua = sm.A2[2 * xa], ea = sm.A2[2 * xa + 1];
+            double ub = sm.A2[2 * xb], eb = sm.A2[2 * xb + 1];
+#define ARB_SUBST_STEP(I, XV, YV, U, E)                                                          \
+    {                                                                                            \
+        const int i_ = (I);                                                                      \
+        const double v_ = fma(E, vp, U);                                                         \
+        const int xi_ = XV;                                                                      \
+        U = sm.A2[2 * YV];                                                                       \
+        E = sm.A2[2 * YV + 1];                                                                   \
+        XV = YV;                                                                                 \
+        YV = cv_at(i_ + 4);                                                                      \
+        vp = v_;                                                                                 \
+        if (i_ < ce) sm.X[xi_] = v_;                                                             \
+    }
+            for (int i = cs; i < ce; i += 2) {
+                ARB_SUBST_STEP(i, xa, ya, ua, ea)
+                ARB_SUBST_STEP(i + 1, xb, yb, ub, eb)
             }
+#undef ARB_SUBST_STEP
         }
         __syncwarp();
     }
@@ -231,23 +358,30 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             const int64_t li = i - off;
             double G, GE;
             membrane(a, sm.glin[li], sm.gelin[li], sm.hidx[li], Ys, G, GE);
-            sm.d[li] = sm.cdt[li] + G + sm.dsig[li];
-            sm.b[li] = sm.cdt[li] * Vs[i] + GE;
+            sm.A2[2 * li] = (sm.cdt[li] + G + sm.dsig[li]) * sm.rho[li];
+            sm.A2[2 * li + 1] = (sm.cdt[li] * Vs[i] + GE) * sm.beta[li];
         }
         __syncthreads();
         if (tid < 32) {
             if (tid == 0) {
                 const double t = (double)(a.k0 + s) * a.dt;
                 for (int64_t q = a.st_ptr[c]; q < a.st_ptr[c + 1]; ++q)
-                    if (a.st_on[q] <= t && t < a.st_on[q] + a.st_dur[q]) sm.b[a.st_cv[q] - off] += a.st_amp[q];
+                    if (a.st_on[q] <= t && t < a.st_on[q] + a.st_dur[q]) {
+                        const int64_t x = a.st_cv[q] - off;
+                        sm.A2[2 * x + 1] = fma(a.st_amp[q], sm.beta[x], sm.A2[2 * x + 1]);
+                    }
             }
             __syncwarp();
-            chain_solve(a, c, lane, sm);
+            tree_eliminate(a, c, lane, sm);
         }
+        __syncthreads();
+        tree_coefficients((int)n, sm);
+        __syncthreads();
+        if (tid < 32) tree_substitute(a, c, lane, sm);
         __syncthreads();
         // new voltage, gates with it, loss
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
-            const double v = sm.b[i - off];
+            const double v = sm.X[i - off];
             Vd[i] = v;
             const int32_t j = sm.hidx[i - off];
             if (j >= 0) {
@@ -339,7 +473,7 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             const int64_t li = i - off;
             double G, GE;
             membrane(a, sm.glin[li], sm.gelin[li], sm.hidx[li], Y0, G, GE);
-            sm.d[li] = sm.cdt[li] + G + sm.dsig[li];
+            sm.A2[2 * li] = (sm.cdt[li] + G + sm.dsig[li]) * sm.rho[li];
             double vb = sm.cdt[li] * a.lam[i];
             const int32_t o = a.obs[i];
             if (o >= 0) vb += 2.0 * a.loss_scale * (V1[i] - a.target[s * a.n_obs + o]);
@@ -352,14 +486,18 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                 yb[nhh + j] *= G6[4 * nhh + j];
                 yb[2 * nhh + j] *= G6[5 * nhh + j];
             }
-            sm.b[i - off] = vb;
+            sm.A2[2 * li + 1] = vb * sm.beta[li];
         }
         __syncthreads();
-        if (tid < 32) chain_solve(a, c, lane, sm);
+        if (tid < 32) tree_eliminate(a, c, lane, sm);
+        __syncthreads();
+        tree_coefficients((int)n, sm);
+        __syncthreads();
+        if (tid < 32) tree_substitute(a, c, lane, sm);
         __syncthreads();
         // lam_s; gradient terms; gate adjoint of y^s
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
-            const double lam = sm.b[i - off];
+            const double lam = sm.X[i - off];
             a.lam[i] = lam;
             const double v1 = V1[i];
             a.gacc[3 * ncv + i] += lam * (V0[i] - v1) / dt * (a.area[i] * 1e-5);
@@ -418,10 +556,7 @@ __global__ void k_adj_reduce(AdjArgs a) {
 
 }  // namespace
 
-size_t adj_smem_bytes(const AdjArgs& a) {
-    return sizeof(double) * (8 * (size_t)a.smem_cv + 2 * (size_t)a.smem_ch) +
-           sizeof(int32_t) * (3 * (size_t)a.smem_cv + 4 * (size_t)a.smem_ch + 4);
-}
+size_t adj_smem_bytes(const AdjArgs& a) { return adj_smem_bytes_for(a.smem_cv, a.smem_ch); }
 
 cudaError_t adj_prepare(const AdjArgs& a) {
     const int bytes = (int)adj_smem_bytes(a);

@@ -342,6 +342,13 @@ struct AdjArgs {
     const int32_t* ch_cvs;     // cell-local CVs of each chain, head (nearest the root) first
     const int64_t* ch_kid_ptr; // [n_chains+1] range of the chain's child chains in ch_kids
     const int64_t* ch_kids;    // global chain indices
+    // constants of the scaled chain recurrence (model order; see arb_adjoint.cu)
+    const double* rho;         // [n_cv] c_{k-1} / c_k (1 at a chain's tail)
+    const double* beta;        // [n_cv] c_{k-1} / g_k (1 at a chain's tail)
+    const double* gcf;         // [n_cv] g_k / c_k
+    const double* srf;         // [n_cv] s_k rho_k (0 at the root)
+    const int32_t* prev;       // [n_cv] cell-local CV before this one in its chain, -1 at a tail
+    const double* kpw;         // [n_chains][2] s_h^2 rho_h, s_h g_h / c_h of the chain's head h
     int32_t smem_cv;           // shared-memory slots per cell (largest cell)
     int32_t smem_ch;           // largest chain count of a cell
     const int64_t* grp_ptr;    // [n_groups+1] CVs of each parameter group, ascending
@@ -349,6 +356,12 @@ struct AdjArgs {
     int32_t n_groups;
     double* grad;              // [n_groups][4] output
 };
+
+// Dynamic shared memory of one adjoint block: per CV 14 doubles and 4 int32, per chain 4
+// doubles and 4 int32, and 4 int32 of level bounds.
+inline size_t adj_smem_bytes_for(int64_t cvs, int64_t chains) {
+    return 8 * (14 * (size_t)cvs + 4 * (size_t)chains) + 4 * (4 * (size_t)cvs + 4 * (size_t)chains + 4);
+}
 
 #ifdef ARB_DEBUG
 __device__ __forceinline__ int64_t dbg_idx(int64_t i, int64_t n, Ctl* ctl) {

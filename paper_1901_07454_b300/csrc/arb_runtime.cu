@@ -2911,38 +2911,118 @@ struct AdjLayout {
     }
 };
 
-// Tree-solve schedule of the adjoint kernels: per cell, its unbranched chains (maximal runs
-// of CVs with one child each, head nearest the root) ordered by level.
+// Tree-solve schedule of the adjoint kernels: per cell, its unbranched chains (runs of CVs
+// with one child each, head nearest the root) ordered by level, and the constants of the
+// scaled chain recurrence (arb_adjoint.cu). Along a chain, from its tail (k = 0), with s_k the
+// axial conductance from CV k to its parent,
+//   rho_0 = 1, gam_0 = 1,  rho_k = 1 / (s_{k-1}^2 rho_{k-1}),  gam_k = s_{k-1} rho_{k-1} gam_{k-1}
+// (rho_k = c_{k-1} / c_k and gam_k = c_k / g_k), so that beta_k = rho_k gam_k, g_k / c_k =
+// 1 / gam_k. P^_k / P^_{k-1} = D_k rho_k, and every pivot lies in [s_k + C_k/dt, dmax_k] (the
+// matrix is an M-matrix whose diagonal exceeds the axial conductances by C/dt), which bounds
+// P^. A chain is cut before the CV at which any of these would leave 2^{+-kChainRange}: the
+// part below becomes a chain of its own whose parent is that CV (the same elimination in exact
+// arithmetic). The recurrences run in long double.
 struct ChainPlan {
     std::vector<int64_t> ch_ptr, lev_off, lev_bound, ch_cv_ptr, ch_kid_ptr, ch_kids;
-    std::vector<int32_t> ch_cvs;
+    std::vector<int32_t> ch_cvs, prev;
+    std::vector<double> rho, beta, gcf, srf, kpw;
     int32_t max_cv = 0, max_ch = 0;
 };
 
-ChainPlan chain_plan(const arb_sim* sim) {
+constexpr long double kChainRange = 300.0L;
+
+ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt, const double* dmax) {
     ChainPlan P;
     const int32_t nc = sim->n_cells;
+    const int64_t ncv = sim->n_cv;
     P.ch_ptr.assign(nc + 1, 0);
     P.lev_off.assign(nc + 1, 0);
     P.ch_cv_ptr.push_back(0);
     P.ch_kid_ptr.push_back(0);
+    P.rho.assign(ncv, 1.0);
+    P.beta.assign(ncv, 1.0);
+    P.gcf.assign(ncv, 1.0);
+    P.srf.assign(ncv, 0.0);
+    P.prev.assign(ncv, -1);
     for (int32_t c = 0; c < nc; ++c) {
         const int64_t off = sim->cv_offset[c];
         const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
         const int32_t* par = sim->parent.data() + off;
         std::vector<int32_t> nch(n, 0), only(n, -1);
         for (int32_t i = 1; i < n; ++i) { nch[par[i]]++; only[par[i]] = i; }
-        // chains, in ascending head order (a parent chain's head precedes its children's)
-        std::vector<std::vector<int32_t>> cvs;
+        // chains in ascending head order (a parent chain's head precedes its children's); a
+        // run that is cut contributes its parts from the top down, so that this still holds
+        std::vector<std::vector<int32_t>> cvs;     // head first
+        std::vector<std::array<double, 2>> kq;     // per chain: s_h^2 rho_h, s_h / gam_h
         std::vector<int32_t> chain_of_tail(n, -1), parent_chain;
         for (int32_t h = 0; h < n; ++h) {
             if (h != 0 && nch[par[h]] == 1) continue;   // continues its parent's chain
-            std::vector<int32_t> v{h};
-            int32_t x = h;
-            while (nch[x] == 1) { x = only[x]; v.push_back(x); }
-            chain_of_tail[x] = (int32_t)cvs.size();
-            parent_chain.push_back(h == 0 ? -1 : par[h]);   // parent CV for now
-            cvs.push_back(std::move(v));
+            std::vector<int32_t> t{h};                   // the run, head first
+            for (int32_t x = h; nch[x] == 1;) { x = only[x]; t.push_back(x); }
+            std::reverse(t.begin(), t.end());            // tail first
+            // walk from the tail, cutting where the scaled quantities would leave the range
+            std::vector<std::pair<int32_t, int32_t>> parts;   // [begin, end) in t
+            std::vector<std::array<double, 2>> kparts;
+            int32_t b = 0;
+            long double rho = 1.0L, gam = 1.0L, lo = 0.0L, hi = 0.0L;
+            for (int32_t i = 0; i <= (int32_t)t.size(); ++i) {
+                bool cut = i == (int32_t)t.size();
+                long double r2 = rho, g2 = gam, lo2 = lo, hi2 = hi;
+                if (!cut) {
+                    const int64_t y = off + t[i];
+                    const long double s_y = par[t[i]] >= 0 ? (long double)sigma[y] : 0.0L;
+                    const long double dlo = s_y + (long double)cdt[y], dhi = (long double)dmax[y];
+                    if (i == b) {
+                        r2 = 1.0L;
+                        g2 = 1.0L;
+                        lo2 = std::log2(dlo);
+                        hi2 = std::log2(dhi);
+                    } else {
+                        const long double s = (long double)sigma[off + t[i - 1]];
+                        r2 = 1.0L / (s * s * rho);
+                        g2 = s * gam * rho;
+                        lo2 = lo + std::log2(dlo * r2);
+                        hi2 = hi + std::log2(dhi * r2);
+                    }
+                    const long double lr = std::log2(r2), lg = std::log2(g2);
+                    if (i > b && (std::fabs(lr) > kChainRange || std::fabs(lg) > kChainRange ||
+                                  std::fabs(lr + lg) > kChainRange || std::fabs(lo2) > kChainRange ||
+                                  std::fabs(hi2) > kChainRange))
+                        cut = true;
+                }
+                if (cut) {
+                    // the part [b, i): its head t[i-1] has the constants rho, gam
+                    const int64_t hg = off + t[i - 1];
+                    const long double sh = par[t[i - 1]] >= 0 ? (long double)sigma[hg] : 0.0L;
+                    parts.push_back({b, i});
+                    kparts.push_back({(double)(sh * sh * rho), (double)(sh / gam)});
+                    if (i == (int32_t)t.size()) break;
+                    b = i;
+                    --i;                                 // restart the walk at t[b]
+                    rho = 1.0L;
+                    gam = 1.0L;
+                    continue;
+                }
+                rho = r2;
+                gam = g2;
+                lo = lo2;
+                hi = hi2;
+                const int64_t y = off + t[i];
+                const long double s_y = par[t[i]] >= 0 ? (long double)sigma[y] : 0.0L;
+                P.rho[y] = (double)rho;
+                P.beta[y] = (double)(rho * gam);
+                P.gcf[y] = (double)(1.0L / gam);
+                P.srf[y] = (double)(s_y * rho);
+                P.prev[y] = i > b ? t[i - 1] : -1;
+            }
+            for (int32_t pi = (int32_t)parts.size() - 1; pi >= 0; --pi) {   // top part first
+                std::vector<int32_t> v(t.begin() + parts[pi].first, t.begin() + parts[pi].second);
+                std::reverse(v.begin(), v.end());                            // head first
+                chain_of_tail[v.back()] = (int32_t)cvs.size();
+                parent_chain.push_back(par[v.front()]);                     // parent CV for now
+                kq.push_back(kparts[pi]);
+                cvs.push_back(std::move(v));
+            }
         }
         const int32_t nq = (int32_t)cvs.size();
         for (int32_t q = 0; q < nq; ++q)
@@ -2973,6 +3053,8 @@ ChainPlan chain_plan(const arb_sim* sim) {
             P.ch_cv_ptr.push_back((int64_t)P.ch_cvs.size());
             for (int32_t k : kids[q]) P.ch_kids.push_back(gidx[k]);
             P.ch_kid_ptr.push_back((int64_t)P.ch_kids.size());
+            P.kpw.push_back(kq[q][0]);
+            P.kpw.push_back(kq[q][1]);
         }
         P.ch_ptr[c + 1] = q0 + nq;
         P.max_cv = std::max(P.max_cv, n);
@@ -3016,6 +3098,9 @@ AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t 
     L.add("ch_cvs", 4 * ncv);
     L.add("ch_kid_ptr", 8 * (ncv + 1));
     L.add("ch_kids", 8 * ncv);
+    for (const char* n : {"rho", "beta", "gcf", "srf"}) L.add(n, 8 * ncv);
+    L.add("prev", 4 * ncv);
+    L.add("kpw", 16 * ncv);                  // at most one chain per CV
     return L;
 }
 
@@ -3115,10 +3200,13 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
             st_amp[w] = sim->st_amp[q];
         }
     }
-    const ChainPlan CP = chain_plan(sim);
-    if (8 * (8 * (size_t)CP.max_cv + 2 * (size_t)CP.max_ch) + 4 * (3 * (size_t)CP.max_cv + 4 * (size_t)CP.max_ch + 4) >
-        (size_t)200 * 1024)
-        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to ~2,900 CVs)");
+    // largest diagonal each CV can reach (every gate open): bounds the scaled chain recurrence
+    std::vector<double> dmax(ncv);
+    for (int64_t i = 0; i < ncv; ++i) dmax[i] = cdt[i] + dsig[i] + glin[i];
+    for (int64_t j = 0; j < nhh; ++j) dmax[sim->hh_cv[j]] += gna[j] + gk[j] + gl[j];
+    const ChainPlan CP = chain_plan(sim, sigma.data(), cdt.data(), dmax.data());
+    if (adj_smem_bytes_for(CP.max_cv, CP.max_ch) > (size_t)200 * 1024)
+        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to ~1,500 CVs)");
     arb_status st = sync_in(sim);
     if (st != ARB_OK) return st;
     char* base = (char*)workspace;
@@ -3144,7 +3232,10 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         (st = up("ch_cv_ptr", CP.ch_cv_ptr.data(), 8 * CP.ch_cv_ptr.size())) != ARB_OK ||
         (st = up("ch_cvs", CP.ch_cvs.data(), 4 * CP.ch_cvs.size())) != ARB_OK ||
         (st = up("ch_kid_ptr", CP.ch_kid_ptr.data(), 8 * CP.ch_kid_ptr.size())) != ARB_OK ||
-        (st = up("ch_kids", CP.ch_kids.data(), 8 * CP.ch_kids.size())) != ARB_OK)
+        (st = up("ch_kids", CP.ch_kids.data(), 8 * CP.ch_kids.size())) != ARB_OK ||
+        (st = up("rho", CP.rho.data(), 8 * ncv)) != ARB_OK || (st = up("beta", CP.beta.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("gcf", CP.gcf.data(), 8 * ncv)) != ARB_OK || (st = up("srf", CP.srf.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("prev", CP.prev.data(), 4 * ncv)) != ARB_OK || (st = up("kpw", CP.kpw.data(), 8 * CP.kpw.size())) != ARB_OK)
         return st;
     AdjArgs a{};
     a.n_cells = (int32_t)nc;
@@ -3197,6 +3288,12 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.ch_cvs = (const int32_t*)L.at(base, "ch_cvs");
     a.ch_kid_ptr = (const int64_t*)L.at(base, "ch_kid_ptr");
     a.ch_kids = (const int64_t*)L.at(base, "ch_kids");
+    a.rho = (const double*)L.at(base, "rho");
+    a.beta = (const double*)L.at(base, "beta");
+    a.gcf = (const double*)L.at(base, "gcf");
+    a.srf = (const double*)L.at(base, "srf");
+    a.prev = (const int32_t*)L.at(base, "prev");
+    a.kpw = (const double*)L.at(base, "kpw");
     a.smem_cv = std::max<int32_t>(CP.max_cv, 1);
     a.smem_ch = std::max<int32_t>(CP.max_ch, 1);
     CU(adj_prepare(a));
