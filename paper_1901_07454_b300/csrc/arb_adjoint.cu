@@ -157,99 +157,99 @@ __device__ void load_cell(const AdjArgs& a, int c, const Smem& sm) {
     __syncthreads();
 }
 
-// Double-precision helpers on 32-bit halves (integer pipe): a select, a sign flip and a shuffle.
-// Selecting or moving a double as one 64-bit value measured slower here.
-__device__ __forceinline__ double sel_d(bool c, double a, double b) {
-    return __hiloint2double(c ? __double2hiint(a) : __double2hiint(b), c ? __double2loint(a) : __double2loint(b));
-}
-__device__ __forceinline__ double neg_d(double x) {
-    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
-}
-__device__ __forceinline__ double shfl_d(double x, int src) {
-    return __hiloint2double(__shfl_sync(0xffffffffu, __double2hiint(x), src),
-                            __shfl_sync(0xffffffffu, __double2loint(x), src));
-}
+// Barrier of the block's first two warps (the elimination's P and W warps); barrier 0 stays
+// the block-wide one.
+__device__ __forceinline__ void elim_pair_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
 
-// Elimination of cell c (first warp), leaf chains first. Input: sm.A2 = (d rho, b beta) per CV.
-// Output: P^ and W^ of every CV in sm.PW, and each chain's elimination into its parent in sm.CDB.
-// Lanes 2j and 2j+1 take the j-th chain of a group of 16; every lane runs the group's longest
-// chain so that the pair exchange stays converged. Step k is one multiply-add fma(A, X, Y) on
-// each lane; with p = k on the P lane and p = k - 2 on the W lane (the CV it works on):
-//   P lane: A = d_p rho_p,    X = P^_{p-1}, Y = -P^_{p-2}  ->  P^_p    (1 <= p <= len-1)
-//   W lane: A = b_p beta_p,   X = P^_{p-1}, Y = W^_{p-1}   ->  W^_p    (1 <= p <= len-1; A = 0 for p <= 0)
-// The W lane gets P^ from its partner by a shuffle issued one step before it is needed, so
-// neither the shuffle's latency nor a move waiting on it is on the dependent path. Operands are
-// loaded two steps ahead and the loop is unrolled by two with one register set per parity, so
-// no instruction waits on a shared-memory load; everything except the final select is formed
-// before the multiply-add, and the store of its result comes last.
-__device__ void tree_eliminate(const AdjArgs& a, int c, int lane, const Smem& sm) {
+// Elimination of cell c by the first two warps (tid < 64), leaf chains first. Input: sm.A2 =
+// (d rho, b beta) per CV. Output: P^ and W^ of every CV in sm.PW, and each chain's elimination
+// into its parent in sm.CDB. The pivots do not depend on the right-hand side, so warp 0 runs the
+// P^ recurrence of a level while warp 1 runs the W^ recurrence of the level before (which needs
+// that level's P^), one lane per chain each; the two meet at a barrier between levels. Each step
+// is one multiply-add:
+//   warp 0: P^_k = (d_k rho_k) P^_{k-1} - P^_{k-2}     (P^_{-1} = 1, P^_0 = D_0)
+//   warp 1: W^_k = (b_k beta_k) P^_{k-1} + W^_{k-1}    (W^_0 = B_0)
+// An FP64 result that passes through an integer instruction (a select, a sign flip, a move
+// under a predicate) before the next multiply-add costs tens of cycles here, so the loops have
+// none: the negation is the multiply-add's own, each lane runs exactly its chain's steps (a
+// remainder step after the loop unrolled by two), operands are loaded two steps ahead from
+// always-valid indices, and a result is stored only after the next multiply-add is issued.
+__device__ void tree_eliminate(const AdjArgs& a, int c, int tid, const Smem& sm) {
     const int nl = (int)(a.lev_off[c + 1] - a.lev_off[c]) - 1;
-    const int role = lane & 1;                   // 0: P^, 1: W^
-    const int lag = 2 * role;
-    const unsigned full = 0xffffffffu;
-    for (int L = 0; L < nl; ++L) {
-        const int q1 = sm.levb[L + 1];
-        for (int qb = sm.levb[L]; qb < q1; qb += 16) {
-            const int q = qb + (lane >> 1);
-            const bool on = q < q1;
-            int cs = 0, len = 0;
-            if (on) {
-                cs = sm.chp[q];
-                len = sm.chp[q + 1] - cs;
-            }
-            const int e0 = cs + len - 1;         // the tail's position in cvs; CV p of the chain is cvs[e0 - p]
-            auto cv_at = [&](int k) -> int {
-                const int p = k - lag;
-                return (on && p >= 0 && p <= len - 1) ? sm.cvs[e0 - p] : 0;
-            };
-            auto opnd = [&](int k, int x) -> double {
-                const int p = k - lag;
-                return (on && p >= 1 && p <= len - 1) ? sm.A2[2 * x + role] : 0.0;
-            };
-            // the tail: its own diagonal / right-hand side and the eliminations of its child chains
-            double X = 1.0, Y = -1.0;            // P lane: P^_0, -P^_{-1}; W lane: P^_{-1}, W^_0
-            if (on) {
+    const int w = tid >> 5, lane = tid & 31;
+    for (int it = 0; it <= nl; ++it) {
+        const int L = it - w;                    // warp 1 runs one level behind
+        if (L >= 0 && L < nl) {
+            for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
+                const int cs = sm.chp[q], len = sm.chp[q + 1] - cs;
+                const int e0 = cs + len - 1;     // the tail's position in cvs; CV k of the chain is cvs[e0 - k]
+                auto cv_at = [&](int k) -> int { return sm.cvs[k < len ? e0 - k : e0]; };
                 const int x0 = sm.cvs[e0];
-                double acc = sm.A2[2 * x0 + role];
-                for (int k = sm.kidp[q]; k < sm.kidp[q + 1]; ++k) acc += sm.CDB[2 * sm.kids[k] + role];
-                sm.PW[2 * x0 + role] = acc;
-                if (role) Y = acc;
-                else X = acc;
-            }
-            int m = len;
-            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(full, m, o));
-            m += 1;                              // the W lane's last step
-            int sxa = cv_at(1), sxb = cv_at(2), cva = cv_at(3), cvb = cv_at(4);
-            double Aa = opnd(1, sxa), Ab = opnd(2, sxb);
-            double sha = 1.0, shb = 1.0;
-#define ARB_ELIM_STEP(K, A, SX, CV, SH_NEW, SH_USE)                                            \
+                // the tail: its own diagonal / right-hand side and its child chains' eliminations
+                double acc = sm.A2[2 * x0 + w];
+                for (int k = sm.kidp[q]; k < sm.kidp[q + 1]; ++k) acc += sm.CDB[2 * sm.kids[k] + w];
+                sm.PW[2 * x0 + w] = acc;
+                int xa = cv_at(1), xb = cv_at(2), ya = cv_at(3), yb = cv_at(4);
+                int ks = x0;                     // CV of the result waiting to be stored
+                if (w == 0) {
+                    double X = acc, Y = 1.0;     // P^_{k-1}, P^_{k-2}
+                    double Aa = sm.A2[2 * xa], Ab = sm.A2[2 * xb];
+                    double S = acc;              // the result waiting to be stored
+#define ARB_P_STEP(K, XV, YV, AV)                                                                \
     {                                                                                            \
-        const int k_ = (K);                                                                      \
-        const int p_ = k_ - lag;                                                                 \
-        const bool act_ = on && p_ <= len - 1;                                                   \
-        const bool st_ = act_ && p_ >= 0;                                                        \
-        SH_NEW = shfl_d(X, lane & ~1);                                                           \
-        const double xalt_ = sel_d(act_ && role, SH_USE, X);                                     \
-        const double yalt_ = sel_d(act_ && !role, neg_d(X), Y);                                  \
-        const double out_ = fma(A, X, Y);                                                        \
-        const int sx_k_ = SX;                                                                    \
-        A = opnd(k_ + 2, CV);                                                                    \
-        SX = CV;                                                                                 \
-        CV = cv_at(k_ + 4);                                                                      \
-        X = sel_d(act_ && !role, out_, xalt_);                                                   \
-        Y = sel_d(act_ && role, out_, yalt_);                                                    \
-        if (st_) sm.PW[2 * sx_k_ + role] = out_;                                                 \
+        const double out_ = fma(AV, X, -Y);                                                      \
+        sm.PW[2 * ks] = S;                                                                       \
+        ks = XV;                                                                                 \
+        S = out_;                                                                                \
+        AV = sm.A2[2 * YV];                                                                      \
+        XV = YV;                                                                                 \
+        YV = cv_at((K) + 4);                                                                     \
+        Y = X;                                                                                   \
+        X = out_;                                                                                \
     }
-            for (int k = 1; k <= m; k += 2) {
-                ARB_ELIM_STEP(k, Aa, sxa, cva, sha, shb)
-                ARB_ELIM_STEP(k + 1, Ab, sxb, cvb, shb, sha)
+                    int k = 1;
+                    for (; k + 1 < len; k += 2) {
+                        ARB_P_STEP(k, xa, ya, Aa)
+                        ARB_P_STEP(k + 1, xb, yb, Ab)
+                    }
+                    if (k < len) ARB_P_STEP(k, xa, ya, Aa)
+#undef ARB_P_STEP
+                    sm.PW[2 * ks] = S;
+                    // the head's elimination into the parent's diagonal: -s_h^2 / D_h
+                    if (sm.par[sm.cvs[cs]] >= 0) sm.CDB[2 * q] = (-sm.KPW[2 * q] * Y) * rcp_nr(X);
+                } else {
+                    double Y = acc;              // W^_{k-1}
+                    // operands of step k: b_k beta_k and P^_{k-1} (of the CV before k in the chain)
+                    double Ba = sm.A2[2 * xa + 1], Bb = sm.A2[2 * xb + 1];
+                    double Pa = sm.PW[2 * x0], Pb = sm.PW[2 * xa];
+                    double S = acc;
+#define ARB_W_STEP(K, XV, YV, BV, PV)                                                            \
+    {                                                                                            \
+        const double out_ = fma(BV, PV, Y);                                                      \
+        sm.PW[2 * ks + 1] = S;                                                                   \
+        ks = XV;                                                                                 \
+        S = out_;                                                                                \
+        BV = sm.A2[2 * YV + 1];                                                                  \
+        PV = sm.PW[2 * cv_at((K) + 1)];                                                          \
+        XV = YV;                                                                                 \
+        YV = cv_at((K) + 4);                                                                     \
+        Y = out_;                                                                                \
+    }
+                    int k = 1;
+                    for (; k + 1 < len; k += 2) {
+                        ARB_W_STEP(k, xa, ya, Ba, Pa)
+                        ARB_W_STEP(k + 1, xb, yb, Bb, Pb)
+                    }
+                    if (k < len) ARB_W_STEP(k, xa, ya, Ba, Pa)
+#undef ARB_W_STEP
+                    sm.PW[2 * ks + 1] = S;
+                    // the head's elimination into the parent's right-hand side: s_h B_h / D_h
+                    const int h = sm.cvs[cs];
+                    if (sm.par[h] >= 0) sm.CDB[2 * q + 1] = (sm.KPW[2 * q + 1] * Y) * rcp_nr(sm.PW[2 * h]);
+                }
             }
-#undef ARB_ELIM_STEP
-            // the head's elimination into its parent: P lane -s_h^2 / D_h, W lane s_h B_h / D_h
-            // (X = P^_h on both lanes; Y = -P^_{h-1} on the P lane, W^_h on the W lane)
-            if (on && sm.par[sm.cvs[cs]] >= 0) sm.CDB[2 * q + role] = (sm.KPW[2 * q + role] * Y) * rcp_nr(X);
         }
-        __syncwarp();
+        elim_pair_sync();
     }
 }
 
@@ -268,38 +268,42 @@ __device__ void tree_coefficients(int n, const Smem& sm) {
 }
 
 // Back substitution (first warp): levels in reverse order, each chain from its head (using its
-// parent's solution; e = 0 at the root) to its tail, one lane per chain, one multiply-add per CV.
-// As in the elimination, operands come two CVs ahead, unrolled by two with a register set per
-// parity, and the store of each value comes after the next multiply-add. Result in sm.X.
+// parent's solution; e = 0 at the root) to its tail, one lane per chain, one multiply-add per CV,
+// written as the elimination's loops are (no select on the dependent path, operands two CVs
+// ahead from always-valid indices, each value stored after the next multiply-add). Result in sm.X.
 __device__ void tree_substitute(const AdjArgs& a, int c, int lane, const Smem& sm) {
     const int nl = (int)(a.lev_off[c + 1] - a.lev_off[c]) - 1;
     for (int L = nl - 1; L >= 0; --L) {
         for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
             const int cs = sm.chp[q], ce = sm.chp[q + 1];
-            auto cv_at = [&](int i) -> int { return i < ce ? sm.cvs[i] : 0; };
+            auto cv_at = [&](int i) -> int { return sm.cvs[i < ce ? i : ce - 1]; };
             const int x0 = sm.cvs[cs];
             const int32_t p = sm.par[x0];
-            double vp = p >= 0 ? sm.X[p] : 0.0;
+            double vp = sm.X[p >= 0 ? p : 0];    // e = 0 at the root, so any finite value serves
+            if (p < 0) vp = 0.0;
             int xa = x0, xb = cv_at(cs + 1), ya = cv_at(cs + 2), yb = cv_at(cs + 3);
             double ua = sm.A2[2 * xa], ea = sm.A2[2 * xa + 1];
             double ub = sm.A2[2 * xb], eb = sm.A2[2 * xb + 1];
+            int ks = -1;                          // CV of the value waiting to be stored
 #define ARB_SUBST_STEP(I, XV, YV, U, E)                                                          \
     {                                                                                            \
-        const int i_ = (I);                                                                      \
         const double v_ = fma(E, vp, U);                                                         \
-        const int xi_ = XV;                                                                      \
+        if (ks >= 0) sm.X[ks] = vp;                                                              \
+        ks = XV;                                                                                 \
         U = sm.A2[2 * YV];                                                                       \
         E = sm.A2[2 * YV + 1];                                                                   \
         XV = YV;                                                                                 \
-        YV = cv_at(i_ + 4);                                                                      \
+        YV = cv_at((I) + 4);                                                                     \
         vp = v_;                                                                                 \
-        if (i_ < ce) sm.X[xi_] = v_;                                                             \
     }
-            for (int i = cs; i < ce; i += 2) {
+            int i = cs;
+            for (; i + 1 < ce; i += 2) {
                 ARB_SUBST_STEP(i, xa, ya, ua, ea)
                 ARB_SUBST_STEP(i + 1, xb, yb, ub, eb)
             }
+            if (i < ce) ARB_SUBST_STEP(i, xa, ya, ua, ea)
 #undef ARB_SUBST_STEP
+            sm.X[ks] = vp;
         }
         __syncwarp();
     }
@@ -362,7 +366,7 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             sm.A2[2 * li + 1] = (sm.cdt[li] * Vs[i] + GE) * sm.beta[li];
         }
         __syncthreads();
-        if (tid < 32) {
+        if (tid < 64) {
             if (tid == 0) {
                 const double t = (double)(a.k0 + s) * a.dt;
                 for (int64_t q = a.st_ptr[c]; q < a.st_ptr[c + 1]; ++q)
@@ -371,8 +375,7 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                         sm.A2[2 * x + 1] = fma(a.st_amp[q], sm.beta[x], sm.A2[2 * x + 1]);
                     }
             }
-            __syncwarp();
-            tree_eliminate(a, c, lane, sm);
+            tree_eliminate(a, c, tid, sm);
         }
         __syncthreads();
         tree_coefficients((int)n, sm);
@@ -489,7 +492,7 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
             sm.A2[2 * li + 1] = vb * sm.beta[li];
         }
         __syncthreads();
-        if (tid < 32) tree_eliminate(a, c, lane, sm);
+        if (tid < 64) tree_eliminate(a, c, tid, sm);
         __syncthreads();
         tree_coefficients((int)n, sm);
         __syncthreads();
