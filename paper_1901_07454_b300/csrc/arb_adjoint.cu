@@ -71,8 +71,8 @@ __device__ __forceinline__ void membrane(const AdjArgs& a, double gl, double gel
 struct Smem {
     double* A2;    // [2 smem_cv] per CV: d rho (even), b beta (odd); then (u, e) of the back substitution
     double* PW;    // [2 smem_cv] per CV: P^ (even), W^ (odd)
-    double* X;     // [smem_cv] solution
-    double* sig;   // [smem_cv] axial conductance to the parent (cell-local CV order)
+    double* X;     // [smem_cv] solution (in PW's space, which the back substitution no longer needs)
+    double* GA;    // [4 smem_cv] reverse sweep: the gradient sums of the cell's CVs during a launch
     double* cdt;   // [smem_cv] C / dt
     double* dsig;  // [smem_cv] sum of the CV's axial conductances (own + children)
     double* glin;  // [smem_cv] passive conductance
@@ -99,9 +99,9 @@ __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
     const int ncv = a.smem_cv, nch = a.smem_ch;
     m.A2 = adj_smem;
     m.PW = m.A2 + 2 * ncv;
-    m.X = m.PW + 2 * ncv;
-    m.sig = m.X + ncv;
-    m.cdt = m.sig + ncv;
+    m.X = m.PW;
+    m.GA = m.PW + 2 * ncv;
+    m.cdt = m.GA + 4 * ncv;
     m.dsig = m.cdt + ncv;
     m.glin = m.dsig + ncv;
     m.gelin = m.glin + ncv;
@@ -130,7 +130,6 @@ __device__ void load_cell(const AdjArgs& a, int c, const Smem& sm) {
     const int64_t l0 = a.lev_off[c], nlb = a.lev_off[c + 1] - l0;
     const int64_t cv0 = a.ch_cv_ptr[q0], k0 = a.ch_kid_ptr[q0];
     for (int64_t i = tid; i < n; i += kAdjThreads) {
-        sm.sig[i] = a.sig[off + i];
         sm.cdt[i] = a.cdt[off + i];
         sm.dsig[i] = a.dsig[off + i];
         sm.glin[i] = a.glin[off + i];
@@ -464,9 +463,12 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
     const double* const segY = a.segY[buf];
     const double* const segG = a.segG[buf];
     const int64_t nhh = a.n_hh, ncv = a.n_cv;
-    const double dt = a.dt;
     const Smem sm = smem_of(a);
     load_cell(a, c, sm);
+    // the cell's gradient sums stay in shared memory for the launch (each thread keeps the CVs it
+    // updates), in the same order of additions as in global memory
+    for (int64_t i = off + tid; i < off + n; i += kAdjThreads)
+        for (int g = 0; g < 4; ++g) sm.GA[4 * (i - off) + g] = a.gacc[g * ncv + i];
     for (int64_t s = s1 - 1; s >= s0; --s) {
         const double* V0 = segV + (s - s0) * ncv;
         const double* V1 = V0 + ncv;
@@ -499,27 +501,37 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         if (tid < 32) tree_substitute(a, c, lane, sm);
         __syncthreads();
         // lam_s; gradient terms; gate adjoint of y^s
+        // (dA/dtheta V^{s+1} - dRHS/dtheta) against lam_s: with w = lam_s, per unit density
+        //   cm:    (area 1e-5 / dt) (V^s - V^{s+1}) w          (nF/ms per uF/cm^2)
+        //   gnabar: area 1e-2 m^3 h (E_Na - V^{s+1}) w, gkbar: area 1e-2 n^4 (E_K - V^{s+1}) w,
+        //   gl:     area 1e-2 (E_L - V^{s+1}) w;
+        // the gate adjoints take d(G V - GE)/dgate from the same terms. Per-CV factors come from
+        // the host (kcm = area 1e-5 / dt, ksc = area 1e-2), so no division is left here.
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
             const double lam = sm.X[i - off];
             a.lam[i] = lam;
             const double v1 = V1[i];
-            a.gacc[3 * ncv + i] += lam * (V0[i] - v1) / dt * (a.area[i] * 1e-5);
+            double* ga = sm.GA + 4 * (i - off);
+            ga[3] = fma(lam * (V0[i] - v1), a.kcm[i], ga[3]);
             const int32_t j = sm.hidx[i - off];
             if (j >= 0) {
                 const double m = Y0[j], h = Y0[nhh + j], nn = Y0[2 * nhh + j];
                 const double lna = lam * (kENa - v1), lk = lam * (kEK - v1), ll = lam * (kEL - v1);
-                const double sc = a.area[i] * 1e-2;
-                const double m3h = m * m * m * h, n2 = nn * nn;
-                a.gacc[i] += m3h * lna * sc;
-                a.gacc[ncv + i] += n2 * n2 * lk * sc;
-                a.gacc[2 * ncv + i] += ll * sc;
-                a.ybar[j] += a.gna[j] * 3.0 * m * m * h * lna;
-                a.ybar[nhh + j] += a.gna[j] * m * m * m * lna;
-                a.ybar[2 * nhh + j] += a.gk[j] * 4.0 * n2 * nn * lk;
+                const double sc = a.ksc[i];
+                const double m2 = m * m, m2h = m2 * h, n2 = nn * nn, n3 = n2 * nn;
+                ga[0] = fma(m2h * m * sc, lna, ga[0]);
+                ga[1] = fma(n3 * nn * sc, lk, ga[1]);
+                ga[2] = fma(ll, sc, ga[2]);
+                const double g3 = a.gna3[j];
+                a.ybar[j] = fma(g3 * m2h, lna, a.ybar[j]);
+                a.ybar[nhh + j] = fma(a.gna[j] * (m2 * m), lna, a.ybar[nhh + j]);
+                a.ybar[2 * nhh + j] = fma(a.gk4[j] * n3, lk, a.ybar[2 * nhh + j]);
             }
         }
         __syncthreads();
     }
+    for (int64_t i = off + tid; i < off + n; i += kAdjThreads)
+        for (int g = 0; g < 4; ++g) a.gacc[g * ncv + i] = sm.GA[4 * (i - off) + g];
 }
 
 // Forward pass with checkpoints and the loss: one block per cell.

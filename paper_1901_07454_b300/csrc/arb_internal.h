@@ -302,11 +302,15 @@ struct AdjArgs {
     const double* glin;        // [n_cv] passive conductance (uS)
     const double* gelin;       // [n_cv] passive conductance x reversal (nA)
     const double* area;        // [n_cv] um^2
+    const double* kcm;         // [n_cv] area 1e-5 / dt: the cm gradient's factor
+    const double* ksc;         // [n_cv] area 1e-2: the channel densities' factor
     const int32_t* hidx;       // [n_cv] HH instance on the CV, -1 none
     const double* hh_tab;      // tabulated gate update of the simulation's dt, or null
     const double* gna;         // [n_hh] uS
     const double* gk;
     const double* gl;
+    const double* gna3;        // [n_hh] 3 gna
+    const double* gk4;         // [n_hh] 4 gk
     const int64_t* st_ptr;     // [n_cells+1] clamps of each cell
     const int64_t* st_cv;      // global CV
     const double* st_on;
@@ -357,10 +361,10 @@ struct AdjArgs {
     double* grad;              // [n_groups][4] output
 };
 
-// Dynamic shared memory of one adjoint block: per CV 14 doubles and 4 int32, per chain 4
+// Dynamic shared memory of one adjoint block: per CV 16 doubles and 4 int32, per chain 4
 // doubles and 4 int32, and 4 int32 of level bounds.
 inline size_t adj_smem_bytes_for(int64_t cvs, int64_t chains) {
-    return 8 * (14 * (size_t)cvs + 4 * (size_t)chains) + 4 * (4 * (size_t)cvs + 4 * (size_t)chains + 4);
+    return 8 * (16 * (size_t)cvs + 4 * (size_t)chains) + 4 * (4 * (size_t)cvs + 4 * (size_t)chains + 4);
 }
 
 #ifdef ARB_DEBUG

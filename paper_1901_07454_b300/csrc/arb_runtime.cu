@@ -3071,9 +3071,9 @@ AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t 
     AdjLayout L;
     L.add("off", 8 * (nc + 1));
     L.add("parent", 4 * ncv);
-    for (const char* n : {"cdt", "sig", "dsig", "glin", "gelin", "area"}) L.add(n, 8 * ncv);
+    for (const char* n : {"cdt", "sig", "dsig", "glin", "gelin", "area", "kcm", "ksc"}) L.add(n, 8 * ncv);
     L.add("hidx", 4 * ncv);
-    for (const char* n : {"gna", "gk", "gl"}) L.add(n, 8 * nhh);
+    for (const char* n : {"gna", "gk", "gl", "gna3", "gk4"}) L.add(n, 8 * nhh);
     L.add("st_ptr", 8 * (nc + 1));
     for (const char* n : {"st_cv", "st_on", "st_dur", "st_amp"}) L.add(n, 8 * nst);
     L.add("obs", 4 * ncv);
@@ -3173,14 +3173,21 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         glin[cv] += G;
         gelin[cv] += G * sim->e_pas[q];
     }
+    std::vector<double> kcm(ncv), ksc(ncv);
+    for (int64_t i = 0; i < ncv; ++i) {
+        kcm[i] = area[i] * 1e-5 / dt;
+        ksc[i] = area[i] * 1e-2;
+    }
     std::vector<int32_t> hidx(ncv, -1);
-    std::vector<double> gna(nhh), gk(nhh), gl(nhh);
+    std::vector<double> gna(nhh), gk(nhh), gl(nhh), gna3(nhh), gk4(nhh);
     for (int64_t j = 0; j < nhh; ++j) {
         const int64_t cv = sim->hh_cv[j];
         hidx[cv] = (int32_t)j;
         gna[j] = sim->gnabar[j] * area[cv] * 1e-2;
         gk[j] = sim->gkbar[j] * area[cv] * 1e-2;
         gl[j] = sim->gl[j] * area[cv] * 1e-2;
+        gna3[j] = 3.0 * gna[j];
+        gk4[j] = 4.0 * gk[j];
     }
     // clamps grouped by cell
     std::vector<int64_t> st_ptr(nc + 1, 0), st_cv(nst);
@@ -3206,7 +3213,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     for (int64_t j = 0; j < nhh; ++j) dmax[sim->hh_cv[j]] += gna[j] + gk[j] + gl[j];
     const ChainPlan CP = chain_plan(sim, sigma.data(), cdt.data(), dmax.data());
     if (adj_smem_bytes_for(CP.max_cv, CP.max_ch) > (size_t)200 * 1024)
-        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to ~1,500 CVs)");
+        return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to about 1,000 to 1,400 CVs, by chain count)");
     arb_status st = sync_in(sim);
     if (st != ARB_OK) return st;
     char* base = (char*)workspace;
@@ -3219,6 +3226,8 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         (st = up("cdt", cdt.data(), 8 * ncv)) != ARB_OK || (st = up("sig", sigma.data(), 8 * ncv)) != ARB_OK ||
         (st = up("dsig", dsig.data(), 8 * ncv)) != ARB_OK || (st = up("glin", glin.data(), 8 * ncv)) != ARB_OK ||
         (st = up("gelin", gelin.data(), 8 * ncv)) != ARB_OK || (st = up("area", area.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("kcm", kcm.data(), 8 * ncv)) != ARB_OK || (st = up("ksc", ksc.data(), 8 * ncv)) != ARB_OK ||
+        (st = up("gna3", gna3.data(), 8 * nhh)) != ARB_OK || (st = up("gk4", gk4.data(), 8 * nhh)) != ARB_OK ||
         (st = up("hidx", hidx.data(), 4 * ncv)) != ARB_OK || (st = up("gna", gna.data(), 8 * nhh)) != ARB_OK ||
         (st = up("gk", gk.data(), 8 * nhh)) != ARB_OK || (st = up("gl", gl.data(), 8 * nhh)) != ARB_OK ||
         (st = up("st_ptr", st_ptr.data(), 8 * (nc + 1))) != ARB_OK || (st = up("st_cv", st_cv.data(), 8 * nst)) != ARB_OK ||
@@ -3249,10 +3258,14 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.glin = (const double*)L.at(base, "glin");
     a.gelin = (const double*)L.at(base, "gelin");
     a.area = (const double*)L.at(base, "area");
+    a.kcm = (const double*)L.at(base, "kcm");
+    a.ksc = (const double*)L.at(base, "ksc");
     a.hidx = (const int32_t*)L.at(base, "hidx");
     a.gna = (const double*)L.at(base, "gna");
     a.gk = (const double*)L.at(base, "gk");
     a.gl = (const double*)L.at(base, "gl");
+    a.gna3 = (const double*)L.at(base, "gna3");
+    a.gk4 = (const double*)L.at(base, "gk4");
     a.st_ptr = (const int64_t*)L.at(base, "st_ptr");
     a.st_cv = (const int64_t*)L.at(base, "st_cv");
     a.st_on = (const double*)L.at(base, "st_on");
