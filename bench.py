@@ -68,14 +68,15 @@ STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 119.0}
 
 
 # Discrete adjoint (every CV with HH, checkpoint every 500 steps): FP64 thread instructions per
-# gradient CV-step of the forward, recompute and reverse kernels together (ncu on the 256-cell
-# fitting workload, profiles/adjoint_config4_256cells.md: 51.1 in k_adj_forward, 162 in
-# k_adj_stage), and the algorithmic state bytes per gradient CV-step: forward V and gates
-# read+write (64), recompute V and gates read and V, gates, dPhi/dV and decay factors written
-# (112), reverse segment states and factors read, lambda, gate adjoints and gradient sums
-# read+write (216).
-ADJ_FP64_PER_CV_STEP = 213.0
-ADJ_BYTES_PER_CV_STEP = 392.0
+# gradient CV-step of the forward, recompute and reverse kernels together (ncu, 64 cells of the
+# fitting workload, profiles/adjoint_config4_256cells.md: 55.6 in k_adj_forward, 153.1 in
+# k_adj_stage); the algorithmic DRAM bytes per gradient CV-step: the recompute writes V, the
+# three gates and, per HH CV, three dPhi/dV and three decay factors (80 B), which the reverse
+# sweep reads back (80 B) -- the running state, lambda, the gate adjoints and the gradient sums
+# stay in shared memory or L2; and the DRAM bytes the same capture measured (164.8 B).
+ADJ_FP64_PER_CV_STEP = 208.7
+ADJ_BYTES_PER_CV_STEP = 160.0
+ADJ_DRAM_BYTES_PER_CV_STEP = 164.8
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
@@ -301,7 +302,9 @@ def run_adjoint(args, model, spec):
     hbm_ach = ADJ_BYTES_PER_CV_STEP * units / args.steps / (kern_mean * 1e-3) / 1e9
     peak, peak_kind = peaks()
     roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_INST_PER_S, "unit": "FP64 inst/s",
-                "frac": ach / FP64_PEAK_INST_PER_S, "traffic": None,
+                "frac": ach / FP64_PEAK_INST_PER_S,
+                "traffic": ADJ_DRAM_BYTES_PER_CV_STEP * units / args.steps,
+                "traffic_unit": "DRAM bytes per gradient, all launches (ncu, per CV-step x CV-steps)",
                 "peak_kind": "derived: 148 SMs x 2 FP64 FMA/clk x 2032 MHz",
                 "fp64_inst_per_cv_step": ADJ_FP64_PER_CV_STEP, "kernel": "k_adj_forward + k_adj_stage",
                 "kernel_ms_mean": kern_mean,
