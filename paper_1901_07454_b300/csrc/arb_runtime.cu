@@ -24,6 +24,9 @@
 #include <thread>
 #include <vector>
 
+#include <stdlib.h>
+#include <sys/mman.h>
+
 #include "../../include/arb.h"
 #include "arb_internal.h"
 
@@ -87,6 +90,22 @@ struct UninitAlloc : std::allocator<T> {
     UninitAlloc() = default;
     template <class U>
     UninitAlloc(const UninitAlloc<U>&) {}
+    // Blocks of 8 MB and more are 2 MB aligned and marked for transparent huge pages: the plan's
+    // arrays (tens of millions of entries) are first touched by many threads at once, and 4 KB
+    // page faults taken in parallel contend in the kernel.
+    static constexpr size_t kHuge = (size_t)2 << 20;
+    T* allocate(size_t n) {
+        const size_t bytes = n * sizeof(T);
+        if (bytes < 4 * kHuge) return std::allocator<T>::allocate(n);
+        void* q = nullptr;
+        if (posix_memalign(&q, kHuge, (bytes + kHuge - 1) / kHuge * kHuge) != 0) throw std::bad_alloc();
+        madvise(q, (bytes + kHuge - 1) / kHuge * kHuge, MADV_HUGEPAGE);   // advice only: failure is harmless
+        return static_cast<T*>(q);
+    }
+    void deallocate(T* q, size_t n) {
+        if (n * sizeof(T) < 4 * kHuge) std::allocator<T>::deallocate(q, n);
+        else free(q);
+    }
     template <class U>
     void construct(U* p) noexcept { ::new ((void*)p) U; }
     template <class U, class... A>
@@ -360,9 +379,9 @@ void build_hh_table(double dt, double* tab) {
 // cylinders between their centres in series (Sec. "Model", Eq. discrete-v).
 void cv_geometry(const arb_sim* sim, hvec<double>& area, hvec<double>& cap, hvec<double>& sigma) {
     const int64_t ncv = sim->n_cv;
-    par_assign(area, ncv, 0.0);
-    par_assign(cap, ncv, 0.0);
-    par_assign(sigma, ncv, 0.0);
+    area.resize(ncv);   // every element is written below (first touch by the threads that use it)
+    cap.resize(ncv);
+    sigma.resize(ncv);
     parallel_for(sim->n_cells, [&](int64_t c) {
         const int64_t off = sim->cv_offset[c], n = sim->cv_offset[c + 1] - off;
         for (int64_t i = 0; i < n; ++i) {
@@ -376,6 +395,8 @@ void cv_geometry(const arb_sim* sim, hvec<double>& area, hvec<double>& cap, hvec
                 const double half_i = sim->Ra[g] * h / (200.0 * kPi * r * r);
                 const double half_p = sim->Ra[pg] * sim->length[pg] / (200.0 * kPi * sim->radius[pg] * sim->radius[pg]);
                 sigma[g] = 1.0 / (half_i + half_p);       // uS
+            } else {
+                sigma[g] = 0.0;
             }
         }
     });
@@ -1076,30 +1097,51 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
     par_assign(Glin, ncv, 0.0);
     par_assign(GElin, ncv, 0.0);
     cv_geometry(sim, area, cap, sigma);
-    for (size_t i = 0; i < sim->pas_cv.size(); ++i) {
-        const int64_t cv = sim->pas_cv[i];
-        const double G = sim->g_pas[i] * area[cv] * 1e-2;  // S/cm^2 * um^2 -> uS
-        Glin[cv] += G;
-        GElin[cv] += G * sim->e_pas[i];
+    {
+        // passive entries: in parallel chunks when their CVs are strictly increasing (one writer
+        // per CV), else in order; then HH instances, which sit on distinct CVs (checked above)
+        const int64_t npas = (int64_t)sim->pas_cv.size();
+        bool inc = true;
+        for (int64_t i = 1; i < npas && inc; ++i) inc = sim->pas_cv[i] > sim->pas_cv[i - 1];
+        auto pas = [&](int64_t i) {
+            const int64_t cv = sim->pas_cv[i];
+            const double G = sim->g_pas[i] * area[cv] * 1e-2;  // S/cm^2 * um^2 -> uS
+            Glin[cv] += G;
+            GElin[cv] += G * sim->e_pas[i];
+        };
+        constexpr int64_t kChunk = 1 << 16;
+        if (inc) {
+            parallel_for((npas + kChunk - 1) / kChunk, [&](int64_t ch) {
+                for (int64_t i = ch * kChunk; i < std::min<int64_t>(npas, (ch + 1) * kChunk); ++i) pas(i);
+            });
+        } else {
+            for (int64_t i = 0; i < npas; ++i) pas(i);
+        }
     }
     std::vector<double> hh_gna(sim->hh_cv.size()), hh_gk(sim->hh_cv.size());
-    for (size_t i = 0; i < sim->hh_cv.size(); ++i) {
-        const int64_t cv = sim->hh_cv[i];
-        const double G = sim->gl[i] * area[cv] * 1e-2;
-        Glin[cv] += G;
-        GElin[cv] += G * kEL;
-        hh_gna[i] = sim->gnabar[i] * area[cv] * 1e-2;
-        hh_gk[i] = sim->gkbar[i] * area[cv] * 1e-2;
+    {
+        const int64_t nhh = (int64_t)sim->hh_cv.size();
+        constexpr int64_t kChunk = 1 << 16;
+        parallel_for((nhh + kChunk - 1) / kChunk, [&](int64_t ch) {
+            for (int64_t i = ch * kChunk; i < std::min<int64_t>(nhh, (ch + 1) * kChunk); ++i) {
+                const int64_t cv = sim->hh_cv[i];
+                const double G = sim->gl[i] * area[cv] * 1e-2;
+                Glin[cv] += G;
+                GElin[cv] += G * kEL;
+                hh_gna[i] = sim->gnabar[i] * area[cv] * 1e-2;
+                hh_gk[i] = sim->gkbar[i] * area[cv] * 1e-2;
+            }
+        });
     }
 
     // ------------------------------------------------------------------ factorisation
     std::vector<CellOrder> ord(nc);
-    hvec<double> invd, ck, ce, ca, cb;
-    par_assign(invd, ncv, 0.0);
-    par_assign(ck, ncv, 0.0);
-    par_assign(ce, ncv, 0.0);
-    par_assign(ca, ncv, 0.0);
-    par_assign(cb, ncv, 0.0);
+    hvec<double> invd, ck, ce, ca, cb;   // every element is written in the cell loop below
+    invd.resize(ncv);
+    ck.resize(ncv);
+    ce.resize(ncv);
+    ca.resize(ncv);
+    cb.resize(ncv);
     {
         // cells are independent: each thread orders and factorises whole cells
         parallel_for(nc, [&](int64_t c) {
@@ -1139,6 +1181,9 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                         const double a = -sigma[g];
                         ck[g] = a * invd[off + o.dfs[o.dpar[q]]];
                         ce[g] = a * invd[g];
+                    } else {
+                        ck[g] = 0.0;
+                        ce[g] = 0.0;
                     }
                 }
             }
