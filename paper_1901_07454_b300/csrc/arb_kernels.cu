@@ -1205,7 +1205,11 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
     MT* nS = d.hh_n + (size_t)pk.hh_row0 * kWarp;
     FwdRow* fr = reinterpret_cast<FwdRow*>(ring);
     BwdRow* br = reinterpret_cast<BwdRow*>(ring);
-    double2* stk = stack;                      // [depth][32] (one cell per lane)
+    // hand-over stack (one cell per lane): three planes of [depth][32] -- the child's coupling K,
+    // its e and its u -- so that a push is three stores and the parent's pop two multiply-adds
+    double* stkK = (double*)stack;
+    double* stkE = stkK + (size_t)pk.stack * kWarp;
+    double* stkU = stkE + (size_t)pk.stack * kWarp;
     double* mbd = (double*)stack;              // mailbox (cells spread over lanes): [nmb] x (d, b),
     double* mbb = mbd + pk.nmb;                // and the published voltages over d in the back
     double* mbv = mbd;                         // substitution
@@ -1325,9 +1329,10 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                     if (mb_in != kMbNone) { dd -= mbd[ARB_IDX(mb_in, pk.nmb, d.ctl)]; bb += mbb[ARB_IDX(mb_in, pk.nmb, d.ctl)]; }
                 } else {
                     for (int q = f & kFlagPopMask; q > 0; --q) {
-                        const double2 c2 = stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane];
-                        dd -= c2.x;
-                        bb += c2.y;
+                        const int o = ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane;
+                        const double kc = stkK[o];
+                        dd = fma(-kc, stkE[o], dd);
+                        bb = fma(kc, stkU[o], bb);
                     }
                 }
                 const double rr = rcp_nr(dd);
@@ -1336,8 +1341,16 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 UE[(size_t)j * kWarp + lane] = make_double2(uu, ee);
                 const bool remote = (f & kFlagRemote) != 0;
                 if (remote && !(f & kFlagRoot)) {
-                    if (kShared) { mbd[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * ee; mbb[ARB_IDX(mb_out, pk.nmb, d.ctl)] += K * uu; }
-                    else stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(K * ee, K * uu);
+                    if (kShared) {
+                        const int o = ARB_IDX(mb_out, pk.nmb, d.ctl);
+                        mbd[o] = fma(K, ee, mbd[o]);
+                        mbb[o] = fma(K, uu, mbb[o]);
+                    } else {
+                        const int o = ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane;
+                        stkK[o] = K;
+                        stkE[o] = ee;
+                        stkU[o] = uu;
+                    }
                 }
                 kprev = remote ? 0.0 : K;
                 eprev = ee;
@@ -1366,14 +1379,14 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 }
                 double vp;
                 if (f & kFlagRoot) vp = 0.0;
-                else if (f & kFlagRemote) vp = kShared ? mbv[ARB_IDX((f >> kMbOutShift) & kMbNone, pk.nmb, d.ctl)] : stk[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane].x;
+                else if (f & kFlagRemote) vp = kShared ? mbv[ARB_IDX((f >> kMbOutShift) & kMbNone, pk.nmb, d.ctl)] : stkK[ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane];
                 else vp = vnext;
                 const double v = fma(ue.y, vp, ue.x);
                 if (kShared) {
                     const int mb_in = (int)((unsigned)f >> kMbInShift);
                     if (mb_in != kMbNone) mbv[ARB_IDX(mb_in, pk.nmb, d.ctl)] = v;
                 } else {
-                    for (int q = f & kFlagPopMask; q > 0; --q) stk[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = make_double2(v, 0.0);
+                    for (int q = f & kFlagPopMask; q > 0; --q) stkK[ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane] = v;
                 }
                 Vg[(size_t)j * kWarp + lane] = v;
                 if (last) bad |= !isfinite(v);

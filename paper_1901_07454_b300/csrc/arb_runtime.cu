@@ -1890,7 +1890,10 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
         }
         pl.stack_depth = max_depth;
         pl.stream_imp = ring_path;
-        pl.warp_smem = std::max<int64_t>((int64_t)max_depth * kWarp, ((int64_t)(ring_path ? 2 : 3) * max_mb + 1) / 2);
+        // per warp: the hand-over stack (row-ring path: three planes K, e, u of [depth][32]
+        // doubles; otherwise [depth][32] double2) or the mailbox of cells spread over lanes
+        const int64_t stack_d2 = ring_path ? ((int64_t)3 * max_depth * kWarp + 1) / 2 : (int64_t)max_depth * kWarp;
+        pl.warp_smem = std::max<int64_t>(stack_d2, ((int64_t)(ring_path ? 2 : 3) * max_mb + 1) / 2);
         pl.split_cvs = split;
         pl.smem_packs = 0;
         for (const SGroup& G : sg) pl.smem_packs += G.shared;
