@@ -180,3 +180,40 @@ def test_adjoint_ragged_trees_passive_dendrites_partial_groups():
     # no observations: zero loss, zero gradient
     l0, g0 = sim.adjoint(10, np.zeros(0, np.int64), np.zeros((10, 0)), 1.0, group, ng)
     assert l0 == 0.0 and not np.any(g0.cpu().numpy())
+
+
+def test_adjoint_long_cable_cut_into_several_chains():
+    # One unbranched 900-CV cable: along a chain the scaled pivots of the tree solve grow by
+    # about a factor 2 per CV here, so the host cuts the cable into four chains (about every
+    # 280-300 CVs) to keep them inside 2^{+-300}; each cut part hands its elimination to the
+    # next like a child chain. HH on the first 100 CVs, a current pulse at the root,
+    # observations along the cable, nine parameter groups of 100 CVs.
+    import paper_1901_07454_b300 as arb
+    from inputs.configs import uniform_cable_model
+    m = uniform_cable_model(900, 4500.0, 1.0)
+    m.hh_cv = np.arange(100)
+    m.gnabar, m.gkbar, m.gl = np.full(100, 0.12), np.full(100, 0.036), np.full(100, 3e-4)
+    m.pas_cv = np.arange(100, 900)
+    m.g_pas, m.e_pas = np.full(800, 1e-4), np.full(800, -65.0)
+    m.stim_cv = np.array([0])
+    m.stim_t_on, m.stim_dur, m.stim_amp = np.array([1.0]), np.array([2.0]), np.array([1.5])
+    m.branch_of_cv = (np.arange(900) // 100).astype(np.int32)
+    m.__post_init__()
+    spec = SimSpec(dt=0.025, t_end=12.0, epoch_steps=400)
+    K = spec.n_steps
+    obs = np.array([0, 50, 300, 600, 899])
+    rng = np.random.default_rng(11)
+    target = -65.0 + 30.0 * rng.random((K, obs.size))
+    group, ng = m.param_groups()
+    assert ng == 9
+    lo, go = oracle.OracleSim(m, spec.dt, 400).adjoint(K, obs, target, 1.0 / K, group, ng)
+    sim = arb.Simulation(m, dt=spec.dt)
+    lg, gg = sim.adjoint(K, obs, target, 1.0 / K, group, ng, checkpoint_every=64)
+    gg = gg.cpu().numpy()
+    errs = [float(np.max(np.abs(gg[:, p] - go[:, p])) / max(np.max(np.abs(go[:, p])), 1e-300)) for p in range(4)]
+    print("long cable: loss rel err %.2e, gradient rel errs %s" % (abs(lg - lo) / lo, ["%.1e" % e for e in errs]))
+    assert abs(lg - lo) <= 1e-10 * lo, (lg, lo)
+    # the passive groups have no HH: their gna/gk/gl gradients are zero on both sides
+    assert np.all(gg[1:, :3] == 0.0) and np.all(go[1:, :3] == 0.0)
+    for p in range(4):
+        assert errs[p] <= 1e-8, (p, errs[p])
