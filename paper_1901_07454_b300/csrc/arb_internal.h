@@ -295,7 +295,7 @@ struct AdjArgs {
     int32_t n_cells;
     int64_t n_cv, n_hh;
     const int64_t* off;        // [n_cells+1]
-    const int32_t* parent;     // [n_cv] cell-local parent, -1 at the root
+    const int32_t* parent;     // [n_cv] cell-local parent in the tree the solve uses (the cell re-rooted), -1 at its root
     const double* cdt;         // [n_cv] C / dt (nF/ms = uS)
     const double* sig;         // [n_cv] axial conductance to the parent (uS), 0 at the root
     const double* dsig;        // [n_cv] sum of the axial conductances of the CV (own + children)

@@ -2959,6 +2959,123 @@ struct AdjLayout {
     }
 };
 
+// The tree each adjoint block solves: a cell's CVs and axial conductances, rooted where the
+// level-by-level critical path of the chain solve (the sum over levels of the longest chain) is
+// shortest. A tridiagonal tree system can be eliminated toward any node, so the root is free:
+// the matrix is the same, only which end of an edge is the "parent" changes. Candidates are
+// the nodes in the middle 40% of the cell's longest path (up to kRootCandidates of them, the
+// centre first); each is scored by building its chains and levels.
+constexpr int kRootCandidates = 24;
+
+// Level-by-level critical path of the chain solve of a tree given by parent p (root r) and its
+// breadth-first order: chains are maximal runs of CVs with one child each, a chain's level is one
+// more than its highest child chain's.
+int32_t chain_critical_path(const std::vector<int32_t>& p, const std::vector<int32_t>& bfs) {
+    const int32_t n = (int32_t)p.size();
+    std::vector<int32_t> nch(n, 0), only(n, -1), chain_of(n, -1), len, lev, parent_chain;
+    for (int32_t i = 0; i < n; ++i)
+        if (p[i] >= 0) { nch[p[i]]++; only[p[i]] = i; }
+    for (int32_t h : bfs) {
+        if (p[h] >= 0 && nch[p[h]] == 1) continue;   // continues its parent's chain
+        const int32_t q = (int32_t)len.size();
+        int32_t x = h, l = 1;
+        chain_of[h] = q;
+        while (nch[x] == 1) { x = only[x]; chain_of[x] = q; ++l; }
+        len.push_back(l);
+        parent_chain.push_back(p[h] >= 0 ? chain_of[p[h]] : -1);
+    }
+    const int32_t nq = (int32_t)len.size();
+    lev.assign(nq, 0);
+    int32_t maxl = 0;
+    for (int32_t q = nq - 1; q >= 0; --q) {              // children after parents in bfs order
+        maxl = std::max(maxl, lev[q]);
+        if (parent_chain[q] >= 0) lev[parent_chain[q]] = std::max(lev[parent_chain[q]], lev[q] + 1);
+    }
+    std::vector<int32_t> longest(maxl + 1, 0);
+    for (int32_t q = 0; q < nq; ++q) longest[lev[q]] = std::max(longest[lev[q]], len[q]);
+    int32_t cp = 0;
+    for (int32_t v : longest) cp += v;
+    return cp;
+}
+
+// Re-roots a cell (model parents mp, cell-local) at r: solve parent sp, axial conductance to
+// it ss (from the model's per-child conductances sg; 0 at r) and the breadth-first order.
+void reroot_cell(const int32_t* mp, const double* sg, int32_t n, const std::vector<int32_t>& adj_ptr,
+                 const std::vector<int32_t>& adj, int32_t r, std::vector<int32_t>& sp, std::vector<double>* ss,
+                 std::vector<int32_t>& bfs) {
+    sp.assign(n, -2);
+    bfs.clear();
+    bfs.push_back(r);
+    sp[r] = -1;
+    for (size_t h = 0; h < bfs.size(); ++h) {
+        const int32_t v = bfs[h];
+        for (int32_t e = adj_ptr[v]; e < adj_ptr[v + 1]; ++e) {
+            const int32_t u = adj[e];
+            if (sp[u] != -2) continue;
+            sp[u] = v;
+            bfs.push_back(u);
+        }
+    }
+    if (ss) {
+        ss->assign(n, 0.0);
+        for (int32_t i = 0; i < n; ++i) {
+            if (sp[i] < 0) continue;
+            (*ss)[i] = mp[i] == sp[i] ? sg[i] : sg[sp[i]];   // the edge's conductance, stored at its model child
+        }
+    }
+}
+
+// Solve trees of all cells (model order, cell-local indices): parents, conductances to them, and
+// each cell's breadth-first order. Cells are independent: chosen in parallel.
+void solve_trees(const arb_sim* sim, const double* sigma, std::vector<int32_t>& SP, std::vector<double>& SS,
+                 std::vector<int32_t>& SB) {
+    const int32_t nc = sim->n_cells;
+    const int64_t ncv = sim->n_cv;
+    SP.assign(ncv, -1);
+    SS.assign(ncv, 0.0);
+    SB.assign(ncv, 0);
+    // scoring every candidate costs O(candidates x CVs); large models score fewer
+    const int cand = ncv * (int64_t)kRootCandidates <= (int64_t)400000000 ? kRootCandidates : 1;
+    parallel_for(nc, [&](int64_t c) {
+        const int64_t off = sim->cv_offset[c];
+        const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
+        const int32_t* mp = sim->parent.data() + off;
+        std::vector<int32_t> deg(n + 1, 0), adj_ptr(n + 1, 0), adj(n > 0 ? 2 * (n - 1) : 0);
+        for (int32_t i = 1; i < n; ++i) { deg[i]++; deg[mp[i]]++; }
+        for (int32_t i = 0; i < n; ++i) adj_ptr[i + 1] = adj_ptr[i] + deg[i];
+        std::vector<int32_t> fill(adj_ptr.begin(), adj_ptr.end() - 1);
+        for (int32_t i = 1; i < n; ++i) { adj[fill[i]++] = mp[i]; adj[fill[mp[i]]++] = i; }
+        // the longest path: the farthest node from CV 0, then the farthest from that one
+        std::vector<int32_t> sp, bfs;
+        reroot_cell(mp, nullptr, n, adj_ptr, adj, 0, sp, nullptr, bfs);
+        const int32_t a = bfs.back();
+        reroot_cell(mp, nullptr, n, adj_ptr, adj, a, sp, nullptr, bfs);
+        std::vector<int32_t> path{bfs.back()};
+        while (sp[path.back()] >= 0) path.push_back(sp[path.back()]);
+        const int32_t L = (int32_t)path.size();
+        std::vector<int32_t> cands{path[L / 2]};
+        if (cand > 1) {
+            const int32_t lo = (int32_t)(0.3 * (L - 1)), hi = (int32_t)(0.7 * (L - 1));
+            const int32_t span = hi - lo + 1, step = std::max<int32_t>(1, (span + cand - 2) / (cand - 1));
+            for (int32_t k = lo; k <= hi; k += step)
+                if (path[k] != cands[0]) cands.push_back(path[k]);
+        }
+        int32_t best = cands[0], best_cp = INT32_MAX;
+        for (int32_t r : cands) {
+            reroot_cell(mp, nullptr, n, adj_ptr, adj, r, sp, nullptr, bfs);
+            const int32_t cp = chain_critical_path(sp, bfs);
+            if (cp < best_cp) { best_cp = cp; best = r; }
+        }
+        std::vector<double> ss;
+        reroot_cell(mp, sigma + off, n, adj_ptr, adj, best, sp, &ss, bfs);
+        for (int32_t i = 0; i < n; ++i) {
+            SP[off + i] = sp[i];
+            SS[off + i] = ss[i];
+            SB[off + i] = bfs[i];
+        }
+    });
+}
+
 // Tree-solve schedule of the adjoint kernels: per cell, its unbranched chains (runs of CVs
 // with one child each, head nearest the root) ordered by level, and the constants of the
 // scaled chain recurrence (arb_adjoint.cu). Along a chain, from its tail (k = 0), with s_k the
@@ -2973,6 +3090,7 @@ struct AdjLayout {
 struct ChainPlan {
     std::vector<int64_t> ch_ptr, lev_off, lev_bound, ch_cv_ptr, ch_kid_ptr, ch_kids;
     std::vector<int32_t> ch_cvs, prev;
+    std::vector<int32_t> spar;                     // per CV: its parent in the solve tree (cell-local)
     std::vector<double> rho, beta, gcf, srf, kpw;
     int32_t max_cv = 0, max_ch = 0;
 };
@@ -2992,19 +3110,25 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
     P.gcf.assign(ncv, 1.0);
     P.srf.assign(ncv, 0.0);
     P.prev.assign(ncv, -1);
+    std::vector<int32_t> SB;
+    std::vector<double> SS;
+    solve_trees(sim, sigma, P.spar, SS, SB);
     for (int32_t c = 0; c < nc; ++c) {
         const int64_t off = sim->cv_offset[c];
         const int32_t n = (int32_t)(sim->cv_offset[c + 1] - off);
-        const int32_t* par = sim->parent.data() + off;
+        const int32_t* par = P.spar.data() + off;          // the solve tree
+        const double* ssig = SS.data() + off;              // axial conductance to the solve parent
         std::vector<int32_t> nch(n, 0), only(n, -1);
-        for (int32_t i = 1; i < n; ++i) { nch[par[i]]++; only[par[i]] = i; }
-        // chains in ascending head order (a parent chain's head precedes its children's); a
+        for (int32_t i = 0; i < n; ++i)
+            if (par[i] >= 0) { nch[par[i]]++; only[par[i]] = i; }
+        // chains in breadth-first head order (a parent chain's head precedes its children's); a
         // run that is cut contributes its parts from the top down, so that this still holds
         std::vector<std::vector<int32_t>> cvs;     // head first
         std::vector<std::array<double, 2>> kq;     // per chain: s_h^2 rho_h, s_h / gam_h
         std::vector<int32_t> chain_of_tail(n, -1), parent_chain;
-        for (int32_t h = 0; h < n; ++h) {
-            if (h != 0 && nch[par[h]] == 1) continue;   // continues its parent's chain
+        for (int32_t bi = 0; bi < n; ++bi) {
+            const int32_t h = SB[off + bi];
+            if (par[h] >= 0 && nch[par[h]] == 1) continue;   // continues its parent's chain
             std::vector<int32_t> t{h};                   // the run, head first
             for (int32_t x = h; nch[x] == 1;) { x = only[x]; t.push_back(x); }
             std::reverse(t.begin(), t.end());            // tail first
@@ -3018,7 +3142,7 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
                 long double r2 = rho, g2 = gam, lo2 = lo, hi2 = hi;
                 if (!cut) {
                     const int64_t y = off + t[i];
-                    const long double s_y = par[t[i]] >= 0 ? (long double)sigma[y] : 0.0L;
+                    const long double s_y = par[t[i]] >= 0 ? (long double)ssig[t[i]] : 0.0L;
                     const long double dlo = s_y + (long double)cdt[y], dhi = (long double)dmax[y];
                     if (i == b) {
                         r2 = 1.0L;
@@ -3026,7 +3150,7 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
                         lo2 = std::log2(dlo);
                         hi2 = std::log2(dhi);
                     } else {
-                        const long double s = (long double)sigma[off + t[i - 1]];
+                        const long double s = (long double)ssig[t[i - 1]];
                         r2 = 1.0L / (s * s * rho);
                         g2 = s * gam * rho;
                         lo2 = lo + std::log2(dlo * r2);
@@ -3040,8 +3164,7 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
                 }
                 if (cut) {
                     // the part [b, i): its head t[i-1] has the constants rho, gam
-                    const int64_t hg = off + t[i - 1];
-                    const long double sh = par[t[i - 1]] >= 0 ? (long double)sigma[hg] : 0.0L;
+                    const long double sh = par[t[i - 1]] >= 0 ? (long double)ssig[t[i - 1]] : 0.0L;
                     parts.push_back({b, i});
                     kparts.push_back({(double)(sh * sh * rho), (double)(sh / gam)});
                     if (i == (int32_t)t.size()) break;
@@ -3056,7 +3179,7 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
                 lo = lo2;
                 hi = hi2;
                 const int64_t y = off + t[i];
-                const long double s_y = par[t[i]] >= 0 ? (long double)sigma[y] : 0.0L;
+                const long double s_y = par[t[i]] >= 0 ? (long double)ssig[t[i]] : 0.0L;
                 P.rho[y] = (double)rho;
                 P.beta[y] = (double)(rho * gam);
                 P.gcf[y] = (double)(1.0L / gam);
@@ -3270,7 +3393,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         CU(cudaMemcpyAsync(L.at(base, name), src, bytes, cudaMemcpyHostToDevice, sim->s));
         return ARB_OK;
     };
-    if ((st = up("off", sim->cv_offset.data(), 8 * (nc + 1))) != ARB_OK || (st = up("parent", sim->parent.data(), 4 * ncv)) != ARB_OK ||
+    if ((st = up("off", sim->cv_offset.data(), 8 * (nc + 1))) != ARB_OK || (st = up("parent", CP.spar.data(), 4 * ncv)) != ARB_OK ||
         (st = up("cdt", cdt.data(), 8 * ncv)) != ARB_OK || (st = up("sig", sigma.data(), 8 * ncv)) != ARB_OK ||
         (st = up("dsig", dsig.data(), 8 * ncv)) != ARB_OK || (st = up("glin", glin.data(), 8 * ncv)) != ARB_OK ||
         (st = up("gelin", gelin.data(), 8 * ncv)) != ARB_OK || (st = up("area", area.data(), 8 * ncv)) != ARB_OK ||
