@@ -72,6 +72,7 @@ struct Smem {
     double* A2;    // [2 smem_cv] per CV: d rho (even), b beta (odd); then (u, e) of the back substitution
     double* PW;    // [2 smem_cv] per CV: P^ (even), W^ (odd)
     double* X;     // [smem_cv] solution (in PW's space, which the back substitution no longer needs)
+    double* Bb;    // [smem_cv] factors b of split chains' lower parts (the rest of PW's space)
     double* GA;    // [4 smem_cv] reverse sweep: the gradient sums of the cell's CVs during a launch
     double* cdt;   // [smem_cv] C / dt
     double* dsig;  // [smem_cv] sum of the CV's axial conductances (own + children)
@@ -91,6 +92,9 @@ struct Smem {
     int32_t* kidp; // [smem_ch + 1] cell-local chain -> range in kids
     int32_t* kids; // [smem_ch] cell-local child chains
     int32_t* levb; // [smem_ch + 2] first cell-local chain of each level, then the end
+    int32_t* fixa; // [smem_cv] anchor whose value a lower-part CV still needs, -1 none
+    int32_t* tkb;  // [smem_ch + 2] first back-substitution task of each level, then the end
+    int32_t* tk;   // [smem_tk][4] tasks: start, end (positions in cvs), kind, anchor CV
 };
 
 __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
@@ -100,6 +104,7 @@ __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
     m.A2 = adj_smem;
     m.PW = m.A2 + 2 * ncv;
     m.X = m.PW;
+    m.Bb = m.PW + ncv;
     m.GA = m.PW + 2 * ncv;
     m.cdt = m.GA + 4 * ncv;
     m.dsig = m.cdt + ncv;
@@ -119,6 +124,9 @@ __device__ __forceinline__ Smem smem_of(const AdjArgs& a) {
     m.kidp = m.chp + nch + 1;
     m.kids = m.kidp + nch + 1;
     m.levb = m.kids + nch;
+    m.fixa = m.levb + nch + 2;
+    m.tkb = m.fixa + ncv;
+    m.tk = m.tkb + nch + 2;
     return m;
 }
 
@@ -141,6 +149,7 @@ __device__ void load_cell(const AdjArgs& a, int c, const Smem& sm) {
         sm.par[i] = a.parent[off + i];
         sm.hidx[i] = a.hidx[off + i];
         sm.prev[i] = a.prev[off + i];
+        sm.fixa[i] = a.fixa[off + i];
         sm.cvs[i] = a.ch_cvs[cv0 + i];          // a cell's chains hold each of its CVs once
     }
     for (int64_t q = tid; q <= nq; q += kAdjThreads) {
@@ -152,7 +161,12 @@ __device__ void load_cell(const AdjArgs& a, int c, const Smem& sm) {
         sm.KPW[2 * q + 1] = a.kpw[2 * (q0 + q) + 1];
     }
     for (int64_t k = tid; k < a.ch_kid_ptr[q0 + nq] - k0; k += kAdjThreads) sm.kids[k] = (int32_t)(a.ch_kids[k0 + k] - q0);
-    for (int64_t L = tid; L < nlb; L += kAdjThreads) sm.levb[L] = (int32_t)(a.lev_bound[l0 + L] - q0);
+    for (int64_t L = tid; L < nlb; L += kAdjThreads) {
+        sm.levb[L] = (int32_t)(a.lev_bound[l0 + L] - q0);
+        sm.tkb[L] = a.tkb[l0 + L];
+    }
+    const int64_t t0 = a.tk_ptr[c], nt = a.tk_ptr[c + 1] - t0;
+    for (int64_t t = tid; t < 4 * nt; t += kAdjThreads) sm.tk[t] = a.tk[4 * t0 + t];
     __syncthreads();
 }
 
@@ -266,30 +280,42 @@ __device__ void tree_coefficients(int n, const Smem& sm) {
     }
 }
 
-// Back substitution (first warp): levels in reverse order, each chain from its head (using its
-// parent's solution; e = 0 at the root) to its tail, one lane per chain, one multiply-add per CV,
-// written as the elimination's loops are (no select on the dependent path, operands two CVs
-// ahead from always-valid indices, each value stored after the next multiply-add). Result in sm.X.
+// Back substitution (first warp): levels in reverse order, V_k = u_k + e_k V_parent along each
+// chain from its head (V_parent from the parent chain; e = 0 at the root), one multiply-add per
+// CV, one lane per task. In a level with few chains the host split each longer chain in two:
+// one lane takes the upper part as usual, and two lanes take the lower part at once, one
+// forming the offsets a_k (the same recurrence from V_anchor = 0) into sm.X, the other the
+// factors b_k (u masked to 0, from 1) into sm.Bb, so that V_k = a_k + b_k V_anchor with the
+// anchor the upper part's last CV. The three run the same instructions. A lower part's tail is
+// fixed at the end of the level (child chains hang from tails); its other CVs are fixed where the
+// solution is read (sm.fixa). Operands come two CVs ahead from always-valid indices and each
+// value is stored after the next multiply-add, so no integer instruction sits between them.
 __device__ void tree_substitute(const AdjArgs& a, int c, int lane, const Smem& sm) {
     const int nl = (int)(a.lev_off[c + 1] - a.lev_off[c]) - 1;
     for (int L = nl - 1; L >= 0; --L) {
-        for (int q = sm.levb[L] + lane; q < sm.levb[L + 1]; q += 32) {
-            const int cs = sm.chp[q], ce = sm.chp[q + 1];
+        for (int t = sm.tkb[L] + lane; t < sm.tkb[L + 1]; t += 32) {
+            const int cs = sm.tk[4 * t], ce = sm.tk[4 * t + 1], kind = sm.tk[4 * t + 2];
             auto cv_at = [&](int i) -> int { return sm.cvs[i < ce ? i : ce - 1]; };
             const int x0 = sm.cvs[cs];
             const int32_t p = sm.par[x0];
-            double vp = sm.X[p >= 0 ? p : 0];    // e = 0 at the root, so any finite value serves
-            if (p < 0) vp = 0.0;
+            double vp = kind == 2 ? 1.0 : 0.0;
+            if (kind == 0 && p >= 0) vp = sm.X[p];          // e = 0 at the root
+            const int umask = kind == 2 ? 0 : -1;             // the factors' recurrence has u = 0
+            double* out = kind == 2 ? sm.Bb : sm.X;
+            auto u_at = [&](int x) -> double {
+                const double u = sm.A2[2 * x];
+                return __hiloint2double(__double2hiint(u) & umask, __double2loint(u) & umask);
+            };
             int xa = x0, xb = cv_at(cs + 1), ya = cv_at(cs + 2), yb = cv_at(cs + 3);
-            double ua = sm.A2[2 * xa], ea = sm.A2[2 * xa + 1];
-            double ub = sm.A2[2 * xb], eb = sm.A2[2 * xb + 1];
+            double ua = u_at(xa), ea = sm.A2[2 * xa + 1];
+            double ub = u_at(xb), eb = sm.A2[2 * xb + 1];
             int ks = -1;                          // CV of the value waiting to be stored
 #define ARB_SUBST_STEP(I, XV, YV, U, E)                                                          \
     {                                                                                            \
         const double v_ = fma(E, vp, U);                                                         \
-        if (ks >= 0) sm.X[ks] = vp;                                                              \
+        if (ks >= 0) out[ks] = vp;                                                               \
         ks = XV;                                                                                 \
-        U = sm.A2[2 * YV];                                                                       \
+        U = u_at(YV);                                                                            \
         E = sm.A2[2 * YV + 1];                                                                   \
         XV = YV;                                                                                 \
         YV = cv_at((I) + 4);                                                                     \
@@ -302,10 +328,22 @@ __device__ void tree_substitute(const AdjArgs& a, int c, int lane, const Smem& s
             }
             if (i < ce) ARB_SUBST_STEP(i, xa, ya, ua, ea)
 #undef ARB_SUBST_STEP
-            sm.X[ks] = vp;
+            out[ks] = vp;
         }
         __syncwarp();
+        for (int t = sm.tkb[L] + lane; t < sm.tkb[L + 1]; t += 32)
+            if (sm.tk[4 * t + 2] == 1) {                      // a lower part's tail: V = a + b V_anchor
+                const int x = sm.cvs[sm.tk[4 * t + 1] - 1];
+                sm.X[x] = fma(sm.Bb[x], sm.X[sm.tk[4 * t + 3]], sm.X[x]);
+            }
+        __syncwarp();
     }
+}
+
+// The solution at cell-local CV li, with a split chain's lower part completed.
+__device__ __forceinline__ double solution(const Smem& sm, int li) {
+    const int an = sm.fixa[li];
+    return an >= 0 ? fma(sm.Bb[li], sm.X[an], sm.X[li]) : sm.X[li];
 }
 
 // mode 0: steps [s0, s1) from the running state (a.V, a.Y), in place, with a checkpoint
@@ -383,7 +421,7 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         __syncthreads();
         // new voltage, gates with it, loss
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
-            const double v = sm.X[i - off];
+            const double v = solution(sm, (int)(i - off));
             Vd[i] = v;
             const int32_t j = sm.hidx[i - off];
             if (j >= 0) {
@@ -508,7 +546,7 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         // the gate adjoints take d(G V - GE)/dgate from the same terms. Per-CV factors come from
         // the host (kcm = area 1e-5 / dt, ksc = area 1e-2), so no division is left here.
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
-            const double lam = sm.X[i - off];
+            const double lam = solution(sm, (int)(i - off));
             a.lam[i] = lam;
             const double v1 = V1[i];
             double* ga = sm.GA + 4 * (i - off);
@@ -571,7 +609,7 @@ __global__ void k_adj_reduce(AdjArgs a) {
 
 }  // namespace
 
-size_t adj_smem_bytes(const AdjArgs& a) { return adj_smem_bytes_for(a.smem_cv, a.smem_ch); }
+size_t adj_smem_bytes(const AdjArgs& a) { return adj_smem_bytes_for(a.smem_cv, a.smem_ch, a.smem_tk); }
 
 cudaError_t adj_prepare(const AdjArgs& a) {
     const int bytes = (int)adj_smem_bytes(a);

@@ -353,6 +353,13 @@ struct AdjArgs {
     const double* srf;         // [n_cv] s_k rho_k (0 at the root)
     const int32_t* prev;       // [n_cv] cell-local CV before this one in its chain, -1 at a tail
     const double* kpw;         // [n_chains][2] s_h^2 rho_h, s_h g_h / c_h of the chain's head h
+    // back-substitution tasks: [start, end) positions in the cell's chain list, kind (0 a chain or
+    // its upper part, 1 a lower part's offsets, 2 its factors), anchor CV (cell-local)
+    const int32_t* tk;         // [tasks][4]
+    const int64_t* tk_ptr;     // [n_cells+1] first task of each cell
+    const int32_t* tkb;        // per cell (laid out as lev_bound): cell-local first task of each level, then the end
+    const int32_t* fixa;       // [n_cv] cell-local anchor whose value a lower-part CV still needs, -1 none
+    int32_t smem_tk;           // largest task count of a cell
     int32_t smem_cv;           // shared-memory slots per cell (largest cell)
     int32_t smem_ch;           // largest chain count of a cell
     const int64_t* grp_ptr;    // [n_groups+1] CVs of each parameter group, ascending
@@ -361,10 +368,11 @@ struct AdjArgs {
     double* grad;              // [n_groups][4] output
 };
 
-// Dynamic shared memory of one adjoint block: per CV 16 doubles and 4 int32, per chain 4
-// doubles and 4 int32, and 4 int32 of level bounds.
-inline size_t adj_smem_bytes_for(int64_t cvs, int64_t chains) {
-    return 8 * (16 * (size_t)cvs + 4 * (size_t)chains) + 4 * (4 * (size_t)cvs + 4 * (size_t)chains + 4);
+// Dynamic shared memory of one adjoint block: per CV 16 doubles and 5 int32, per chain 4
+// doubles and 5 int32 (with the level bounds of the tasks), per back-substitution task 4 int32,
+// and 8 int32 more of level bounds.
+inline size_t adj_smem_bytes_for(int64_t cvs, int64_t chains, int64_t tasks) {
+    return 8 * (16 * (size_t)cvs + 4 * (size_t)chains) + 4 * (5 * (size_t)cvs + 5 * (size_t)chains + 4 * (size_t)tasks + 8);
 }
 
 #ifdef ARB_DEBUG

@@ -3091,6 +3091,12 @@ struct ChainPlan {
     std::vector<int64_t> ch_ptr, lev_off, lev_bound, ch_cv_ptr, ch_kid_ptr, ch_kids;
     std::vector<int32_t> ch_cvs, prev;
     std::vector<int32_t> spar;                     // per CV: its parent in the solve tree (cell-local)
+    // back-substitution tasks: per cell, [start, end) positions in the cell's chain list, kind
+    // (0 a chain or its upper part, 1 a lower part's offsets a, 2 its factors b) and the anchor
+    // CV (the upper part's last); per level of lev_bound, the cell-local first task
+    std::vector<int32_t> tk, tkb, fixa;           // fixa: per CV, the anchor its value still needs, -1 none
+    std::vector<int64_t> tk_ptr;
+    int32_t max_tk = 0;
     std::vector<double> rho, beta, gcf, srf, kpw;
     int32_t max_cv = 0, max_ch = 0;
 };
@@ -3110,6 +3116,8 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
     P.gcf.assign(ncv, 1.0);
     P.srf.assign(ncv, 0.0);
     P.prev.assign(ncv, -1);
+    P.fixa.assign(ncv, -1);
+    P.tk_ptr.assign(nc + 1, 0);
     std::vector<int32_t> SB;
     std::vector<double> SS;
     solve_trees(sim, sigma, P.spar, SS, SB);
@@ -3230,6 +3238,36 @@ ChainPlan chain_plan(const arb_sim* sim, const double* sigma, const double* cdt,
         P.ch_ptr[c + 1] = q0 + nq;
         P.max_cv = std::max(P.max_cv, n);
         P.max_ch = std::max(P.max_ch, nq);
+        // back-substitution tasks, level by level: in a level of at most kSplitLevel chains, each
+        // chain of at least 8 CVs is split in two; its lower part runs on two more lanes (the
+        // offsets a with V_anchor = 0, the factors b = prod e), so the level takes half as long
+        {
+            constexpr int32_t kSplitLevel = 10;
+            const int64_t cv0 = P.ch_cv_ptr[q0];
+            const int32_t tk0 = (int32_t)(P.tk.size() / 4);
+            for (int32_t L = 0; L <= maxl; ++L) {
+                P.tkb.push_back((int32_t)(P.tk.size() / 4) - tk0);
+                const int64_t lb = P.lev_bound[P.lev_off[c] + L], le = P.lev_bound[P.lev_off[c] + L + 1];
+                const bool split = le - lb <= kSplitLevel;
+                for (int64_t gq = lb; gq < le; ++gq) {
+                    const int32_t cs = (int32_t)(P.ch_cv_ptr[gq] - cv0), ce = (int32_t)(P.ch_cv_ptr[gq + 1] - cv0);
+                    const int32_t len = ce - cs;
+                    if (!split || len < 8) {
+                        for (int32_t v : {cs, ce, 0, -1}) P.tk.push_back(v);
+                        continue;
+                    }
+                    const int32_t m = cs + (len + 1) / 2;
+                    const int32_t anchor = P.ch_cvs[cv0 + m - 1];
+                    for (int32_t v : {cs, m, 0, -1}) P.tk.push_back(v);
+                    for (int32_t v : {m, ce, 1, anchor}) P.tk.push_back(v);
+                    for (int32_t v : {m, ce, 2, anchor}) P.tk.push_back(v);
+                    for (int32_t i = m; i < ce - 1; ++i) P.fixa[off + P.ch_cvs[cv0 + i]] = anchor;   // the tail is fixed in the solve
+                }
+            }
+            P.tkb.push_back((int32_t)(P.tk.size() / 4) - tk0);   // the end: as many entries as lev_bound
+            P.tk_ptr[c + 1] = (int64_t)(P.tk.size() / 4);
+            P.max_tk = std::max<int32_t>(P.max_tk, (int32_t)(P.tk.size() / 4) - tk0);
+        }
     }
     P.lev_off[nc] = (int64_t)P.lev_bound.size();
     return P;
@@ -3272,6 +3310,10 @@ AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t 
     for (const char* n : {"rho", "beta", "gcf", "srf"}) L.add(n, 8 * ncv);
     L.add("prev", 4 * ncv);
     L.add("kpw", 16 * ncv);                  // at most one chain per CV
+    L.add("tk", 48 * ncv);                   // at most three back-substitution tasks per chain
+    L.add("tk_ptr", 8 * (nc + 1));
+    L.add("tkb", 4 * (ncv + nc));
+    L.add("fixa", 4 * ncv);
     return L;
 }
 
@@ -3383,7 +3425,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     for (int64_t i = 0; i < ncv; ++i) dmax[i] = cdt[i] + dsig[i] + glin[i];
     for (int64_t j = 0; j < nhh; ++j) dmax[sim->hh_cv[j]] += gna[j] + gk[j] + gl[j];
     const ChainPlan CP = chain_plan(sim, sigma.data(), cdt.data(), dmax.data());
-    if (adj_smem_bytes_for(CP.max_cv, CP.max_ch) > (size_t)200 * 1024)
+    if (adj_smem_bytes_for(CP.max_cv, CP.max_ch, CP.max_tk) > (size_t)200 * 1024)
         return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to about 1,000 to 1,400 CVs, by chain count)");
     arb_status st = sync_in(sim);
     if (st != ARB_OK) return st;
@@ -3415,7 +3457,9 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         (st = up("ch_kids", CP.ch_kids.data(), 8 * CP.ch_kids.size())) != ARB_OK ||
         (st = up("rho", CP.rho.data(), 8 * ncv)) != ARB_OK || (st = up("beta", CP.beta.data(), 8 * ncv)) != ARB_OK ||
         (st = up("gcf", CP.gcf.data(), 8 * ncv)) != ARB_OK || (st = up("srf", CP.srf.data(), 8 * ncv)) != ARB_OK ||
-        (st = up("prev", CP.prev.data(), 4 * ncv)) != ARB_OK || (st = up("kpw", CP.kpw.data(), 8 * CP.kpw.size())) != ARB_OK)
+        (st = up("prev", CP.prev.data(), 4 * ncv)) != ARB_OK || (st = up("kpw", CP.kpw.data(), 8 * CP.kpw.size())) != ARB_OK ||
+        (st = up("tk", CP.tk.data(), 4 * CP.tk.size())) != ARB_OK || (st = up("tk_ptr", CP.tk_ptr.data(), 8 * CP.tk_ptr.size())) != ARB_OK ||
+        (st = up("tkb", CP.tkb.data(), 4 * CP.tkb.size())) != ARB_OK || (st = up("fixa", CP.fixa.data(), 4 * ncv)) != ARB_OK)
         return st;
     AdjArgs a{};
     a.n_cells = (int32_t)nc;
@@ -3478,8 +3522,13 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.srf = (const double*)L.at(base, "srf");
     a.prev = (const int32_t*)L.at(base, "prev");
     a.kpw = (const double*)L.at(base, "kpw");
+    a.tk = (const int32_t*)L.at(base, "tk");
+    a.tk_ptr = (const int64_t*)L.at(base, "tk_ptr");
+    a.tkb = (const int32_t*)L.at(base, "tkb");
+    a.fixa = (const int32_t*)L.at(base, "fixa");
     a.smem_cv = std::max<int32_t>(CP.max_cv, 1);
     a.smem_ch = std::max<int32_t>(CP.max_ch, 1);
+    a.smem_tk = std::max<int32_t>(CP.max_tk, 1);
     CU(adj_prepare(a));
     a.grp_ptr = (const int64_t*)L.at(base, "grp_ptr");
     a.grp_cv = (const int64_t*)L.at(base, "grp_cv");
