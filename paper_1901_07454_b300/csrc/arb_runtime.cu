@@ -13,6 +13,7 @@
 #include <atomic>
 #include <array>
 #include <functional>
+#include <memory>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -205,6 +206,8 @@ struct arb_sim {
     char* ws = nullptr;
     int64_t ws_bytes = 0;
     std::vector<std::pair<std::string, Region>> regions;
+    std::shared_ptr<void> adj_plan;         // the adjoint's solve schedule (ChainPlan), built on first use:
+                                            // it depends only on the model and dt, fixed for the handle
     int n_sm = 148;
     int variant = 0;                // compiled variant of the streamed kernel (row-ring path)
     int warps_per_cta = 2;
@@ -3424,7 +3427,8 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     std::vector<double> dmax(ncv);
     for (int64_t i = 0; i < ncv; ++i) dmax[i] = cdt[i] + dsig[i] + glin[i];
     for (int64_t j = 0; j < nhh; ++j) dmax[sim->hh_cv[j]] += gna[j] + gk[j] + gl[j];
-    const ChainPlan CP = chain_plan(sim, sigma.data(), cdt.data(), dmax.data());
+    if (!sim->adj_plan) sim->adj_plan = std::make_shared<ChainPlan>(chain_plan(sim, sigma.data(), cdt.data(), dmax.data()));
+    const ChainPlan& CP = *static_cast<const ChainPlan*>(sim->adj_plan.get());
     if (adj_smem_bytes_for(CP.max_cv, CP.max_ch, CP.max_tk) > (size_t)200 * 1024)
         return fail(sim, ARB_E_ARG, "the adjoint needs every cell's solve and constants in shared memory (cells up to about 1,000 to 1,400 CVs, by chain count)");
     arb_status st = sync_in(sim);
