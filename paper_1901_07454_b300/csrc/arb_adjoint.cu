@@ -29,13 +29,15 @@
 // Scaled by per-CV constants (P^_k = P_k / c_k, W^_k = W_k / g_k with c_k = s_{k-1}^2 c_{k-2},
 // g_k = s_{k-1} g_{k-1}) each step is one fused multiply-add:
 //   P^_k = (d_k rho_k) P^_{k-1} - P^_{k-2},   W^_k = (b_k beta_k) P^_{k-1} + W^_{k-1},
-// rho_k = c_{k-1} / c_k, beta_k = c_{k-1} / g_k. Two lanes take one chain: the even lane carries
-// P^, the odd lane W^ one CV behind, in the same instruction. No division is on that path. The
-// chain's elimination into its parent (-s_h^2 / D_h and s_h B_h / D_h at its head h) takes one
-// reciprocal per chain. Then every thread forms, per CV, u_k = B_k / D_k and e_k = s_k / D_k
-// (one reciprocal each, in parallel), and the back substitution, V_k = u_k + e_k V_parent, is
-// one fused multiply-add per CV. The host computes the constants and cuts a chain wherever
-// their range, or the range P^ can reach, would leave about 2^{+-300}.
+// rho_k = c_{k-1} / c_k, beta_k = c_{k-1} / g_k. Warp 0 runs the P^ recurrences of a level while
+// warp 1 runs the W^ recurrences of the level before, one lane per chain. No division is on that
+// path. The chain's elimination into its parent (-s_h^2 / D_h and s_h B_h / D_h at its head h)
+// takes one reciprocal per chain. Then every thread forms, per CV, u_k = B_k / D_k and
+// e_k = s_k / D_k (one reciprocal each, in parallel), and the back substitution,
+// V_k = u_k + e_k V_parent, is one fused multiply-add per CV (long chains of small levels split
+// over three lanes). The host computes the constants, cuts a chain wherever their range, or the
+// range P^ can reach, would leave about 2^{+-300}, and roots each cell's tree where the
+// level-by-level critical path is shortest.
 #include <cuda_runtime.h>
 
 #include <cstdint>
