@@ -270,8 +270,11 @@ arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t*
  *   workspace: caller-owned device memory of arb_adjoint_workspace_bytes bytes, 256-byte
  *   aligned. It holds one state every checkpoint_every steps and every state of one segment
  *   of checkpoint_every steps, which the reverse sweep recomputes from its checkpoint.
- * Work is ordered on the handle's stream after the caller's stream; the call returns after
- * the loss has been copied back. */
+ * Each cell's tree solve runs in one block's shared memory: cells of more than about 1,000 to
+ * 1,400 CVs (depending on their number of unbranched chains) are refused with ARB_E_ARG. The
+ * handle keeps the solve schedule it builds on the first call (it depends only on the model
+ * and dt). Work is ordered on the handle's stream after the caller's stream; the call returns
+ * after the loss has been copied back; ARB_E_STATE if the handle has no bound workspace. */
 arb_status arb_adjoint_workspace_bytes(const arb_sim* sim, int64_t n_steps, int32_t checkpoint_every,
                                        int64_t n_obs, int32_t n_groups, int64_t* bytes);
 arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, int64_t n_obs,
