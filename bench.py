@@ -69,14 +69,14 @@ STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 119.4}
 
 # Discrete adjoint (every CV with HH, checkpoint every 500 steps): FP64 thread instructions per
 # gradient CV-step of the forward, recompute and reverse kernels together (ncu, 64 cells of the
-# fitting workload, profiles/adjoint_config4_256cells.md: 55.6 in k_adj_forward, 153.3 in
+# fitting workload, profiles/adjoint_config4_256cells.md: 56.3 in k_adj_forward, 156.6 in
 # k_adj_stage); the algorithmic DRAM bytes per gradient CV-step: the recompute writes V, the
 # three gates and, per HH CV, three dPhi/dV and three decay factors (80 B), which the reverse
 # sweep reads back (80 B) -- the running state, lambda, the gate adjoints and the gradient sums
-# stay in shared memory or L2; and the DRAM bytes the same capture measured (164.6 B).
-ADJ_FP64_PER_CV_STEP = 208.9
+# stay in shared memory or L2; and the DRAM bytes the same capture measured (164.5 B).
+ADJ_FP64_PER_CV_STEP = 212.9
 ADJ_BYTES_PER_CV_STEP = 160.0
-ADJ_DRAM_BYTES_PER_CV_STEP = 164.6
+ADJ_DRAM_BYTES_PER_CV_STEP = 164.5
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
