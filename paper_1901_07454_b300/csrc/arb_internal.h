@@ -34,6 +34,8 @@ struct PackDesc {
     int32_t nmb;         // streamed shared packs: mailbox slots (cross-lane hand-overs)
     int32_t nsc;         // streamed packs: compact slots [0, nsc) are the CVs with synapses,
                          // whose terms the synapse pass writes whole (no read-modify-write)
+    int32_t mb0;         // streamed shared packs: first of the pack's entries in mb_ent / mb_cs
+    int32_t pad_mb;
 };
 
 // Pack modes: staged in shared memory (small batches, several cells share a warp), or
@@ -223,6 +225,10 @@ struct DevModel {
     const int32_t* cpos;
     const int32_t* row_cs;
     const int32_t* row_cn;
+    // streamed shared packs on the row-ring path: per mailbox slot (pack after pack, from the
+    // pack's mb0) the parent's entry in its pack and that entry's compact slot (-1 none)
+    const int32_t* mb_ent;
+    const int32_t* mb_cs;
     // FP32 mechanisms: float copies of the per-synapse decay factor and reversal and of the HH
     // conductances (null otherwise)
     const float* syn_decay_f;

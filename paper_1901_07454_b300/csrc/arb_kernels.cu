@@ -1297,13 +1297,24 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
         // forward elimination, leaves to root
         {
             if (kShared) {
-                for (int i = lane; i < pk.nmb; i += kWarp) { mbd[i] = 0.0; mbb[i] = 0.0; }
+                // each slot starts from its parent's own diagonal and right-hand-side term; the
+                // children add their contributions, and the parent takes the sums in their place
+                const int32_t* me = d.mb_ent + pk.mb0;
+                const int32_t* mc = d.mb_cs + pk.mb0;
+                for (int i = lane; i < pk.nmb; i += kWarp) {
+                    const int t = ARB_IDX(__ldg(me + i), J * kWarp, d.ctl);
+                    const int c = __ldg(mc + i);
+                    const int cc = c < 0 ? -1 : ARB_IDX(c, pk.nvc, d.ctl);
+                    mbd[i] = cc >= 0 ? Gm[cc] : __ldg(ce_p + t);
+                    mbb[i] = cc >= 0 ? Em[cc] : __ldg(cb_p + t);
+                }
                 __syncwarp();
             }
             q_cur = -1;
 #pragma unroll
             for (int u = 0; u < kRF; ++u) issue_f(u);
             int sp = 0, left = R;
+            int acc = -1;   // cells over lanes: the slot the previous row's hand-over is still added to
             double yprev = 0.0, kprev = 0.0, eprev = 0.0;
             for (int j = 0; j < J; ++j) {
                 cp_async_wait<kRF - 1>();                // row j has landed (this lane's copies)
@@ -1312,8 +1323,8 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 const FwdRec x = r.rec[lane];
                 const int cp = x.cpos < 0 ? -1 : ARB_IDX(x.cpos, kWarp, d.ctl);
                 const double V = x.v, A = x.a, K = x.k;
-                const double E = cp >= 0 ? r.gm[cp] : x.e;
-                const double Bc = cp >= 0 ? r.em[cp] : x.b;
+                double E = cp >= 0 ? r.gm[cp] : x.e;
+                double Bc = cp >= 0 ? r.em[cp] : x.b;
                 const int f = x.f;
                 __syncwarp();                            // slot read by every lane before refilling it
                 issue_f(j + kRF);
@@ -1323,11 +1334,30 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 }
                 const int mb_in = kShared ? (int)((unsigned)f >> kMbInShift) : kMbNone;
                 const int mb_out = kShared ? ((f >> kMbOutShift) & kMbNone) : kMbNone;
-                double dd = fma(-kprev, eprev, E);
-                double bb = fma(kprev, yprev, fma(A, V, Bc));
+                double dd, bb;
                 if (kShared) {
-                    if (mb_in != kMbNone) { dd -= mbd[ARB_IDX(mb_in, pk.nmb, d.ctl)]; bb += mbb[ARB_IDX(mb_in, pk.nmb, d.ctl)]; }
+                    // A row after a hand-over has no child in registers: its two multiply-adds
+                    // add the previous row's (K e, K u) into that parent's slot instead, so a
+                    // hand-over costs no FP64 instruction of its own in either row.
+                    if (mb_in != kMbNone) {
+                        const int o = ARB_IDX(mb_in, pk.nmb, d.ctl);
+                        E = mbd[o];
+                        Bc = mbb[o];
+                    }
+                    const double bz = fma(A, V, Bc);
+                    const double zd = acc >= 0 ? mbd[acc] : E;
+                    const double zb = acc >= 0 ? mbb[acc] : bz;
+                    const double fd = fma(-kprev, eprev, zd);
+                    const double fb = fma(kprev, yprev, zb);
+                    if (acc >= 0) {
+                        mbd[acc] = fd;
+                        mbb[acc] = fb;
+                    }
+                    dd = acc >= 0 ? E : fd;
+                    bb = acc >= 0 ? bz : fb;
                 } else {
+                    dd = fma(-kprev, eprev, E);
+                    bb = fma(kprev, yprev, fma(A, V, Bc));
                     for (int q = f & kFlagPopMask; q > 0; --q) {
                         const int o = ARB_IDX(--sp, pk.stack, d.ctl) * kWarp + lane;
                         const double kc = stkK[o];
@@ -1340,19 +1370,18 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 const double ee = K * rr;
                 UE[(size_t)j * kWarp + lane] = make_double2(uu, ee);
                 const bool remote = (f & kFlagRemote) != 0;
-                if (remote && !(f & kFlagRoot)) {
-                    if (kShared) {
-                        const int o = ARB_IDX(mb_out, pk.nmb, d.ctl);
-                        mbd[o] = fma(K, ee, mbd[o]);
-                        mbb[o] = fma(K, uu, mbb[o]);
-                    } else {
+                if (kShared) {
+                    acc = (remote && !(f & kFlagRoot)) ? ARB_IDX(mb_out, pk.nmb, d.ctl) : -1;
+                    kprev = K;   // a root's (and padding's) coupling is 0
+                } else {
+                    if (remote && !(f & kFlagRoot)) {
                         const int o = ARB_IDX(sp++, pk.stack, d.ctl) * kWarp + lane;
                         stkK[o] = K;
                         stkE[o] = ee;
                         stkU[o] = uu;
                     }
+                    kprev = remote ? 0.0 : K;
                 }
-                kprev = remote ? 0.0 : K;
                 eprev = ee;
                 yprev = uu;
             }

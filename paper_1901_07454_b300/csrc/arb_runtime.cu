@@ -157,6 +157,8 @@ struct Plan {
     bool stream_imp = false;                // streamed packs on the row-ring path (implicit, step-start events)
     hvec<int32_t> cpos;                     // row-ring path: per entry, its position among its row's slots
     hvec<int32_t> row_cs, row_cn;           // row-ring path: per row, its compact slot ranges
+    std::vector<int32_t> mb_ent, mb_cs;     // per mailbox slot: its parent's entry in the pack, and
+                                            // that entry's compact mechanism slot (-1 none)
 };
 
 struct Region {
@@ -474,9 +476,12 @@ PackRows schedule_affinity(const std::vector<int32_t>& cells, const std::vector<
 // on another lane hands its contribution over through shared memory, so the parent must
 // start in a later round; at most one lane writes a given parent per round, which keeps the
 // accumulation order fixed. A lane that completes the last child of a chain may continue
-// straight into that chain (the contribution then stays in a register).
+// straight into that chain (the contribution then stays in a register). With shift = 1 the
+// contribution is written one row after the chain's head (the row-ring kernel adds it with the
+// multiply-adds of the lane's next row, which has no child in a register), so a head on the
+// last row of a round writes in the next round, and its parent waits one round more.
 PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<CellOrder>& ord,
-                         const std::vector<int64_t>& cv_offset, int R) {
+                         const std::vector<int64_t>& cv_offset, int R, int shift = 0) {
     struct Chain {
         int64_t base;        // global CV offset of the cell
         const CellOrder* o;
@@ -539,11 +544,15 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
     pos.fill(0);
     int32_t done = 0;
     int32_t round = 0;
+    std::vector<int32_t> newly_next, written_next;   // writes that land in the next round (shift)
+    int idle = 0;
     while (done < nchain) {
         const size_t r0 = pr.rows.size();
         for (int rr = 0; rr < R; ++rr) pr.rows.push_back(empty);
-        std::vector<int32_t> newly;
-        std::vector<int32_t> written;   // parent chains that received a remote contribution this round
+        std::vector<int32_t> newly = std::move(newly_next);     // parents ready after this round
+        std::vector<int32_t> written = std::move(written_next); // parents written in this round
+        newly_next.clear();
+        written_next.clear();
         int32_t progressed = 0;
         for (int l = 0; l < 32; ++l) {
             for (int rr = 0; rr < R; ++rr) {
@@ -556,14 +565,16 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
                 Chain& x = ch[cur[l]];
                 const int32_t len = x.tail - x.head + 1;
                 const bool head_row = pos[l] == len - 1;
+                const bool late = rr + shift >= R;   // a hand-over from this row is written next round
                 bool cont = false;
                 if (head_row && x.parent >= 0) {
                     Chain& P = ch[x.parent];
-                    // continuation: this is the last child and every sibling ended in an earlier round
+                    const std::vector<int32_t>& wl = late ? written_next : written;
+                    // continuation: this is the last child and every sibling's write is in an earlier round
                     if (P.pending == 1 && P.child_round < round) {
                         cont = true;
-                    } else if (std::find(written.begin(), written.end(), x.parent) != written.end()) {
-                        break;   // a sibling already writes this parent in this round: wait
+                    } else if (std::find(wl.begin(), wl.end(), x.parent) != wl.end()) {
+                        break;   // a sibling already writes this parent in that round: wait
                     }
                 }
                 pr.rows[r0 + rr][l] = x.base + x.o->dfs[x.tail - pos[l]];
@@ -576,13 +587,15 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
                     cur[l] = -1;
                     if (pidx >= 0) {
                         ch[pidx].pending--;
-                        ch[pidx].child_round = std::max(ch[pidx].child_round, round);
                         if (cont) {
+                            ch[pidx].child_round = std::max(ch[pidx].child_round, round);
                             cur[l] = pidx;
                             pos[l] = 0;
                         } else {
-                            written.push_back(pidx);
-                            if (ch[pidx].pending == 0) newly.push_back(pidx);
+                            ch[pidx].child_round = std::max(ch[pidx].child_round, late ? round + 1 : round);
+                            (late ? written_next : written).push_back(pidx);
+                            // ready once every child's write has landed
+                            if (ch[pidx].pending == 0) (ch[pidx].child_round > round ? newly_next : newly).push_back(pidx);
                         }
                     }
                 }
@@ -590,10 +603,11 @@ PackRows schedule_shared(const std::vector<int32_t>& cells, const std::vector<Ce
         }
         for (int32_t i : newly) ready.push(i);
         ++round;
-        if (progressed == 0 && done < nchain) {
-            // cannot happen: some chain is always ready or running
-            break;
-        }
+        // a round without progress happens only while a write of the round before blocks a
+        // lane; three in a row cannot happen (some chain is always ready, running or about to
+        // be ready)
+        idle = progressed == 0 ? idle + 1 : 0;
+        if (idle > 2 && done < nchain) break;
     }
     // trim trailing empty rows
     while (!pr.rows.empty()) {
@@ -630,6 +644,7 @@ static void layout_regions(arb_sim* sim) {
         {"Sg", 8 * std::max<int64_t>(pl.stream_imp ? 1 : pl.sg_total, 1)}, {"Rg", 8 * std::max<int64_t>(pl.stream_imp ? 1 : pl.sg_total, 1)},
         {"UE", 16 * std::max<int64_t>(pl.stream_imp ? ne : 1, 1)}, {"cpos", 4 * std::max<int64_t>((int64_t)pl.cpos.size(), 1)},
         {"row_cs", 4 * std::max<int64_t>((int64_t)pl.row_cs.size(), 1)}, {"row_cn", 4 * std::max<int64_t>((int64_t)pl.row_cn.size(), 1)},
+        {"mb_ent", 4 * std::max<int64_t>((int64_t)pl.mb_ent.size(), 1)}, {"mb_cs", 4 * std::max<int64_t>((int64_t)pl.mb_cs.size(), 1)},
         {"Gm", 8 * std::max<int64_t>(pl.c_total, 1)}, {"Em", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"cE", 8 * std::max<int64_t>(pl.c_total, 1)}, {"cB", 8 * std::max<int64_t>(pl.c_total, 1)},
         {"syn_slot", 4 * pl.syn_rows * kWarp}, {"syn_vs", 4 * pl.syn_rows * kWarp}, {"syn_g", mt * pl.syn_rows * kWarp},
@@ -751,6 +766,8 @@ static void fill_devmodel(arb_sim* sim, DevModel<MT>& d) {
     d.cpos = (const int32_t*)region(sim, "cpos");
     d.row_cs = (const int32_t*)region(sim, "row_cs");
     d.row_cn = (const int32_t*)region(sim, "row_cn");
+    d.mb_ent = (const int32_t*)region(sim, "mb_ent");
+    d.mb_cs = (const int32_t*)region(sim, "mb_cs");
     d.syn_slot = (const int32_t*)region(sim, "syn_slot");
     d.syn_vs = (const int32_t*)region(sim, "syn_vs");
     d.syn_g = (MT*)region(sim, "syn_g");
@@ -1418,7 +1435,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 G.cells = cs;
                 G.shared = true;
                 const bool fits = branch_points(cs) <= mb_max;
-                if (fits) G.rows = schedule_shared(cs, ord, sim->cv_offset, kStreamRound);
+                if (fits) G.rows = schedule_shared(cs, ord, sim->cv_offset, kStreamRound, ring_path ? 1 : 0);
                 if (cs.size() > 1 && (!fits || (double)G.rows.rows.size() > kSpreadOver * (double)target)) {
                     const size_t h = cs.size() / 2;
                     place_shared(std::vector<int32_t>(cs.begin(), cs.begin() + h), target, out);
@@ -1728,6 +1745,16 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             if (err[pi] == 1) return bad("a CV has more than 255 handed-over children");
             if (err[pi] == 2) return bad("internal error: mailbox overflow");
         }
+        // mailbox slots of all packs, numbered pack after pack (each slot's parent entry and
+        // compact mechanism slot are filled in below)
+        int64_t mb_total = 0;
+        for (int32_t pi = 0; pi < npk; ++pi) {
+            pl.packs[pi].mb0 = (int32_t)mb_total;
+            mb_total += sg[pi].shared ? nmb[pi] : 0;
+            if (mb_total > INT32_MAX) return bad("model too large for one handle");
+        }
+        pl.mb_ent.assign((size_t)std::max<int64_t>(mb_total, 1), 0);
+        pl.mb_cs.assign((size_t)std::max<int64_t>(mb_total, 1), -1);
         // compact mechanism slots; stack depths (one cell per lane) and the round rule of the
         // mailbox (cells over several lanes)
         std::vector<char> mech(ncv, 0);
@@ -1773,8 +1800,10 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             p_nvc[pi] = nvc;
             if (sg[pi].shared) {
                 pd.nmb = nmb[pi];
-                // a hand-over between lanes crosses a round boundary (both sweeps), and within a
-                // round at most one lane adds to a given slot
+                // a hand-over between lanes is written (on the row-ring path: one row after the
+                // child, see schedule_shared) in an earlier round than the parent reads it, and
+                // within a round at most one lane adds to a given slot
+                const int32_t wsh = ring_path ? 1 : 0;
                 std::vector<int32_t> w_round(pd.nmb, -1), w_lane(pd.nmb, -1);   // last writer of each slot
                 for (int32_t j = 0; j < pd.nrow; ++j)
                     for (int l = 0; l < kWarp; ++l) {
@@ -1786,7 +1815,8 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                         }
                         if (!(f & kFlagRemote) || (f & kFlagRoot)) continue;
                         if (so == kMbNone) { p_err[pi] = 2; return; }
-                        const int32_t rd = j / kStreamRound;
+                        if (j + wsh >= pd.nrow) { p_err[pi] = 5; return; }
+                        const int32_t rd = (j + wsh) / kStreamRound;
                         if (w_round[so] == rd && w_lane[so] != l) { p_err[pi] = 3; return; }
                         w_round[so] = rd;
                         w_lane[so] = l;
@@ -1796,11 +1826,19 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                         const int64_t t = pl.cv_tile[cv], tp = pl.cv_tile[sim->cv_offset[c] + sim->parent[cv]];
                         if (t % kWarp == tp % kWarp) {
                             if (tp <= t) { p_err[pi] = 4; return; }
-                        } else if ((t / kWarp - pd.row0) / kStreamRound >= (tp / kWarp - pd.row0) / kStreamRound) {
+                        } else if ((t / kWarp - pd.row0 + wsh) / kStreamRound >= (tp / kWarp - pd.row0) / kStreamRound) {
                             p_err[pi] = 5;
                             return;
                         }
                     }
+                // the slot's parent: its entry in the pack and its compact mechanism slot, from
+                // which the kernel starts the slot's sums each step
+                for (int64_t t = base; t < base + (int64_t)pd.nrow * kWarp; ++t) {
+                    const int32_t si = (int32_t)((uint32_t)pl.pslot[t] >> kMbInShift);
+                    if (si == kMbNone) continue;
+                    pl.mb_ent[(size_t)pd.mb0 + si] = (int32_t)(t - base);
+                    pl.mb_cs[(size_t)pd.mb0 + si] = pl.vmap[t];
+                }
                 pd.stack = 0;
                 return;
             }
@@ -2462,7 +2500,7 @@ arb_status arb_bind_workspace(arb_sim* sim, void* dev_ptr, int64_t bytes) {
     UP("ca", pl.ca); UP("cb", pl.cb); UP("ck", pl.ck); UP("ce", pl.ce); UP("pslot", pl.pslot); UP("vmap", pl.vmap);
     UP("V", pl.V0);
     UP("cE", pl.cE); UP("cB", pl.cB);
-    if (pl.stream_imp) { UP("cpos", pl.cpos); UP("row_cs", pl.row_cs); UP("row_cn", pl.row_cn); }
+    if (pl.stream_imp) { UP("cpos", pl.cpos); UP("row_cs", pl.row_cs); UP("row_cn", pl.row_cn); UP("mb_ent", pl.mb_ent); UP("mb_cs", pl.mb_cs); }
     UP("syn_ntau", pl.syn_ntau); UP("slot_lo", pl.slot_lo); UP("slot_hi", pl.slot_hi);
     UP("syn_slot", pl.syn_slot); UP("syn_vs", pl.syn_vs); UP("syn_e", pl.syn_e); UP("syn_decay", pl.syn_decay); UP("syn_sc", pl.syn_sc);
     if (!sim->hh_tab.empty()) UP("hh_tab", sim->hh_tab);
