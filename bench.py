@@ -60,11 +60,12 @@ FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
 
 # FP64 thread instructions (DFMA + DMUL + DADD) the streamed epoch kernel executes per
 # CV-step, and its DRAM bytes per CV-step, on the batched workload: from the ncu capture of
-# 40,000 cells with the row-ring kernel at 12 warps per SM (profiles/stream_kernel_batched_40000cells.md,
-# capture of the kernel as of commit 3ab9df3), which has the same cell-size mix, synapse and HH
-# densities per CV as the full 65,536-cell workload. Re-measure when the kernel changes.
-STREAM_FP64_PER_CV_STEP = {"batched": 11.87}
-STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 119.4}
+# 40,000 cells with the row-ring kernel at 16 warps per SM, cells above 222 CVs spread over
+# lanes (profiles/stream_kernel_batched_40000cells.md, capture of the kernel as of commit
+# 4f8040b), which has the same cell-size mix, synapse and HH densities per CV as the full
+# 65,536-cell workload. Re-measure when the kernel changes.
+STREAM_FP64_PER_CV_STEP = {"batched": 11.74}
+STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 123.9}
 
 
 # Discrete adjoint (every CV with HH, checkpoint every 500 steps): FP64 thread instructions per
