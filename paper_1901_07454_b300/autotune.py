@@ -58,7 +58,7 @@ def autotune_packing(model, dt=0.025, epoch_steps=0, candidates=None, events=Non
 def autotune_streamed(model, dt=0.025, epoch_steps=0, events=None, warmup=1, epochs=2, refine=2, **kw):
     """Streamed plans (one cell per lane, large cells spread over lanes): first every compiled
     kernel variant with the plan its cost model chooses, then, for the `refine` fastest, the
-    split threshold at 0.4, 0.55 and 0.75 of the chosen one and the spread packs' rows at 0.96 and
+    split threshold at 0.27, 0.4, 0.55 and 0.75 of the chosen one and the spread packs' rows at 0.96 and
     1.06 of the chosen ones. Returns (best settings dict, [(settings, plan summary, epoch-kernel
     ms)])."""
     trials = []
@@ -77,7 +77,8 @@ def autotune_streamed(model, dt=0.025, epoch_steps=0, events=None, warmup=1, epo
         s, r = info["split_cvs"], info["spread_rows"]
         if s <= 0 or r <= 0:
             continue
-        for cand in (dict(split_cvs=int(0.4 * s), spread_rows=r), dict(split_cvs=int(0.55 * s), spread_rows=r),
+        for cand in (dict(split_cvs=int(0.27 * s), spread_rows=r), dict(split_cvs=int(0.4 * s), spread_rows=r),
+                     dict(split_cvs=int(0.55 * s), spread_rows=r),
                      dict(split_cvs=int(0.75 * s), spread_rows=r), dict(split_cvs=s, spread_rows=int(0.96 * r)),
                      dict(split_cvs=s, spread_rows=int(1.06 * r))):
             run(dict(cells_per_pack=32, kernel_variant=v, **cand))

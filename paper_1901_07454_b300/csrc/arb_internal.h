@@ -59,7 +59,10 @@ constexpr int kMbInShift = 21;
 #define ARB_STREAM_WARPS 16
 #endif
 constexpr int kStreamWarps = ARB_STREAM_WARPS;   // warps per CTA of the streamed kernel (one CTA per SM)
-constexpr int kStreamRound = 8;        // rows per round in streamed shared packs
+#ifndef ARB_STREAM_ROUND
+#define ARB_STREAM_ROUND 4
+#endif
+constexpr int kStreamRound = ARB_STREAM_ROUND;   // rows per round in streamed shared packs
 
 // Event delivered inside one epoch, bucketed per owner lane and sorted by
 // (step_rel, js, t, src, idx).

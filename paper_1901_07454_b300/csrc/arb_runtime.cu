@@ -1448,10 +1448,11 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 }
                 out.push_back(std::move(G));
             };
-        constexpr double kSpreadFill = 0.93;   // lane-rows holding a CV in a round schedule
+        constexpr double kSpreadFill = 0.95;   // lane-rows holding a CV in a round schedule
+        constexpr double kSpreadRow = 1.0;     // cost of a spread pack's solve row (hand-overs cost no FP64 work)
         // Cost model of a pack's run time (measured on the batched workload: the epoch kernel's
         // time follows the makespan of the warp slots under this cost): a solve row costs 1, a row
-        // of a pack whose cells are spread over lanes 1.05, and each synapse, HH and clamp row 1.
+        // of a pack whose cells are spread over lanes kSpreadRow, and each synapse, HH and clamp row 1.
         std::vector<int64_t> nsyn_of(nc), nhh_of(nc), nst_of(nc);
         for (int32_t c = 0; c < nc; ++c) {
             nsyn_of[c] = (int64_t)cell_syn[c].size();
@@ -1471,12 +1472,12 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
             return (double)rows + (double)sy + (double)st + (double)((hh + 31) / 32);
         };
         // Packs of large cells are grouped by estimated cost, not by CVs alone: a cell weighs its
-        // solve rows in a round schedule (its CVs over kSpreadFill x 32 lane-rows, x 1.05) plus its
+        // solve rows in a round schedule (its CVs over kSpreadFill x 32 lane-rows, x kSpreadRow) plus its
         // mechanism rows spread over the 32 lanes; a group is closed when its weight would pass
         // the target, which is `target` solve rows of a pack of average composition (so a pack
         // of cells with many synapses gets fewer CVs and every pack costs about the same).
         auto spread_weight = [&](int32_t c) {
-            return 1.05 * (double)ncv_of[c] / (kSpreadFill * 32.0) + 1.1 * (double)(nsyn_of[c] + nst_of[c]) / 32.0 +
+            return kSpreadRow * (double)ncv_of[c] / (kSpreadFill * 32.0) + 1.1 * (double)(nsyn_of[c] + nst_of[c]) / 32.0 +
                    (double)nhh_of[c] / 32.0;
         };
         auto target_weight = [&](const std::vector<int32_t>& big, int64_t target) {
@@ -1485,7 +1486,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 rows += (double)ncv_of[c] / (kSpreadFill * 32.0);
                 mech += 1.1 * (double)(nsyn_of[c] + nst_of[c]) / 32.0 + (double)nhh_of[c] / 32.0;
             }
-            return (double)target * (1.05 + (rows > 0.0 ? mech / rows : 0.0));
+            return (double)target * (kSpreadRow + (rows > 0.0 ? mech / rows : 0.0));
         };
         // estimated costs of the greedy packs of large cells
         auto est_shared = [&](const std::vector<int32_t>& big, int64_t target, std::vector<double>& cost) {
@@ -1508,7 +1509,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                     ++k;
                 }
                 const double rows = std::max((double)sum / (kSpreadFill * 32.0), (double)(dep + kStreamRound));
-                cost.push_back(1.05 * rows + 1.1 * (double)(sy + st) / 32.0 + (double)((hh + 31) / 32));
+                cost.push_back(kSpreadRow * rows + 1.1 * (double)(sy + st) / 32.0 + (double)((hh + 31) / 32));
                 i += k;
             }
         };
@@ -1606,7 +1607,7 @@ arb_status arb_create(const arb_model* m, const arb_params* pp, arb_sim** out) {
                 if (G.shared) {
                     int64_t s_all = 0, t_all = 0;
                     for (int32_t c : G.cells) { s_all += nsyn_of[c]; t_all += nst_of[c]; hh += nhh_of[c]; }
-                    pc[k] = 1.05 * (double)G.rows.rows.size() + 1.1 * (double)(s_all + t_all) / 32.0 + (double)((hh + 31) / 32);
+                    pc[k] = kSpreadRow * (double)G.rows.rows.size() + 1.1 * (double)(s_all + t_all) / 32.0 + (double)((hh + 31) / 32);
                 } else {
                     int64_t ms = 0, mt = 0;
                     for (size_t l = 0; l < G.cells.size() && l < 32; ++l) {
