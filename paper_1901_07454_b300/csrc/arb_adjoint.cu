@@ -48,7 +48,7 @@
 namespace arbk {
 namespace {
 
-constexpr int kAdjThreads = 128;   // threads per cell (block)
+constexpr int kAdjThreads = kAdjBlock;   // threads per cell (block)
 
 // Conductance (uS) and conductance x reversal (nA) of CV i with the gates of one step; gl, gel and
 // hj are the CV's passive conductance, its product with the reversal and its HH instance.
@@ -350,7 +350,9 @@ __device__ __forceinline__ double solution(const Smem& sm, int li) {
 
 // mode 0: steps [s0, s1) from the running state (a.V, a.Y), in place, with a checkpoint
 //         before every step that is a multiple of ckpt, and the loss;
-// mode 1: steps [s0, s1) from checkpoint s0 / ckpt, every state kept in segment buffer buf.
+// mode 1: steps [s0, s1) from checkpoint s0 / ckpt, every state kept in segment buffer buf;
+// mode 2: steps [s0, s1) from the running state, every state kept in segment buffer buf, and
+//         the loss (the last segment of the forward pass, which then needs no recompute).
 __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, int mode, int buf) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t off = a.off[c], n = a.off[c + 1] - off;
@@ -360,9 +362,9 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
     const int64_t nhh = a.n_hh;
     const Smem sm = smem_of(a);
     load_cell(a, c, sm);
-    if (mode == 1) {
-        const double* cV = a.ckV + (s0 / a.ckpt) * a.n_cv;
-        const double* cY = a.ckY + (s0 / a.ckpt) * 3 * nhh;
+    if (mode != 0) {
+        const double* cV = mode == 1 ? a.ckV + (s0 / a.ckpt) * a.n_cv : a.V;
+        const double* cY = mode == 1 ? a.ckY + (s0 / a.ckpt) * 3 * nhh : a.Y;
         for (int64_t i = off + tid; i < off + n; i += kAdjThreads) {
             segV[i] = cV[i];
             const int32_t j = sm.hidx[i - off];
@@ -371,7 +373,8 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         }
         __syncthreads();
     }
-    double lsum = 0.0;
+    // each thread's loss sum runs over all steps in order, across the two forward launches
+    double lsum = mode == 2 ? a.loss_part[(int64_t)c * kAdjThreads + tid] : 0.0;
     for (int64_t s = s0; s < s1; ++s) {
         const double* Vs;
         const double* Ys;
@@ -471,7 +474,7 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                     G6[5 * nhh + j] = en;
                 }
             }
-            if (mode == 0) {
+            if (mode != 1) {
                 const int32_t o = a.obs[i];
                 if (o >= 0) {
                     const double e = v - a.target[s * a.n_obs + o];
@@ -481,7 +484,8 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         }
         __syncthreads();
     }
-    if (mode == 0) {
+    if (mode == 0) a.loss_part[(int64_t)c * kAdjThreads + tid] = lsum;
+    if (mode == 2) {
         // fixed-order reduction: warps, then the warp sums in order
         __shared__ double wsum[kAdjThreads / 32];
         for (int sh = 16; sh > 0; sh >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, sh);
@@ -574,9 +578,10 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
         for (int g = 0; g < 4; ++g) a.gacc[g * ncv + i] = sm.GA[4 * (i - off) + g];
 }
 
-// Forward pass with checkpoints and the loss: one block per cell.
-__global__ void __launch_bounds__(kAdjThreads) k_adj_forward(AdjArgs a, int64_t s0, int64_t s1) {
-    forward_cell(a, blockIdx.x, s0, s1, 0, 0);
+// Forward pass with the loss (mode 0: with checkpoints; mode 2: into segment buffer buf): one
+// block per cell.
+__global__ void __launch_bounds__(kAdjThreads) k_adj_forward(AdjArgs a, int64_t s0, int64_t s1, int mode, int buf) {
+    forward_cell(a, blockIdx.x, s0, s1, mode, buf);
 }
 
 // One backward stage: blocks [0, n_cells) sweep segment [r0, r1) (buffer rbuf) backwards,
@@ -620,9 +625,9 @@ cudaError_t adj_prepare(const AdjArgs& a) {
     return cudaFuncSetAttribute(k_adj_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s) {
+cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, int mode, int buf, cudaStream_t s) {
     if (a.n_cells == 0 || s1 <= s0) return cudaSuccess;
-    k_adj_forward<<<a.n_cells, kAdjThreads, adj_smem_bytes(a), s>>>(a, s0, s1);
+    k_adj_forward<<<a.n_cells, kAdjThreads, adj_smem_bytes(a), s>>>(a, s0, s1, mode, buf);
     return cudaGetLastError();
 }
 

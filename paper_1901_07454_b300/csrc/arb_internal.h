@@ -298,6 +298,8 @@ __host__ __device__ inline int64_t event_step(double t, double dt, bool exact) {
     return j;
 }
 
+constexpr int kAdjBlock = 128;   // adjoint kernels: threads per block (one block per cell)
+
 // Discrete adjoint (model order: CVs of a cell contiguous, parent index below the child's).
 // Per-step state: V [n_cv] and the gates Y [3][n_hh] (m, h, n of HH instance j).
 struct AdjArgs {
@@ -346,6 +348,7 @@ struct AdjArgs {
     double* ybar;              // [3][n_hh]
     double* gacc;              // [4][n_cv] gradient per CV: gnabar, gkbar, gl, cm
     double* cell_loss;         // [n_cells]
+    double* loss_part;         // [n_cells][kAdjBlock] each thread's loss sum, carried between forward launches
     // tree solve schedule: the unbranched chains of each cell, ordered by level (leaf chains
     // level 0, a chain's level is one more than its highest child chain)
     const int64_t* ch_ptr;     // [n_cells+1] chains of cell c (global chain indices)

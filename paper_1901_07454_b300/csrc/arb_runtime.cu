@@ -53,7 +53,7 @@ template <class T>
 cudaError_t launch_gather(double* out, const T* src, const int64_t* idx, int64_t n, cudaStream_t s);
 template <class T>
 cudaError_t launch_scatter(T* dst, const double* src, const int64_t* idx, int64_t n, cudaStream_t s);
-cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, cudaStream_t s);
+cudaError_t launch_adj_forward(const AdjArgs& a, int64_t s0, int64_t s1, int mode, int buf, cudaStream_t s);
 cudaError_t launch_adj_stage(const AdjArgs& a, int64_t r0, int64_t r1, int rbuf, int64_t f0, int64_t f1,
                              cudaStream_t s);
 cudaError_t launch_adj_reduce(const AdjArgs& a, cudaStream_t s);
@@ -3339,6 +3339,7 @@ AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t 
     L.add("ybar", 24 * nhh);
     L.add("gacc", 32 * ncv);
     L.add("cell_loss", 8 * nc);
+    L.add("loss_part", 8 * nc * (int64_t)kAdjBlock);
     L.add("grp_ptr", 8 * ((int64_t)n_groups + 1));
     L.add("grp_cv", 8 * ncv);
     // chain schedule: at most one chain per CV, at most n_cv + 1 level bounds per cell
@@ -3552,6 +3553,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.ybar = (double*)L.at(base, "ybar");
     a.gacc = (double*)L.at(base, "gacc");
     a.cell_loss = (double*)L.at(base, "cell_loss");
+    a.loss_part = (double*)L.at(base, "loss_part");
     a.ch_ptr = (const int64_t*)L.at(base, "ch_ptr");
     a.lev_off = (const int64_t*)L.at(base, "lev_off");
     a.lev_bound = (const int64_t*)L.at(base, "lev_bound");
@@ -3589,11 +3591,12 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     if (nhh > 0) CU(cudaMemsetAsync(a.ybar, 0, 24 * nhh, sim->s));
     CU(cudaMemsetAsync(a.gacc, 0, 32 * ncv, sim->s));
     CU(cudaMemsetAsync(a.cell_loss, 0, 8 * nc, sim->s));
+    CU(cudaMemsetAsync(a.loss_part, 0, 8 * nc * (int64_t)kAdjBlock, sim->s));
     // forward with checkpoints, then segment by segment backwards: recompute, reverse sweep
     CU(cudaEventRecord(sim->t0[0], sim->s));
-    CU(launch_adj_forward(a, 0, n_steps, sim->s));
     // segment g lives in buffer g % 2; each stage sweeps segment g backwards while the
-    // segment before it is recomputed from its checkpoint into the other buffer
+    // segment before it is recomputed from its checkpoint into the other buffer. The forward
+    // pass keeps every state of the last segment, which therefore needs no recompute.
     const int64_t nck = (n_steps + checkpoint_every - 1) / checkpoint_every;
     auto seg = [&](int64_t g, int64_t& s0, int64_t& s1) {
         s0 = g * checkpoint_every;
@@ -3602,7 +3605,8 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     {
         int64_t f0, f1;
         seg(nck - 1, f0, f1);
-        CU(launch_adj_stage(a, 0, 0, (int)((nck - 1) % 2) ^ 1, f0, f1, sim->s));   // recompute only
+        CU(launch_adj_forward(a, 0, f0, 0, 0, sim->s));                              // with checkpoints
+        CU(launch_adj_forward(a, f0, f1, 2, (int)((nck - 1) % 2), sim->s));          // last segment
     }
     for (int64_t g = nck - 1; g >= 0; --g) {
         int64_t r0, r1, f0 = 0, f1 = 0;
@@ -3619,7 +3623,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     CU(cudaEventElapsedTime(&ms, sim->t0[0], sim->t1[0]));
     sim->pending_time[0] = false;
     sim->last_epoch_ms = ms;
-    sim->last_launches = 3 + nck;
+    sim->last_launches = (nck > 1 ? 2 : 1) + nck + 1;
     double total = 0.0;
     for (double x : cl) total += x;
     *loss = total;
