@@ -70,14 +70,15 @@ STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 123.9}
 
 # Discrete adjoint (every CV with HH, checkpoint every 500 steps): FP64 thread instructions per
 # gradient CV-step of the forward, recompute and reverse kernels together (ncu, 64 cells of the
-# fitting workload, profiles/adjoint_config4_256cells.md: 56.3 in k_adj_forward, 156.6 in
-# k_adj_stage); the algorithmic DRAM bytes per gradient CV-step: the recompute writes V, the
-# three gates and, per HH CV, three dPhi/dV and three decay factors (80 B), which the reverse
+# fitting workload, profiles/adjoint_config4_256cells.md: the sum over the two k_adj_forward and
+# the 16 k_adj_stage launches of one gradient); the algorithmic DRAM bytes per gradient
+# CV-step: the recompute (for the last segment the forward pass) writes V, the three gates
+# and, per HH CV, three dPhi/dV and three decay factors (80 B), which the reverse
 # sweep reads back (80 B) -- the running state, lambda, the gate adjoints and the gradient sums
-# stay in shared memory or L2; and the DRAM bytes the same capture measured (164.5 B).
-ADJ_FP64_PER_CV_STEP = 212.9
+# stay in shared memory or L2; and the DRAM bytes the same capture measured (164.0 B).
+ADJ_FP64_PER_CV_STEP = 209.4
 ADJ_BYTES_PER_CV_STEP = 160.0
-ADJ_DRAM_BYTES_PER_CV_STEP = 164.5
+ADJ_DRAM_BYTES_PER_CV_STEP = 164.0
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):

@@ -15,7 +15,8 @@
 // The forward pass keeps a checkpoint of the state every `ckpt` steps. The backward pass goes
 // segment by segment: each stage sweeps one segment backwards while other blocks of the same
 // launch recompute the previous segment from its checkpoint into the second segment buffer,
-// keeping every state and the gate-update derivatives the sweep will need.
+// keeping every state and the gate-update derivatives the sweep will need. The forward pass
+// records the last segment that way itself, so the first stage already sweeps.
 //
 // Tree solve. On this GPU a warp issues at most one FP64 instruction every 64 cycles, however
 // many of its lanes are active, so the solve's time is the number of FP64 instructions on its
