@@ -500,6 +500,16 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
     }
 }
 
+// Asks L2 for the 128-byte lines of count doubles from p (threads of the block in turn), every
+// address inside the range.
+__device__ __forceinline__ void prefetch_l2(const double* p, int64_t count, int tid) {
+    const char* b = reinterpret_cast<const char*>(p);
+    const int64_t bytes = count * 8;
+    for (int64_t o = (int64_t)tid * 128; o < bytes; o += (int64_t)kAdjThreads * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(b + o));
+    if (tid == 0 && bytes > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(b + bytes - 8));
+}
+
 // Reverse sweep over the segment [s0, s1) held in segment buffer buf.
 __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, int buf) {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -514,7 +524,25 @@ __device__ void reverse_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
     // updates), in the same order of additions as in global memory
     for (int64_t i = off + tid; i < off + n; i += kAdjThreads)
         for (int g = 0; g < 4; ++g) sm.GA[4 * (i - off) + g] = a.gacc[g * ncv + i];
+    // the cell's range of HH instances, for the prefetch of the segment rows
+    __shared__ int hlo, hhi;
+    if (tid == 0) { hlo = 0x7fffffff; hhi = -1; }
+    __syncthreads();
+    for (int64_t li = tid; li < n; li += kAdjThreads) {
+        const int32_t j = sm.hidx[li];
+        if (j >= 0) { atomicMin(&hlo, j); atomicMax(&hhi, j); }
+    }
+    __syncthreads();
+    const int64_t j0 = hlo, nh = hhi >= hlo ? (int64_t)hhi - hlo + 1 : 0;
     for (int64_t s = s1 - 1; s >= s0; --s) {
+        // the rows of step s - 1 were written a segment ago and are read from DRAM: ask for them
+        // now, a step ahead (the rows of step s + 1 it also reads are still cached)
+        if (s > s0) {
+            const int64_t sp = s - 1 - s0;
+            prefetch_l2(segV + sp * ncv + off, n, tid);
+            for (int g = 0; g < 3; ++g) prefetch_l2(segY + (sp * 3 + g) * nhh + j0, nh, tid);
+            for (int g = 0; g < 6; ++g) prefetch_l2(segG + (sp * 6 + g) * nhh + j0, nh, tid);
+        }
         const double* V0 = segV + (s - s0) * ncv;
         const double* V1 = V0 + ncv;
         const double* Y0 = segY + (s - s0) * 3 * nhh;
