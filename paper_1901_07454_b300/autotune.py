@@ -55,7 +55,7 @@ def autotune_packing(model, dt=0.025, epoch_steps=0, candidates=None, events=Non
     return best, times
 
 
-def autotune_streamed(model, dt=0.025, epoch_steps=0, events=None, warmup=1, epochs=2, refine=2, **kw):
+def autotune_streamed(model, dt=0.025, epoch_steps=0, events=None, warmup=1, epochs=2, refine=3, **kw):
     """Streamed plans (one cell per lane, large cells spread over lanes): first every compiled
     kernel variant with the plan its cost model chooses, then, for the `refine` fastest, the
     split threshold at 0.27, 0.4, 0.55 and 0.75 of the chosen one and the spread packs' rows at 0.96 and
