@@ -59,13 +59,22 @@ def peaks():
 FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
 
 # FP64 thread instructions (DFMA + DMUL + DADD) the streamed epoch kernel executes per
-# CV-step, and its DRAM bytes per CV-step, on the batched workload: from the ncu capture of
-# 40,000 cells with the row-ring kernel at 16 warps per SM, cells above 222 CVs spread over
-# lanes (profiles/stream_kernel_batched_40000cells.md, capture of the kernel as of commit
-# 4f8040b), which has the same cell-size mix, synapse and HH densities per CV as the full
-# 65,536-cell workload. Re-measure when the kernel changes.
-STREAM_FP64_PER_CV_STEP = {"batched": 11.74}
-STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": 123.9}
+# CV-step, and its DRAM bytes per CV-step, on the batched workload, per kernel variant with the
+# plan the autotuner chose for it on the full workload: from ncu captures of 40,000 cells
+# (profiles/stream_kernel_batched_40000cells.md, kernel as of commit 4f8040b, spread cells in
+# rounds of 4 rows as of dbd679c), which have the same cell-size mix, synapse and HH densities per CV as the
+# full 65,536-cell workload. Variant 0 (16 warps per SM): cells above 305 CVs spread into packs
+# of about 555 rows; variant 3 (12 warps): above 592 CVs, packs of about 766 rows. Another
+# variant takes their mean. Re-measure when the kernel changes.
+STREAM_FP64_PER_CV_STEP = {"batched": {0: 11.59, 3: 11.42}}
+STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": {0: 121.9, 3: 118.7}}
+
+
+def _per_variant(table, workload, variant):
+    t = table.get(workload)
+    if t is None:
+        return None
+    return t.get(variant, sum(t.values()) / len(t))
 
 
 # Discrete adjoint (every CV with HH, checkpoint every 500 steps): FP64 thread instructions per
@@ -529,8 +538,8 @@ def main():
     kname = "arb_stream_kernel" if streamed else "arb_epoch_kernel"
     cv_steps_launch = model.n_cv * (E // lps)
     counted = streamed and precision == "fp64" and not args.exact_events   # the kernel the ncu counts are of
-    fp64_per = STREAM_FP64_PER_CV_STEP.get(args.workload) if counted else None
-    dram_per = STREAM_DRAM_BYTES_PER_CV_STEP.get(args.workload) if counted else None
+    fp64_per = _per_variant(STREAM_FP64_PER_CV_STEP, args.workload, info["kernel_variant"]) if counted else None
+    dram_per = _per_variant(STREAM_DRAM_BYTES_PER_CV_STEP, args.workload, info["kernel_variant"]) if counted else None
     hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
            "algorithmic_bytes_per_cv_step": bpc,
            "traffic": dram_per * cv_steps_launch if dram_per else None}
