@@ -92,6 +92,24 @@ def test_streamed_plan_spreads_large_cells(arb):
     _expect_error(arb, m, "split_cvs", cells_per_pack=32, split_cvs=-2)
 
 
+def test_spread_schedules_keep_the_hand_over_rounds(arb):
+    """Cells spread over lanes hand their contributions over through shared memory in rounds of
+    rows. arb_create refuses a schedule in which such a write does not land in an earlier round
+    than its parent reads it, or in which two lanes add to one slot in a round; on the implicit
+    scheme's row-ring path the write lands one row after the child's last row, so a child on a
+    round's last row writes in the next round. Plans of the batched workload's cells with most of
+    them spread, for both schemes, every kernel variant and several split thresholds, pass."""
+    m, spec = make_config(2, n_cells=1200, t_end=10.0)
+    nv = len(arb.kernel_variants())
+    for scheme in ("implicit", "explicit"):
+        for split in (40, 150, 500):
+            for v in range(nv):
+                info = arb.Plan(m, dt=spec.dt, cells_per_pack=32, split_cvs=split, spread_rows=400,
+                                kernel_variant=v, scheme=scheme).plan_info()
+                assert info["split_cvs"] == split and info["smem_packs"] >= 1, (scheme, split, v, info)
+                assert 0.5 < info["lane_efficiency"] <= 1.0, (scheme, split, v, info)
+
+
 def test_epoch_is_derived_from_min_delay(arb):
     m, spec = make_config(1, n_cells=8, t_end=10.0)
     assert arb.Plan(m, dt=0.025).plan_info()["epoch_steps"] == 200
