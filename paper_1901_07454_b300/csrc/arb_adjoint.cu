@@ -441,7 +441,7 @@ __device__ void forward_cell(const AdjArgs& a, int c, int64_t s0, int64_t s1, in
                     Yd[j] = gate(Ys[j], r.am, r.bm, a.dt);
                     Yd[nhh + j] = gate(Ys[nhh + j], r.ah, r.bh, a.dt);
                     Yd[2 * nhh + j] = gate(Ys[2 * nhh + j], r.an, r.bn, a.dt);
-                } else if (hh_gates_tab_dv(a.hh_tab, v, xg, dvg, eg)) {
+                } else if (hh_gates_tab_dv(a.hh_tab, a.hh_dtab, v, xg, dvg, eg)) {
                     // from the table: the gate update, dPhi/dV and exp(-dt (alpha + beta))
                     Yd[j] = xg.m;
                     Yd[nhh + j] = xg.h;

@@ -159,21 +159,24 @@ __device__ __forceinline__ bool hh_gates_tab_f(const float* tab, double vd, floa
 
 // The same from the table, with what the reverse sweep of the adjoint needs: each gate x of
 // (m, h, n) becomes x_inf + (x - x_inf) e, with dx'/dV = x_inf' (1 - e) + (x - x_inf) e' (slopes
-// of the cubics) in dv and e in ef, in that order. False when there is no table or V lies
-// outside it.
+// of the cubics, from dtab: per interval and quantity the coefficients of the slope per mV) in
+// dv and e in ef, in that order. False when there is no table or V lies outside it.
 struct Gates3 { double m, h, n; };
-__device__ __forceinline__ bool hh_gates_tab_dv(const double* tab, double vd, Gates3& x, Gates3& dv, Gates3& ef) {
+__device__ __forceinline__ bool hh_gates_tab_dv(const double* tab, const double* dtab, double vd, Gates3& x, Gates3& dv,
+                                                Gates3& ef) {
     const double tv = fma(vd, kHHTabPerMV, -kHHTabVlo * kHHTabPerMV);
     if (tab == nullptr || !(tv >= 0.0 && tv < (double)kHHTabN)) return false;
     const int it = (int)tv;
     const double s = tv - (double)it;
     const double2* c = reinterpret_cast<const double2*>(tab + (size_t)it * kHHTabStride);
+    const double2* cd = reinterpret_cast<const double2*>(dtab + (size_t)it * kHHTabStride);
     double f[6], g[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         const double2 lo = __ldg(c + 2 * q), hi = __ldg(c + 2 * q + 1);
+        const double2 dlo = __ldg(cd + 2 * q), dhi = __ldg(cd + 2 * q + 1);
         f[q] = fma(fma(fma(hi.y, s, hi.x), s, lo.y), s, lo.x);
-        g[q] = fma(fma(3.0 * hi.y, s, 2.0 * hi.x), s, lo.y) * kHHTabPerMV;
+        g[q] = fma(fma(dhi.x, s, dlo.y), s, dlo.x);
     }
     auto one = [&](double& xx, double& dd, double& ee, int q) {
         const double xinf = f[2 * q], e = f[2 * q + 1], d = xx - xinf;

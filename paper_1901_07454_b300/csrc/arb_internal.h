@@ -317,6 +317,7 @@ struct AdjArgs {
     const double* ksc;         // [n_cv] area 1e-2: the channel densities' factor
     const int32_t* hidx;       // [n_cv] HH instance on the CV, -1 none
     const double* hh_tab;      // tabulated gate update of the simulation's dt, or null
+    const double* hh_dtab;     // slopes per mV of the table's cubics ([kHHTabN][24]: c1, 2 c2, 3 c3, 0 per quantity), or null
     const double* gna;         // [n_hh] uS
     const double* gk;
     const double* gl;

@@ -3339,6 +3339,7 @@ AdjLayout adj_layout(const arb_sim* sim, int64_t n_steps, int32_t ckpt, int64_t 
     L.add("ybar", 24 * nhh);
     L.add("gacc", 32 * ncv);
     L.add("cell_loss", 8 * nc);
+    L.add("hh_dtab", sim->hh_tab.empty() ? 0 : 8 * (int64_t)kHHTabN * kHHTabStride);
     L.add("loss_part", 8 * nc * (int64_t)kAdjBlock);
     L.add("grp_ptr", 8 * ((int64_t)n_groups + 1));
     L.add("grp_cv", 8 * ncv);
@@ -3505,6 +3506,22 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
         (st = up("tk", CP.tk.data(), 4 * CP.tk.size())) != ARB_OK || (st = up("tk_ptr", CP.tk_ptr.data(), 8 * CP.tk_ptr.size())) != ARB_OK ||
         (st = up("tkb", CP.tkb.data(), 4 * CP.tkb.size())) != ARB_OK || (st = up("fixa", CP.fixa.data(), 4 * ncv)) != ARB_OK)
         return st;
+    // slopes of the gate table's cubics per mV, for the recording passes: per interval and
+    // quantity (c1, 2 c2, 3 c3) x kHHTabPerMV of the cubic c0 + c1 s + c2 s^2 + c3 s^3
+    std::vector<double> dtab;
+    if (!sim->hh_tab.empty()) {
+        dtab.assign((size_t)kHHTabN * kHHTabStride, 0.0);
+        const double* tb = sim->hh_tab.data();
+        for (int64_t it = 0; it < kHHTabN; ++it)
+            for (int q = 0; q < 6; ++q) {
+                const double* cq = tb + it * kHHTabStride + 4 * q;
+                double* dq = dtab.data() + it * kHHTabStride + 4 * q;
+                dq[0] = cq[1] * kHHTabPerMV;
+                dq[1] = 2.0 * cq[2] * kHHTabPerMV;
+                dq[2] = 3.0 * cq[3] * kHHTabPerMV;
+            }
+        if ((st = up("hh_dtab", dtab.data(), 8 * dtab.size())) != ARB_OK) return st;
+    }
     AdjArgs a{};
     a.n_cells = (int32_t)nc;
     a.n_cv = ncv;
@@ -3536,6 +3553,7 @@ arb_status arb_adjoint(arb_sim* sim, int64_t n_steps, int32_t checkpoint_every, 
     a.loss_scale = loss_scale;
     a.dt = dt;
     a.hh_tab = sim->hh_tab.empty() ? nullptr : (const double*)region(sim, "hh_tab");
+    a.hh_dtab = sim->hh_tab.empty() ? nullptr : (const double*)L.at(base, "hh_dtab");
     a.k0 = sim->k;
     a.n_steps = n_steps;
     a.ckpt = checkpoint_every;
