@@ -84,10 +84,10 @@ def _per_variant(table, workload, variant):
 # CV-step: the recompute (for the last segment the forward pass) writes V, the three gates
 # and, per HH CV, three dPhi/dV and three decay factors (80 B), which the reverse
 # sweep reads back (80 B) -- the running state, lambda, the gate adjoints and the gradient sums
-# stay in shared memory or L2; and the DRAM bytes the same capture measured (164.0 B).
-ADJ_FP64_PER_CV_STEP = 209.4
+# stay in shared memory or L2; and the DRAM bytes the same capture measured (168.2 B).
+ADJ_FP64_PER_CV_STEP = 189.4
 ADJ_BYTES_PER_CV_STEP = 160.0
-ADJ_DRAM_BYTES_PER_CV_STEP = 164.0
+ADJ_DRAM_BYTES_PER_CV_STEP = 168.2
 
 
 def algorithmic_bytes_per_cv_step(model, precision, coalesce=False):
