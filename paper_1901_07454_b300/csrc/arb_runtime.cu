@@ -718,7 +718,7 @@ static arb_status check_canaries(arb_sim* sim) {
                                                   sim->regions[i].first + "' were overwritten");
     return ARB_OK;
 #else
-    return fail(sim, ARB_OK, "this build keeps no guard words (build with ARB_DEBUG)");
+    return fail(sim, ARB_OK, "the release library keeps no guard words (build with ARB_DEBUG)");
 #endif
 }
 
