@@ -1301,6 +1301,7 @@ __device__ void run_pack_stream_imp(const DevModel<MT>& d, int p, char* ring, do
                 // children add their contributions, and the parent takes the sums in their place
                 const int32_t* me = d.mb_ent + pk.mb0;
                 const int32_t* mc = d.mb_cs + pk.mb0;
+#pragma unroll 4
                 for (int i = lane; i < pk.nmb; i += kWarp) {
                     const int t = ARB_IDX(__ldg(me + i), J * kWarp, d.ctl);
                     const int c = __ldg(mc + i);
