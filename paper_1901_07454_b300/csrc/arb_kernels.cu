@@ -455,6 +455,7 @@ __device__ __forceinline__ void stream_mech(const DevModel<MT>& d, const PackDes
         // implicit: the slots start from the constant diagonal and right-hand side of their
         // entry, so the forward sweep adds nothing for them. Slots [0, nsc) belong to CVs with
         // synapses and are written whole by the synapse pass below.
+#pragma unroll 4
         for (int c = pk.nsc + lane; c < pk.nvc; c += kWarp) {
             if (kImp) {
                 Gm[c] = __ldg(cE + c);
