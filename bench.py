@@ -61,13 +61,13 @@ FP64_PEAK_INST_PER_S = 148 * 2 * 2032e6
 # FP64 thread instructions (DFMA + DMUL + DADD) the streamed epoch kernel executes per
 # CV-step, and its DRAM bytes per CV-step, on the batched workload, per kernel variant with the
 # plan the autotuner chose for it on the full workload: from ncu captures of 40,000 cells
-# (profiles/stream_kernel_batched_40000cells.md, kernel as of commit 4f8040b, spread cells in
-# rounds of 4 rows as of dbd679c), which have the same cell-size mix, synapse and HH densities per CV as the
+# (profiles/stream_kernel_batched_40000cells.md, kernel as of commit f122cae, spread cells in
+# rounds of 4 rows), which have the same cell-size mix, synapse and HH densities per CV as the
 # full 65,536-cell workload. Variant 0 (16 warps per SM): cells above 305 CVs spread into packs
 # of about 555 rows; variant 3 (12 warps): above 592 CVs, packs of about 766 rows. Another
 # variant takes their mean. Re-measure when the kernel changes.
 STREAM_FP64_PER_CV_STEP = {"batched": {0: 11.59, 3: 11.42}}
-STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": {0: 121.9, 3: 118.7}}
+STREAM_DRAM_BYTES_PER_CV_STEP = {"batched": {0: 122.0, 3: 118.6}}
 
 
 def _per_variant(table, workload, variant):
