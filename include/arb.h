@@ -268,8 +268,10 @@ arb_status arb_last_timing(const arb_sim* sim, double* epoch_kernel_ms, int64_t*
  *   obs_cv [n_obs]: host, distinct CVs. target [n_steps][n_obs]: device. group_of_cv [n_cv]: host.
  *   grad [n_groups][4]: device, written. loss: host, written.
  *   workspace: caller-owned device memory of arb_adjoint_workspace_bytes bytes, 256-byte
- *   aligned. It holds one state every checkpoint_every steps and every state of one segment
- *   of checkpoint_every steps, which the reverse sweep recomputes from its checkpoint.
+ *   aligned. It holds one state every checkpoint_every steps, two buffers of every state (and
+ *   gate-update factor) of a segment of checkpoint_every steps (the forward pass fills one for
+ *   the last segment, the reverse sweep recomputes each earlier one from its checkpoint), the
+ *   solve schedule and constants, and a table of the gate cubics' slopes.
  * Each cell's tree solve runs in one block's shared memory: cells of more than about 1,000 to
  * 1,400 CVs (depending on their number of unbranched chains) are refused with ARB_E_ARG. The
  * handle keeps the solve schedule it builds on the first call (it depends only on the model
